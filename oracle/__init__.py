@@ -1,0 +1,302 @@
+"""CPU oracle for the BSSN moving-puncture hot path (TEST INFRASTRUCTURE ONLY).
+
+A plain FP64 C statement of the discrete scheme of "The Einstein Toolkit"
+(arXiv:1111.3344), Sec. "Spacetime Curvature Evolution" (BSSN equations,
+Ricci pieces, gauge), Sec. "Initial Conditions", Sec. "Boundary Conditions"
+(Sommerfeld/NewRad) and Sec. "Other analysis modules" (constraints).  The
+arithmetic lives in ``bssn_oracle.c``; this module compiles it with gcc and
+marshals numpy arrays through ctypes.
+
+Only the test suite, ``__graft_entry__.smoke()`` and the ``cpu_baseline`` /
+``--impl reference`` legs of ``bench.py`` may import this package.  The CUDA
+library shares no code with it.
+
+Array convention: a state is a C-contiguous float64 array of shape
+``(24, n2+6, n1+6, n0+6)`` -- field, z, y, x -- with three ghost layers on
+every side and no padding.  Point index ``i`` on an axis sits at
+``xmin + (i - 3 + 0.5) h``.
+
+Parity status per function: every function is pinned by tests under
+``tests/test_oracle_*.py`` except the Sommerfeld power-law correction term
+and the per-variable X0/v0 choice, which are readings of an under-specified
+passage (parity unpinned beyond the pure outgoing-wave part).
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+import subprocess
+import threading
+from dataclasses import dataclass, field
+from typing import Sequence
+
+import numpy as np
+
+NF = 24
+GHOST = 3
+
+# field indices
+F_CHI, F_GT, F_TRK, F_AT, F_GAM, F_ALP, F_BETA, F_B = 0, 1, 7, 8, 14, 17, 18, 21
+FIELD_NAMES = (
+    ["chi", "gt_xx", "gt_xy", "gt_xz", "gt_yy", "gt_yz", "gt_zz", "trK",
+     "At_xx", "At_xy", "At_xz", "At_yy", "At_yz", "At_zz",
+     "Gt_x", "Gt_y", "Gt_z", "alpha", "beta_x", "beta_y", "beta_z",
+     "B_x", "B_y", "B_z"])
+
+SLICING = {"1+log": 0, "harmonic": 1, "geodesic": 2}
+SHIFT = {"gamma-driver": 0, "frozen": 1}
+ID_KIND = {"flat": 0, "gauge_wave": 1, "bl": 2, "kasner": 3}
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "bssn_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+class _OCfg(ctypes.Structure):
+    _fields_ = [
+        ("n", ctypes.c_int * 3),
+        ("xmin", ctypes.c_double * 3),
+        ("h", ctypes.c_double),
+        ("periodic", ctypes.c_int),
+        ("use_w", ctypes.c_int),
+        ("slicing", ctypes.c_int),
+        ("shift", ctypes.c_int),
+        ("eta", ctypes.c_double),
+        ("q_R", ctypes.c_double),
+        ("ko_eps", ctypes.c_double),
+        ("dt", ctypes.c_double),
+        ("w_floor", ctypes.c_double),
+        ("r_excise", ctypes.c_double),
+        ("npunct", ctypes.c_int),
+        ("punct", (ctypes.c_double * 4) * 8),
+    ]
+
+
+@dataclass
+class Config:
+    """Grid and method parameters (mirrors the C struct of the oracle)."""
+    n: Sequence[int] = (24, 24, 24)
+    xmin: Sequence[float] = (-0.5, -0.5, -0.5)
+    h: float = 1.0 / 24.0
+    periodic: bool = True
+    use_w: bool = True
+    slicing: str = "1+log"
+    shift: str = "gamma-driver"
+    eta: float = 2.0
+    q_R: float = math.inf
+    ko_eps: float = 0.1
+    dt: float = 0.25 / 24.0
+    w_floor: float = 1e-10
+    r_excise: float = 1.0
+    punctures: list = field(default_factory=list)  # [(m, x, y, z), ...]
+
+    @property
+    def shape(self):
+        return (NF, self.n[2] + 2 * GHOST, self.n[1] + 2 * GHOST, self.n[0] + 2 * GHOST)
+
+    def _c(self) -> _OCfg:
+        c = _OCfg()
+        for d in range(3):
+            c.n[d] = int(self.n[d])
+            c.xmin[d] = float(self.xmin[d])
+        c.h = float(self.h)
+        c.periodic = 1 if self.periodic else 0
+        c.use_w = 1 if self.use_w else 0
+        c.slicing = SLICING[self.slicing]
+        c.shift = SHIFT[self.shift]
+        c.eta = float(self.eta)
+        c.q_R = float(self.q_R)
+        c.ko_eps = float(self.ko_eps)
+        c.dt = float(self.dt)
+        c.w_floor = float(self.w_floor)
+        c.r_excise = float(self.r_excise)
+        if len(self.punctures) > 8:
+            raise ValueError("at most 8 punctures")
+        c.npunct = len(self.punctures)
+        for a, p in enumerate(self.punctures):
+            for q in range(4):
+                c.punct[a][q] = float(p[q])
+        return c
+
+    def coords(self, axis: int) -> np.ndarray:
+        i = np.arange(self.n[axis] + 2 * GHOST)
+        return self.xmin[axis] + (i - GHOST + 0.5) * self.h
+
+
+def build(force: bool = False) -> str:
+    """Compile bssn_oracle.c with gcc into oracle/_build/liboracle.so."""
+    with _lock:
+        os.makedirs(_BUILD, exist_ok=True)
+        if (not force and os.path.exists(_LIB_PATH)
+                and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+            return _LIB_PATH
+        tmp = _LIB_PATH + f".{os.getpid()}.tmp"
+        cmd = ["gcc", "-O2", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared",
+               "-std=gnu11", "-o", tmp, _SRC, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB_PATH)
+        return _LIB_PATH
+
+
+def _load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = build()
+    lib = ctypes.CDLL(path)
+    P = ctypes.POINTER
+    dp = P(ctypes.c_double)
+    ip = P(ctypes.c_int)
+    cp = P(_OCfg)
+    lib.oracle_npoints.argtypes = [cp]
+    lib.oracle_npoints.restype = ctypes.c_size_t
+    lib.oracle_apply_stencil.argtypes = [cp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                         ctypes.c_double, dp, dp]
+    lib.oracle_rhs.argtypes = [cp, dp, dp]
+    lib.oracle_sommerfeld.argtypes = [cp, dp, dp]
+    lib.oracle_rhs_points.argtypes = [cp, dp, ctypes.c_int, ip, dp]
+    lib.oracle_fill_periodic.argtypes = [cp, dp]
+    lib.oracle_rk4.argtypes = [cp, dp, ctypes.c_int]
+    lib.oracle_rk4.restype = ctypes.c_int
+    lib.oracle_initial_data.argtypes = [cp, ctypes.c_int, dp, ctypes.c_int, dp]
+    lib.oracle_initial_data.restype = ctypes.c_int
+    lib.oracle_adm_to_bssn.argtypes = [cp, dp, dp, dp, dp, dp]
+    lib.oracle_constraints.argtypes = [cp, dp, dp, dp, dp]
+    lib.oracle_constraints.restype = ctypes.c_int
+    lib.oracle_constraints_points.argtypes = [cp, dp, ctypes.c_int, ip, dp]
+    lib.oracle_constraints_points.restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _dp(a: np.ndarray):
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _state(cfg: Config, st: np.ndarray) -> np.ndarray:
+    st = np.ascontiguousarray(st, dtype=np.float64)
+    if st.shape != cfg.shape:
+        raise ValueError(f"state shape {st.shape} != {cfg.shape}")
+    return st
+
+
+def apply_stencil(cfg: Config, op: str, f: np.ndarray, a: int = 0, b: int = 0,
+                  sign: float = 1.0) -> np.ndarray:
+    """Apply one stencil to a scalar grid function (shape cfg.shape[1:])."""
+    ops = {"d1": 0, "dd": 1, "up": 2, "ko": 3}
+    lib = _load()
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    assert f.shape == cfg.shape[1:]
+    out = np.zeros_like(f)
+    c = cfg._c()
+    lib.oracle_apply_stencil(ctypes.byref(c), ops[op], a, b, float(sign), _dp(f), _dp(out))
+    return out
+
+
+def rhs(cfg: Config, st: np.ndarray) -> np.ndarray:
+    """Right-hand side at every stored point (Sommerfeld ghosts, or 0 if periodic)."""
+    lib = _load()
+    st = _state(cfg, st)
+    out = np.zeros_like(st)
+    c = cfg._c()
+    lib.oracle_rhs(ctypes.byref(c), _dp(st), _dp(out))
+    return out
+
+
+def sommerfeld(cfg: Config, st: np.ndarray, rhs_in: np.ndarray) -> np.ndarray:
+    """Fill ghost-point right-hand sides by the Sommerfeld condition, given the
+    interior right-hand side in rhs_in (returns a new array)."""
+    lib = _load()
+    st = _state(cfg, st)
+    out = _state(cfg, rhs_in).copy()
+    c = cfg._c()
+    lib.oracle_sommerfeld(ctypes.byref(c), _dp(st), _dp(out))
+    return out
+
+
+def rhs_points(cfg: Config, st: np.ndarray, ijk: np.ndarray) -> np.ndarray:
+    """Right-hand side at stored points ijk (shape (P, 3), x/y/z array indices)."""
+    lib = _load()
+    st = _state(cfg, st)
+    ijk = np.ascontiguousarray(ijk, dtype=np.int32).reshape(-1, 3)
+    out = np.zeros((ijk.shape[0], NF))
+    c = cfg._c()
+    lib.oracle_rhs_points(ctypes.byref(c), _dp(st), ijk.shape[0],
+                          ijk.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _dp(out))
+    return out
+
+
+def fill_periodic(cfg: Config, st: np.ndarray) -> np.ndarray:
+    lib = _load()
+    st = _state(cfg, st).copy()
+    c = cfg._c()
+    lib.oracle_fill_periodic(ctypes.byref(c), _dp(st))
+    return st
+
+
+def rk4(cfg: Config, st: np.ndarray, nsteps: int) -> np.ndarray:
+    """Advance nsteps classical RK4 steps; returns a new array."""
+    lib = _load()
+    y = _state(cfg, st).copy()
+    c = cfg._c()
+    if lib.oracle_rk4(ctypes.byref(c), _dp(y), int(nsteps)) != 0:
+        raise MemoryError("oracle_rk4: allocation failed")
+    return y
+
+
+def initial_data(cfg: Config, kind: str, params: Sequence[float]) -> np.ndarray:
+    """Analytic initial data converted to BSSN variables (all stored points)."""
+    lib = _load()
+    p = np.ascontiguousarray(params, dtype=np.float64)
+    st = np.zeros(cfg.shape)
+    c = cfg._c()
+    bad = lib.oracle_initial_data(ctypes.byref(c), ID_KIND[kind], _dp(p), p.size, _dp(st))
+    if bad:
+        raise ValueError(f"bad initial-data parameters for {kind}: {params}")
+    return st
+
+
+def adm_to_bssn(cfg: Config, alpha, beta3, gam6, K6) -> np.ndarray:
+    """BSSN variables from ADM grids by the definitions (Gt and B set to 0)."""
+    lib = _load()
+    S = cfg.shape[1:]
+    alpha = np.ascontiguousarray(alpha, dtype=np.float64).reshape(S)
+    beta3 = np.ascontiguousarray(beta3, dtype=np.float64).reshape((3,) + S)
+    gam6 = np.ascontiguousarray(gam6, dtype=np.float64).reshape((6,) + S)
+    K6 = np.ascontiguousarray(K6, dtype=np.float64).reshape((6,) + S)
+    st = np.zeros(cfg.shape)
+    c = cfg._c()
+    lib.oracle_adm_to_bssn(ctypes.byref(c), _dp(alpha), _dp(beta3), _dp(gam6), _dp(K6), _dp(st))
+    return st
+
+
+def constraints(cfg: Config, st: np.ndarray):
+    """(norms16, H, M): norms in the order L2 H,Mx,My,Mz, Linf H,Mx,My,Mz,
+    full interior then excised; H (grid) and M (3, grid) at interior points."""
+    lib = _load()
+    st = _state(cfg, st)
+    out = np.zeros(16)
+    H = np.zeros(cfg.shape[1:])
+    M = np.zeros((3,) + cfg.shape[1:])
+    c = cfg._c()
+    if lib.oracle_constraints(ctypes.byref(c), _dp(st), _dp(out), _dp(H), _dp(M)) != 0:
+        raise MemoryError("oracle_constraints: allocation failed")
+    return out, H, M
+
+
+def constraints_points(cfg: Config, st: np.ndarray, ijk: np.ndarray) -> np.ndarray:
+    lib = _load()
+    st = _state(cfg, st)
+    ijk = np.ascontiguousarray(ijk, dtype=np.int32).reshape(-1, 3)
+    out = np.zeros((ijk.shape[0], 4))
+    c = cfg._c()
+    if lib.oracle_constraints_points(ctypes.byref(c), _dp(st), ijk.shape[0],
+                                     ijk.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                                     _dp(out)) != 0:
+        raise MemoryError("oracle_constraints_points: allocation failed")
+    return out

@@ -1,0 +1,197 @@
+"""Exact vacuum spacetimes in 3+1 form, converted to BSSN variables, with their
+exact time derivatives -- used to pin the oracle's right-hand side.
+
+Nothing here uses the oracle or the CUDA library.  A spacetime is a 4-metric
+g_{mu nu} in base coordinates, pulled back through a smooth, time-dependent
+coordinate map (base coordinates as functions of the grid coordinates
+(t, x, y, z)).  The ADM fields follow from g by the 3+1 split
+(gamma_ij = g_ij, beta_i = g_0i, alpha^2 = beta^i beta_i - g_00), K_ij from
+the ADM evolution equation for the metric,
+    K_ij = (1 / 2 alpha) (-d_t gamma_ij + beta^k d_k gamma_ij
+                          + gamma_kj d_i beta^k + gamma_ik d_j beta^k),
+and the BSSN fields from the definitions of the paper's Sec. "Spacetime
+Curvature Evolution" (phi = ln(det gamma)/12, W = exp(-2 phi), gt = e^{-4 phi}
+gamma, K = gamma^ij K_ij, At = e^{-4 phi}(K_ij - gamma_ij K/3),
+Gt^i = -d_j gt^{ij}).  All derivatives are exact: the whole chain is evaluated
+in truncated Taylor arithmetic (tests/jets.py).
+
+Because these are exact solutions of the vacuum Einstein equations, the BSSN
+right-hand side of phi/W, gt, K, At and Gt evaluated on their data must equal
+the exact time derivative up to the O(h^4) truncation error of the stencils,
+whatever the gauge.  The gauge fields (alpha, beta, B) are checked against
+their defining equations evaluated with exact values.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from jets import Jet, cos, sin, sqrt
+
+SYM6 = [(0, 0), (0, 1), (0, 2), (1, 1), (1, 2), (2, 2)]
+ETA = np.diag([-1.0, 1.0, 1.0, 1.0])
+
+
+def minkowski(tb, xb):
+    return [[ETA[a, b] for b in range(4)] for a in range(4)]
+
+
+def kerr_schild(M):
+    """Schwarzschild in Kerr-Schild form, g = eta + 2 (M/r) l l, l = (1, x/r)."""
+    def g(tb, xb):
+        r = sqrt(xb[0] * xb[0] + xb[1] * xb[1] + xb[2] * xb[2])
+        H = r.recip() * M
+        l = [1.0] + [xb[i] / r for i in range(3)]
+        return [[(H * l[a] * l[b]) * 2.0 + ETA[a, b] for b in range(4)] for a in range(4)]
+    return g
+
+
+def _flat_wavy_map(t, x, y, z):
+    e = 0.05
+    tb = t + sin((x + 2.0 * y - z) * (2 * np.pi / 3) + t) * (e / 2)
+    xb = [x + sin((y + z) * (2 * np.pi / 3) + t * 0.5) * e,
+          y + cos((z - x) * (2 * np.pi / 3) - t) * (e / 2),
+          z + sin((x - y) * (2 * np.pi / 3)) * cos(t) * (e / 2)]
+    return tb, xb
+
+
+def _flat_wavy_B(t, x, y, z):
+    return [sin(x + 2.0 * z) * 0.1, cos(y - x) * 0.1, sin(x * y + z) * 0.1]
+
+
+def _ks_wavy_map(t, x, y, z):
+    e = 0.05
+    xb = [x + sin(y - z + t * (1 / 3)) * e,
+          y + cos(z + x) * (e / 2),
+          z + sin(x + 2.0 * y - t * 0.5) * (e / 2)]
+    return t, xb
+
+
+def _ks_wavy_B(t, x, y, z):
+    return [cos(y + z) * 0.1, sin(z - x) * 0.1, cos(x + y) * 0.1]
+
+
+def _gauge_wave_metric(A, d):
+    """ds^2 = H (-dt^2 + dx^2) + dy^2 + dz^2, H = 1 - A sin(2 pi (x - t) / d):
+    flat space in harmonic slicing with zero shift."""
+    def g(tb, xb):
+        H = 1.0 - sin((xb[0] - tb) * (2 * np.pi / d)) * A
+        return [[-H, 0.0, 0.0, 0.0], [0.0, H, 0.0, 0.0], [0.0, 0.0, 1.0, 0.0], [0.0, 0.0, 0.0, 1.0]]
+    return g
+
+
+def _identity_map(t, x, y, z):
+    return t, [x, y, z]
+
+
+def _zero_B(t, x, y, z):
+    return [x * 0.0, x * 0.0, x * 0.0]
+
+
+SPACETIMES = {
+    "gauge_wave": {"metric": _gauge_wave_metric(0.01, 1.0), "map": _identity_map, "B": _zero_B},
+    # Flat space in a time-dependent, curl-carrying, anisotropic coordinate
+    # system: curved slices (K != 0), non-trivial lapse and a shift whose
+    # gradient is not symmetric.
+    "flat_wavy": {"metric": minkowski, "map": _flat_wavy_map, "B": _flat_wavy_B},
+    # Schwarzschild (M = 1) in Kerr-Schild form seen from a moving, sheared
+    # grid: 3-curvature, conformal factor and Gt all non-trivial.
+    "ks_wavy": {"metric": kerr_schild(1.0), "map": _ks_wavy_map, "B": _ks_wavy_B},
+}
+
+
+def _det3(m):
+    return (m[0][0] * (m[1][1] * m[2][2] - m[1][2] * m[2][1])
+            - m[0][1] * (m[1][0] * m[2][2] - m[1][2] * m[2][0])
+            + m[0][2] * (m[1][0] * m[2][1] - m[1][1] * m[2][0]))
+
+
+def _adj3(m):
+    def c(i, j):  # cofactor C_ij
+        r = [a for a in range(3) if a != i]
+        s = [b for b in range(3) if b != j]
+        v = m[r[0]][s[0]] * m[r[1]][s[1]] - m[r[0]][s[1]] * m[r[1]][s[0]]
+        return v if (i + j) % 2 == 0 else -v
+    return [[c(j, i) for j in range(3)] for i in range(3)]  # adjugate = C^T
+
+
+def evaluate(name: str, X, Y, Z, time=0.0, use_w=True):
+    """Evaluate the spacetime on coordinate arrays.
+
+    Returns (state, dtstate, grad):
+      state  (24, ...) BSSN fields in the oracle's field order
+      dtstate (24, ...) exact d_t of fields 0..16 (phi|W, gt, K, At, Gt);
+              fields 17..23 are NaN (gauge: checked separately)
+      grad dict with 'alpha' (3,...) d_k alpha, 'beta' (3,3,...) [i][k] = d_k beta^i,
+              'Gt' (3,3,...) [i][k] = d_k Gt^i, 'B' (3,3,...) [i][k] = d_k B^i
+    """
+    spec = SPACETIMES[name]
+    X, Y, Z = np.broadcast_arrays(*(np.asarray(v, dtype=np.float64) for v in (X, Y, Z)))
+    shape = X.shape
+    T = Jet.var(0, np.full(shape, float(time)))
+    xs = [Jet.var(1, X), Jet.var(2, Y), Jet.var(3, Z)]
+    tb, xb = spec["map"](T, *xs)
+    base = [tb] + list(xb)
+    Jm = [[base[a].d(m) for m in range(4)] for a in range(4)]  # d base^a / d x^m
+    gb = spec["metric"](tb, xb)
+    g4 = [[None] * 4 for _ in range(4)]
+    for m in range(4):
+        for n in range(m, 4):
+            s = None
+            for a in range(4):
+                for b in range(4):
+                    gab = gb[a][b]
+                    if not isinstance(gab, Jet) and gab == 0.0:
+                        continue
+                    term = Jm[a][m] * Jm[b][n] * gab
+                    s = term if s is None else s + term
+            g4[m][n] = g4[n][m] = s
+    gam = [[g4[i + 1][j + 1] for j in range(3)] for i in range(3)]
+    bl = [g4[0][i + 1] for i in range(3)]
+    det = _det3(gam)
+    idet = det.recip()
+    gu = [[a * idet for a in row] for row in _adj3(gam)]
+    bu = [gu[i][0] * bl[0] + gu[i][1] * bl[1] + gu[i][2] * bl[2] for i in range(3)]
+    alpha = sqrt(bu[0] * bl[0] + bu[1] * bl[1] + bu[2] * bl[2] - g4[0][0])
+
+    def dt(j):
+        return j.d(0)
+
+    def dx(j, k):
+        return j.d(k + 1)
+
+    Kij = [[None] * 3 for _ in range(3)]
+    for i in range(3):
+        for j in range(i, 3):
+            s = -dt(gam[i][j])
+            for k in range(3):
+                s = s + bu[k] * dx(gam[i][j], k) + gam[k][j] * dx(bu[k], i) + gam[i][k] * dx(bu[k], j)
+            Kij[i][j] = Kij[j][i] = s / (alpha * 2.0)
+    trK = None
+    for i in range(3):
+        for j in range(3):
+            v = gu[i][j] * Kij[i][j]
+            trK = v if trK is None else trK + v
+    phi = det.log() * (1.0 / 12.0)
+    W = det ** (-1.0 / 6.0)
+    em4 = det ** (-1.0 / 3.0)
+    gt = [gam[i][j] * em4 for (i, j) in SYM6]
+    At = [(Kij[i][j] - gam[i][j] * trK * (1.0 / 3.0)) * em4 for (i, j) in SYM6]
+    cbrt_det = det ** (1.0 / 3.0)
+    gtu = [[gu[i][j] * cbrt_det for j in range(3)] for i in range(3)]
+    Gt = [-(dx(gtu[i][0], 0) + dx(gtu[i][1], 1) + dx(gtu[i][2], 2)) for i in range(3)]
+    Bv = spec["B"](T, *xs)
+
+    chi = W if use_w else phi
+    evolved = [chi] + gt + [trK] + At + Gt
+    state = np.stack([f.val for f in evolved + [alpha] + bu + Bv])
+    dts = np.full_like(state, np.nan)
+    for f, j in enumerate(evolved):
+        dts[f] = dt(j).val
+    grad = {
+        "dt_alpha": dt(alpha).val,
+        "alpha": np.stack([dx(alpha, k).val for k in range(3)]),
+        "beta": np.stack([np.stack([dx(bu[i], k).val for k in range(3)]) for i in range(3)]),
+        "Gt": np.stack([np.stack([dx(Gt[i], k).val for k in range(3)]) for i in range(3)]),
+        "B": np.stack([np.stack([dx(Bv[i], k).val for k in range(3)]) for i in range(3)]),
+    }
+    return np.ascontiguousarray(state), dts, grad
