@@ -1,0 +1,306 @@
+#!/usr/bin/env python3
+"""Benchmark: BSSN moving-puncture evolution, RK4 method of lines, on GB300.
+
+Workload (default): single Brill-Lindquist puncture, M = 1, on a 128^3 grid
+over [-8, 8]^3 (puncture half a cell off every grid point), W variable, 1+log
+slicing, Gamma-driver shift with eta = 2/M, Sommerfeld outer boundary, three
+ghost layers, RK4 with dt = 0.25 h, float64.  One "step" is one full RK4 step
+(four fused right-hand-side stages plus the boundary) over the whole grid.
+Throughput is reported as interior point-updates per second (one point
+advanced one RK4 step).
+
+Launch: ``python bench.py [--gpus N] [--steps K] [--warmup W]`` for N = 1, or
+under torchrun for N > 1 (one independent replica per GPU: the path does not
+shard, so ranks exchange nothing but the timing barrier).
+``--impl reference`` times the CPU oracle (plain float64 C) on a bounded
+sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_SIDE = 128
+DOMAIN = 8.0
+# Float64 work per interior point per fused stage launch (right-hand side plus
+# RK4 combine), from the ncu instruction counts of the stage kernel
+# (profiles/stage_fp64_bl64.md): 1032 DADD + 308 DMUL + 1530 DFMA.
+FLOP_PER_POINT_RHS = 4400.0        # DADD + DMUL + 2 DFMA
+DPINST_PER_POINT_RHS = 2870.0      # float64 instructions issued
+HBM_BYTES_PER_POINT_STEP = 3072.0  # 16 register passes x 24 fields x 8 B
+FP64_PEAK_GFLOPS = 1250.0          # nominal GB300 FP64 rate
+FP64_MEASURED_GFLOPS = 1196.0      # dependent-chain DFMA microbenchmark on this pool
+
+
+def workload_params(precision="fp64"):
+    from paper_1111_3344_gb300.bssn import Params
+    h = 2 * DOMAIN / N_SIDE
+    return Params(n=(N_SIDE,) * 3, xmin=(-DOMAIN,) * 3, h=h, boundary="sommerfeld", conformal="W",
+                  slicing="1+log", shift="gamma-driver", eta=2.0, ko_eps=0.1, dt=0.25 * h,
+                  precision=precision, r_excise=1.0)
+
+
+BL_P = [1, 1.0, 0.0, 0.0, 0.0]
+
+
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([c.strip() for c in line.split(",")])
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=5)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[1]))
+                mx = float(r[2])
+            except (ValueError, IndexError):
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup(n_gpus):
+    import torch
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world != n_gpus:
+        raise SystemExit(f"--gpus {n_gpus} but WORLD_SIZE={world}")
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    return rank, world, local
+
+
+def barrier(world):
+    import torch
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+
+
+def max_over_ranks(x, world):
+    import torch
+    if world == 1:
+        return x
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def oracle_cpu_baseline(steps_budget_s=30.0):
+    """The float64 CPU oracle on one full RK4 step of the same workload."""
+    import oracle as O
+    cfg = O.Config(n=(N_SIDE,) * 3, xmin=(-DOMAIN,) * 3, h=2 * DOMAIN / N_SIDE, periodic=False,
+                   use_w=True, slicing="1+log", shift="gamma-driver", eta=2.0, ko_eps=0.1,
+                   dt=0.25 * 2 * DOMAIN / N_SIDE, punctures=[(1.0, 0.0, 0.0, 0.0)])
+    st = O.initial_data(cfg, "bl", BL_P)
+    t0 = time.perf_counter()
+    O.rk4(cfg, st, 1)
+    dt = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": N_SIDE ** 3 / dt / 1e6, "unit": "Mpoint-updates/s", "cores": cores, "kind": "oracle",
+            "sample": f"one full RK4 step of the {N_SIDE}^3 puncture workload ({dt:.1f} s)"}
+
+
+def run_reference(args):
+    """--impl reference: the CPU oracle, bounded sample per step."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle as O
+    cfg = O.Config(n=(N_SIDE,) * 3, xmin=(-DOMAIN,) * 3, h=2 * DOMAIN / N_SIDE, periodic=False,
+                   use_w=True, slicing="1+log", shift="gamma-driver", eta=2.0, ko_eps=0.1,
+                   dt=0.25 * 2 * DOMAIN / N_SIDE, punctures=[(1.0, 0.0, 0.0, 0.0)])
+    st = O.initial_data(cfg, "bl", BL_P)
+    rng = np.random.default_rng(0)
+    npts = 8192
+    ijk = np.stack([rng.integers(3, 3 + N_SIDE, npts) for _ in range(3)], axis=1).astype(np.int32)
+    for _ in range(args.warmup):
+        O.rhs_points(cfg, st, ijk)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        for _ in range(4):  # four right-hand sides per RK4 point-update
+            O.rhs_points(cfg, st, ijk)
+        times.append(time.perf_counter() - t0)
+    tot = sum(times)
+    value = npts * args.steps / tot / 1e6
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    line = {
+        "metric": "BSSN RK4 point-updates/s (FP64, Brill-Lindquist puncture 128^3)",
+        "value": value, "unit": "Mpoint-updates/s", "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "impl": "reference",
+        "config": {"workload": "single Brill-Lindquist puncture M=1, 128^3 on [-8,8]^3, W, 1+log, "
+                               "Gamma-driver eta=2, Sommerfeld, RK4 dt=0.25h",
+                   "sample": f"{npts} random interior points x 4 right-hand sides per step"},
+        "cpu_baseline": {"value": value, "unit": "Mpoint-updates/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{npts} random interior points x 4 right-hand sides per step"},
+        "e2e": {"value": value, "unit": "Mpoint-updates/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def run_ours(args):
+    import torch
+
+    from paper_1111_3344_gb300 import bssn as B
+    rank, world, local = dist_setup(args.gpus)
+    params = workload_params(args.precision)
+    evo = B.Evolution(params)
+    evo.set_initial_data("bl", BL_P)
+    stream = evo.stream
+    for _ in range(args.warmup):
+        evo.rk4_step(1)
+    barrier(world)
+    clocks = ClockSampler(local)
+    clocks.start()
+    B.bssn_profile(evo.ctx, True)
+    start = torch.cuda.Event(enable_timing=True)
+    stop = torch.cuda.Event(enable_timing=True)
+    barrier(world)
+    start.record(stream)
+    for _ in range(args.steps):
+        evo.rk4_step(1)
+    stop.record(stream)
+    stop.synchronize()
+    barrier(world)
+    ms_local = start.elapsed_time(stop)
+    stage_ms, stage_n, bc_ms, bc_n = B.bssn_profile(evo.ctx, False)
+    clk = clocks.stop()
+    ms = max_over_ranks(ms_local, world)
+    pts = N_SIDE ** 3
+    value = pts * args.steps * world / (ms * 1e-3) / 1e6
+
+    # end to end through the C ABI with pinned host buffers: upload state,
+    # one RK4 step, read the state back, every step
+    host_in = torch.empty(evo.shape, dtype=torch.float64, pin_memory=True).numpy()
+    host_out = torch.empty(evo.shape, dtype=torch.float64, pin_memory=True).numpy()
+    host_in[...], _ = evo.get_state()
+    e2e_steps = max(2, min(args.steps, 5))
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        evo.set_state(host_in, 0.0)
+        evo.rk4_step(1)
+        B.bssn_get_state(evo.ctx, host_out)
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world)
+    e2e_value = pts * e2e_steps * world / e2e_s / 1e6
+    nbytes = host_in.nbytes
+
+    flop_launch = FLOP_PER_POINT_RHS * pts
+    stage_launch_ms = stage_ms / max(stage_n, 1)
+    achieved = flop_launch / (stage_launch_ms * 1e-3) / 1e12
+    line = {
+        "metric": "BSSN RK4 point-updates/s (FP64, Brill-Lindquist puncture 128^3)",
+        "value": value, "unit": "Mpoint-updates/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f64",
+        "data": "synthetic",
+        "config": {"workload": "single Brill-Lindquist puncture M=1, 128^3 on [-8,8]^3, W, 1+log, "
+                               "Gamma-driver eta=2, Sommerfeld, RK4 dt=0.25h",
+                   "global_batch": world, "grid": [N_SIDE] * 3, "parallelism": f"replicas{world}",
+                   "precision": args.precision,
+                   "l2": "inputs larger than L2 (4 float64 registers of 469 MB each)"},
+        "roofline": {"bound": "alu", "kernel": "stage_fp64_kernel", "achieved": achieved * 1e3,
+                     "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s (FP64)",
+                     "frac": achieved * 1e3 / FP64_PEAK_GFLOPS,
+                     "frac_of_measured_dfma": achieved * 1e3 / FP64_MEASURED_GFLOPS,
+                     "fp64_issue_frac": DPINST_PER_POINT_RHS * pts / (stage_launch_ms * 1e-3)
+                                        / (FP64_MEASURED_GFLOPS * 1e9 / 2),
+                     "traffic": None, "launch_ms": stage_launch_ms, "launches": stage_n,
+                     "hbm_frac": (HBM_BYTES_PER_POINT_STEP * pts * args.steps / (ms * 1e-3)) / 6764e9},
+        "e2e": {"value": e2e_value, "unit": "Mpoint-updates/s", "h2d_bytes_per_step": nbytes,
+                "d2h_bytes_per_step": nbytes, "steps": e2e_steps},
+        "gpu_launches": stage_n + bc_n,
+        "clocks": clk,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = oracle_cpu_baseline()
+    if rank == 0:
+        print(json.dumps(line))
+    evo.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--n", type=int, default=128,
+                    help="grid points per side (128 is the benchmark workload; smaller sizes are "
+                         "for profiling captures only)")
+    args = ap.parse_args()
+    global N_SIDE
+    N_SIDE = args.n
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,188 @@
+/*
+ * bssn.h -- C ABI of libbssn: the BSSN moving-puncture right-hand side of
+ * "The Einstein Toolkit" (arXiv:1111.3344), Sec. "Spacetime Curvature
+ * Evolution", advanced by fourth-order Runge-Kutta method of lines on a
+ * uniform cell-centred grid with three ghost layers, on one NVIDIA GB300
+ * (sm_103a).
+ *
+ * Conventions
+ *  - Every call returns bssn_status (BSSN_OK = 0).  On failure,
+ *    bssn_last_error() returns a message for the calling thread.
+ *  - The caller owns all bulk device memory and the CUDA stream.  The library
+ *    carves its registers and small tables out of the block given to
+ *    bssn_alloc and never calls cudaMalloc.
+ *  - Calls are asynchronous on the bound stream unless their comment says
+ *    "synchronises".
+ *  - Device state layout (structure of arrays): element (f, k, j, i) of a
+ *    register lives at f*field_stride + k*plane + j*pitch + i, for field
+ *    f in [0, 24), stored point (i, j, k) in [0, n0+6) x [0, n1+6) x
+ *    [0, n2+6); point i on an axis sits at xmin + (i - 3 + 1/2) h.  pitch is
+ *    a multiple of 8 elements; see bssn_layout.
+ *  - Host state layout (bssn_get_state / bssn_set_state): the same order
+ *    without padding, float64, shape (24, n2+6, n1+6, n0+6).
+ *  - Field order: 0 phi or W, 1..6 conformal metric gt_xx gt_xy gt_xz gt_yy
+ *    gt_yz gt_zz, 7 trace K, 8..13 trace-free At_ij (same order), 14..16
+ *    conformal connection Gt^i, 17 lapse alpha, 18..20 shift beta^i,
+ *    21..23 B^i (the 24 evolved grid functions of the paper's BSSN system).
+ */
+#ifndef BSSN_H
+#define BSSN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define BSSN_NUM_FIELDS 24
+#define BSSN_GHOST 3
+
+typedef enum {
+  BSSN_OK = 0,
+  BSSN_EINVAL = 1,    /* bad argument or parameter */
+  BSSN_ENOMEM = 2,    /* memory block too small / budget exceeded */
+  BSSN_ECUDA = 3,     /* a CUDA call failed (message has the CUDA error) */
+  BSSN_EAGAIN = 4,    /* poll: request not finished yet */
+  BSSN_ETIMEOUT = 5,  /* a bounded wait expired */
+  BSSN_ENOTFOUND = 6, /* unknown ticket */
+  BSSN_EFAILED = 7    /* NaN/Inf detected in a request's state */
+} bssn_status;
+
+enum { BSSN_BC_PERIODIC = 0, BSSN_BC_SOMMERFELD = 1 };
+enum { BSSN_PHI = 0, BSSN_W = 1 };
+enum { BSSN_1PLUSLOG = 0, BSSN_HARMONIC = 1, BSSN_GEODESIC = 2 };
+enum { BSSN_GAMMA_DRIVER = 0, BSSN_SHIFT_FROZEN = 1 };
+enum { BSSN_FP64 = 0, BSSN_MIXED = 1 };
+enum { BSSN_ID_FLAT = 0, BSSN_ID_GAUGE_WAVE = 1, BSSN_ID_BL = 2, BSSN_ID_KASNER = 3 };
+
+/* Grid and method parameters.
+ *  n, ghost, xmin, h   uniform cell-centred grid (Sec. "Simulation Domain,
+ *                      Symmetries, Boundaries": physical vs discrete domain);
+ *                      n[d] >= 4, ghost == 3, h > 0.
+ *  boundary            periodic ghosts or the Sommerfeld radiative condition
+ *                      of Sec. "Boundary Conditions".
+ *  conformal           evolve phi (the paper's variable) or W = exp(-2 phi).
+ *  slicing             d_0 alpha = -alpha^2 f K with f = 2/alpha (1+log,
+ *                      Sec. "Spacetime Curvature Evolution"), f = 1
+ *                      (harmonic) or f = 0 (geodesic).
+ *  shift               Gamma-driver (d_0 beta = (3/4) B, d_0 B = d_0 Gt -
+ *                      eta q(r) B) or frozen (beta, B right-hand sides 0).
+ *  eta, q_R            Gamma-driver damping and the radius R of q(r) = 1
+ *                      (r <= R), R/r (r > R); q_R <= 0 or inf means q = 1.
+ *  ko_eps              Kreiss-Oliger epsilon.
+ *  dt                  RK4 time step.
+ *  precision           BSSN_FP64: everything in float64.  BSSN_MIXED:
+ *                      stencils and right-hand side in float32, RK4 state
+ *                      and constraint reductions in float64.
+ *  w_fp64_threshold    mixed precision: points with W below this take the
+ *                      W/phi right-hand side in float64.
+ *  r_excise            constraint norms: excised set is r > r_excise from
+ *                      every puncture.
+ *  w_floor             lower bound on W wherever W divides (default 1e-10).
+ */
+typedef struct bssn_params {
+  int32_t n[3];
+  int32_t ghost;
+  double xmin[3];
+  double h;
+  int32_t boundary;
+  int32_t conformal;
+  int32_t slicing;
+  int32_t shift;
+  double eta;
+  double q_R;
+  double ko_eps;
+  double dt;
+  int32_t precision;
+  int32_t reserved0;
+  double w_fp64_threshold;
+  double r_excise;
+  double w_floor;
+} bssn_params;
+
+/* Register layout of one evolution (all counts in elements). */
+typedef struct bssn_layout {
+  int32_t stored[3];      /* n[d] + 6 */
+  int32_t ghost;          /* 3 */
+  int64_t pitch;          /* elements per x-row, multiple of 8 */
+  int64_t plane;          /* pitch * stored[1] */
+  int64_t field_stride;   /* plane * stored[2] */
+  int64_t register_elems; /* 24 * field_stride */
+} bssn_layout;
+
+typedef struct bssn_ctx bssn_ctx;       /* one evolution (opaque) */
+typedef struct bssn_server bssn_server; /* continuous-batching server (opaque) */
+
+/* Thread-local message for the last failed call on this thread. */
+const char* bssn_last_error(void);
+
+/* Fill *out with the register layout for p.  Host only.  EINVAL on bad p. */
+bssn_status bssn_layout_of(const bssn_params* p, bssn_layout* out);
+
+/* Device bytes bssn_alloc needs for p (registers y_n, accumulator, two stage
+ * buffers, boundary-anchor buffer, reduction scratch).  Host only; 0 on bad p. */
+size_t bssn_required_bytes(const bssn_params* p);
+
+/* Bind an evolution to caller-owned device memory d_mem (>= required bytes,
+ * 256-byte aligned) and a CUDA stream (cudaStream_t as void*, NULL = legacy
+ * default stream).  Validates p; allocates only the host-side context.  The
+ * state is undefined until set_initial_data or set_state.  t starts at 0. */
+bssn_status bssn_alloc(const bssn_params* p, void* d_mem, size_t bytes, void* cuda_stream,
+                       bssn_ctx** out);
+
+/* Release the host-side context (does not free d_mem; synchronises the stream). */
+bssn_status bssn_free(bssn_ctx* ctx);
+
+/* Device pointer of the current state register y_n (float64, layout above). */
+bssn_status bssn_state_ptr(bssn_ctx* ctx, double** d_state);
+
+/* Analytic initial data, converted to BSSN by the definitions of Sec.
+ * "Spacetime Curvature Evolution" with B^i = 0 (Sec. "Initial Conditions"),
+ * evaluated on the device at every stored point; t is reset to 0.
+ *   BSSN_ID_FLAT        p ignored.
+ *   BSSN_ID_GAUGE_WAVE  p = {A, d}: ds^2 = H(-dt^2 + dx^2) + dy^2 + dz^2,
+ *                       H = 1 - A sin(2 pi x / d) at t = 0.
+ *   BSSN_ID_BL          p = {npunct, m_1, x_1, y_1, z_1, ...} (npunct <= 8):
+ *                       Brill-Lindquist, psi = 1 + sum m_a / (2 r_a),
+ *                       gamma = psi^4 delta, K_ij = 0 (Sec. "Initial Data",
+ *                       TwoPunctures with u = 1 at K = 0); alpha = psi^-2.
+ *                       The punctures also define the excised norm set.
+ *   BSSN_ID_KASNER      p = {t0}: Kasner slice of Sec. "Cosmology",
+ *                       gamma = diag(t0^{4/3}, t0^{4/3}, t0^{-2/3}), alpha = 1.
+ * EINVAL on an unknown kind or too few parameters. */
+bssn_status bssn_set_initial_data(bssn_ctx* ctx, int32_t kind, const double* p, int32_t np);
+
+/* One right-hand side, interior points by the BSSN equations (4th-order
+ * centred stencils, upwinded advection, KO dissipation), ghost points by the
+ * Sommerfeld condition (or 0 when periodic).  d_state: a float64 register in
+ * the layout above (NULL = the context's y_n); d_rhs: a float64 register the
+ * caller owns.  Ghost values of d_state must be valid (periodic: filled). */
+bssn_status bssn_rhs(bssn_ctx* ctx, const void* d_state, void* d_rhs);
+
+/* Advance y_n by nsteps classical RK4 steps of size dt (t += nsteps dt). */
+bssn_status bssn_rk4_step(bssn_ctx* ctx, int32_t nsteps);
+
+/* Constraint norms of y_n (synchronises): out[0..3] L2 (root mean square)
+ * of H, M_x, M_y, M_z over interior points, out[4..7] their max-abs, out[8..15]
+ * the same over interior points farther than r_excise from every puncture.
+ * H = R - K^i_j K^j_i + K^2, M_i = nabla_j K_i^j - nabla_i K (vacuum) from the
+ * ADM fields (Sec. "Other analysis modules"), float64 in every precision. */
+bssn_status bssn_constraints(bssn_ctx* ctx, double out[16]);
+
+/* Copy y_n to / from host memory (unpadded float64 layout; synchronises).
+ * Pinned host memory gives full transfer speed.  t may be NULL. */
+bssn_status bssn_get_state(bssn_ctx* ctx, double* host_state, double* t);
+bssn_status bssn_set_state(bssn_ctx* ctx, const double* host_state, double t);
+
+/* Launch timing.  enable != 0: start recording CUDA events on the bound
+ * stream around every fused stage launch and every boundary launch of
+ * bssn_rk4_step (out unused).  enable == 0: stop, synchronise and write
+ * out[0] = total stage-kernel milliseconds, out[1] = stage launches,
+ * out[2] = total boundary-kernel milliseconds, out[3] = boundary launches. */
+bssn_status bssn_profile(bssn_ctx* ctx, int32_t enable, double out[4]);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BSSN_H */

@@ -1,0 +1,324 @@
+"""ctypes binding of libbssn (include/bssn.h): the same entry points with the
+same names, argument marshalling only.  Every step of the evolution runs in
+the CUDA library; PyTorch supplies device memory and the stream.
+
+There is no fallback: if the library is missing or no GPU is present, the
+calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import build as _build
+
+NUM_FIELDS = 24
+GHOST = 3
+
+BC = {"periodic": 0, "sommerfeld": 1}
+CONFORMAL = {"phi": 0, "W": 1}
+SLICING = {"1+log": 0, "harmonic": 1, "geodesic": 2}
+SHIFT = {"gamma-driver": 0, "frozen": 1}
+PRECISION = {"fp64": 0, "mixed": 1}
+ID_KIND = {"flat": 0, "gauge_wave": 1, "bl": 2, "kasner": 3}
+STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "EAGAIN", 5: "ETIMEOUT",
+          6: "ENOTFOUND", 7: "EFAILED"}
+
+
+class BssnError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class bssn_params(ctypes.Structure):
+    _fields_ = [
+        ("n", ctypes.c_int32 * 3),
+        ("ghost", ctypes.c_int32),
+        ("xmin", ctypes.c_double * 3),
+        ("h", ctypes.c_double),
+        ("boundary", ctypes.c_int32),
+        ("conformal", ctypes.c_int32),
+        ("slicing", ctypes.c_int32),
+        ("shift", ctypes.c_int32),
+        ("eta", ctypes.c_double),
+        ("q_R", ctypes.c_double),
+        ("ko_eps", ctypes.c_double),
+        ("dt", ctypes.c_double),
+        ("precision", ctypes.c_int32),
+        ("reserved0", ctypes.c_int32),
+        ("w_fp64_threshold", ctypes.c_double),
+        ("r_excise", ctypes.c_double),
+        ("w_floor", ctypes.c_double),
+    ]
+
+
+class bssn_layout(ctypes.Structure):
+    _fields_ = [
+        ("stored", ctypes.c_int32 * 3),
+        ("ghost", ctypes.c_int32),
+        ("pitch", ctypes.c_int64),
+        ("plane", ctypes.c_int64),
+        ("field_stride", ctypes.c_int64),
+        ("register_elems", ctypes.c_int64),
+    ]
+
+
+@dataclass
+class Params:
+    """Python mirror of bssn_params with readable enum values."""
+    n: tuple = (24, 24, 24)
+    xmin: tuple = (-0.5, -0.5, -0.5)
+    h: float = 1.0 / 24.0
+    boundary: str = "periodic"
+    conformal: str = "W"
+    slicing: str = "1+log"
+    shift: str = "gamma-driver"
+    eta: float = 2.0
+    q_R: float = math.inf
+    ko_eps: float = 0.1
+    dt: float = 0.25 / 24.0
+    precision: str = "fp64"
+    w_fp64_threshold: float = 0.0
+    r_excise: float = 1.0
+    w_floor: float = 1e-10
+
+    def c(self) -> bssn_params:
+        p = bssn_params()
+        for d in range(3):
+            p.n[d] = int(self.n[d])
+            p.xmin[d] = float(self.xmin[d])
+        p.ghost = GHOST
+        p.h = float(self.h)
+        p.boundary = BC[self.boundary]
+        p.conformal = CONFORMAL[self.conformal]
+        p.slicing = SLICING[self.slicing]
+        p.shift = SHIFT[self.shift]
+        p.eta = float(self.eta)
+        p.q_R = float(self.q_R)
+        p.ko_eps = float(self.ko_eps)
+        p.dt = float(self.dt)
+        p.precision = PRECISION[self.precision]
+        p.w_fp64_threshold = float(self.w_fp64_threshold)
+        p.r_excise = float(self.r_excise)
+        p.w_floor = float(self.w_floor)
+        return p
+
+
+_lib = None
+
+# (name, argtypes, restype) of every exported entry point
+_SIGS = [
+    ("bssn_last_error", [], ctypes.c_char_p),
+    ("bssn_layout_of", [ctypes.POINTER(bssn_params), ctypes.POINTER(bssn_layout)], ctypes.c_int),
+    ("bssn_required_bytes", [ctypes.POINTER(bssn_params)], ctypes.c_size_t),
+    ("bssn_alloc", [ctypes.POINTER(bssn_params), ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p,
+                    ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int),
+    ("bssn_free", [ctypes.c_void_p], ctypes.c_int),
+    ("bssn_state_ptr", [ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int),
+    ("bssn_set_initial_data", [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
+                               ctypes.c_int32], ctypes.c_int),
+    ("bssn_rhs", [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
+    ("bssn_rk4_step", [ctypes.c_void_p, ctypes.c_int32], ctypes.c_int),
+    ("bssn_constraints", [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+    ("bssn_get_state", [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+    ("bssn_set_state", [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double], ctypes.c_int),
+    ("bssn_profile", [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+]
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libbssn.so (building it first if it is missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_missing:
+        _build.build()
+    if not os.path.exists(_build.LIB):
+        raise RuntimeError(f"libbssn.so not found at {_build.LIB}; run paper_1111_3344_gb300.build.build()")
+    lib = ctypes.CDLL(_build.LIB)
+    for name, args, res in _SIGS:
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = lib
+    return lib
+
+
+def exported_symbols():
+    return [s[0] for s in _SIGS]
+
+
+def _check(status):
+    if status != 0:
+        raise BssnError(status, load().bssn_last_error().decode())
+
+
+def _dbl_array(vals):
+    arr = (ctypes.c_double * max(1, len(vals)))(*[float(v) for v in vals])
+    return arr
+
+
+# ---------------------------------------------------------------- raw ABI
+def bssn_layout_of(params: Params) -> dict:
+    p = params.c()
+    lay = bssn_layout()
+    _check(load().bssn_layout_of(ctypes.byref(p), ctypes.byref(lay)))
+    return {"stored": tuple(lay.stored), "ghost": lay.ghost, "pitch": lay.pitch,
+            "plane": lay.plane, "field_stride": lay.field_stride,
+            "register_elems": lay.register_elems}
+
+
+def bssn_required_bytes(params: Params) -> int:
+    p = params.c()
+    n = load().bssn_required_bytes(ctypes.byref(p))
+    if n == 0:
+        raise BssnError(1, load().bssn_last_error().decode())
+    return int(n)
+
+
+def bssn_alloc(params: Params, d_mem: int, nbytes: int, stream: int) -> int:
+    p = params.c()
+    out = ctypes.c_void_p()
+    _check(load().bssn_alloc(ctypes.byref(p), ctypes.c_void_p(d_mem), nbytes,
+                             ctypes.c_void_p(stream), ctypes.byref(out)))
+    return out.value
+
+
+def bssn_free(ctx: int):
+    _check(load().bssn_free(ctypes.c_void_p(ctx)))
+
+
+def bssn_state_ptr(ctx: int) -> int:
+    out = ctypes.c_void_p()
+    _check(load().bssn_state_ptr(ctypes.c_void_p(ctx), ctypes.byref(out)))
+    return out.value
+
+
+def bssn_set_initial_data(ctx: int, kind: str, p=()):
+    arr = _dbl_array(p)
+    _check(load().bssn_set_initial_data(ctypes.c_void_p(ctx), ID_KIND[kind], arr, len(p)))
+
+
+def bssn_rhs(ctx: int, d_state, d_rhs: int):
+    _check(load().bssn_rhs(ctypes.c_void_p(ctx), ctypes.c_void_p(d_state or 0), ctypes.c_void_p(d_rhs)))
+
+
+def bssn_rk4_step(ctx: int, nsteps: int):
+    _check(load().bssn_rk4_step(ctypes.c_void_p(ctx), int(nsteps)))
+
+
+def bssn_constraints(ctx: int) -> np.ndarray:
+    out = (ctypes.c_double * 16)()
+    _check(load().bssn_constraints(ctypes.c_void_p(ctx), out))
+    return np.array(out[:], dtype=np.float64)
+
+
+def bssn_get_state(ctx: int, host: np.ndarray) -> float:
+    assert host.dtype == np.float64 and host.flags.c_contiguous
+    t = ctypes.c_double()
+    _check(load().bssn_get_state(ctypes.c_void_p(ctx), ctypes.c_void_p(host.ctypes.data), ctypes.byref(t)))
+    return t.value
+
+
+def bssn_set_state(ctx: int, host: np.ndarray, t: float = 0.0):
+    assert host.dtype == np.float64 and host.flags.c_contiguous
+    _check(load().bssn_set_state(ctypes.c_void_p(ctx), ctypes.c_void_p(host.ctypes.data), float(t)))
+
+
+def bssn_profile(ctx: int, enable: bool):
+    """Start (enable=True) or stop launch timing; on stop returns
+    (stage_ms, stage_launches, boundary_ms, boundary_launches)."""
+    out = (ctypes.c_double * 4)()
+    _check(load().bssn_profile(ctypes.c_void_p(ctx), 1 if enable else 0, out))
+    return None if enable else (out[0], int(out[1]), out[2], int(out[3]))
+
+
+# ------------------------------------------------------- convenience class
+class Evolution:
+    """One evolution bound to a torch-owned device block and a CUDA stream."""
+
+    def __init__(self, params: Params, device: str = "cuda", stream=None):
+        import torch
+
+        self.torch = torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("a CUDA device is required (no CPU path)")
+        self.params = params
+        self.layout = bssn_layout_of(params)
+        self.nbytes = bssn_required_bytes(params)
+        self.device = torch.device(device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.mem = torch.empty(self.nbytes, dtype=torch.uint8, device=self.device)
+        self.ctx = bssn_alloc(params, self.mem.data_ptr(), self.nbytes, self.stream.cuda_stream)
+
+    def close(self):
+        if self.ctx:
+            bssn_free(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # register helpers (marshalling between host arrays and the padded layout)
+    @property
+    def shape(self):
+        sx, sy, sz = self.layout["stored"]
+        return (NUM_FIELDS, sz, sy, sx)
+
+    def new_register(self):
+        return self.torch.zeros(self.layout["register_elems"], dtype=self.torch.float64, device=self.device)
+
+    def register_to_numpy(self, reg) -> np.ndarray:
+        sx, sy, sz = self.layout["stored"]
+        a = reg.view(NUM_FIELDS, sz, sy, self.layout["pitch"])[..., :sx]
+        return a.cpu().numpy().copy()
+
+    def numpy_to_register(self, arr: np.ndarray):
+        sx, sy, sz = self.layout["stored"]
+        reg = self.new_register()
+        v = reg.view(NUM_FIELDS, sz, sy, self.layout["pitch"])
+        v[..., :sx] = self.torch.from_numpy(np.ascontiguousarray(arr, dtype=np.float64)).to(self.device)
+        return reg
+
+    def state_view(self):
+        """torch view of y_n in the padded device layout (valid until the next step)."""
+        sx, sy, sz = self.layout["stored"]
+        ptr = bssn_state_ptr(self.ctx)
+        off = (ptr - self.mem.data_ptr()) // 8
+        flat = self.mem.view(self.torch.float64)
+        return flat[off:off + self.layout["register_elems"]].view(NUM_FIELDS, sz, sy, self.layout["pitch"])
+
+    # ABI calls
+    def set_initial_data(self, kind, p=()):
+        bssn_set_initial_data(self.ctx, kind, p)
+
+    def rhs(self, state_reg=None):
+        out = self.new_register()
+        bssn_rhs(self.ctx, state_reg.data_ptr() if state_reg is not None else None, out.data_ptr())
+        return out
+
+    def rk4_step(self, nsteps=1):
+        bssn_rk4_step(self.ctx, nsteps)
+
+    def constraints(self):
+        return bssn_constraints(self.ctx)
+
+    def get_state(self):
+        host = np.empty(self.shape, dtype=np.float64)
+        t = bssn_get_state(self.ctx, host)
+        return host, t
+
+    def set_state(self, host: np.ndarray, t: float = 0.0):
+        bssn_set_state(self.ctx, np.ascontiguousarray(host, dtype=np.float64), t)

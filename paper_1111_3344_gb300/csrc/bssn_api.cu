@@ -1,0 +1,488 @@
+// C ABI of libbssn (include/bssn.h): parameter validation, binding of
+// caller-owned device memory, launch sequencing of the RK4 method of lines,
+// constraint norms and host<->device state transfer.  No allocation of
+// device memory happens here; registers and tables are carved from the block
+// given to bssn_alloc.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "bssn_internal.cuh"
+
+using namespace bssn;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+bssn_status fail(bssn_status s, const std::string& msg) {
+  g_last_error = msg;
+  return s;
+}
+
+bssn_status cuda_fail(cudaError_t e, const char* where) {
+  return fail(BSSN_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+constexpr size_t ALIGN = 256;
+size_t align_up(size_t v) { return (v + ALIGN - 1) / ALIGN * ALIGN; }
+
+bool validate(const bssn_params* p, std::string& why) {
+  if (!p) { why = "params is NULL"; return false; }
+  for (int d = 0; d < 3; d++)
+    if (p->n[d] < 4 || p->n[d] > 4096) { why = "n[d] must be in [4, 4096]"; return false; }
+  if (p->ghost != BSSN_GHOST) { why = "ghost must be 3"; return false; }
+  if (!(p->h > 0.0) || !std::isfinite(p->h)) { why = "h must be positive and finite"; return false; }
+  for (int d = 0; d < 3; d++)
+    if (!std::isfinite(p->xmin[d])) { why = "xmin must be finite"; return false; }
+  if (p->boundary != BSSN_BC_PERIODIC && p->boundary != BSSN_BC_SOMMERFELD) { why = "bad boundary"; return false; }
+  if (p->conformal != BSSN_PHI && p->conformal != BSSN_W) { why = "bad conformal"; return false; }
+  if (p->slicing < BSSN_1PLUSLOG || p->slicing > BSSN_GEODESIC) { why = "bad slicing"; return false; }
+  if (p->shift != BSSN_GAMMA_DRIVER && p->shift != BSSN_SHIFT_FROZEN) { why = "bad shift"; return false; }
+  if (p->precision != BSSN_FP64 && p->precision != BSSN_MIXED) { why = "bad precision"; return false; }
+  if (!(p->w_fp64_threshold >= 0.0) || !std::isfinite(p->w_fp64_threshold)) {
+    why = "w_fp64_threshold must be finite and >= 0";
+    return false;
+  }
+  if (!std::isfinite(p->dt) || !std::isfinite(p->ko_eps) || !std::isfinite(p->eta)) {
+    why = "dt, ko_eps and eta must be finite";
+    return false;
+  }
+  if (!(p->w_floor > 0.0)) { why = "w_floor must be positive"; return false; }
+  return true;
+}
+
+Grid make_grid(const bssn_params* p) {
+  Grid g{};
+  g.n0 = p->n[0];
+  g.n1 = p->n[1];
+  g.n2 = p->n[2];
+  g.sx = g.n0 + 2 * GH;
+  g.sy = g.n1 + 2 * GH;
+  g.sz = g.n2 + 2 * GH;
+  g.pitch = (g.sx + 7) / 8 * 8;
+  g.plane = g.pitch * g.sy;
+  g.fstride = g.plane * g.sz;
+  g.xmin0 = p->xmin[0];
+  g.xmin1 = p->xmin[1];
+  g.xmin2 = p->xmin[2];
+  g.h = p->h;
+  g.periodic = p->boundary == BSSN_BC_PERIODIC;
+  g.use_w = p->conformal == BSSN_W;
+  g.slicing = p->slicing;
+  g.shift = p->shift;
+  g.eta = p->eta;
+  g.q_R = p->q_R;
+  g.ko_eps = p->ko_eps;
+  g.w_floor = p->w_floor;
+  return g;
+}
+
+// Device block layout.  float64: y_n, acc, s1, s2 (+ anchor buffer for
+// Sommerfeld).  mixed: y_n, acc in float64; three float stage buffers m[0..2]
+// (m[0] is the float shadow of y_n), each with a float64 W array; float anchors.
+struct Carve {
+  size_t reg, yn, acc, s1, s2, ksh, part, out16, total;
+  size_t m32[3], mw[3];
+  int nblocks;
+};
+
+Carve carve(const bssn_params* p, const Grid& g) {
+  Carve c{};
+  const size_t regb = align_up((size_t)NF * (size_t)g.fstride * sizeof(double));
+  const size_t reg32 = align_up((size_t)NF * (size_t)g.fstride * sizeof(float));
+  const size_t wb = align_up((size_t)g.fstride * sizeof(double));
+  c.reg = regb;
+  size_t o = 0;
+  c.yn = o; o += regb;
+  c.acc = o; o += regb;
+  if (p->precision == BSSN_FP64) {
+    c.s1 = o; o += regb;
+    c.s2 = o; o += regb;
+    c.ksh = o;
+    if (p->boundary == BSSN_BC_SOMMERFELD) o += regb;
+  } else {
+    for (int q = 0; q < 3; q++) {
+      c.m32[q] = o; o += reg32;
+      c.mw[q] = o; o += wb;
+    }
+    c.ksh = o;
+    if (p->boundary == BSSN_BC_SOMMERFELD) o += reg32;
+  }
+  c.nblocks = constraints_blocks(g);
+  c.part = o; o += align_up((size_t)c.nblocks * 18 * sizeof(double));
+  c.out16 = o; o += align_up(16 * sizeof(double));
+  c.total = o;
+  return c;
+}
+
+}  // namespace
+
+struct bssn_ctx {
+  bssn_params p;
+  Grid g;
+  Carve c;
+  cudaStream_t stream;
+  char* mem;
+  double* yn;
+  double* acc;
+  double* s1;
+  double* s2;
+  double* ksh;
+  float* m32[3];
+  double* mw[3];
+  float* ksh32;
+  bool shadow_valid;
+  double* part;
+  double* out16;
+  double t;
+  int npunct;
+  double punct[8][4];
+  // launch timing (bssn_profile): event pairs around stage and boundary launches
+  bool prof;
+  std::vector<cudaEvent_t> ev_stage, ev_bc;
+};
+
+namespace {
+cudaError_t prof_mark(bssn_ctx* ctx, std::vector<cudaEvent_t>& v) {
+  cudaEvent_t e;
+  cudaError_t r = cudaEventCreate(&e);
+  if (r != cudaSuccess) return r;
+  v.push_back(e);
+  return cudaEventRecord(e, ctx->stream);
+}
+void prof_clear(bssn_ctx* ctx) {
+  for (auto e : ctx->ev_stage) cudaEventDestroy(e);
+  for (auto e : ctx->ev_bc) cudaEventDestroy(e);
+  ctx->ev_stage.clear();
+  ctx->ev_bc.clear();
+}
+}  // namespace
+
+extern "C" {
+
+const char* bssn_last_error(void) { return g_last_error.c_str(); }
+
+bssn_status bssn_layout_of(const bssn_params* p, bssn_layout* out) {
+  std::string why;
+  if (!out) return fail(BSSN_EINVAL, "out is NULL");
+  if (!validate(p, why)) return fail(BSSN_EINVAL, why);
+  Grid g = make_grid(p);
+  out->stored[0] = g.sx;
+  out->stored[1] = g.sy;
+  out->stored[2] = g.sz;
+  out->ghost = GH;
+  out->pitch = g.pitch;
+  out->plane = g.plane;
+  out->field_stride = g.fstride;
+  out->register_elems = (int64_t)NF * g.fstride;
+  return BSSN_OK;
+}
+
+size_t bssn_required_bytes(const bssn_params* p) {
+  std::string why;
+  if (!validate(p, why)) {
+    g_last_error = why;
+    return 0;
+  }
+  Grid g = make_grid(p);
+  return carve(p, g).total;
+}
+
+bssn_status bssn_alloc(const bssn_params* p, void* d_mem, size_t bytes, void* cuda_stream,
+                       bssn_ctx** out) {
+  std::string why;
+  if (!out) return fail(BSSN_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!validate(p, why)) return fail(BSSN_EINVAL, why);
+  if (!d_mem) return fail(BSSN_EINVAL, "d_mem is NULL");
+  if (((uintptr_t)d_mem) % ALIGN) return fail(BSSN_EINVAL, "d_mem must be 256-byte aligned");
+  Grid g = make_grid(p);
+  Carve c = carve(p, g);
+  if (bytes < c.total)
+    return fail(BSSN_ENOMEM, "memory block too small: need " + std::to_string(c.total) +
+                                 " bytes, got " + std::to_string(bytes));
+  bssn_ctx* ctx = new (std::nothrow) bssn_ctx();
+  if (!ctx) return fail(BSSN_ENOMEM, "host allocation failed");
+  ctx->p = *p;
+  ctx->g = g;
+  ctx->c = c;
+  ctx->stream = (cudaStream_t)cuda_stream;
+  ctx->mem = (char*)d_mem;
+  ctx->yn = (double*)(ctx->mem + c.yn);
+  ctx->acc = (double*)(ctx->mem + c.acc);
+  ctx->s1 = (double*)(ctx->mem + c.s1);
+  ctx->s2 = (double*)(ctx->mem + c.s2);
+  const bool som = p->boundary == BSSN_BC_SOMMERFELD;
+  if (p->precision == BSSN_FP64) {
+    ctx->ksh = som ? (double*)(ctx->mem + c.ksh) : nullptr;
+  } else {
+    for (int q = 0; q < 3; q++) {
+      ctx->m32[q] = (float*)(ctx->mem + c.m32[q]);
+      ctx->mw[q] = (double*)(ctx->mem + c.mw[q]);
+    }
+    ctx->ksh32 = som ? (float*)(ctx->mem + c.ksh) : nullptr;
+  }
+  ctx->shadow_valid = false;
+  ctx->part = (double*)(ctx->mem + c.part);
+  ctx->out16 = (double*)(ctx->mem + c.out16);
+  ctx->t = 0.0;
+  ctx->npunct = 0;
+  ctx->prof = false;
+  *out = ctx;
+  return BSSN_OK;
+}
+
+bssn_status bssn_free(bssn_ctx* ctx) {
+  if (!ctx) return fail(BSSN_EINVAL, "ctx is NULL");
+  cudaError_t e = cudaStreamSynchronize(ctx->stream);
+  prof_clear(ctx);
+  delete ctx;
+  if (e != cudaSuccess) return cuda_fail(e, "bssn_free");
+  return BSSN_OK;
+}
+
+bssn_status bssn_state_ptr(bssn_ctx* ctx, double** d_state) {
+  if (!ctx || !d_state) return fail(BSSN_EINVAL, "NULL argument");
+  *d_state = ctx->yn;
+  return BSSN_OK;
+}
+
+bssn_status bssn_set_initial_data(bssn_ctx* ctx, int32_t kind, const double* p, int32_t np) {
+  if (!ctx) return fail(BSSN_EINVAL, "ctx is NULL");
+  if (np < 0 || (np > 0 && !p)) return fail(BSSN_EINVAL, "bad parameter array");
+  double buf[33] = {0};
+  int npunct = 0;
+  if (kind == BSSN_ID_FLAT) {
+  } else if (kind == BSSN_ID_GAUGE_WAVE) {
+    if (np < 2) return fail(BSSN_EINVAL, "gauge wave needs {A, d}");
+    if (!(p[1] != 0.0) || !(std::fabs(p[0]) < 1.0)) return fail(BSSN_EINVAL, "gauge wave: need |A| < 1, d != 0");
+  } else if (kind == BSSN_ID_BL) {
+    if (np < 1) return fail(BSSN_EINVAL, "BL needs {npunct, m, x, y, z, ...}");
+    npunct = (int)p[0];
+    if (npunct < 1 || npunct > 8 || (double)npunct != p[0] || np < 1 + 4 * npunct)
+      return fail(BSSN_EINVAL, "BL: npunct must be 1..8 with 4 values each");
+  } else if (kind == BSSN_ID_KASNER) {
+    if (np < 1 || !(p[0] > 0.0)) return fail(BSSN_EINVAL, "Kasner needs {t0 > 0}");
+  } else {
+    return fail(BSSN_EINVAL, "unknown initial-data kind");
+  }
+  const int n = np < 33 ? np : 33;
+  for (int q = 0; q < n; q++) buf[q] = p[q];
+  cudaError_t e = launch_initial_data(ctx->g, kind, buf, n, ctx->yn, ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "initial data");
+  ctx->shadow_valid = false;
+  ctx->npunct = npunct;
+  for (int a = 0; a < npunct; a++)
+    for (int q = 0; q < 4; q++) ctx->punct[a][q] = p[1 + 4 * a + q];
+  ctx->t = 0.0;
+  return BSSN_OK;
+}
+
+bssn_status bssn_rhs(bssn_ctx* ctx, const void* d_state, void* d_rhs) {
+  if (!ctx || !d_rhs) return fail(BSSN_EINVAL, "NULL argument");
+  const double* src = d_state ? (const double*)d_state : ctx->yn;
+  double* out = (double*)d_rhs;
+  cudaError_t e;
+  if (ctx->g.periodic) {
+    e = cudaMemsetAsync(out, 0, (size_t)NF * ctx->g.fstride * sizeof(double), ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "bssn_rhs memset");
+  }
+  if (ctx->p.precision == BSSN_FP64) {
+    StageArgs a{};
+    a.src = src;
+    a.rhs = out;
+    a.mode = MODE_RHS;
+    e = launch_stage_fp64(ctx->g, a, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "bssn_rhs interior");
+    if (!ctx->g.periodic) {
+      e = launch_sommerfeld(ctx->g, a, nullptr, ctx->stream);
+      if (e != cudaSuccess) return cuda_fail(e, "bssn_rhs boundary");
+    }
+    return BSSN_OK;
+  }
+  // mixed: float copy of the state (with float64 W) in stage buffer 2
+  e = launch_shadow(ctx->g, src, ctx->m32[2], ctx->mw[2], ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "bssn_rhs shadow");
+  StageArgsMixed a{};
+  a.src = ctx->m32[2];
+  a.srcw = ctx->mw[2];
+  a.rhs = out;
+  a.w_thr = ctx->p.w_fp64_threshold;
+  a.mode = MODE_RHS;
+  e = launch_stage_mixed(ctx->g, a, ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "bssn_rhs interior");
+  if (!ctx->g.periodic) {
+    e = launch_sommerfeld_mixed(ctx->g, a, nullptr, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "bssn_rhs boundary");
+  }
+  return BSSN_OK;
+}
+
+static bssn_status run_stage(bssn_ctx* ctx, const double* src, int mode, double* out0,
+                             double a_dt, double b_dt) {
+  StageArgs a{};
+  a.src = src;
+  a.yn = ctx->yn;
+  a.out0 = out0;
+  a.acc = ctx->acc;
+  a.kshell = ctx->ksh;
+  a.a_dt = a_dt;
+  a.b_dt = b_dt;
+  a.mode = mode;
+  cudaError_t e;
+  if (ctx->prof && (e = prof_mark(ctx, ctx->ev_stage)) != cudaSuccess) return cuda_fail(e, "profile");
+  e = launch_stage_fp64(ctx->g, a, ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "stage");
+  if (ctx->prof && (e = prof_mark(ctx, ctx->ev_stage)) != cudaSuccess) return cuda_fail(e, "profile");
+  if (ctx->prof && (e = prof_mark(ctx, ctx->ev_bc)) != cudaSuccess) return cuda_fail(e, "profile");
+  if (ctx->g.periodic) {
+    e = launch_periodic_fill(ctx->g, mode == MODE_LAST ? ctx->acc : out0, ctx->stream);
+  } else {
+    e = launch_sommerfeld(ctx->g, a, ctx->ksh, ctx->stream);
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "boundary");
+  if (ctx->prof && (e = prof_mark(ctx, ctx->ev_bc)) != cudaSuccess) return cuda_fail(e, "profile");
+  return BSSN_OK;
+}
+
+// mixed stage: src/out are stage-buffer indices into m32/mw
+static bssn_status run_stage_mixed(bssn_ctx* ctx, int src, int mode, int out, double a_dt,
+                                   double b_dt) {
+  StageArgsMixed a{};
+  a.src = ctx->m32[src];
+  a.srcw = ctx->mw[src];
+  a.yn = ctx->yn;
+  a.out0 = ctx->m32[out];
+  a.out0w = ctx->mw[out];
+  a.acc = ctx->acc;
+  a.kshell = ctx->ksh32;
+  a.a_dt = a_dt;
+  a.b_dt = b_dt;
+  a.w_thr = ctx->p.w_fp64_threshold;
+  a.mode = mode;
+  cudaError_t e;
+  if (ctx->prof && (e = prof_mark(ctx, ctx->ev_stage)) != cudaSuccess) return cuda_fail(e, "profile");
+  e = launch_stage_mixed(ctx->g, a, ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "stage");
+  if (ctx->prof && (e = prof_mark(ctx, ctx->ev_stage)) != cudaSuccess) return cuda_fail(e, "profile");
+  if (ctx->prof && (e = prof_mark(ctx, ctx->ev_bc)) != cudaSuccess) return cuda_fail(e, "profile");
+  if (ctx->g.periodic) {
+    e = launch_periodic_fill_mixed(ctx->g, ctx->m32[out], ctx->mw[out], ctx->stream);
+    if (e == cudaSuccess && mode == MODE_LAST) e = launch_periodic_fill(ctx->g, ctx->acc, ctx->stream);
+  } else {
+    e = launch_sommerfeld_mixed(ctx->g, a, ctx->ksh32, ctx->stream);
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "boundary");
+  if (ctx->prof && (e = prof_mark(ctx, ctx->ev_bc)) != cudaSuccess) return cuda_fail(e, "profile");
+  return BSSN_OK;
+}
+
+bssn_status bssn_rk4_step(bssn_ctx* ctx, int32_t nsteps) {
+  if (!ctx) return fail(BSSN_EINVAL, "ctx is NULL");
+  if (nsteps < 0) return fail(BSSN_EINVAL, "nsteps < 0");
+  const double dt = ctx->p.dt;
+  const bool mixed = ctx->p.precision == BSSN_MIXED;
+  for (int s = 0; s < nsteps; s++) {
+    bssn_status st;
+    cudaError_t e;
+    if (ctx->g.periodic && !(mixed && ctx->shadow_valid)) {
+      e = launch_periodic_fill(ctx->g, ctx->yn, ctx->stream);
+      if (e != cudaSuccess) return cuda_fail(e, "periodic fill");
+    }
+    if (!mixed) {
+      if ((st = run_stage(ctx, ctx->yn, MODE_FIRST, ctx->s1, 0.5 * dt, dt / 6.0)) != BSSN_OK) return st;
+      if ((st = run_stage(ctx, ctx->s1, MODE_MID, ctx->s2, 0.5 * dt, dt / 3.0)) != BSSN_OK) return st;
+      if ((st = run_stage(ctx, ctx->s2, MODE_MID, ctx->s1, dt, dt / 3.0)) != BSSN_OK) return st;
+      if ((st = run_stage(ctx, ctx->s1, MODE_LAST, nullptr, 0.0, dt / 6.0)) != BSSN_OK) return st;
+    } else {
+      if (!ctx->shadow_valid) {
+        e = launch_shadow(ctx->g, ctx->yn, ctx->m32[0], ctx->mw[0], ctx->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "shadow");
+        ctx->shadow_valid = true;
+      }
+      if ((st = run_stage_mixed(ctx, 0, MODE_FIRST, 1, 0.5 * dt, dt / 6.0)) != BSSN_OK) return st;
+      if ((st = run_stage_mixed(ctx, 1, MODE_MID, 2, 0.5 * dt, dt / 3.0)) != BSSN_OK) return st;
+      if ((st = run_stage_mixed(ctx, 2, MODE_MID, 1, dt, dt / 3.0)) != BSSN_OK) return st;
+      if ((st = run_stage_mixed(ctx, 1, MODE_LAST, 0, 0.0, dt / 6.0)) != BSSN_OK) return st;
+    }
+    double* tmp = ctx->yn;
+    ctx->yn = ctx->acc;
+    ctx->acc = tmp;
+    ctx->t += dt;
+  }
+  return BSSN_OK;
+}
+
+bssn_status bssn_constraints(bssn_ctx* ctx, double out[16]) {
+  if (!ctx || !out) return fail(BSSN_EINVAL, "NULL argument");
+  cudaError_t e = launch_constraints(ctx->g, ctx->yn, &ctx->punct[0][0], ctx->npunct,
+                                     ctx->p.r_excise, ctx->part, ctx->c.nblocks, ctx->out16,
+                                     ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "constraints");
+  e = cudaMemcpyAsync(out, ctx->out16, 16 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "constraints copy");
+  e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "constraints sync");
+  return BSSN_OK;
+}
+
+bssn_status bssn_get_state(bssn_ctx* ctx, double* host, double* t) {
+  if (!ctx || !host) return fail(BSSN_EINVAL, "NULL argument");
+  const Grid& g = ctx->g;
+  cudaError_t e = cudaMemcpy2DAsync(host, (size_t)g.sx * sizeof(double), ctx->yn,
+                                    (size_t)g.pitch * sizeof(double), (size_t)g.sx * sizeof(double),
+                                    (size_t)NF * g.sz * g.sy, cudaMemcpyDeviceToHost, ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "get_state copy");
+  e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "get_state sync");
+  if (t) *t = ctx->t;
+  return BSSN_OK;
+}
+
+bssn_status bssn_set_state(bssn_ctx* ctx, const double* host, double t) {
+  if (!ctx || !host) return fail(BSSN_EINVAL, "NULL argument");
+  const Grid& g = ctx->g;
+  cudaError_t e = cudaMemcpy2DAsync(ctx->yn, (size_t)g.pitch * sizeof(double), host,
+                                    (size_t)g.sx * sizeof(double), (size_t)g.sx * sizeof(double),
+                                    (size_t)NF * g.sz * g.sy, cudaMemcpyHostToDevice, ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "set_state copy");
+  e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "set_state sync");
+  ctx->t = t;
+  ctx->shadow_valid = false;
+  return BSSN_OK;
+}
+
+bssn_status bssn_profile(bssn_ctx* ctx, int32_t enable, double out[4]) {
+  if (!ctx) return fail(BSSN_EINVAL, "ctx is NULL");
+  if (enable) {
+    prof_clear(ctx);
+    ctx->prof = true;
+    return BSSN_OK;
+  }
+  ctx->prof = false;
+  if (!out) return fail(BSSN_EINVAL, "out is NULL");
+  cudaError_t e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "profile sync");
+  std::vector<cudaEvent_t>* lists[2] = {&ctx->ev_stage, &ctx->ev_bc};
+  for (int q = 0; q < 2; q++) {
+    double ms = 0.0;
+    const auto& v = *lists[q];
+    for (size_t i = 0; i + 1 < v.size(); i += 2) {
+      float x = 0.f;
+      e = cudaEventElapsedTime(&x, v[i], v[i + 1]);
+      if (e != cudaSuccess) return cuda_fail(e, "profile elapsed");
+      ms += x;
+    }
+    out[2 * q] = ms;
+    out[2 * q + 1] = (double)(v.size() / 2);
+  }
+  prof_clear(ctx);
+  return BSSN_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,297 @@
+// Hamiltonian and momentum constraints with deterministic norm reductions
+// (arXiv:1111.3344, Sec. "Other analysis modules"): H = R - K^i_j K^j_i + K^2,
+// M_i = nabla_j K_i^j - nabla_i K in vacuum, from the ADM fields
+// gamma_ij = e^{4 phi} gt_ij and K_ij = e^{4 phi}(At_ij + gt_ij K / 3), which
+// are formed pointwise at every stencil point on the fly (no scratch grids),
+// then differenced with the same 4th-order stencils as the evolution.
+//   R_ij = 1/2 gamma^kl (d_k d_j g_il + d_i d_l g_kj - d_k d_l g_ij - d_i d_j g_kl)
+//          + gamma^kl (Gamma^m_il Gamma_mkj - Gamma^m_ij Gamma_mkl)
+//   M_i  = gamma^jk (d_k K_ij - d_i K_jk) - Gamma^l K_il + Gamma^l_ij K_l^j
+// (the Christoffel terms of gamma^jk (nabla_k K_ij - nabla_i K_jk) after the
+// symmetric pair cancels).  Float64 in every precision mode.
+//
+// Reduction: one thread per interior point, a fixed-shape shared-memory tree
+// per block into per-block partials (8 sums of squares, 8 maxima, 2 counts),
+// then one block folds the partials in a fixed order: the result does not
+// depend on scheduling.
+#include "bssn_internal.cuh"
+
+namespace bssn {
+
+// max that lets a NaN through (so a blown-up state shows in the Linf norms)
+__device__ __forceinline__ double nanmax(double a, double b) { return (b > a || b != b) ? b : a; }
+
+constexpr int CB = 256;   // threads per block
+constexpr int NPART = 18; // partial values per block
+
+struct Punct {
+  double p[8][4];
+  int n;
+  double r_ex;
+};
+
+__device__ __forceinline__ void adm_at(const Grid& g, const double* __restrict__ y, long long id,
+                                       double gam[6], double K[6], bool needK) {
+  const long long fs = g.fstride;
+  const double chi = __ldg(y + F_CHI * fs + id);
+  const double e4 = g.use_w ? 1.0 / (chi * chi) : exp(4.0 * chi);
+  const double tr3 = needK ? __ldg(y + F_TRK * fs + id) * (1.0 / 3.0) : 0.0;
+#pragma unroll
+  for (int m = 0; m < 6; m++) {
+    const double gt = __ldg(y + (F_GT + m) * fs + id);
+    gam[m] = e4 * gt;
+    if (needK) K[m] = e4 * (__ldg(y + (F_AT + m) * fs + id) + gt * tr3);
+  }
+}
+
+__device__ void constraints_point(const Grid& g, const double* __restrict__ y, long long id,
+                                  double out[4]) {
+  const long long sd[3] = {1, g.pitch, g.plane};
+  const double i12h = 1.0 / (12.0 * g.h);
+  const double i12h2 = 1.0 / (12.0 * g.h * g.h);
+  const double i144h2 = 1.0 / (144.0 * g.h * g.h);
+  double g0[6], k0[6];
+  adm_at(g, y, id, g0, k0, true);
+  double dg[3][6], dk[3][6], ddg[6][6];
+#pragma unroll
+  for (int d = 0; d < 3; d++) {
+    double gp1[6], gm1[6], gp2[6], gm2[6], kp1[6], km1[6], kp2[6], km2[6];
+    adm_at(g, y, id + sd[d], gp1, kp1, true);
+    adm_at(g, y, id - sd[d], gm1, km1, true);
+    adm_at(g, y, id + 2 * sd[d], gp2, kp2, true);
+    adm_at(g, y, id - 2 * sd[d], gm2, km2, true);
+#pragma unroll
+    for (int m = 0; m < 6; m++) {
+      dg[d][m] = fma(8.0, gp1[m] - gm1[m], -(gp2[m] - gm2[m])) * i12h;
+      dk[d][m] = fma(8.0, kp1[m] - km1[m], -(kp2[m] - km2[m])) * i12h;
+      ddg[sym(d, d)][m] = fma(-30.0, g0[m], fma(16.0, gp1[m] + gm1[m], -(gp2[m] + gm2[m]))) * i12h2;
+    }
+  }
+  const double c[4] = {1.0, -8.0, 8.0, -1.0};
+  const int off[4] = {-2, -1, 1, 2};
+#pragma unroll
+  for (int a = 0; a < 3; a++)
+#pragma unroll
+    for (int b = a + 1; b < 3; b++) {
+      double acc[6] = {0, 0, 0, 0, 0, 0};
+      double dummy[6];
+#pragma unroll
+      for (int p = 0; p < 4; p++)
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+          double gv[6];
+          adm_at(g, y, id + off[p] * sd[a] + off[q] * sd[b], gv, dummy, false);
+          const double w = c[p] * c[q];
+#pragma unroll
+          for (int m = 0; m < 6; m++) acc[m] = fma(w, gv[m], acc[m]);
+        }
+#pragma unroll
+      for (int m = 0; m < 6; m++) ddg[sym(a, b)][m] = acc[m] * i144h2;
+    }
+
+  // inverse metric
+  double gu[6];
+  {
+    const double c00 = g0[3] * g0[5] - g0[4] * g0[4];
+    const double c01 = g0[2] * g0[4] - g0[1] * g0[5];
+    const double c02 = g0[1] * g0[4] - g0[2] * g0[3];
+    const double idet = 1.0 / (g0[0] * c00 + g0[1] * c01 + g0[2] * c02);
+    gu[0] = c00 * idet;
+    gu[1] = c01 * idet;
+    gu[2] = c02 * idet;
+    gu[3] = (g0[0] * g0[5] - g0[2] * g0[2]) * idet;
+    gu[4] = (g0[1] * g0[2] - g0[0] * g0[4]) * idet;
+    gu[5] = (g0[0] * g0[3] - g0[1] * g0[1]) * idet;
+  }
+  double G1[3][6], G2[3][6];
+#pragma unroll
+  for (int k = 0; k < 3; k++)
+#pragma unroll
+    for (int a = 0; a < 3; a++)
+#pragma unroll
+      for (int b = a; b < 3; b++)
+        G1[k][sym(a, b)] = 0.5 * (dg[a][sym(k, b)] + dg[b][sym(k, a)] - dg[k][sym(a, b)]);
+#pragma unroll
+  for (int k = 0; k < 3; k++)
+#pragma unroll
+    for (int m = 0; m < 6; m++)
+      G2[k][m] = gu[sym(k, 0)] * G1[0][m] + gu[sym(k, 1)] * G1[1][m] + gu[sym(k, 2)] * G1[2][m];
+
+  double R = 0.0;
+#pragma unroll
+  for (int i = 0; i < 3; i++)
+#pragma unroll
+    for (int j = i; j < 3; j++) {
+      double s = 0.0;
+#pragma unroll
+      for (int k = 0; k < 3; k++)
+#pragma unroll
+        for (int l = 0; l < 3; l++) {
+          const double gkl = gu[sym(k, l)];
+          const double dd = ddg[sym(k, j)][sym(i, l)] + ddg[sym(i, l)][sym(k, j)] -
+                            ddg[sym(k, l)][sym(i, j)] - ddg[sym(i, j)][sym(k, l)];
+          double q = 0.5 * dd;
+#pragma unroll
+          for (int m = 0; m < 3; m++)
+            q += G2[m][sym(i, l)] * G1[m][sym(k, j)] - G2[m][sym(i, j)] * G1[m][sym(k, l)];
+          s = fma(gkl, q, s);
+        }
+      R = fma(i == j ? gu[sym(i, j)] : 2.0 * gu[sym(i, j)], s, R);
+    }
+  double Kud[3][3];
+#pragma unroll
+  for (int a = 0; a < 3; a++)
+#pragma unroll
+    for (int b = 0; b < 3; b++)
+      Kud[a][b] = gu[sym(a, 0)] * k0[sym(0, b)] + gu[sym(a, 1)] * k0[sym(1, b)] +
+                  gu[sym(a, 2)] * k0[sym(2, b)];
+  const double trK = Kud[0][0] + Kud[1][1] + Kud[2][2];
+  double KK = 0.0;
+#pragma unroll
+  for (int a = 0; a < 3; a++)
+#pragma unroll
+    for (int b = 0; b < 3; b++) KK = fma(Kud[a][b], Kud[b][a], KK);
+  out[0] = R - KK + trK * trK;
+
+  // Gamma^l = gamma^jk Gamma^l_jk
+  double Gc[3];
+#pragma unroll
+  for (int l = 0; l < 3; l++) {
+    double s = 0.0;
+#pragma unroll
+    for (int j = 0; j < 3; j++)
+#pragma unroll
+      for (int k = 0; k < 3; k++) s = fma(gu[sym(j, k)], G2[l][sym(j, k)], s);
+    Gc[l] = s;
+  }
+#pragma unroll
+  for (int i = 0; i < 3; i++) {
+    double s = 0.0;
+#pragma unroll
+    for (int j = 0; j < 3; j++)
+#pragma unroll
+      for (int k = 0; k < 3; k++) s = fma(gu[sym(j, k)], dk[k][sym(i, j)] - dk[i][sym(j, k)], s);
+#pragma unroll
+    for (int l = 0; l < 3; l++) {
+      s = fma(-Gc[l], k0[sym(i, l)], s);
+      // Gamma^l_ij K_l^j with K_l^j = Kud[j][l] (K symmetric)
+#pragma unroll
+      for (int j = 0; j < 3; j++) s = fma(G2[l][sym(i, j)], Kud[j][l], s);
+    }
+    out[1 + i] = s;
+  }
+}
+
+__global__ void __launch_bounds__(CB) constraints_kernel(Grid g, const double* __restrict__ y,
+                                                         Punct pu, double* __restrict__ partials) {
+  __shared__ double sh[NPART][CB];
+  const long long npts = (long long)g.n0 * g.n1 * g.n2;
+  const long long tid = (long long)blockIdx.x * CB + threadIdx.x;
+  double v[NPART];
+#pragma unroll
+  for (int q = 0; q < NPART; q++) v[q] = 0.0;
+  if (tid < npts) {
+    const int ii = (int)(tid % g.n0);
+    const int jj = (int)((tid / g.n0) % g.n1);
+    const int kk = (int)(tid / ((long long)g.n0 * g.n1));
+    const int i = ii + GH, j = jj + GH, k = kk + GH;
+    double c4[4];
+    constraints_point(g, y, lin(g, i, j, k), c4);
+    const double x = g.xmin0 + (i - GH + 0.5) * g.h;
+    const double yy = g.xmin1 + (j - GH + 0.5) * g.h;
+    const double z = g.xmin2 + (k - GH + 0.5) * g.h;
+    bool outside = true;
+    for (int a = 0; a < pu.n; a++) {
+      const double dx = x - pu.p[a][1], dy = yy - pu.p[a][2], dz = z - pu.p[a][3];
+      if (sqrt(dx * dx + dy * dy + dz * dz) <= pu.r_ex) outside = false;
+    }
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      const double sq = c4[q] * c4[q], ab = fabs(c4[q]);
+      v[q] = sq;
+      v[4 + q] = ab;
+      v[8 + q] = outside ? sq : 0.0;
+      v[12 + q] = outside ? ab : 0.0;
+    }
+    v[16] = 1.0;
+    v[17] = outside ? 1.0 : 0.0;
+  }
+#pragma unroll
+  for (int q = 0; q < NPART; q++) sh[q][threadIdx.x] = v[q];
+  __syncthreads();
+  for (int w = CB / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) {
+#pragma unroll
+      for (int q = 0; q < NPART; q++) {
+        const double o = sh[q][threadIdx.x + w];
+        const bool ismax = (q >= 4 && q < 8) || (q >= 12 && q < 16);
+        sh[q][threadIdx.x] = ismax ? nanmax(sh[q][threadIdx.x], o) : sh[q][threadIdx.x] + o;
+      }
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x < NPART) partials[(long long)blockIdx.x * NPART + threadIdx.x] = sh[threadIdx.x][0];
+}
+
+__global__ void __launch_bounds__(CB) constraints_finalize(const double* __restrict__ partials,
+                                                           int nblocks, double* __restrict__ out) {
+  __shared__ double sh[NPART][CB];
+  double v[NPART];
+#pragma unroll
+  for (int q = 0; q < NPART; q++) v[q] = 0.0;
+  for (int b = threadIdx.x; b < nblocks; b += CB) {
+#pragma unroll
+    for (int q = 0; q < NPART; q++) {
+      const double o = partials[(long long)b * NPART + q];
+      const bool ismax = (q >= 4 && q < 8) || (q >= 12 && q < 16);
+      v[q] = ismax ? nanmax(v[q], o) : v[q] + o;
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < NPART; q++) sh[q][threadIdx.x] = v[q];
+  __syncthreads();
+  for (int w = CB / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) {
+#pragma unroll
+      for (int q = 0; q < NPART; q++) {
+        const double o = sh[q][threadIdx.x + w];
+        const bool ismax = (q >= 4 && q < 8) || (q >= 12 && q < 16);
+        sh[q][threadIdx.x] = ismax ? nanmax(sh[q][threadIdx.x], o) : sh[q][threadIdx.x] + o;
+      }
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x < 16) {
+    const int q = threadIdx.x;
+    const int set = q / 8, within = q % 8;
+    const double cnt = sh[16 + set][0];
+    double r;
+    if (within < 4)
+      r = cnt > 0.0 ? sqrt(sh[set * 8 + within][0] / cnt) : 0.0;
+    else
+      r = sh[set * 8 + within][0];
+    out[q] = r;
+  }
+}
+
+int constraints_blocks(const Grid& g) {
+  const long long npts = (long long)g.n0 * g.n1 * g.n2;
+  return (int)((npts + CB - 1) / CB);
+}
+
+cudaError_t launch_constraints(const Grid& g, const double* y, const double* punct4, int npunct,
+                               double r_excise, double* partials, int nblocks, double* dout16,
+                               cudaStream_t s) {
+  Punct pu{};
+  pu.n = npunct < 8 ? npunct : 8;
+  for (int a = 0; a < pu.n; a++)
+    for (int q = 0; q < 4; q++) pu.p[a][q] = punct4[4 * a + q];
+  pu.r_ex = r_excise;
+  constraints_kernel<<<nblocks, CB, 0, s>>>(g, y, pu, partials);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  constraints_finalize<<<1, CB, 0, s>>>(partials, nblocks, dout16);
+  return cudaGetLastError();
+}
+
+}  // namespace bssn

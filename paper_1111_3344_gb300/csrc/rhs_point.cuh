@@ -1,0 +1,463 @@
+// Pointwise BSSN right-hand side on the device (arXiv:1111.3344, Sec.
+// "Spacetime Curvature Evolution": evolution equations for alpha, K, beta, B,
+// phi, gt, At, Gt with m = 1 in vacuum; Ricci pieces Rt_ij and Rphi_ij; 1+log
+// / harmonic / geodesic slicing; Gamma-driver shift with q(r)).
+//
+// Formulation (same discrete operator as the statement in the paper; the
+// arrangement is chosen to cut float64 instructions, the binding resource on
+// GB300):
+//  - symmetric tensors held as 6 components; gt^{ij} by cofactors over det;
+//  - second derivatives are consumed as they are produced (the
+//    gt^{kl} d_k d_l contractions are accumulated pair by pair) to keep the
+//    live set small;
+//  - d_l gt^{lk} = -gt^{la} gt^{kb} d_l gt_ab from the metric stencils, in Rt
+//    and the Gt equation; only gt_k(i d_j) Gt^k uses the evolved Gt;
+//  - W variant: d phi = -d W / (2W), d d phi = -dd W / (2W) + 2 dphi dphi,
+//    e^{-4 phi} = W^2 (W floored where it divides);
+//  - advection beta^j d_j X with the lopsided stencil on the upwind side,
+//    written as |beta^j| times the mirrored stencil; KO as
+//    +eps/(64h) sum_d delta_d^6 X.
+#pragma once
+#include "bssn_internal.cuh"
+
+namespace bssn {
+
+template <typename T>
+__device__ __forceinline__ T fmaT(T a, T b, T c);
+template <>
+__device__ __forceinline__ double fmaT<double>(double a, double b, double c) { return fma(a, b, c); }
+template <>
+__device__ __forceinline__ float fmaT<float>(float a, float b, float c) { return fmaf(a, b, c); }
+
+template <typename T, typename S>
+__device__ __forceinline__ T ldg(const S* p) {
+  return T(__ldg(p));
+}
+
+// 8 (f1 - f-1) - (f2 - f-2): 12 h times the 4th-order first derivative.
+template <typename T, typename S>
+__device__ __forceinline__ T d1u(const S* p, long long s) {
+  T a = ldg<T>(p + s) - ldg<T>(p - s);
+  T b = ldg<T>(p + 2 * s) - ldg<T>(p - 2 * s);
+  return fmaT<T>(T(8), a, -b);
+}
+// 16 (f1 + f-1) - (f2 + f-2) - 30 f0: 12 h^2 times the 4th-order second derivative.
+template <typename T, typename S>
+__device__ __forceinline__ T d2u(const S* p, long long s, T f0) {
+  T a = ldg<T>(p + s) + ldg<T>(p - s);
+  T b = ldg<T>(p + 2 * s) + ldg<T>(p - 2 * s);
+  return fmaT<T>(T(-30), f0, fmaT<T>(T(16), a, -b));
+}
+// D1_a D1_b (a != b): 144 h^2 times the mixed derivative.
+template <typename T, typename S>
+__device__ __forceinline__ T dmu(const S* p, long long sa, long long sb) {
+  T a = d1u<T>(p + sa, sb) - d1u<T>(p - sa, sb);
+  T b = d1u<T>(p + 2 * sa, sb) - d1u<T>(p - 2 * sa, sb);
+  return fmaT<T>(T(8), a, -b);
+}
+
+struct Adv {
+  long long s[3];  // signed stride toward the upwind side per axis
+};
+
+// Upwinded advection (times 12 h) plus KO sixth differences for one field.
+//   adv = sum_j |beta^j| (-3 f(-s) + 18 f(s) - 6 f(2s) + f(3s)) - 10 f0 sum_j |beta^j|
+//   ko  = sum_d (f-3 + f3) - 6 (f-2 + f2) + 15 (f-1 + f1) - 20 f0
+template <typename T, typename S>
+__device__ __forceinline__ void adv_ko(const S* p, const long long st[3], const Adv& up,
+                                       const T ab[3], T absum, T f0, T& adv, T& ko) {
+  T a = T(0);
+#pragma unroll
+  for (int d = 0; d < 3; d++) {
+    long long s = up.s[d];
+    T u = fmaT<T>(T(-3), ldg<T>(p - s),
+                  fmaT<T>(T(18), ldg<T>(p + s), fmaT<T>(T(-6), ldg<T>(p + 2 * s), ldg<T>(p + 3 * s))));
+    a = fmaT<T>(ab[d], u, a);
+  }
+  adv = fmaT<T>(T(-10) * absum, f0, a);
+  T s1 = T(0), s2 = T(0), s3 = T(0);
+#pragma unroll
+  for (int d = 0; d < 3; d++) {
+    long long s = st[d];
+    s1 += ldg<T>(p + s) + ldg<T>(p - s);
+    s2 += ldg<T>(p + 2 * s) + ldg<T>(p - 2 * s);
+    s3 += ldg<T>(p + 3 * s) + ldg<T>(p - 3 * s);
+  }
+  ko = fmaT<T>(T(-60), f0, fmaT<T>(T(15), s1, fmaT<T>(T(-6), s2, s3)));
+}
+
+// Right-hand side of all 24 fields at interior point (i, j, k) with linear
+// index id, reading the state register st (field stride g.fstride).
+template <typename T, typename S>
+__device__ __forceinline__ void rhs_point(const Grid& g, const S* __restrict__ st, long long id,
+                                          int i, int j, int k, T out[NF]) {
+  const long long fs = g.fstride;
+  const long long sd[3] = {1, g.pitch, g.plane};
+  const T hinv = T(1.0 / g.h);
+  const T i12h = T(1.0 / (12.0 * g.h));
+  const T i12h2 = T(1.0 / (12.0 * g.h * g.h));
+  const T i144h2 = T(1.0 / (144.0 * g.h * g.h));
+  (void)hinv;
+#define PF(f) (st + (long long)(f) * fs + id)
+
+  // ---- point values
+  T chi = ldg<T>(PF(F_CHI));
+  T gt[6], At[6];
+#pragma unroll
+  for (int m = 0; m < 6; m++) {
+    gt[m] = ldg<T>(PF(F_GT + m));
+    At[m] = ldg<T>(PF(F_AT + m));
+  }
+  T trK = ldg<T>(PF(F_TRK));
+  T alp = ldg<T>(PF(F_ALP));
+  T beta[3], Bv[3];
+#pragma unroll
+  for (int a = 0; a < 3; a++) {
+    beta[a] = ldg<T>(PF(F_BETA + a));
+    Bv[a] = ldg<T>(PF(F_B + a));
+  }
+
+  // ---- inverse conformal metric (cofactors / det)
+  T gu[6];
+  {
+    T c00 = gt[3] * gt[5] - gt[4] * gt[4];
+    T c01 = gt[2] * gt[4] - gt[1] * gt[5];
+    T c02 = gt[1] * gt[4] - gt[2] * gt[3];
+    T det = gt[0] * c00 + gt[1] * c01 + gt[2] * c02;
+    T idet = T(1) / det;
+    gu[0] = c00 * idet;
+    gu[1] = c01 * idet;
+    gu[2] = c02 * idet;
+    gu[3] = (gt[0] * gt[5] - gt[2] * gt[2]) * idet;
+    gu[4] = (gt[1] * gt[2] - gt[0] * gt[4]) * idet;
+    gu[5] = (gt[0] * gt[3] - gt[1] * gt[1]) * idet;
+  }
+
+  // ---- first derivatives
+  T dgt[3][6], dchi[3], dalp[3], dK[3], db[3][3], dG[3][3];
+#pragma unroll
+  for (int d = 0; d < 3; d++) {
+#pragma unroll
+    for (int m = 0; m < 6; m++) dgt[d][m] = d1u<T>(PF(F_GT + m), sd[d]) * i12h;
+    dchi[d] = d1u<T>(PF(F_CHI), sd[d]) * i12h;
+    dalp[d] = d1u<T>(PF(F_ALP), sd[d]) * i12h;
+    dK[d] = d1u<T>(PF(F_TRK), sd[d]) * i12h;
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+      db[d][a] = d1u<T>(PF(F_BETA + a), sd[d]) * i12h;
+      dG[d][a] = d1u<T>(PF(F_GAM + a), sd[d]) * i12h;
+    }
+  }
+
+  // ---- second derivatives, consumed pair by pair
+  T Rdd[6];      // -1/2 gt^{kl} d_k d_l gt_ij
+  T lapb[3];     // gt^{kl} d_k d_l beta^i
+  T gdiv[3];     // d_j d_k beta^k
+  T ddchi[6], ddalp[6];
+#pragma unroll
+  for (int m = 0; m < 6; m++) Rdd[m] = T(0);
+#pragma unroll
+  for (int a = 0; a < 3; a++) lapb[a] = gdiv[a] = T(0);
+  {
+#pragma unroll
+    for (int pa = 0; pa < 3; pa++) {
+#pragma unroll
+      for (int pb = pa; pb < 3; pb++) {
+        const int pq = sym(pa, pb);
+        const T w = (pa == pb) ? T(-0.5) * gu[pq] : -gu[pq];  // -1/2 gt^{kl}, both orders
+        T dd[6];
+        if (pa == pb) {
+#pragma unroll
+          for (int m = 0; m < 6; m++) dd[m] = d2u<T>(PF(F_GT + m), sd[pa], gt[m]) * i12h2;
+          ddchi[pq] = d2u<T>(PF(F_CHI), sd[pa], chi) * i12h2;
+          ddalp[pq] = d2u<T>(PF(F_ALP), sd[pa], alp) * i12h2;
+        } else {
+#pragma unroll
+          for (int m = 0; m < 6; m++) dd[m] = dmu<T>(PF(F_GT + m), sd[pa], sd[pb]) * i144h2;
+          ddchi[pq] = dmu<T>(PF(F_CHI), sd[pa], sd[pb]) * i144h2;
+          ddalp[pq] = dmu<T>(PF(F_ALP), sd[pa], sd[pb]) * i144h2;
+        }
+#pragma unroll
+        for (int m = 0; m < 6; m++) Rdd[m] = fmaT<T>(w, dd[m], Rdd[m]);
+        // shift second derivatives enter the Gt equation even when the shift
+        // itself is frozen
+        const T wb = (pa == pb) ? gu[pq] : T(2) * gu[pq];
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+          T v = (pa == pb) ? d2u<T>(PF(F_BETA + a), sd[pa], beta[a]) * i12h2
+                           : dmu<T>(PF(F_BETA + a), sd[pa], sd[pb]) * i144h2;
+          lapb[a] = fmaT<T>(wb, v, lapb[a]);
+          // d_pa d_pb beta^a contributes to gdiv[pa] when a == pb, gdiv[pb] when a == pa
+          if (a == pb) gdiv[pa] += v;
+          if (pa != pb && a == pa) gdiv[pb] += v;
+        }
+      }
+    }
+  }
+
+  // ---- conformal factor
+  T em4, dphi[3], ddphi[6];
+  if (g.use_w) {
+    T Wd = chi > T(g.w_floor) ? chi : T(g.w_floor);
+    T ih = T(0.5) / Wd;
+    em4 = chi * chi;
+#pragma unroll
+    for (int a = 0; a < 3; a++) dphi[a] = -dchi[a] * ih;
+#pragma unroll
+    for (int a = 0; a < 3; a++)
+#pragma unroll
+      for (int b = a; b < 3; b++)
+        ddphi[sym(a, b)] = fmaT<T>(T(2) * dphi[a], dphi[b], -ddchi[sym(a, b)] * ih);
+  } else {
+    em4 = exp(T(-4) * chi);
+#pragma unroll
+    for (int a = 0; a < 3; a++) dphi[a] = dchi[a];
+#pragma unroll
+    for (int m = 0; m < 6; m++) ddphi[m] = ddchi[m];
+  }
+
+  // ---- Christoffel symbols: first kind G1[k][ij] = (d_i g_kj + d_j g_ki - d_k g_ij)/2
+  T G1[3][6], G2[3][6];
+#pragma unroll
+  for (int kk = 0; kk < 3; kk++)
+#pragma unroll
+    for (int a = 0; a < 3; a++)
+#pragma unroll
+      for (int b = a; b < 3; b++)
+        G1[kk][sym(a, b)] = T(0.5) * (dgt[a][sym(kk, b)] + dgt[b][sym(kk, a)] - dgt[kk][sym(a, b)]);
+#pragma unroll
+  for (int kk = 0; kk < 3; kk++)
+#pragma unroll
+    for (int m = 0; m < 6; m++)
+      G2[kk][m] = gu[sym(kk, 0)] * G1[0][m] + gu[sym(kk, 1)] * G1[1][m] + gu[sym(kk, 2)] * G1[2][m];
+
+  // d_l gt^{lk} = -gt^{kb} (gt^{la} d_l gt_ab)
+  T dgu[3];
+  {
+    T Tb[3];
+#pragma unroll
+    for (int b = 0; b < 3; b++) {
+      T s = T(0);
+#pragma unroll
+      for (int l = 0; l < 3; l++)
+#pragma unroll
+        for (int a = 0; a < 3; a++) s = fmaT<T>(gu[sym(l, a)], dgt[l][sym(a, b)], s);
+      Tb[b] = s;
+    }
+#pragma unroll
+    for (int kk = 0; kk < 3; kk++)
+      dgu[kk] = -(gu[sym(kk, 0)] * Tb[0] + gu[sym(kk, 1)] * Tb[1] + gu[sym(kk, 2)] * Tb[2]);
+  }
+
+  // ---- Rt_ij
+  T Rt[6];
+  {
+    // G1u[j][k][l] = gt^{ls} Gt_jks (first kind, last index raised)
+    T G1u[3][3][3];
+#pragma unroll
+    for (int jj = 0; jj < 3; jj++)
+#pragma unroll
+      for (int kk = 0; kk < 3; kk++)
+#pragma unroll
+        for (int l = 0; l < 3; l++)
+          G1u[jj][kk][l] = gu[sym(l, 0)] * G1[jj][sym(kk, 0)] + gu[sym(l, 1)] * G1[jj][sym(kk, 1)] +
+                           gu[sym(l, 2)] * G1[jj][sym(kk, 2)];
+#pragma unroll
+    for (int a = 0; a < 3; a++)
+#pragma unroll
+      for (int b = a; b < 3; b++) {
+        const int ab = sym(a, b);
+        T s = Rdd[ab];
+        T t = T(0);
+#pragma unroll
+        for (int kk = 0; kk < 3; kk++) {
+          t = fmaT<T>(gt[sym(kk, a)], dG[b][kk], t);
+          t = fmaT<T>(gt[sym(kk, b)], dG[a][kk], t);
+          t = fmaT<T>(-(G1[a][sym(b, kk)] + G1[b][sym(a, kk)]), dgu[kk], t);
+        }
+        s = fmaT<T>(T(0.5), t, s);
+#pragma unroll
+        for (int kk = 0; kk < 3; kk++)
+#pragma unroll
+          for (int l = 0; l < 3; l++) {
+            s = fmaT<T>(G2[kk][sym(l, a)], G1u[b][kk][l], s);
+            s = fmaT<T>(G2[kk][sym(l, b)], G1u[a][kk][l], s);
+            s = fmaT<T>(G2[kk][sym(a, l)], G1u[kk][b][l], s);
+          }
+        Rt[ab] = s;
+      }
+  }
+
+  // ---- Rphi_ij, Dt Dt alpha
+  T X[6];
+  T lap_alp, dphi_dalp;
+  {
+    T DDphi[6], DDalp[6];
+#pragma unroll
+    for (int m = 0; m < 6; m++) {
+      DDphi[m] = ddphi[m] - (G2[0][m] * dphi[0] + G2[1][m] * dphi[1] + G2[2][m] * dphi[2]);
+      DDalp[m] = ddalp[m] - (G2[0][m] * dalp[0] + G2[1][m] * dalp[1] + G2[2][m] * dalp[2]);
+    }
+    T lap_phi = T(0), grad2 = T(0);
+    lap_alp = T(0);
+    dphi_dalp = T(0);
+#pragma unroll
+    for (int a = 0; a < 3; a++)
+#pragma unroll
+      for (int b = 0; b < 3; b++) {
+        const T gab = gu[sym(a, b)];
+        lap_phi = fmaT<T>(gab, DDphi[sym(a, b)], lap_phi);
+        lap_alp = fmaT<T>(gab, DDalp[sym(a, b)], lap_alp);
+        grad2 = fmaT<T>(gab, dphi[a] * dphi[b], grad2);
+        dphi_dalp = fmaT<T>(gab, dphi[a] * dalp[b], dphi_dalp);
+      }
+#pragma unroll
+    for (int a = 0; a < 3; a++)
+#pragma unroll
+      for (int b = a; b < 3; b++) {
+        const int ab = sym(a, b);
+        T rphi = T(-2) * DDphi[ab] - T(2) * gt[ab] * lap_phi + T(4) * dphi[a] * dphi[b] -
+                 T(4) * gt[ab] * grad2;
+        X[ab] = alp * (Rt[ab] + rphi) - DDalp[ab] + T(2) * (dphi[a] * dalp[b] + dphi[b] * dalp[a]);
+      }
+  }
+
+  // ---- At with raised indices
+  T Aud[3][3], Auu[6];
+#pragma unroll
+  for (int a = 0; a < 3; a++)
+#pragma unroll
+    for (int b = 0; b < 3; b++)
+      Aud[a][b] = gu[sym(a, 0)] * At[sym(0, b)] + gu[sym(a, 1)] * At[sym(1, b)] +
+                  gu[sym(a, 2)] * At[sym(2, b)];
+#pragma unroll
+  for (int a = 0; a < 3; a++)
+#pragma unroll
+    for (int b = a; b < 3; b++)
+      Auu[sym(a, b)] = Aud[a][0] * gu[sym(0, b)] + Aud[a][1] * gu[sym(1, b)] + Aud[a][2] * gu[sym(2, b)];
+  T AA = T(0);
+#pragma unroll
+  for (int a = 0; a < 3; a++)
+#pragma unroll
+    for (int b = 0; b < 3; b++) AA = fmaT<T>(Auu[sym(a, b)], At[sym(a, b)], AA);
+  const T divb = db[0][0] + db[1][1] + db[2][2];
+
+  // ---- assemble
+  if (g.use_w)
+    out[F_CHI] = (chi * T(1.0 / 3.0)) * (alp * trK - divb);
+  else
+    out[F_CHI] = T(-1.0 / 6.0) * alp * trK + divb * T(1.0 / 6.0);
+
+  {
+    T trX = T(0);
+#pragma unroll
+    for (int a = 0; a < 3; a++)
+#pragma unroll
+      for (int b = 0; b < 3; b++) trX = fmaT<T>(gu[sym(a, b)], X[sym(a, b)], trX);
+    const T trX3 = trX * T(1.0 / 3.0);
+    const T divb23 = T(2.0 / 3.0) * divb;
+#pragma unroll
+    for (int a = 0; a < 3; a++)
+#pragma unroll
+      for (int b = a; b < 3; b++) {
+        const int ab = sym(a, b);
+        T sg = T(-2) * alp * At[ab] - gt[ab] * divb23;
+        T sa = em4 * (X[ab] - gt[ab] * trX3) + alp * trK * At[ab] - At[ab] * divb23;
+#pragma unroll
+        for (int kk = 0; kk < 3; kk++) {
+          sg = fmaT<T>(gt[sym(kk, a)], db[b][kk], sg);
+          sg = fmaT<T>(gt[sym(kk, b)], db[a][kk], sg);
+          sa = fmaT<T>(T(-2) * alp * At[sym(a, kk)], Aud[kk][b], sa);
+          sa = fmaT<T>(At[sym(kk, a)], db[b][kk], sa);
+          sa = fmaT<T>(At[sym(kk, b)], db[a][kk], sa);
+        }
+        out[F_GT + ab] = sg;
+        out[F_AT + ab] = sa;
+      }
+  }
+
+  out[F_TRK] = -em4 * (lap_alp + T(2) * dphi_dalp) + alp * (AA + trK * trK * T(1.0 / 3.0));
+
+  T gam_rhs[3];
+#pragma unroll
+  for (int a = 0; a < 3; a++) {
+    T s = lapb[a];
+    s = fmaT<T>(T(1.0 / 3.0),
+                gu[sym(a, 0)] * gdiv[0] + gu[sym(a, 1)] * gdiv[1] + gu[sym(a, 2)] * gdiv[2], s);
+    s = fmaT<T>(dgu[0], db[0][a], s);
+    s = fmaT<T>(dgu[1], db[1][a], s);
+    s = fmaT<T>(dgu[2], db[2][a], s);
+    s = fmaT<T>(T(-2.0 / 3.0) * dgu[a], divb, s);
+    T br = T(0);
+#pragma unroll
+    for (int jj = 0; jj < 3; jj++) {
+      s = fmaT<T>(T(-2) * Auu[sym(a, jj)], dalp[jj], s);
+      br = fmaT<T>(T(-2.0 / 3.0) * gu[sym(a, jj)], dK[jj], br);
+      br = fmaT<T>(T(6) * Auu[sym(a, jj)], dphi[jj], br);
+    }
+#pragma unroll
+    for (int kk = 0; kk < 3; kk++)
+#pragma unroll
+      for (int l = 0; l < 3; l++) br = fmaT<T>(G2[a][sym(kk, l)], Auu[sym(kk, l)], br);
+    s = fmaT<T>(T(2) * alp, br, s);
+    gam_rhs[a] = s;
+    out[F_GAM + a] = s;
+  }
+
+  if (g.slicing == BSSN_1PLUSLOG)
+    out[F_ALP] = T(-2) * alp * trK;
+  else if (g.slicing == BSSN_HARMONIC)
+    out[F_ALP] = -alp * alp * trK;
+  else
+    out[F_ALP] = T(0);
+
+  const bool frozen = (g.shift == BSSN_SHIFT_FROZEN);
+  if (!frozen) {
+    T q = T(1);
+    if (g.q_R > 0.0 && !isinf(g.q_R)) {
+      double x = g.xmin0 + (i - GH + 0.5) * g.h, y = g.xmin1 + (j - GH + 0.5) * g.h,
+             z = g.xmin2 + (k - GH + 0.5) * g.h;
+      double r = sqrt(x * x + y * y + z * z);
+      q = r <= g.q_R ? T(1) : T(g.q_R / r);
+    }
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+      out[F_BETA + a] = T(0.75) * Bv[a];
+      out[F_B + a] = gam_rhs[a] - T(g.eta) * q * Bv[a];
+    }
+  }
+
+  // ---- advection and dissipation, every field
+  Adv up;
+  T ab[3];
+#pragma unroll
+  for (int d = 0; d < 3; d++) {
+    up.s[d] = beta[d] >= T(0) ? sd[d] : -sd[d];
+    ab[d] = fabs(beta[d]);
+  }
+  const T absum = ab[0] + ab[1] + ab[2];
+  const T kos = T(g.ko_eps / (64.0 * g.h));
+  const int nf = frozen ? F_BETA : NF;
+#pragma unroll
+  for (int f = 0; f < NF; f++) {
+    if (f >= nf) {
+      out[f] = T(0);
+      continue;
+    }
+    T f0;
+    if (f == F_CHI) f0 = chi;
+    else if (f >= F_GT && f < F_GT + 6) f0 = gt[f - F_GT];
+    else if (f == F_TRK) f0 = trK;
+    else if (f >= F_AT && f < F_AT + 6) f0 = At[f - F_AT];
+    else if (f == F_ALP) f0 = alp;
+    else if (f >= F_BETA && f < F_BETA + 3) f0 = beta[f - F_BETA];
+    else if (f >= F_B) f0 = Bv[f - F_B];
+    else f0 = ldg<T>(PF(f));
+    T adv, ko;
+    adv_ko<T>(PF(f), sd, up, ab, absum, f0, adv, ko);
+    out[f] = fmaT<T>(kos, ko, fmaT<T>(i12h, adv, out[f]));
+  }
+#undef PF
+}
+
+}  // namespace bssn

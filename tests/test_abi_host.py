@@ -1,0 +1,64 @@
+"""Host-side checks of the C ABI that need no GPU: the library loads, exports
+every entry point include/bssn.h declares, and validates parameters."""
+import math
+import os
+import re
+
+import pytest
+
+from paper_1111_3344_gb300 import bssn as B
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    src = open(os.path.join(ROOT, "include", "bssn.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(bssn_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_library_exports_every_declared_symbol():
+    lib = B.load()
+    names = declared_symbols()
+    assert len(names) >= 12
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(names) == set(B.exported_symbols())
+
+
+def test_layout_and_required_bytes():
+    p = B.Params(n=(128, 128, 128), xmin=(-8.0,) * 3, h=0.125, boundary="sommerfeld")
+    lay = B.bssn_layout_of(p)
+    assert lay["stored"] == (134, 134, 134)
+    assert lay["pitch"] % 8 == 0 and lay["pitch"] >= 134
+    assert lay["field_stride"] == lay["plane"] * 134 and lay["plane"] == lay["pitch"] * 134
+    nb = B.bssn_required_bytes(p)
+    # y_n, acc, two stage buffers and the boundary-anchor buffer
+    assert nb >= 5 * 24 * lay["field_stride"] * 8
+    p2 = B.Params(n=(128, 128, 128), xmin=(-8.0,) * 3, h=0.125, boundary="periodic")
+    assert B.bssn_required_bytes(p2) < nb
+
+
+@pytest.mark.parametrize("bad", [
+    dict(n=(3, 8, 8)), dict(n=(8, 8, 4097)), dict(h=0.0), dict(h=math.nan),
+    dict(boundary="periodic", dt=math.inf), dict(w_floor=0.0),
+])
+def test_invalid_params_rejected(bad):
+    kw = dict(n=(8, 8, 8), xmin=(0.0,) * 3, h=0.1)
+    kw.update(bad)
+    p = B.Params(**kw)
+    with pytest.raises(B.BssnError) as e:
+        B.bssn_layout_of(p)
+    assert e.value.status == 1
+    with pytest.raises(B.BssnError):
+        B.bssn_required_bytes(p)
+
+
+def test_alloc_rejects_null_and_small_memory():
+    p = B.Params(n=(8, 8, 8), xmin=(0.0,) * 3, h=0.1)
+    with pytest.raises(B.BssnError) as e:
+        B.bssn_alloc(p, 0, 1 << 30, 0)
+    assert e.value.status == 1
+    with pytest.raises(B.BssnError) as e:
+        B.bssn_alloc(p, 256, 16, 0)  # never dereferenced: size check fails first
+    assert e.value.status == 2

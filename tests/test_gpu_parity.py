@@ -1,0 +1,139 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Bar (float64 path): per field, normwise relative error <= 1e-12 per
+right-hand-side call; RK4 steps compound a few calls, so their bar is
+1e-11.  Inputs come from the oracle or from the seeded generators in
+paper_1111_3344_gb300/inputs.py, never from the CUDA path."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from cases import bl_params, gpu_params, normwise_errors, oracle_cfg
+from paper_1111_3344_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+TOL_RHS = 1e-12
+TOL_STEP = 1e-11
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    return torch
+
+
+def _evo(case):
+    from paper_1111_3344_gb300.bssn import Evolution
+    return Evolution(gpu_params(case))
+
+
+BL1 = dict(n=(37, 21, 19), xmin=(-4.1, -2.3, -2.2), h=0.2203, boundary="sommerfeld",
+           punctures=[(1.0, 0.05, -0.02, 0.01)], r_excise=0.8)
+CASES = {
+    # moving-puncture setting with a perturbed state exercising every term; ragged tiles
+    "bl_w_1pluslog_sommerfeld": dict(BL1, conformal="W", slicing="1+log", shift="gamma-driver",
+                                     eta=2.0, q_R=1.7),
+    "bl_phi_harmonic_sommerfeld": dict(BL1, conformal="phi", slicing="harmonic", shift="gamma-driver",
+                                       eta=0.5),
+    "random_periodic_w_geodesic": dict(n=(33, 9, 12), xmin=(-0.5, -0.2, -0.3), h=1.0 / 33,
+                                       boundary="periodic", conformal="W", slicing="geodesic"),
+    "random_periodic_phi_frozen": dict(n=(16, 40, 8), xmin=(0.0, 0.0, 0.0), h=0.05,
+                                       boundary="periodic", conformal="phi", slicing="1+log",
+                                       shift="frozen"),
+    "minimal_grid": dict(n=(4, 4, 4), xmin=(-0.2, -0.2, -0.2), h=0.1, boundary="sommerfeld",
+                         conformal="W"),
+}
+
+
+def _state_for(name, case):
+    cfg = oracle_cfg(case)
+    if case.get("punctures"):
+        bg = O.initial_data(cfg, "bl", bl_params(case))
+        return inputs.random_state(7, case["n"], case["xmin"], case["h"], amp=0.05, background=bg)
+    return inputs.random_state(11, case["n"], case["xmin"], case["h"], amp=0.1)
+
+
+@pytest.mark.parametrize("kind", ["flat", "gauge_wave", "bl", "kasner"])
+@pytest.mark.parametrize("conformal", ["W", "phi"])
+def test_initial_data_parity(torch_cuda, kind, conformal):
+    case = dict(n=(20, 13, 9), xmin=(-0.5, -0.7, -0.3), h=0.07, boundary="sommerfeld",
+                conformal=conformal, punctures=[(0.7, 0.05, 0.0, 0.0), (0.4, -0.3, 0.1, 0.0)])
+    p = {"flat": [], "gauge_wave": [0.01, 1.0], "bl": bl_params(case), "kasner": [1.3]}[kind]
+    evo = _evo(case)
+    evo.set_initial_data(kind, p)
+    got, t = evo.get_state()
+    want = O.initial_data(oracle_cfg(case), kind, p)
+    e = normwise_errors(got, want)
+    assert e.max() <= 1e-13, e
+    assert t == 0.0
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_rhs_parity(torch_cuda, name):
+    case = CASES[name]
+    st = _state_for(name, case)
+    evo = _evo(case)
+    reg = evo.numpy_to_register(st)
+    got = evo.register_to_numpy(evo.rhs(reg))
+    want = O.rhs(oracle_cfg(case), st)
+    e = normwise_errors(got, want)
+    assert e.max() <= TOL_RHS, dict(zip(O.FIELD_NAMES, e))
+    # every field's right-hand side is non-trivial in the perturbed cases
+    if name.startswith(("bl_", "random_periodic_w")):
+        assert (np.abs(want).reshape(24, -1).max(axis=1)[:18] > 0).all()
+
+
+@pytest.mark.parametrize("name", ["bl_w_1pluslog_sommerfeld", "random_periodic_w_geodesic",
+                                  "random_periodic_phi_frozen", "minimal_grid"])
+def test_rk4_parity(torch_cuda, name):
+    case = CASES[name]
+    st = _state_for(name, case)
+    evo = _evo(case)
+    evo.set_state(st, 0.0)
+    evo.rk4_step(3)
+    got, t = evo.get_state()
+    want = O.rk4(oracle_cfg(case), st, 3)
+    e = normwise_errors(got, want)
+    assert e.max() <= TOL_STEP, dict(zip(O.FIELD_NAMES, e))
+    assert t == pytest.approx(3 * case.get("dt", 0.25 * case["h"]))
+
+
+def test_zero_steps_leave_state_unchanged(torch_cuda):
+    case = CASES["bl_w_1pluslog_sommerfeld"]
+    st = _state_for("bl", case)
+    evo = _evo(case)
+    evo.set_state(st, 1.5)
+    evo.rk4_step(0)
+    got, t = evo.get_state()
+    assert np.array_equal(got, st) and t == 1.5
+
+
+@pytest.mark.parametrize("name", ["bl_w_1pluslog_sommerfeld", "bl_phi_harmonic_sommerfeld",
+                                  "random_periodic_w_geodesic"])
+def test_constraint_norm_parity(torch_cuda, name):
+    case = CASES[name]
+    st = _state_for(name, case)
+    evo = _evo(case)
+    evo.set_state(st, 0.0)
+    if case.get("punctures"):
+        evo.set_initial_data("bl", bl_params(case))  # registers the punctures for excision
+        evo.set_state(st, 0.0)
+    got = evo.constraints()
+    want, _, _ = O.constraints(oracle_cfg(case), st)
+    np.testing.assert_allclose(got, want, rtol=1e-12, atol=0)
+
+
+def test_flat_space_stays_flat_on_gpu(torch_cuda):
+    case = dict(n=(12, 12, 12), xmin=(-0.5,) * 3, h=1 / 12, boundary="sommerfeld", conformal="W")
+    evo = _evo(case)
+    evo.set_initial_data("flat")
+    st0, _ = evo.get_state()
+    evo.rk4_step(5)
+    st, _ = evo.get_state()
+    assert np.array_equal(st, st0)
+    assert np.all(evo.constraints() == 0.0)
