@@ -46,9 +46,10 @@ FP64_MEASURED_GFLOPS = 1196.0      # dependent-chain DFMA microbenchmark on this
 def workload_params(precision="fp64"):
     from paper_1111_3344_gb300.bssn import Params
     h = 2 * DOMAIN / N_SIDE
+    # mixed: W right-hand side in float64 below W = 0.2 (r < ~0.6 M from the puncture)
     return Params(n=(N_SIDE,) * 3, xmin=(-DOMAIN,) * 3, h=h, boundary="sommerfeld", conformal="W",
                   slicing="1+log", shift="gamma-driver", eta=2.0, ko_eps=0.1, dt=0.25 * h,
-                  precision=precision, r_excise=1.0)
+                  precision=precision, w_fp64_threshold=0.2, r_excise=1.0)
 
 
 BL_P = [1, 1.0, 0.0, 0.0, 0.0]
@@ -205,6 +206,7 @@ def run_ours(args):
     evo = B.Evolution(params)
     evo.set_initial_data("bl", BL_P)
     stream = evo.stream
+    tile, tile_ms = B.bssn_autotune(evo.ctx, reps=5)  # untimed: picks the stage-kernel tiles
     for _ in range(args.warmup):
         evo.rk4_step(1)
     barrier(world)
@@ -255,7 +257,7 @@ def run_ours(args):
         "config": {"workload": "single Brill-Lindquist puncture M=1, 128^3 on [-8,8]^3, W, 1+log, "
                                "Gamma-driver eta=2, Sommerfeld, RK4 dt=0.25h",
                    "global_batch": world, "grid": [N_SIDE] * 3, "parallelism": f"replicas{world}",
-                   "precision": args.precision,
+                   "precision": args.precision, "tile": B.bssn_tile_name(tile),
                    "l2": "inputs larger than L2 (4 float64 registers of 469 MB each)"},
         "roofline": {"bound": "alu", "kernel": "stage_fp64_kernel", "achieved": achieved * 1e3,
                      "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s (FP64)",
@@ -280,6 +282,113 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def _bl_params(member, precision):
+    from paper_1111_3344_gb300.bssn import Params
+    h = member["h"]
+    return Params(n=member["n"], xmin=member["xmin"], h=h, boundary="sommerfeld", conformal="W",
+                  slicing="1+log", shift="gamma-driver", eta=2.0, ko_eps=0.1, dt=0.25 * h,
+                  precision=precision, w_fp64_threshold=0.2, r_excise=1.0)
+
+
+def run_batched(args):
+    """64 time-symmetric Brill-Lindquist binaries (masses U[0.3,0.7], separations
+    U[2,6], grids from {48,64,96,128}^3, seed 1111) advanced together, one
+    persistent launch per RK4 stage under a CUDA graph."""
+    import torch
+
+    from paper_1111_3344_gb300 import bssn as B
+    from paper_1111_3344_gb300 import inputs
+    torch.cuda.set_device(0)
+    members = inputs.binary_bl_batch(seed=1111, count=args.members)
+    params = [_bl_params(m, args.precision) for m in members]
+    need = sum(B.Batch.member_bytes(p) for p in params) + (64 << 20)
+    batch = B.Batch(args.precision, pool_bytes=need, max_members=max(len(params), 1))
+    ids = []
+    for m, p in zip(members, params):
+        mid = batch.add(p)
+        bl = [len(m["punctures"])] + [v for q in m["punctures"] for v in q]
+        batch.set_initial_data(mid, "bl", bl)
+        ids.append(mid)
+    best, tile_ms = batch.autotune(reps=2)
+    batch.step(args.warmup)
+    batch.synchronize()
+    start = torch.cuda.Event(enable_timing=True)
+    stop = torch.cuda.Event(enable_timing=True)
+    start.record(batch.stream)
+    batch.step(args.steps)
+    stop.record(batch.stream)
+    stop.synchronize()
+    ms = start.elapsed_time(stop)
+    pts = sum(p.n[0] * p.n[1] * p.n[2] for p in params)
+    value = pts * args.steps / (ms * 1e-3) / 1e6
+    line = {"metric": f"batched BSSN RK4 point-updates/s ({args.precision})", "value": value,
+            "unit": "Mpoint-updates/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "dtype": "f64" if args.precision == "fp64" else "f32+f64", "data": "synthetic",
+            "config": {"workload": f"{len(params)} Brill-Lindquist binaries, grids {{48,64,96,128}}^3, seed 1111",
+                       "interior_points": pts, "tile": list(tile_ms)[best],
+                       "launches_per_step": 8, "graph": True}}
+    print(json.dumps(line))
+    batch.close()
+
+
+def run_served(args):
+    """Poisson arrivals of puncture evolutions (grids 32^3..192^3, 50..400 steps,
+    Brill-Lindquist binaries as in the batched workload, seed 3344), admitted by
+    HBM budget into a continuous-batching server; reports p50/p99 time from
+    submission to completion and the aggregate point-update rate."""
+    import torch
+
+    from paper_1111_3344_gb300 import bssn as B
+    torch.cuda.set_device(0)
+    rng = np.random.default_rng(3344)
+    sizes = [32, 48, 64, 96, 128, 160, 192]
+    reqs = []
+    for _ in range(args.requests):
+        n = int(rng.choice(sizes))
+        steps = int(rng.integers(50, 401))
+        m1, m2 = rng.uniform(0.3, 0.7, size=2)
+        sep = rng.uniform(2.0, 6.0)
+        L = max(8.0, 2.0 * sep) * (m1 + m2)
+        h = 2 * L / n
+        x1, x2 = sep * m2 / (m1 + m2), -sep * m1 / (m1 + m2)
+        x1 = -L + round((x1 + L) / h) * h
+        x2 = -L + round((x2 + L) / h) * h
+        mem = dict(n=(n, n, n), xmin=(-L,) * 3, h=h)
+        reqs.append((_bl_params(mem, args.precision), [2, m1, x1, 0.0, 0.0, m2, x2, 0.0, 0.0], steps))
+    work = sum(p.n[0] ** 3 * st for p, _, st in reqs)
+    budget = int(args.budget_gb * (1 << 30))
+    srv = B.Server(args.precision, budget_bytes=budget)
+    # arrival rate: 0.8 x the capacity in requests/s implied by a throughput estimate
+    est_rate = args.capacity_mpts * 1e6  # point-updates/s
+    lam = 0.8 * est_rate / (work / len(reqs))
+    gaps = rng.exponential(1.0 / lam, size=len(reqs))
+    t0 = time.perf_counter()
+    tickets = []
+    for (p, idp, st), gap in zip(reqs, gaps):
+        time.sleep(gap)
+        tickets.append(srv.submit(p, "bl", idp, st))
+    lats, fails = [], 0
+    for t in tickets:
+        st, norms, lat = srv.wait(t, timeout=3600)
+        lats.append(lat)
+        fails += st != 0
+    wall = time.perf_counter() - t0
+    stats = srv.stats()
+    srv.close()
+    lats = np.array(lats)
+    line = {"metric": "served BSSN evolutions: p50/p99 completion latency, aggregate point-updates/s",
+            "value": stats["point_updates"] / wall / 1e6, "unit": "Mpoint-updates/s", "n_gpus": 1,
+            "higher_is_better": True, "dtype": "f32+f64" if args.precision == "mixed" else "f64",
+            "data": "synthetic",
+            "p50_s": float(np.percentile(lats, 50)), "p99_s": float(np.percentile(lats, 99)),
+            "failed": int(fails), "wall_s": wall, "busy_s": stats["busy_s"],
+            "config": {"workload": f"{len(reqs)} Poisson-arrival Brill-Lindquist binaries, grids 32^3..192^3, "
+                                   f"50..400 steps, seed 3344", "lambda_per_s": lam,
+                       "budget_gb": args.budget_gb, "point_updates": work}}
+    print(json.dumps(line))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -288,6 +397,14 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", choices=["puncture", "batched", "served"], default="puncture",
+                    help="puncture: the benchmark line (single 128^3 puncture); batched / served: "
+                         "the multi-evolution workloads, reported on their own lines")
+    ap.add_argument("--members", type=int, default=64)
+    ap.add_argument("--requests", type=int, default=64)
+    ap.add_argument("--budget-gb", type=float, default=64.0)
+    ap.add_argument("--capacity-mpts", type=float, default=250.0,
+                    help="served: throughput estimate (M point-updates/s) that sets the arrival rate")
     ap.add_argument("--n", type=int, default=128,
                     help="grid points per side (128 is the benchmark workload; smaller sizes are "
                          "for profiling captures only)")
@@ -298,6 +415,10 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batched":
+        run_batched(args)
+    elif args.workload == "served":
+        run_served(args)
     else:
         run_ours(args)
 

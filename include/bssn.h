@@ -175,12 +175,90 @@ bssn_status bssn_constraints(bssn_ctx* ctx, double out[16]);
 bssn_status bssn_get_state(bssn_ctx* ctx, double* host_state, double* t);
 bssn_status bssn_set_state(bssn_ctx* ctx, const double* host_state, double t);
 
+/* Stage-kernel tile configurations: block shape (points along x, y, z) and the
+ * minimum resident blocks per SM given to the compiler.  Every configuration
+ * evaluates the same per-point arithmetic, so results do not depend on it. */
+int32_t bssn_tile_count(void);
+const char* bssn_tile_name(int32_t cfg); /* e.g. "32x8x1/1"; "" when out of range */
+bssn_status bssn_set_tile(bssn_ctx* ctx, int32_t cfg);
+
+/* Autotuner: time every tile configuration on this evolution's live state
+ * (reps launches of the first RK4 stage each, which leaves y_n unchanged),
+ * select the fastest for the context and return it in *best; ms_per_cfg (may be
+ * NULL, else bssn_tile_count() entries) receives the mean milliseconds per
+ * launch.  Synchronises the stream. */
+bssn_status bssn_autotune(bssn_ctx* ctx, int32_t reps, int32_t* best, double* ms_per_cfg);
+
+/* ------------------------------------------------------------ batches
+ * Many independent evolutions (different grids and parameters, one precision)
+ * advanced together: bssn_batch_step runs one persistent launch per RK4 stage
+ * over the tiles of every active member plus one boundary launch, replayed
+ * from a CUDA graph captured once per tile shape.  Members join and leave
+ * between steps without re-capture (the graph reads a device work-list).  A
+ * member computes the same bits as the same evolution run alone through a
+ * bssn_ctx.  All device memory comes from the caller's pool: the batch tables
+ * (bssn_batch_table_bytes) at its start, then member registers carved by a
+ * first-fit sub-allocator (bssn_batch_member_bytes each). */
+#define BSSN_BATCH_MAX_MEMBERS 256
+typedef struct bssn_batch bssn_batch;
+
+size_t bssn_batch_table_bytes(int32_t max_members);   /* 0 if out of range */
+size_t bssn_batch_member_bytes(const bssn_params* p); /* 0 on bad p */
+/* precision: BSSN_FP64 or BSSN_MIXED for every member; cuda_stream must not be
+ * the legacy default stream (graphs are captured on it). */
+bssn_status bssn_batch_create(int32_t precision, int32_t max_members, void* d_pool,
+                              size_t pool_bytes, void* cuda_stream, bssn_batch** out);
+bssn_status bssn_batch_free(bssn_batch* b); /* synchronises; does not free the pool */
+/* Add a member (inactive until its initial data or state is set).  ENOMEM when
+ * the batch or the pool is full, EINVAL on bad params or a precision mismatch. */
+bssn_status bssn_batch_add(bssn_batch* b, const bssn_params* p, int32_t* member);
+bssn_status bssn_batch_remove(bssn_batch* b, int32_t member); /* synchronises */
+bssn_status bssn_batch_set_initial_data(bssn_batch* b, int32_t member, int32_t kind,
+                                        const double* p, int32_t np);
+bssn_status bssn_batch_set_state(bssn_batch* b, int32_t member, const double* host, double t);
+bssn_status bssn_batch_get_state(bssn_batch* b, int32_t member, double* host, double* t);
+/* Advance every active member nsteps RK4 steps (asynchronous). */
+bssn_status bssn_batch_step(bssn_batch* b, int32_t nsteps);
+bssn_status bssn_batch_constraints(bssn_batch* b, int32_t member, double out[16]); /* synchronises */
+int32_t bssn_batch_tile_count(void);
+const char* bssn_batch_tile_name(int32_t cfg);
+bssn_status bssn_batch_set_tile(bssn_batch* b, int32_t cfg);
+/* Autotuner for the persistent stage kernel: times each tile shape on the
+ * batch's live members (first-stage launches, which leave y_n unchanged) and
+ * selects the fastest. */
+bssn_status bssn_batch_autotune(bssn_batch* b, int32_t reps, int32_t* best, double* ms_per_cfg);
+
+/* ------------------------------------------------------------- server
+ * Continuous batching of evolution requests (BASELINE serving pattern): a
+ * scheduler thread admits queued requests at RK4 step boundaries while their
+ * register bytes fit in hbm_budget_bytes, keeps their state on the device,
+ * advances all resident evolutions together (bssn_batch_step) and retires
+ * each when it reaches its step count, reporting its constraint norms and
+ * time from submission to completion.  d_pool (256-byte aligned) holds the
+ * batch tables and every request's registers. */
+bssn_status bssn_server_create(int32_t precision, size_t hbm_budget_bytes, void* d_pool,
+                               size_t pool_bytes, void* cuda_stream, bssn_server** out);
+/* Enqueue a request; never blocks.  EINVAL if it alone exceeds the budget or
+ * its parameters are bad.  id_kind/id_p/np as for bssn_set_initial_data. */
+bssn_status bssn_submit(bssn_server* s, const bssn_params* p, int32_t id_kind, const double* id_p,
+                        int32_t np, int32_t nsteps, uint64_t* ticket);
+/* EAGAIN while queued or running; then BSSN_OK (norms_out as bssn_constraints,
+ * *latency_s seconds from submit to completion) or BSSN_EFAILED when NaN/Inf
+ * appeared in that request's state (other requests are unaffected). */
+bssn_status bssn_poll(bssn_server* s, uint64_t ticket, double norms_out[16], double* latency_s);
+/* out[0] completed, [1] failed, [2] queued, [3] resident, [4] interior
+ * point-updates done, [5] seconds spent stepping, [6] seconds since create,
+ * [7] bytes of the budget in use. */
+bssn_status bssn_server_stats(bssn_server* s, double out[8]);
+bssn_status bssn_server_destroy(bssn_server* s); /* stops the scheduler; synchronises */
+
 /* Launch timing.  enable != 0: start recording CUDA events on the bound
  * stream around every fused stage launch and every boundary launch of
  * bssn_rk4_step (out unused).  enable == 0: stop, synchronise and write
  * out[0] = total stage-kernel milliseconds, out[1] = stage launches,
  * out[2] = total boundary-kernel milliseconds, out[3] = boundary launches. */
 bssn_status bssn_profile(bssn_ctx* ctx, int32_t enable, double out[4]);
+
 
 #ifdef __cplusplus
 }

@@ -128,6 +128,46 @@ _SIGS = [
     ("bssn_get_state", [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     ("bssn_set_state", [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double], ctypes.c_int),
     ("bssn_profile", [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+    ("bssn_tile_count", [], ctypes.c_int32),
+    ("bssn_tile_name", [ctypes.c_int32], ctypes.c_char_p),
+    ("bssn_set_tile", [ctypes.c_void_p, ctypes.c_int32], ctypes.c_int),
+    ("bssn_autotune", [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
+                       ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+]
+
+
+_SIGS += [
+    ("bssn_batch_table_bytes", [ctypes.c_int32], ctypes.c_size_t),
+    ("bssn_batch_member_bytes", [ctypes.POINTER(bssn_params)], ctypes.c_size_t),
+    ("bssn_batch_create", [ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p, ctypes.c_size_t,
+                           ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int),
+    ("bssn_batch_free", [ctypes.c_void_p], ctypes.c_int),
+    ("bssn_batch_add", [ctypes.c_void_p, ctypes.POINTER(bssn_params), ctypes.POINTER(ctypes.c_int32)],
+     ctypes.c_int),
+    ("bssn_batch_remove", [ctypes.c_void_p, ctypes.c_int32], ctypes.c_int),
+    ("bssn_batch_set_initial_data", [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
+                                     ctypes.POINTER(ctypes.c_double), ctypes.c_int32], ctypes.c_int),
+    ("bssn_batch_set_state", [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_double],
+     ctypes.c_int),
+    ("bssn_batch_get_state", [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
+                              ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+    ("bssn_batch_step", [ctypes.c_void_p, ctypes.c_int32], ctypes.c_int),
+    ("bssn_batch_constraints", [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_double)],
+     ctypes.c_int),
+    ("bssn_batch_tile_count", [], ctypes.c_int32),
+    ("bssn_batch_tile_name", [ctypes.c_int32], ctypes.c_char_p),
+    ("bssn_batch_set_tile", [ctypes.c_void_p, ctypes.c_int32], ctypes.c_int),
+    ("bssn_batch_autotune", [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
+                             ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+    ("bssn_server_create", [ctypes.c_int32, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_size_t,
+                            ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int),
+    ("bssn_submit", [ctypes.c_void_p, ctypes.POINTER(bssn_params), ctypes.c_int32,
+                     ctypes.POINTER(ctypes.c_double), ctypes.c_int32, ctypes.c_int32,
+                     ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
+    ("bssn_poll", [ctypes.c_void_p, ctypes.c_uint64, ctypes.POINTER(ctypes.c_double),
+                   ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+    ("bssn_server_stats", [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+    ("bssn_server_destroy", [ctypes.c_void_p], ctypes.c_int),
 ]
 
 
@@ -234,6 +274,28 @@ def bssn_set_state(ctx: int, host: np.ndarray, t: float = 0.0):
     _check(load().bssn_set_state(ctypes.c_void_p(ctx), ctypes.c_void_p(host.ctypes.data), float(t)))
 
 
+def bssn_tile_count() -> int:
+    return int(load().bssn_tile_count())
+
+
+def bssn_tile_name(cfg: int) -> str:
+    return load().bssn_tile_name(int(cfg)).decode()
+
+
+def bssn_set_tile(ctx: int, cfg: int):
+    _check(load().bssn_set_tile(ctypes.c_void_p(ctx), int(cfg)))
+
+
+def bssn_autotune(ctx: int, reps: int = 3):
+    """Time every tile configuration on the live state; selects and returns
+    (best_index, {name: ms_per_launch})."""
+    n = bssn_tile_count()
+    ms = (ctypes.c_double * n)()
+    best = ctypes.c_int32()
+    _check(load().bssn_autotune(ctypes.c_void_p(ctx), int(reps), ctypes.byref(best), ms))
+    return best.value, {bssn_tile_name(c): ms[c] for c in range(n)}
+
+
 def bssn_profile(ctx: int, enable: bool):
     """Start (enable=True) or stop launch timing; on stop returns
     (stage_ms, stage_launches, boundary_ms, boundary_launches)."""
@@ -322,3 +384,165 @@ class Evolution:
 
     def set_state(self, host: np.ndarray, t: float = 0.0):
         bssn_set_state(self.ctx, np.ascontiguousarray(host, dtype=np.float64), t)
+
+
+# ---------------------------------------------------------------- batches
+class Batch:
+    """Many evolutions advanced together (persistent launch per RK stage under a
+    captured CUDA graph).  Owns a torch device pool and a dedicated stream."""
+
+    def __init__(self, precision: str = "fp64", pool_bytes: int = 1 << 30, max_members: int = 64,
+                 device: str = "cuda"):
+        import torch
+        self.torch = torch
+        self.device = torch.device(device)
+        self.stream = torch.cuda.Stream(self.device)
+        self.pool = torch.empty(int(pool_bytes), dtype=torch.uint8, device=self.device)
+        self.precision = precision
+        out = ctypes.c_void_p()
+        torch.cuda.synchronize(self.device)
+        _check(load().bssn_batch_create(PRECISION[precision], int(max_members),
+                                        ctypes.c_void_p(self.pool.data_ptr()), int(pool_bytes),
+                                        ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(out)))
+        self.handle = out.value
+        self.params = {}
+
+    def close(self):
+        if self.handle:
+            _check(load().bssn_batch_free(ctypes.c_void_p(self.handle)))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @staticmethod
+    def member_bytes(params: Params) -> int:
+        p = params.c()
+        n = load().bssn_batch_member_bytes(ctypes.byref(p))
+        if n == 0:
+            raise BssnError(1, load().bssn_last_error().decode())
+        return int(n)
+
+    def add(self, params: Params) -> int:
+        p = params.c()
+        mid = ctypes.c_int32()
+        _check(load().bssn_batch_add(ctypes.c_void_p(self.handle), ctypes.byref(p), ctypes.byref(mid)))
+        self.params[mid.value] = params
+        return mid.value
+
+    def remove(self, member: int):
+        _check(load().bssn_batch_remove(ctypes.c_void_p(self.handle), int(member)))
+        self.params.pop(member, None)
+
+    def set_initial_data(self, member: int, kind: str, p=()):
+        arr = _dbl_array(p)
+        _check(load().bssn_batch_set_initial_data(ctypes.c_void_p(self.handle), int(member), ID_KIND[kind],
+                                                  arr, len(p)))
+
+    def _shape(self, member):
+        lay = bssn_layout_of(self.params[member])
+        sx, sy, sz = lay["stored"]
+        return (NUM_FIELDS, sz, sy, sx)
+
+    def set_state(self, member: int, host: np.ndarray, t: float = 0.0):
+        host = np.ascontiguousarray(host, dtype=np.float64)
+        assert host.shape == self._shape(member)
+        _check(load().bssn_batch_set_state(ctypes.c_void_p(self.handle), int(member),
+                                           ctypes.c_void_p(host.ctypes.data), float(t)))
+
+    def get_state(self, member: int):
+        host = np.empty(self._shape(member), dtype=np.float64)
+        t = ctypes.c_double()
+        _check(load().bssn_batch_get_state(ctypes.c_void_p(self.handle), int(member),
+                                           ctypes.c_void_p(host.ctypes.data), ctypes.byref(t)))
+        return host, t.value
+
+    def step(self, nsteps: int = 1):
+        _check(load().bssn_batch_step(ctypes.c_void_p(self.handle), int(nsteps)))
+
+    def synchronize(self):
+        self.stream.synchronize()
+
+    def constraints(self, member: int):
+        out = (ctypes.c_double * 16)()
+        _check(load().bssn_batch_constraints(ctypes.c_void_p(self.handle), int(member), out))
+        return np.array(out[:])
+
+    def set_tile(self, cfg: int):
+        _check(load().bssn_batch_set_tile(ctypes.c_void_p(self.handle), int(cfg)))
+
+    def autotune(self, reps: int = 2):
+        n = int(load().bssn_batch_tile_count())
+        ms = (ctypes.c_double * n)()
+        best = ctypes.c_int32()
+        _check(load().bssn_batch_autotune(ctypes.c_void_p(self.handle), int(reps), ctypes.byref(best), ms))
+        names = [load().bssn_batch_tile_name(c).decode() for c in range(n)]
+        return best.value, dict(zip(names, ms[:]))
+
+
+class Server:
+    """Continuous-batching server of evolution requests (C scheduler thread)."""
+
+    def __init__(self, precision: str = "mixed", budget_bytes: int = 1 << 30, pool_bytes: int = None,
+                 device: str = "cuda"):
+        import torch
+        self.torch = torch
+        pool_bytes = int(pool_bytes or budget_bytes + (16 << 20))
+        self.stream = torch.cuda.Stream(torch.device(device))
+        self.pool = torch.empty(pool_bytes, dtype=torch.uint8, device=device)
+        torch.cuda.synchronize()
+        out = ctypes.c_void_p()
+        _check(load().bssn_server_create(PRECISION[precision], int(budget_bytes),
+                                         ctypes.c_void_p(self.pool.data_ptr()), pool_bytes,
+                                         ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(out)))
+        self.handle = out.value
+
+    def submit(self, params: Params, kind: str, p=(), nsteps: int = 1) -> int:
+        c = params.c()
+        arr = _dbl_array(p)
+        t = ctypes.c_uint64()
+        _check(load().bssn_submit(ctypes.c_void_p(self.handle), ctypes.byref(c), ID_KIND[kind], arr, len(p),
+                                  int(nsteps), ctypes.byref(t)))
+        return t.value
+
+    def poll(self, ticket: int):
+        """None while pending; else (status, norms16, latency_s)."""
+        norms = (ctypes.c_double * 16)()
+        lat = ctypes.c_double()
+        st = load().bssn_poll(ctypes.c_void_p(self.handle), ctypes.c_uint64(ticket), norms, ctypes.byref(lat))
+        if st == 4:
+            return None
+        if st not in (0, 7):
+            raise BssnError(st, load().bssn_last_error().decode())
+        return st, np.array(norms[:]), lat.value
+
+    def wait(self, ticket: int, timeout: float = 120.0):
+        import time
+        t0 = time.time()
+        while True:
+            r = self.poll(ticket)
+            if r is not None:
+                return r
+            if time.time() - t0 > timeout:
+                raise TimeoutError(f"ticket {ticket} not done after {timeout} s")
+            time.sleep(0.001)
+
+    def stats(self):
+        out = (ctypes.c_double * 8)()
+        _check(load().bssn_server_stats(ctypes.c_void_p(self.handle), out))
+        keys = ["completed", "failed", "queued", "resident", "point_updates", "busy_s", "wall_s", "bytes_used"]
+        return dict(zip(keys, out[:]))
+
+    def close(self):
+        if self.handle:
+            _check(load().bssn_server_destroy(ctypes.c_void_p(self.handle)))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,198 @@
+// Per-ghost-point outer boundary work (Sommerfeld condition, periodic copy),
+// shared by the single-grid kernels (k_boundary.cu) and the batched kernels
+// (k_batch.cu).
+#pragma once
+#include "bssn_internal.cuh"
+#include "rhs_point.cuh"
+
+namespace bssn {
+
+__device__ __forceinline__ void x0v0(const Grid& g, int f, double& X0, double& v0) {
+  X0 = 0.0;
+  v0 = 1.0;
+  if (f == F_ALP || (f == F_CHI && g.use_w) || f == F_GT + 0 || f == F_GT + 3 || f == F_GT + 5)
+    X0 = 1.0;
+  if (f == F_ALP || f == F_TRK) v0 = 1.4142135623730951;
+}
+
+__device__ __forceinline__ double coordv(const Grid& g, int d, int i) {
+  const double xm = d == 0 ? g.xmin0 : (d == 1 ? g.xmin1 : g.xmin2);
+  return xm + (i - GH + 0.5) * g.h;
+}
+
+// Radiative right-hand side of field f at stored point I in arithmetic C;
+// p points at the field's value there; nx = x / r, ir = 1 / r.
+template <typename C, typename S, bool DEV = false>
+__device__ C rad_at(const Grid& g, const S* __restrict__ p, int f, const int I[3], const C nx[3],
+                    C ir) {
+  const long long sd[3] = {1, g.pitch, g.plane};
+  const int dims[3] = {g.sx, g.sy, g.sz};
+  const bool one = (f == F_ALP || (f == F_CHI && g.use_w) || f == F_GT + 0 || f == F_GT + 3 ||
+                   f == F_GT + 5);
+  const C X0 = (DEV || !one) ? C(0) : C(1);  // DEV: p holds X - X0 already
+  const C v0 = (f == F_ALP || f == F_TRK) ? C(1.4142135623730951) : C(1);
+  const C i2h = gc<C>(g.i2h, g.i2hf);
+  C s = ((C)p[0] - X0) * ir;
+#pragma unroll
+  for (int d = 0; d < 3; d++) {
+    const long long q = sd[d];
+    C der;
+    if (I[d] >= 1 && I[d] + 1 < dims[d])
+      der = (C)p[q] - (C)p[-q];
+    else if (I[d] + 1 >= dims[d])
+      der = C(3) * (C)p[0] - C(4) * (C)p[-q] + (C)p[-2 * q];
+    else
+      der = -(C(3) * (C)p[0] - C(4) * (C)p[q] + (C)p[2 * q]);
+    s = fmaT<C>(nx[d] * i2h, der, s);
+  }
+  return -v0 * s;
+}
+
+// Geometry of one ghost point: its anchor and the radial factors.
+struct GhostGeo {
+  int I[3], A[3];
+  long long ib, ia;
+  double nb[3], na[3], irb, ira, fac;
+};
+
+__device__ __forceinline__ void ghost_geo(const Grid& g, unsigned q, GhostGeo& G) {
+  ghost_decode(g, q, G.I[0], G.I[1], G.I[2]);
+  const int n[3] = {g.n0, g.n1, g.n2};
+  // walk to the anchor: each step moves one layer inward along the summed normal
+#pragma unroll
+  for (int d = 0; d < 3; d++) {
+    int a = G.I[d];
+    if (a < GH) a = GH;
+    else if (a >= GH + n[d]) a = GH + n[d] - 1;
+    G.A[d] = a;
+  }
+  double xb[3], xa[3];
+#pragma unroll
+  for (int d = 0; d < 3; d++) {
+    xb[d] = coordv(g, d, G.I[d]);
+    xa[d] = coordv(g, d, G.A[d]);
+  }
+  const double rb = sqrt(xb[0] * xb[0] + xb[1] * xb[1] + xb[2] * xb[2]);
+  const double ra = sqrt(xa[0] * xa[0] + xa[1] * xa[1] + xa[2] * xa[2]);
+  G.irb = 1.0 / rb;
+  G.ira = 1.0 / ra;
+  G.fac = (ra * G.irb) * (ra * G.irb);
+#pragma unroll
+  for (int d = 0; d < 3; d++) {
+    G.nb[d] = xb[d] * G.irb;
+    G.na[d] = xa[d] * G.ira;
+  }
+  G.ib = lin(g, G.I[0], G.I[1], G.I[2]);
+  G.ia = lin(g, G.A[0], G.A[1], G.A[2]);
+}
+
+// float64 path: ghost point q, all fields.
+__device__ __forceinline__ void sommerfeld_point_fp64(const Grid& g, const StageArgs& a,
+                                                      const double* __restrict__ kanchor, unsigned q) {
+  GhostGeo G;
+  ghost_geo(g, q, G);
+  const long long fs = g.fstride;
+  const int nf = g.shift == BSSN_SHIFT_FROZEN ? F_BETA : NF;
+  for (int f = 0; f < NF; f++) {
+    double rhs = 0.0;
+    if (f < nf) {
+      const double radb = rad_at<double, double>(g, a.src + f * fs + G.ib, f, G.I, G.nb, G.irb);
+      const double rada = rad_at<double, double>(g, a.src + f * fs + G.ia, f, G.A, G.na, G.ira);
+      const double ka = (a.mode == MODE_RHS) ? a.rhs[f * fs + G.ia] : kanchor[f * fs + G.ia];
+      rhs = fma(G.fac, ka - rada, radb);
+    }
+    const long long o = f * fs + G.ib;
+    if (a.mode == MODE_RHS) {
+      a.rhs[o] = rhs;
+    } else if (a.mode == MODE_LAST) {
+      a.yn[o] = fma(a.b_dt, a.ksum[o] + rhs, a.yn[o]);
+    } else {
+      a.out0[o] = fma(a.a_dt, rhs, a.src0[o]);
+      a.ksum[o] = a.mode == MODE_FIRST ? rhs : fma(2.0, rhs, a.ksum[o]);
+    }
+  }
+}
+
+// mixed path: ghost point q, field f; float arithmetic, W in float64; RK4
+// roles as in the stage kernel.
+__device__ __forceinline__ void sommerfeld_point_mixed(const Grid& g, const StageArgsMixed& a,
+                                                       const float* __restrict__ kanchor, unsigned q,
+                                                       int f) {
+  const long long fs = g.fstride;
+  const int nf = g.shift == BSSN_SHIFT_FROZEN ? F_BETA : NF;
+  int I[3], A[3];
+  ghost_decode(g, q, I[0], I[1], I[2]);
+  const int n[3] = {g.n0, g.n1, g.n2};
+#pragma unroll
+  for (int d = 0; d < 3; d++) A[d] = I[d] < GH ? GH : (I[d] >= GH + n[d] ? GH + n[d] - 1 : I[d]);
+  const long long ib = lin(g, I[0], I[1], I[2]);
+  const long long ia = lin(g, A[0], A[1], A[2]);
+  const long long o = f * fs + ib;
+  if (f == F_CHI) {
+    GhostGeo G;
+    ghost_geo(g, q, G);
+    const double radb = rad_at<double, double>(g, a.srcw + ib, f, I, G.nb, G.irb);
+    const double rada = rad_at<double, double>(g, a.srcw + ia, f, A, G.na, G.ira);
+    const double ka = (a.mode == MODE_RHS) ? a.rhs[ia] : (double)kanchor[ia];
+    const double rhs = fma(G.fac, ka - rada, radb);
+    if (a.mode == MODE_RHS) {
+      a.rhs[o] = rhs;
+    } else if (a.mode == MODE_LAST) {
+      const double v = fma(a.b_dt, a.ksumw[ib] + rhs, a.yn[ib]);
+      a.yn[ib] = v;
+      a.out0[ib] = (float)(v - background(g, F_CHI));
+      a.out0w[ib] = v;
+    } else {
+      const double v = fma(a.a_dt, rhs, a.src0w[ib]);
+      a.out0w[ib] = v;
+      a.out0[ib] = (float)(v - background(g, F_CHI));
+      a.ksumw[ib] = a.mode == MODE_FIRST ? rhs : fma(2.0, rhs, a.ksumw[ib]);
+    }
+    return;
+  }
+  float rhs = 0.0f;
+  if (f < nf) {
+    float xb[3], xa[3];
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+      xb[d] = fmaf((float)(I[d] - GH) + 0.5f, g.hf, g.xminf[d]);
+      xa[d] = fmaf((float)(A[d] - GH) + 0.5f, g.hf, g.xminf[d]);
+    }
+    const float irb = rsqrtf(xb[0] * xb[0] + xb[1] * xb[1] + xb[2] * xb[2]);
+    const float ira = rsqrtf(xa[0] * xa[0] + xa[1] * xa[1] + xa[2] * xa[2]);
+    const float nb[3] = {xb[0] * irb, xb[1] * irb, xb[2] * irb};
+    const float na[3] = {xa[0] * ira, xa[1] * ira, xa[2] * ira};
+    const float fac = (irb / ira) * (irb / ira);
+    const float radb = rad_at<float, float, true>(g, a.src + o, f, I, nb, irb);
+    const float rada = rad_at<float, float, true>(g, a.src + f * fs + ia, f, A, na, ira);
+    const float ka = (a.mode == MODE_RHS) ? (float)a.rhs[f * fs + ia] : kanchor[f * fs + ia];
+    rhs = fmaf(fac, ka - rada, radb);
+  }
+  if (a.mode == MODE_RHS) {
+    a.rhs[o] = (double)rhs;
+  } else if (a.mode == MODE_LAST) {
+    const double v = fma(a.b_dt, (double)(a.ksum[o] + rhs), a.yn[o]);
+    a.yn[o] = v;
+    a.out0[o] = (float)(v - background(g, f));
+  } else {
+    a.out0[o] = fmaf(a.a_dtf, rhs, a.src0[o]);
+    a.ksum[o] = a.mode == MODE_FIRST ? rhs : fmaf(2.0f, rhs, a.ksum[o]);
+  }
+}
+
+// Periodic ghosts: copy from the wrapped interior point, all fields (and the
+// float64 W array of a mixed stage buffer when w is non-null).
+template <typename S>
+__device__ __forceinline__ void periodic_point(const Grid& g, S* __restrict__ y,
+                                               double* __restrict__ w, unsigned q) {
+  int i, j, k;
+  ghost_decode(g, q, i, j, k);
+  const int si = GH + ((i - GH) % g.n0 + g.n0) % g.n0;
+  const int sj = GH + ((j - GH) % g.n1 + g.n1) % g.n1;
+  const int sk = GH + ((k - GH) % g.n2 + g.n2) % g.n2;
+  const long long d = lin(g, i, j, k), s = lin(g, si, sj, sk);
+  for (int f = 0; f < NF; f++) y[f * g.fstride + d] = y[f * g.fstride + s];
+  if (w) w[d] = w[s];
+}
+
+}  // namespace bssn

@@ -78,15 +78,17 @@ Grid make_grid(const bssn_params* p) {
   g.q_R = p->q_R;
   g.ko_eps = p->ko_eps;
   g.w_floor = p->w_floor;
+  grid_constants(g);
   return g;
 }
 
-// Device block layout.  float64: y_n, acc, s1, s2 (+ anchor buffer for
-// Sommerfeld).  mixed: y_n, acc in float64; three float stage buffers m[0..2]
-// (m[0] is the float shadow of y_n), each with a float64 W array; float anchors.
+// Device block layout.  float64: y_n, k-sum, s1, s2 (+ anchor buffer for
+// Sommerfeld).  mixed: y_n in float64 (advanced in place); three float stage
+// buffers m[0..2] (m[0] is the float shadow of y_n), each with a float64 W
+// array; the float k-sum with its float64 W; float anchors.
 struct Carve {
-  size_t reg, yn, acc, s1, s2, ksh, part, out16, total;
-  size_t m32[3], mw[3];
+  size_t reg, yn, ks, s1, s2, ksh, part, out16, total;
+  size_t m32[3], mw[3], ks32, ksw;
   int nblocks;
 };
 
@@ -98,8 +100,8 @@ Carve carve(const bssn_params* p, const Grid& g) {
   c.reg = regb;
   size_t o = 0;
   c.yn = o; o += regb;
-  c.acc = o; o += regb;
   if (p->precision == BSSN_FP64) {
+    c.ks = o; o += regb;
     c.s1 = o; o += regb;
     c.s2 = o; o += regb;
     c.ksh = o;
@@ -109,6 +111,8 @@ Carve carve(const bssn_params* p, const Grid& g) {
       c.m32[q] = o; o += reg32;
       c.mw[q] = o; o += wb;
     }
+    c.ks32 = o; o += reg32;
+    c.ksw = o; o += wb;
     c.ksh = o;
     if (p->boundary == BSSN_BC_SOMMERFELD) o += reg32;
   }
@@ -121,6 +125,10 @@ Carve carve(const bssn_params* p, const Grid& g) {
 
 }  // namespace
 
+void bssn::set_last_error(const std::string& msg) { g_last_error = msg; }
+bool bssn::validate_params(const bssn_params* p, std::string& why) { return validate(p, why); }
+Grid bssn::grid_of(const bssn_params* p) { return make_grid(p); }
+
 struct bssn_ctx {
   bssn_params p;
   Grid g;
@@ -128,14 +136,17 @@ struct bssn_ctx {
   cudaStream_t stream;
   char* mem;
   double* yn;
-  double* acc;
+  double* ks;
   double* s1;
   double* s2;
   double* ksh;
   float* m32[3];
   double* mw[3];
+  float* ks32;
+  double* ksw;
   float* ksh32;
   bool shadow_valid;
+  int tile;  // stage-kernel tile configuration (see bssn_autotune)
   double* part;
   double* out16;
   double t;
@@ -213,9 +224,9 @@ bssn_status bssn_alloc(const bssn_params* p, void* d_mem, size_t bytes, void* cu
   ctx->stream = (cudaStream_t)cuda_stream;
   ctx->mem = (char*)d_mem;
   ctx->yn = (double*)(ctx->mem + c.yn);
-  ctx->acc = (double*)(ctx->mem + c.acc);
-  ctx->s1 = (double*)(ctx->mem + c.s1);
-  ctx->s2 = (double*)(ctx->mem + c.s2);
+  ctx->ks = p->precision == BSSN_FP64 ? (double*)(ctx->mem + c.ks) : nullptr;
+  ctx->s1 = p->precision == BSSN_FP64 ? (double*)(ctx->mem + c.s1) : nullptr;
+  ctx->s2 = p->precision == BSSN_FP64 ? (double*)(ctx->mem + c.s2) : nullptr;
   const bool som = p->boundary == BSSN_BC_SOMMERFELD;
   if (p->precision == BSSN_FP64) {
     ctx->ksh = som ? (double*)(ctx->mem + c.ksh) : nullptr;
@@ -224,9 +235,12 @@ bssn_status bssn_alloc(const bssn_params* p, void* d_mem, size_t bytes, void* cu
       ctx->m32[q] = (float*)(ctx->mem + c.m32[q]);
       ctx->mw[q] = (double*)(ctx->mem + c.mw[q]);
     }
+    ctx->ks32 = (float*)(ctx->mem + c.ks32);
+    ctx->ksw = (double*)(ctx->mem + c.ksw);
     ctx->ksh32 = som ? (float*)(ctx->mem + c.ksh) : nullptr;
   }
   ctx->shadow_valid = false;
+  ctx->tile = 0;
   ctx->part = (double*)(ctx->mem + c.part);
   ctx->out16 = (double*)(ctx->mem + c.out16);
   ctx->t = 0.0;
@@ -296,7 +310,7 @@ bssn_status bssn_rhs(bssn_ctx* ctx, const void* d_state, void* d_rhs) {
     a.src = src;
     a.rhs = out;
     a.mode = MODE_RHS;
-    e = launch_stage_fp64(ctx->g, a, ctx->stream);
+    e = launch_stage_fp64(ctx->g, a, ctx->stream, ctx->tile);
     if (e != cudaSuccess) return cuda_fail(e, "bssn_rhs interior");
     if (!ctx->g.periodic) {
       e = launch_sommerfeld(ctx->g, a, nullptr, ctx->stream);
@@ -313,7 +327,7 @@ bssn_status bssn_rhs(bssn_ctx* ctx, const void* d_state, void* d_rhs) {
   a.rhs = out;
   a.w_thr = ctx->p.w_fp64_threshold;
   a.mode = MODE_RHS;
-  e = launch_stage_mixed(ctx->g, a, ctx->stream);
+  e = launch_stage_mixed(ctx->g, a, ctx->stream, ctx->tile);
   if (e != cudaSuccess) return cuda_fail(e, "bssn_rhs interior");
   if (!ctx->g.periodic) {
     e = launch_sommerfeld_mixed(ctx->g, a, nullptr, ctx->stream);
@@ -326,21 +340,23 @@ static bssn_status run_stage(bssn_ctx* ctx, const double* src, int mode, double*
                              double a_dt, double b_dt) {
   StageArgs a{};
   a.src = src;
+  a.src0 = ctx->yn;
   a.yn = ctx->yn;
   a.out0 = out0;
-  a.acc = ctx->acc;
+  a.ksum = ctx->ks;
   a.kshell = ctx->ksh;
   a.a_dt = a_dt;
+  a.a_dtf = (float)a_dt;
   a.b_dt = b_dt;
   a.mode = mode;
   cudaError_t e;
   if (ctx->prof && (e = prof_mark(ctx, ctx->ev_stage)) != cudaSuccess) return cuda_fail(e, "profile");
-  e = launch_stage_fp64(ctx->g, a, ctx->stream);
+  e = launch_stage_fp64(ctx->g, a, ctx->stream, ctx->tile);
   if (e != cudaSuccess) return cuda_fail(e, "stage");
   if (ctx->prof && (e = prof_mark(ctx, ctx->ev_stage)) != cudaSuccess) return cuda_fail(e, "profile");
   if (ctx->prof && (e = prof_mark(ctx, ctx->ev_bc)) != cudaSuccess) return cuda_fail(e, "profile");
   if (ctx->g.periodic) {
-    e = launch_periodic_fill(ctx->g, mode == MODE_LAST ? ctx->acc : out0, ctx->stream);
+    e = launch_periodic_fill(ctx->g, mode == MODE_LAST ? ctx->yn : out0, ctx->stream);
   } else {
     e = launch_sommerfeld(ctx->g, a, ctx->ksh, ctx->stream);
   }
@@ -349,30 +365,34 @@ static bssn_status run_stage(bssn_ctx* ctx, const double* src, int mode, double*
   return BSSN_OK;
 }
 
-// mixed stage: src/out are stage-buffer indices into m32/mw
+// mixed stage: src/out are stage-buffer indices into m32/mw (m[0] = shadow of y_n)
 static bssn_status run_stage_mixed(bssn_ctx* ctx, int src, int mode, int out, double a_dt,
                                    double b_dt) {
   StageArgsMixed a{};
   a.src = ctx->m32[src];
   a.srcw = ctx->mw[src];
+  a.src0 = ctx->m32[0];
+  a.src0w = ctx->mw[0];
   a.yn = ctx->yn;
   a.out0 = ctx->m32[out];
   a.out0w = ctx->mw[out];
-  a.acc = ctx->acc;
+  a.ksum = ctx->ks32;
+  a.ksumw = ctx->ksw;
   a.kshell = ctx->ksh32;
   a.a_dt = a_dt;
+  a.a_dtf = (float)a_dt;
   a.b_dt = b_dt;
   a.w_thr = ctx->p.w_fp64_threshold;
   a.mode = mode;
   cudaError_t e;
   if (ctx->prof && (e = prof_mark(ctx, ctx->ev_stage)) != cudaSuccess) return cuda_fail(e, "profile");
-  e = launch_stage_mixed(ctx->g, a, ctx->stream);
+  e = launch_stage_mixed(ctx->g, a, ctx->stream, ctx->tile);
   if (e != cudaSuccess) return cuda_fail(e, "stage");
   if (ctx->prof && (e = prof_mark(ctx, ctx->ev_stage)) != cudaSuccess) return cuda_fail(e, "profile");
   if (ctx->prof && (e = prof_mark(ctx, ctx->ev_bc)) != cudaSuccess) return cuda_fail(e, "profile");
   if (ctx->g.periodic) {
     e = launch_periodic_fill_mixed(ctx->g, ctx->m32[out], ctx->mw[out], ctx->stream);
-    if (e == cudaSuccess && mode == MODE_LAST) e = launch_periodic_fill(ctx->g, ctx->acc, ctx->stream);
+    if (e == cudaSuccess && mode == MODE_LAST) e = launch_periodic_fill(ctx->g, ctx->yn, ctx->stream);
   } else {
     e = launch_sommerfeld_mixed(ctx->g, a, ctx->ksh32, ctx->stream);
   }
@@ -394,9 +414,9 @@ bssn_status bssn_rk4_step(bssn_ctx* ctx, int32_t nsteps) {
       if (e != cudaSuccess) return cuda_fail(e, "periodic fill");
     }
     if (!mixed) {
-      if ((st = run_stage(ctx, ctx->yn, MODE_FIRST, ctx->s1, 0.5 * dt, dt / 6.0)) != BSSN_OK) return st;
-      if ((st = run_stage(ctx, ctx->s1, MODE_MID, ctx->s2, 0.5 * dt, dt / 3.0)) != BSSN_OK) return st;
-      if ((st = run_stage(ctx, ctx->s2, MODE_MID, ctx->s1, dt, dt / 3.0)) != BSSN_OK) return st;
+      if ((st = run_stage(ctx, ctx->yn, MODE_FIRST, ctx->s1, 0.5 * dt, 0.0)) != BSSN_OK) return st;
+      if ((st = run_stage(ctx, ctx->s1, MODE_MID, ctx->s2, 0.5 * dt, 0.0)) != BSSN_OK) return st;
+      if ((st = run_stage(ctx, ctx->s2, MODE_MID, ctx->s1, dt, 0.0)) != BSSN_OK) return st;
       if ((st = run_stage(ctx, ctx->s1, MODE_LAST, nullptr, 0.0, dt / 6.0)) != BSSN_OK) return st;
     } else {
       if (!ctx->shadow_valid) {
@@ -404,14 +424,11 @@ bssn_status bssn_rk4_step(bssn_ctx* ctx, int32_t nsteps) {
         if (e != cudaSuccess) return cuda_fail(e, "shadow");
         ctx->shadow_valid = true;
       }
-      if ((st = run_stage_mixed(ctx, 0, MODE_FIRST, 1, 0.5 * dt, dt / 6.0)) != BSSN_OK) return st;
-      if ((st = run_stage_mixed(ctx, 1, MODE_MID, 2, 0.5 * dt, dt / 3.0)) != BSSN_OK) return st;
-      if ((st = run_stage_mixed(ctx, 2, MODE_MID, 1, dt, dt / 3.0)) != BSSN_OK) return st;
+      if ((st = run_stage_mixed(ctx, 0, MODE_FIRST, 1, 0.5 * dt, 0.0)) != BSSN_OK) return st;
+      if ((st = run_stage_mixed(ctx, 1, MODE_MID, 2, 0.5 * dt, 0.0)) != BSSN_OK) return st;
+      if ((st = run_stage_mixed(ctx, 2, MODE_MID, 1, dt, 0.0)) != BSSN_OK) return st;
       if ((st = run_stage_mixed(ctx, 1, MODE_LAST, 0, 0.0, dt / 6.0)) != BSSN_OK) return st;
     }
-    double* tmp = ctx->yn;
-    ctx->yn = ctx->acc;
-    ctx->acc = tmp;
     ctx->t += dt;
   }
   return BSSN_OK;
@@ -454,6 +471,69 @@ bssn_status bssn_set_state(bssn_ctx* ctx, const double* host, double t) {
   if (e != cudaSuccess) return cuda_fail(e, "set_state sync");
   ctx->t = t;
   ctx->shadow_valid = false;
+  return BSSN_OK;
+}
+
+int32_t bssn_tile_count(void) { return tile_config_count(); }
+
+const char* bssn_tile_name(int32_t cfg) { return tile_config_name(cfg); }
+
+bssn_status bssn_set_tile(bssn_ctx* ctx, int32_t cfg) {
+  if (!ctx) return fail(BSSN_EINVAL, "ctx is NULL");
+  if (cfg < 0 || cfg >= tile_config_count()) return fail(BSSN_EINVAL, "tile config out of range");
+  ctx->tile = cfg;
+  return BSSN_OK;
+}
+
+bssn_status bssn_autotune(bssn_ctx* ctx, int32_t reps, int32_t* best, double* ms_per_cfg) {
+  if (!ctx || reps < 1) return fail(BSSN_EINVAL, "bad argument");
+  const bool mixed = ctx->p.precision == BSSN_MIXED;
+  if (mixed && !ctx->shadow_valid) {
+    cudaError_t e = launch_shadow(ctx->g, ctx->yn, ctx->m32[0], ctx->mw[0], ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "shadow");
+    ctx->shadow_valid = true;
+  }
+  cudaEvent_t e0, e1;
+  cudaError_t e;
+  if ((e = cudaEventCreate(&e0)) != cudaSuccess) return cuda_fail(e, "event");
+  if ((e = cudaEventCreate(&e1)) != cudaSuccess) { cudaEventDestroy(e0); return cuda_fail(e, "event"); }
+  const int ncfg = tile_config_count();
+  double best_ms = 1e300;
+  int best_c = 0;
+  bssn_status st = BSSN_OK;
+  // the first stage leaves y_n (and its float shadow) unchanged
+  for (int c = 0; c < ncfg && st == BSSN_OK; c++) {
+    auto launch = [&]() -> cudaError_t {
+      if (!mixed) {
+        StageArgs a{};
+        a.src = ctx->yn; a.src0 = ctx->yn; a.yn = ctx->yn; a.out0 = ctx->s1; a.ksum = ctx->ks;
+        a.a_dt = 0.5 * ctx->p.dt; a.mode = MODE_FIRST;
+        return launch_stage_fp64(ctx->g, a, ctx->stream, c);
+      }
+      StageArgsMixed a{};
+      a.src = ctx->m32[0]; a.srcw = ctx->mw[0]; a.src0 = ctx->m32[0]; a.src0w = ctx->mw[0];
+      a.yn = ctx->yn; a.out0 = ctx->m32[1]; a.out0w = ctx->mw[1];
+      a.ksum = ctx->ks32; a.ksumw = ctx->ksw; a.a_dt = 0.5 * ctx->p.dt; a.a_dtf = (float)a.a_dt;
+      a.w_thr = ctx->p.w_fp64_threshold; a.mode = MODE_FIRST;
+      return launch_stage_mixed(ctx->g, a, ctx->stream, c);
+    };
+    if ((e = launch()) != cudaSuccess) { st = cuda_fail(e, "autotune warm-up"); break; }
+    cudaEventRecord(e0, ctx->stream);
+    for (int r = 0; r < reps && e == cudaSuccess; r++) e = launch();
+    cudaEventRecord(e1, ctx->stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    if (e != cudaSuccess) { st = cuda_fail(e, "autotune"); break; }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    const double per = ms / reps;
+    if (ms_per_cfg) ms_per_cfg[c] = per;
+    if (per < best_ms) { best_ms = per; best_c = c; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != BSSN_OK) return st;
+  ctx->tile = best_c;
+  if (best) *best = best_c;
   return BSSN_OK;
 }
 

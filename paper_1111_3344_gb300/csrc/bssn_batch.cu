@@ -1,0 +1,822 @@
+// Batches of independent evolutions advanced together (one persistent launch
+// per RK4 stage under a captured CUDA graph) and the continuous-batching
+// server built on them.
+//
+// A batch owns nothing but host bookkeeping: every device byte comes from the
+// pool the caller passes (tables, then member registers carved by a first-fit
+// sub-allocator).  The graph of one RK4 step is captured once per tile shape;
+// it reads the member table and the work-list from device memory, so members
+// can join and leave between steps without re-capture.
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <new>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "batch_internal.cuh"
+
+using namespace bssn;
+
+namespace {
+
+constexpr size_t ALIGN = 256;
+size_t aup(size_t v) { return (v + ALIGN - 1) / ALIGN * ALIGN; }
+
+bssn_status bfail(bssn_status s, const std::string& m) {
+  set_last_error(m);
+  return s;
+}
+bssn_status bcuda(cudaError_t e, const char* where) {
+  return bfail(BSSN_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+// First-fit sub-allocator over [0, size) with coalescing frees.
+struct Pool {
+  size_t size = 0;
+  std::map<size_t, size_t> free_;  // offset -> length
+  void init(size_t base, size_t sz) {
+    size = sz;
+    free_.clear();
+    if (sz > base) free_[base] = sz - base;
+  }
+  bool alloc(size_t n, size_t& off) {
+    n = aup(n);
+    for (auto it = free_.begin(); it != free_.end(); ++it) {
+      if (it->second >= n) {
+        off = it->first;
+        const size_t rest = it->second - n;
+        free_.erase(it);
+        if (rest) free_[off + n] = rest;
+        return true;
+      }
+    }
+    return false;
+  }
+  void release(size_t off, size_t n) {
+    n = aup(n);
+    auto it = free_.emplace(off, n).first;
+    auto nx = std::next(it);
+    if (nx != free_.end() && it->first + it->second == nx->first) {
+      it->second += nx->second;
+      free_.erase(nx);
+    }
+    if (it != free_.begin()) {
+      auto pv = std::prev(it);
+      if (pv->first + pv->second == it->first) {
+        pv->second += it->second;
+        free_.erase(it);
+      }
+    }
+  }
+};
+
+// Register layout of one member inside its pool block.
+struct MemberLayout {
+  size_t yn, ks, s1, s2, ksh;      // float64 path
+  size_t m32[3], mw[3], ks32, ksw; // mixed path
+  size_t part, out16, total;
+  int nblocks;
+};
+
+MemberLayout member_layout(const bssn_params* p, const Grid& g) {
+  MemberLayout L{};
+  const size_t regb = aup((size_t)NF * g.fstride * sizeof(double));
+  const size_t reg32 = aup((size_t)NF * g.fstride * sizeof(float));
+  const size_t wb = aup((size_t)g.fstride * sizeof(double));
+  const bool som = p->boundary == BSSN_BC_SOMMERFELD;
+  size_t o = 0;
+  L.yn = o; o += regb;
+  if (p->precision == BSSN_FP64) {
+    L.ks = o; o += regb;
+    L.s1 = o; o += regb;
+    L.s2 = o; o += regb;
+    L.ksh = o; if (som) o += regb;
+  } else {
+    for (int q = 0; q < 3; q++) {
+      L.m32[q] = o; o += reg32;
+      L.mw[q] = o; o += wb;
+    }
+    L.ks32 = o; o += reg32;
+    L.ksw = o; o += wb;
+    L.ksh = o; if (som) o += reg32;
+  }
+  L.nblocks = constraints_blocks(g);
+  L.part = o; o += aup((size_t)L.nblocks * 18 * sizeof(double));
+  L.out16 = o; o += aup(16 * sizeof(double));
+  L.total = o;
+  return L;
+}
+
+struct Member {
+  bool used = false, active = false;
+  bssn_params p{};
+  Grid g{};
+  MemberLayout L{};
+  size_t off = 0;
+  double t = 0.0;
+  int npunct = 0;
+  double punct[8][4] = {};
+  long long steps = 0;
+};
+
+}  // namespace
+
+struct bssn_batch {
+  int precision;
+  int maxm;
+  cudaStream_t stream;
+  char* pool;
+  size_t pool_bytes;
+  Pool alloc;
+  std::vector<Member> m;
+  MemberDev* d_mem;
+  BatchWork* d_work;
+  std::vector<MemberDev> h_mem;
+  BatchWork h_work;
+  bool work_dirty = true;
+  int cfg = 0;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  std::mutex mu;  // guards everything above against concurrent API calls
+};
+
+namespace {
+
+char* mptr(bssn_batch* b, const Member& M, size_t off) { return b->pool + M.off + off; }
+
+void fill_member_dev(bssn_batch* b, int id) {
+  Member& M = b->m[id];
+  MemberDev& D = b->h_mem[id];
+  memset(&D, 0, sizeof(D));
+  D.g = M.g;
+  int tx, ty, tz;
+  batch_tile_shape(b->cfg, tx, ty, tz);
+  D.tiles[0] = (M.g.n0 + tx - 1) / tx;
+  D.tiles[1] = (M.g.n1 + ty - 1) / ty;
+  D.tiles[2] = (M.g.n2 + tz - 1) / tz;
+  const double dt = M.p.dt;
+  const double a_dt[4] = {0.5 * dt, 0.5 * dt, dt, 0.0};
+  const double b_dt[4] = {0.0, 0.0, 0.0, dt / 6.0};
+  const int mode[4] = {MODE_FIRST, MODE_MID, MODE_MID, MODE_LAST};
+  const bool som = M.p.boundary == BSSN_BC_SOMMERFELD;
+  if (b->precision == BSSN_FP64) {
+    double* yn = (double*)mptr(b, M, M.L.yn);
+    double* s1 = (double*)mptr(b, M, M.L.s1);
+    double* s2 = (double*)mptr(b, M, M.L.s2);
+    double* src[4] = {yn, s1, s2, s1};
+    double* out[4] = {s1, s2, s1, nullptr};
+    for (int s = 0; s < 4; s++) {
+      StageArgs& a = D.a64[s];
+      a.src = src[s];
+      a.src0 = yn;
+      a.yn = yn;
+      a.out0 = out[s];
+      a.ksum = (double*)mptr(b, M, M.L.ks);
+      a.kshell = som ? (double*)mptr(b, M, M.L.ksh) : nullptr;
+      a.a_dt = a_dt[s];
+      a.b_dt = b_dt[s];
+      a.mode = mode[s];
+    }
+  } else {
+    const int src[4] = {0, 1, 2, 1}, out[4] = {1, 2, 1, 0};
+    for (int s = 0; s < 4; s++) {
+      StageArgsMixed& a = D.amx[s];
+      a.src = (float*)mptr(b, M, M.L.m32[src[s]]);
+      a.srcw = (double*)mptr(b, M, M.L.mw[src[s]]);
+      a.src0 = (float*)mptr(b, M, M.L.m32[0]);
+      a.src0w = (double*)mptr(b, M, M.L.mw[0]);
+      a.yn = (double*)mptr(b, M, M.L.yn);
+      a.out0 = (float*)mptr(b, M, M.L.m32[out[s]]);
+      a.out0w = (double*)mptr(b, M, M.L.mw[out[s]]);
+      a.ksum = (float*)mptr(b, M, M.L.ks32);
+      a.ksumw = (double*)mptr(b, M, M.L.ksw);
+      a.kshell = som ? (float*)mptr(b, M, M.L.ksh) : nullptr;
+      a.a_dt = a_dt[s];
+      a.a_dtf = (float)a_dt[s];
+      a.b_dt = b_dt[s];
+      a.w_thr = M.p.w_fp64_threshold;
+      a.mode = mode[s];
+    }
+  }
+}
+
+cudaError_t upload_member(bssn_batch* b, int id) {
+  return cudaMemcpyAsync(b->d_mem + id, &b->h_mem[id], sizeof(MemberDev), cudaMemcpyHostToDevice,
+                         b->stream);
+}
+
+cudaError_t rebuild_work(bssn_batch* b) {
+  BatchWork& W = b->h_work;
+  W.count = 0;
+  W.total_tiles = 0;
+  W.total_bc = 0;
+  unsigned tb = 0;
+  unsigned long long bb = 0;
+  for (int id = 0; id < b->maxm; id++) {
+    const Member& M = b->m[id];
+    if (!M.used || !M.active) continue;
+    const MemberDev& D = b->h_mem[id];
+    W.member[W.count] = id;
+    W.tile_base[W.count] = tb;
+    W.bc_base[W.count] = bb;
+    tb += (unsigned)D.tiles[0] * D.tiles[1] * D.tiles[2];
+    const unsigned long long ng = ghost_count(M.g);
+    bb += (b->precision == BSSN_MIXED && !M.g.periodic) ? ng * NF : ng;
+    W.count++;
+  }
+  W.tile_base[W.count] = tb;
+  W.bc_base[W.count] = bb;
+  W.total_tiles = tb;
+  W.total_bc = bb;
+  b->work_dirty = false;
+  return cudaMemcpyAsync(b->d_work, &W, sizeof(BatchWork), cudaMemcpyHostToDevice, b->stream);
+}
+
+cudaError_t capture(bssn_batch* b) {
+  if (b->exec) {
+    cudaGraphExecDestroy(b->exec);
+    b->exec = nullptr;
+  }
+  if (b->graph) {
+    cudaGraphDestroy(b->graph);
+    b->graph = nullptr;
+  }
+  cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return e;
+  const bool mixed = b->precision == BSSN_MIXED;
+  for (int s = 0; s < 4 && e == cudaSuccess; s++) {
+    e = launch_batch_stage(b->cfg, mixed, b->d_mem, b->d_work, s, b->stream);
+    if (e == cudaSuccess) e = launch_batch_boundary(mixed, b->d_mem, b->d_work, s, b->stream);
+  }
+  cudaGraph_t g = nullptr;
+  cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
+  if (e == cudaSuccess) e = e2;
+  if (e != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return e;
+  }
+  b->graph = g;
+  return cudaGraphInstantiate(&b->exec, g, 0);
+}
+
+// prepare a member's registers after its y_n was written (periodic ghosts,
+// float shadow for the mixed path)
+cudaError_t after_state(bssn_batch* b, Member& M) {
+  double* yn = (double*)mptr(b, M, M.L.yn);
+  cudaError_t e = cudaSuccess;
+  if (M.g.periodic) e = launch_periodic_fill(M.g, yn, b->stream);
+  if (e == cudaSuccess && b->precision == BSSN_MIXED)
+    e = launch_shadow(M.g, yn, (float*)mptr(b, M, M.L.m32[0]), (double*)mptr(b, M, M.L.mw[0]), b->stream);
+  return e;
+}
+
+bool member_ok(bssn_batch* b, int id) { return b && id >= 0 && id < b->maxm && b->m[id].used; }
+
+}  // namespace
+
+extern "C" {
+
+size_t bssn_batch_member_bytes(const bssn_params* p) {
+  std::string why;
+  if (!validate_params(p, why)) {
+    set_last_error(why);
+    return 0;
+  }
+  Grid g = grid_of(p);
+  return member_layout(p, g).total;
+}
+
+size_t bssn_batch_table_bytes(int32_t max_members) {
+  if (max_members < 1 || max_members > BATCH_MAX) return 0;
+  return aup(sizeof(MemberDev) * (size_t)max_members) + aup(sizeof(BatchWork));
+}
+
+bssn_status bssn_batch_create(int32_t precision, int32_t max_members, void* d_pool, size_t pool_bytes,
+                              void* cuda_stream, bssn_batch** out) {
+  if (!out) return bfail(BSSN_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (precision != BSSN_FP64 && precision != BSSN_MIXED) return bfail(BSSN_EINVAL, "bad precision");
+  if (max_members < 1 || max_members > BATCH_MAX)
+    return bfail(BSSN_EINVAL, "max_members must be 1.." + std::to_string(BATCH_MAX));
+  if (!d_pool || ((uintptr_t)d_pool) % ALIGN) return bfail(BSSN_EINVAL, "d_pool must be non-NULL, 256-byte aligned");
+  if (!cuda_stream) return bfail(BSSN_EINVAL, "a batch needs a non-default stream (graph capture)");
+  const size_t tb = bssn_batch_table_bytes(max_members);
+  if (pool_bytes < tb) return bfail(BSSN_ENOMEM, "pool smaller than the batch tables");
+  bssn_batch* b = new (std::nothrow) bssn_batch();
+  if (!b) return bfail(BSSN_ENOMEM, "host allocation failed");
+  b->precision = precision;
+  b->maxm = max_members;
+  b->stream = (cudaStream_t)cuda_stream;
+  b->pool = (char*)d_pool;
+  b->pool_bytes = pool_bytes;
+  b->alloc.init(tb, pool_bytes);
+  b->m.resize(max_members);
+  b->h_mem.resize(max_members);
+  memset(&b->h_work, 0, sizeof(BatchWork));
+  b->d_mem = (MemberDev*)b->pool;
+  b->d_work = (BatchWork*)(b->pool + aup(sizeof(MemberDev) * (size_t)max_members));
+  cudaError_t e = rebuild_work(b);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) {
+    delete b;
+    return bcuda(e, "batch create");
+  }
+  *out = b;
+  return BSSN_OK;
+}
+
+bssn_status bssn_batch_free(bssn_batch* b) {
+  if (!b) return bfail(BSSN_EINVAL, "batch is NULL");
+  cudaError_t e = cudaStreamSynchronize(b->stream);
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  delete b;
+  if (e != cudaSuccess) return bcuda(e, "batch free");
+  return BSSN_OK;
+}
+
+bssn_status bssn_batch_add(bssn_batch* b, const bssn_params* p, int32_t* member) {
+  if (!b || !p || !member) return bfail(BSSN_EINVAL, "NULL argument");
+  std::lock_guard<std::mutex> lk(b->mu);
+  std::string why;
+  if (!validate_params(p, why)) return bfail(BSSN_EINVAL, why);
+  if (p->precision != b->precision) return bfail(BSSN_EINVAL, "member precision differs from the batch's");
+  int id = -1;
+  for (int q = 0; q < b->maxm; q++)
+    if (!b->m[q].used) { id = q; break; }
+  if (id < 0) return bfail(BSSN_ENOMEM, "batch is full");
+  Member M;
+  M.used = true;
+  M.p = *p;
+  M.g = grid_of(p);
+  M.L = member_layout(p, M.g);
+  if (!b->alloc.alloc(M.L.total, M.off))
+    return bfail(BSSN_ENOMEM, "pool exhausted: member needs " + std::to_string(M.L.total) + " bytes");
+  b->m[id] = M;
+  fill_member_dev(b, id);
+  cudaError_t e = upload_member(b, id);
+  if (e != cudaSuccess) return bcuda(e, "batch add");
+  *member = id;
+  return BSSN_OK;
+}
+
+bssn_status bssn_batch_remove(bssn_batch* b, int32_t id) {
+  if (!b) return bfail(BSSN_EINVAL, "batch is NULL");
+  std::lock_guard<std::mutex> lk(b->mu);
+  if (!member_ok(b, id)) return bfail(BSSN_ENOTFOUND, "no such member");
+  // in-flight graph replays may still read the member's registers
+  cudaError_t e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) return bcuda(e, "batch remove");
+  Member& M = b->m[id];
+  const bool was_active = M.active;
+  b->alloc.release(M.off, M.L.total);
+  M = Member();
+  if (was_active) b->work_dirty = true;
+  return BSSN_OK;
+}
+
+bssn_status bssn_batch_set_initial_data(bssn_batch* b, int32_t id, int32_t kind, const double* p,
+                                        int32_t np) {
+  if (!b) return bfail(BSSN_EINVAL, "batch is NULL");
+  std::lock_guard<std::mutex> lk(b->mu);
+  if (!member_ok(b, id)) return bfail(BSSN_ENOTFOUND, "no such member");
+  if (np < 0 || (np > 0 && !p) || np > 33) return bfail(BSSN_EINVAL, "bad parameter array");
+  Member& M = b->m[id];
+  int npunct = 0;
+  if (kind == BSSN_ID_BL) {
+    if (np < 1) return bfail(BSSN_EINVAL, "BL needs {npunct, m, x, y, z, ...}");
+    npunct = (int)p[0];
+    if (npunct < 1 || npunct > 8 || (double)npunct != p[0] || np < 1 + 4 * npunct)
+      return bfail(BSSN_EINVAL, "BL: npunct must be 1..8 with 4 values each");
+  } else if (kind == BSSN_ID_GAUGE_WAVE) {
+    if (np < 2 || !(p[1] != 0.0) || !(std::fabs(p[0]) < 1.0)) return bfail(BSSN_EINVAL, "gauge wave: {A, d}");
+  } else if (kind == BSSN_ID_KASNER) {
+    if (np < 1 || !(p[0] > 0.0)) return bfail(BSSN_EINVAL, "Kasner needs {t0 > 0}");
+  } else if (kind != BSSN_ID_FLAT) {
+    return bfail(BSSN_EINVAL, "unknown initial-data kind");
+  }
+  double* yn = (double*)mptr(b, M, M.L.yn);
+  cudaError_t e = launch_initial_data(M.g, kind, p, np, yn, b->stream);
+  if (e == cudaSuccess) e = after_state(b, M);
+  if (e != cudaSuccess) return bcuda(e, "batch initial data");
+  M.npunct = npunct;
+  for (int a = 0; a < npunct; a++)
+    for (int q = 0; q < 4; q++) M.punct[a][q] = p[1 + 4 * a + q];
+  M.t = 0.0;
+  M.steps = 0;
+  if (!M.active) b->work_dirty = true;
+  M.active = true;
+  return BSSN_OK;
+}
+
+bssn_status bssn_batch_set_state(bssn_batch* b, int32_t id, const double* host, double t) {
+  if (!b || !host) return bfail(BSSN_EINVAL, "NULL argument");
+  std::lock_guard<std::mutex> lk(b->mu);
+  if (!member_ok(b, id)) return bfail(BSSN_ENOTFOUND, "no such member");
+  Member& M = b->m[id];
+  const Grid& g = M.g;
+  double* yn = (double*)mptr(b, M, M.L.yn);
+  cudaError_t e = cudaMemcpy2DAsync(yn, (size_t)g.pitch * 8, host, (size_t)g.sx * 8, (size_t)g.sx * 8,
+                                    (size_t)NF * g.sz * g.sy, cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess) e = after_state(b, M);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) return bcuda(e, "batch set_state");
+  M.t = t;
+  if (!M.active) b->work_dirty = true;
+  M.active = true;
+  return BSSN_OK;
+}
+
+bssn_status bssn_batch_get_state(bssn_batch* b, int32_t id, double* host, double* t) {
+  if (!b || !host) return bfail(BSSN_EINVAL, "NULL argument");
+  std::lock_guard<std::mutex> lk(b->mu);
+  if (!member_ok(b, id)) return bfail(BSSN_ENOTFOUND, "no such member");
+  Member& M = b->m[id];
+  const Grid& g = M.g;
+  const double* yn = (const double*)mptr(b, M, M.L.yn);
+  cudaError_t e = cudaMemcpy2DAsync(host, (size_t)g.sx * 8, yn, (size_t)g.pitch * 8, (size_t)g.sx * 8,
+                                    (size_t)NF * g.sz * g.sy, cudaMemcpyDeviceToHost, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) return bcuda(e, "batch get_state");
+  if (t) *t = M.t;
+  return BSSN_OK;
+}
+
+bssn_status bssn_batch_step(bssn_batch* b, int32_t nsteps) {
+  if (!b) return bfail(BSSN_EINVAL, "batch is NULL");
+  if (nsteps < 0) return bfail(BSSN_EINVAL, "nsteps < 0");
+  std::lock_guard<std::mutex> lk(b->mu);
+  cudaError_t e = cudaSuccess;
+  if (b->work_dirty) e = rebuild_work(b);
+  if (e == cudaSuccess && !b->exec) e = capture(b);
+  if (e != cudaSuccess) return bcuda(e, "batch step setup");
+  if (b->h_work.count == 0) return BSSN_OK;
+  for (int s = 0; s < nsteps; s++) {
+    e = cudaGraphLaunch(b->exec, b->stream);
+    if (e != cudaSuccess) return bcuda(e, "batch graph launch");
+  }
+  for (int id = 0; id < b->maxm; id++) {
+    Member& M = b->m[id];
+    if (M.used && M.active) {
+      M.t += nsteps * M.p.dt;
+      M.steps += nsteps;
+    }
+  }
+  return BSSN_OK;
+}
+
+bssn_status bssn_batch_constraints(bssn_batch* b, int32_t id, double out[16]) {
+  if (!b || !out) return bfail(BSSN_EINVAL, "NULL argument");
+  std::lock_guard<std::mutex> lk(b->mu);
+  if (!member_ok(b, id)) return bfail(BSSN_ENOTFOUND, "no such member");
+  Member& M = b->m[id];
+  double* dout = (double*)mptr(b, M, M.L.out16);
+  cudaError_t e = launch_constraints(M.g, (const double*)mptr(b, M, M.L.yn), &M.punct[0][0], M.npunct,
+                                     M.p.r_excise, (double*)mptr(b, M, M.L.part), M.L.nblocks, dout,
+                                     b->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(out, dout, 16 * sizeof(double), cudaMemcpyDeviceToHost, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) return bcuda(e, "batch constraints");
+  return BSSN_OK;
+}
+
+int32_t bssn_batch_tile_count(void) { return batch_tile_config_count(); }
+const char* bssn_batch_tile_name(int32_t c) { return batch_tile_config_name(c); }
+
+bssn_status bssn_batch_set_tile(bssn_batch* b, int32_t cfg) {
+  if (!b) return bfail(BSSN_EINVAL, "batch is NULL");
+  std::lock_guard<std::mutex> lk(b->mu);
+  if (cfg < 0 || cfg >= batch_tile_config_count()) return bfail(BSSN_EINVAL, "tile config out of range");
+  cudaError_t e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) return bcuda(e, "set tile");
+  b->cfg = cfg;
+  for (int id = 0; id < b->maxm; id++)
+    if (b->m[id].used) {
+      fill_member_dev(b, id);
+      if ((e = upload_member(b, id)) != cudaSuccess) return bcuda(e, "set tile upload");
+    }
+  b->work_dirty = true;
+  if (b->exec) {
+    cudaGraphExecDestroy(b->exec);
+    b->exec = nullptr;
+  }
+  if (b->graph) {
+    cudaGraphDestroy(b->graph);
+    b->graph = nullptr;
+  }
+  return BSSN_OK;
+}
+
+bssn_status bssn_batch_autotune(bssn_batch* b, int32_t reps, int32_t* best, double* ms_per_cfg) {
+  if (!b || reps < 1) return bfail(BSSN_EINVAL, "bad argument");
+  const int n = batch_tile_config_count();
+  double best_ms = 1e300;
+  int best_c = 0;
+  cudaEvent_t e0, e1;
+  cudaError_t e;
+  if ((e = cudaEventCreate(&e0)) != cudaSuccess) return bcuda(e, "event");
+  if ((e = cudaEventCreate(&e1)) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return bcuda(e, "event");
+  }
+  bssn_status st = BSSN_OK;
+  for (int c = 0; c < n && st == BSSN_OK; c++) {
+    if ((st = bssn_batch_set_tile(b, c)) != BSSN_OK) break;
+    std::lock_guard<std::mutex> lk(b->mu);
+    if (b->work_dirty && (e = rebuild_work(b)) != cudaSuccess) { st = bcuda(e, "autotune"); break; }
+    // stage 0 writes only stage buffers and the k-sum: y_n is left unchanged
+    const bool mixed = b->precision == BSSN_MIXED;
+    e = launch_batch_stage(c, mixed, b->d_mem, b->d_work, 0, b->stream);
+    cudaEventRecord(e0, b->stream);
+    for (int r = 0; r < reps && e == cudaSuccess; r++)
+      e = launch_batch_stage(c, mixed, b->d_mem, b->d_work, 0, b->stream);
+    cudaEventRecord(e1, b->stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    if (e != cudaSuccess) { st = bcuda(e, "autotune"); break; }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms_per_cfg) ms_per_cfg[c] = ms / reps;
+    if (ms / reps < best_ms) { best_ms = ms / reps; best_c = c; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != BSSN_OK) return st;
+  if (best) *best = best_c;
+  return bssn_batch_set_tile(b, best_c);
+}
+
+}  // extern "C"
+
+// ================================================================ server
+//
+// Continuous batching: a scheduler thread owns a batch.  At every step
+// boundary it admits queued requests (in arrival order, skipping any that do
+// not fit) while their register bytes fit in the HBM budget and the batch has
+// a slot, sets their initial data on the device, advances every resident
+// evolution one RK4 step in one batched graph replay, and retires the ones
+// that reached their step count: their constraint norms are read back, a
+// NaN/Inf marks only that request failed, and their registers return to the
+// pool.  State stays on the device from admission to retirement.
+namespace {
+
+double now_s() {
+  using namespace std::chrono;
+  return duration<double>(steady_clock::now().time_since_epoch()).count();
+}
+
+struct Req {
+  uint64_t ticket;
+  bssn_params p;
+  int kind;
+  std::vector<double> idp;
+  int nsteps;
+  double t_submit;
+  size_t bytes;
+};
+
+struct Res {
+  bool done = false;
+  bssn_status status = BSSN_EAGAIN;
+  double norms[16] = {};
+  double latency = 0.0;
+};
+
+struct Act {
+  uint64_t ticket;
+  int remaining;
+  size_t bytes;
+  double t_submit;
+  long long points;  // interior points
+};
+
+}  // namespace
+
+struct bssn_server {
+  bssn_batch* batch = nullptr;
+  size_t budget = 0, used = 0;
+  std::mutex mu;
+  std::condition_variable cv;
+  std::deque<Req> queue;
+  std::map<uint64_t, Res> results;
+  std::map<int, Act> active;
+  std::thread th;
+  std::atomic<bool> stop{false};
+  uint64_t next_ticket = 1;
+  // statistics
+  double t_start = 0.0, busy = 0.0;
+  double point_updates = 0.0;
+  uint64_t completed = 0, failed = 0;
+  std::string error;
+};
+
+namespace {
+
+void retire(bssn_server* S, int id, const Act& a) {
+  Res r;
+  double norms[16];
+  bssn_status st = bssn_batch_constraints(S->batch, id, norms);
+  bool bad = st != BSSN_OK;
+  if (!bad)
+    for (int q = 0; q < 16; q++) bad |= !std::isfinite(norms[q]);
+  r.done = true;
+  r.status = st != BSSN_OK ? st : (bad ? BSSN_EFAILED : BSSN_OK);
+  if (st == BSSN_OK) memcpy(r.norms, norms, sizeof(norms));
+  r.latency = now_s() - a.t_submit;
+  bssn_batch_remove(S->batch, id);
+  std::lock_guard<std::mutex> lk(S->mu);
+  S->used -= a.bytes;
+  S->results[a.ticket] = r;
+  S->completed++;
+  if (r.status != BSSN_OK) S->failed++;
+}
+
+void scheduler(bssn_server* S) {
+  while (!S->stop.load()) {
+    // ---- admit at the step boundary
+    std::vector<Req> admit;
+    {
+      std::unique_lock<std::mutex> lk(S->mu);
+      if (S->active.empty() && S->queue.empty()) {
+        S->cv.wait_for(lk, std::chrono::milliseconds(2));
+        continue;
+      }
+      size_t free_b = S->budget - S->used;
+      int slots = BSSN_BATCH_MAX_MEMBERS - (int)S->active.size();
+      for (auto it = S->queue.begin(); it != S->queue.end() && slots > 0;) {
+        if (it->bytes <= free_b) {
+          free_b -= it->bytes;
+          S->used += it->bytes;
+          slots--;
+          admit.push_back(std::move(*it));
+          it = S->queue.erase(it);
+        } else {
+          ++it;
+        }
+      }
+    }
+    for (Req& r : admit) {
+      int32_t id = -1;
+      bssn_status st = bssn_batch_add(S->batch, &r.p, &id);
+      if (st == BSSN_OK)
+        st = bssn_batch_set_initial_data(S->batch, id, r.kind, r.idp.data(), (int32_t)r.idp.size());
+      if (st != BSSN_OK) {
+        if (id >= 0) bssn_batch_remove(S->batch, id);
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->used -= r.bytes;
+        if (st == BSSN_ENOMEM) {  // pool fragmented: retry at a later boundary
+          S->queue.push_front(std::move(r));
+        } else {
+          Res res;
+          res.done = true;
+          res.status = st;
+          res.latency = now_s() - r.t_submit;
+          S->results[r.ticket] = res;
+          S->completed++;
+          S->failed++;
+        }
+        continue;
+      }
+      Act a{r.ticket, r.nsteps, r.bytes, r.t_submit,
+            (long long)r.p.n[0] * r.p.n[1] * r.p.n[2]};
+      if (a.remaining <= 0) {
+        retire(S, id, a);
+        continue;
+      }
+      std::lock_guard<std::mutex> lk(S->mu);
+      S->active[id] = a;
+    }
+    std::vector<std::pair<int, Act>> done;
+    {
+      std::lock_guard<std::mutex> lk(S->mu);
+      if (S->active.empty()) continue;
+    }
+    // ---- one RK4 step for every resident evolution
+    const double t0 = now_s();
+    bssn_status st = bssn_batch_step(S->batch, 1);
+    cudaError_t e = cudaStreamSynchronize(S->batch->stream);
+    const double t1 = now_s();
+    {
+      std::lock_guard<std::mutex> lk(S->mu);
+      S->busy += t1 - t0;
+      if (st != BSSN_OK || e != cudaSuccess) {
+        S->error = st != BSSN_OK ? std::string("batch step failed") : cudaGetErrorString(e);
+        S->stop = true;
+        break;
+      }
+      for (auto it = S->active.begin(); it != S->active.end();) {
+        S->point_updates += (double)it->second.points;
+        if (--it->second.remaining <= 0) {
+          done.push_back(*it);
+          it = S->active.erase(it);
+        } else {
+          ++it;
+        }
+      }
+    }
+    for (auto& d : done) retire(S, d.first, d.second);
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+bssn_status bssn_server_create(int32_t precision, size_t hbm_budget_bytes, void* d_pool,
+                               size_t pool_bytes, void* cuda_stream, bssn_server** out) {
+  if (!out) return bfail(BSSN_EINVAL, "out is NULL");
+  *out = nullptr;
+  bssn_batch* b = nullptr;
+  bssn_status st = bssn_batch_create(precision, BSSN_BATCH_MAX_MEMBERS, d_pool, pool_bytes,
+                                     cuda_stream, &b);
+  if (st != BSSN_OK) return st;
+  bssn_server* S = new (std::nothrow) bssn_server();
+  if (!S) {
+    bssn_batch_free(b);
+    return bfail(BSSN_ENOMEM, "host allocation failed");
+  }
+  S->batch = b;
+  const size_t cap = pool_bytes - bssn_batch_table_bytes(BSSN_BATCH_MAX_MEMBERS);
+  S->budget = std::min(hbm_budget_bytes, cap);
+  S->t_start = now_s();
+  S->th = std::thread(scheduler, S);
+  *out = S;
+  return BSSN_OK;
+}
+
+bssn_status bssn_submit(bssn_server* S, const bssn_params* p, int32_t id_kind, const double* id_p,
+                        int32_t np, int32_t nsteps, uint64_t* ticket) {
+  if (!S || !p || !ticket || nsteps < 0 || np < 0 || (np > 0 && !id_p) || np > 33)
+    return bfail(BSSN_EINVAL, "bad argument");
+  const size_t bytes = bssn_batch_member_bytes(p);
+  if (bytes == 0) return BSSN_EINVAL;  // message set by validation
+  if (p->precision != S->batch->precision) return bfail(BSSN_EINVAL, "request precision differs from the server's");
+  if (bytes > S->budget)
+    return bfail(BSSN_EINVAL, "request needs " + std::to_string(bytes) + " bytes, more than the whole budget");
+  Req r;
+  r.p = *p;
+  r.kind = id_kind;
+  r.idp.assign(id_p, id_p + np);
+  r.nsteps = nsteps;
+  r.t_submit = now_s();
+  r.bytes = bytes;
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    if (S->stop.load()) return bfail(BSSN_EFAILED, "server stopped: " + S->error);
+    r.ticket = S->next_ticket++;
+    S->results[r.ticket] = Res();
+    *ticket = r.ticket;
+    S->queue.push_back(std::move(r));
+  }
+  S->cv.notify_one();
+  return BSSN_OK;
+}
+
+bssn_status bssn_poll(bssn_server* S, uint64_t ticket, double norms_out[16], double* latency_s) {
+  if (!S) return bfail(BSSN_EINVAL, "server is NULL");
+  std::lock_guard<std::mutex> lk(S->mu);
+  auto it = S->results.find(ticket);
+  if (it == S->results.end()) return bfail(BSSN_ENOTFOUND, "unknown ticket");
+  if (!it->second.done) {
+    if (S->stop.load()) return bfail(BSSN_EFAILED, "server stopped: " + S->error);
+    return BSSN_EAGAIN;
+  }
+  if (norms_out) memcpy(norms_out, it->second.norms, sizeof(it->second.norms));
+  if (latency_s) *latency_s = it->second.latency;
+  return it->second.status;
+}
+
+/* out: [0] completed, [1] failed, [2] queued, [3] resident, [4] interior
+ * point-updates, [5] busy seconds, [6] wall seconds since create, [7] bytes in use */
+bssn_status bssn_server_stats(bssn_server* S, double out[8]) {
+  if (!S || !out) return bfail(BSSN_EINVAL, "NULL argument");
+  std::lock_guard<std::mutex> lk(S->mu);
+  out[0] = (double)S->completed;
+  out[1] = (double)S->failed;
+  out[2] = (double)S->queue.size();
+  out[3] = (double)S->active.size();
+  out[4] = S->point_updates;
+  out[5] = S->busy;
+  out[6] = now_s() - S->t_start;
+  out[7] = (double)S->used;
+  return BSSN_OK;
+}
+
+bssn_status bssn_server_destroy(bssn_server* S) {
+  if (!S) return bfail(BSSN_EINVAL, "server is NULL");
+  S->stop = true;
+  S->cv.notify_all();
+  if (S->th.joinable()) S->th.join();
+  bssn_status st = bssn_batch_free(S->batch);
+  delete S;
+  return st;
+}
+
+}  // extern "C"

@@ -2,6 +2,7 @@
 // Not part of the public ABI (include/bssn.h is).
 #pragma once
 #include <cstdint>
+#include <string>
 #include <cuda_runtime.h>
 
 #include "bssn.h"
@@ -37,34 +38,119 @@ struct Grid {
   double eta, q_R;       // q_R <= 0 or inf: q == 1
   double ko_eps;
   double w_floor;
+  // stencil and boundary constants, precomputed on the host in both
+  // precisions (a float64 division or conversion costs a slot of the slow
+  // float64 pipe on every thread that would otherwise compute it)
+  double i12h, i12h2, i144h2, kos, i2h;  // 1/(12h), 1/(12h^2), 1/(144h^2), eps/(64h), 1/(2h)
+  float i12hf, i12h2f, i144h2f, kosf, i2hf, w_floorf, etaf, hf;
+  float xminf[3];
 };
+
+// Host-side fill of the derived constants of a Grid.
+inline void grid_constants(Grid& g) {
+  g.i12h = 1.0 / (12.0 * g.h);
+  g.i12h2 = 1.0 / (12.0 * g.h * g.h);
+  g.i144h2 = 1.0 / (144.0 * g.h * g.h);
+  g.kos = g.ko_eps / (64.0 * g.h);
+  g.i2h = 0.5 / g.h;
+  g.i12hf = (float)g.i12h;
+  g.i12h2f = (float)g.i12h2;
+  g.i144h2f = (float)g.i144h2;
+  g.kosf = (float)g.kos;
+  g.i2hf = (float)g.i2h;
+  g.w_floorf = (float)g.w_floor;
+  g.etaf = (float)g.eta;
+  g.hf = (float)g.h;
+  g.xminf[0] = (float)g.xmin0;
+  g.xminf[1] = (float)g.xmin1;
+  g.xminf[2] = (float)g.xmin2;
+}
+
+// Pick the float64 or float copy of a constant.
+template <typename T>
+__host__ __device__ __forceinline__ T gc(double d, float f);
+template <>
+__host__ __device__ __forceinline__ double gc<double>(double d, float) { return d; }
+template <>
+__host__ __device__ __forceinline__ float gc<float>(double, float f) { return f; }
 
 __host__ __device__ inline long long lin(const Grid& g, int i, int j, int k) {
   return (long long)k * g.plane + (long long)j * g.pitch + i;
 }
 
-// RK4 stage combination modes of the fused stage kernel.
+// Ghost points of a grid, enumerated compactly: the three bottom and three top
+// z-slabs (whole planes), then per interior z-plane the three front and three
+// back y-rows (whole rows) and the three left and three right points of every
+// interior row.  Consecutive indices are mostly consecutive in x.
+__host__ __device__ inline unsigned ghost_count(const Grid& g) {
+  return 6u * g.sx * g.sy + (unsigned)g.n2 * (6u * g.sx + 6u * g.n1);
+}
+__host__ __device__ inline void ghost_decode(const Grid& g, unsigned q, int& i, int& j, int& k) {
+  const unsigned pl = (unsigned)g.sx * g.sy;
+  const unsigned slab = 3u * pl;
+  if (q < 2u * slab) {
+    const unsigned top = q >= slab;
+    const unsigned r = q - top * slab;
+    k = (int)(r / pl) + (top ? GH + g.n2 : 0);
+    const unsigned rem = r % pl;
+    j = (int)(rem / g.sx);
+    i = (int)(rem % g.sx);
+    return;
+  }
+  const unsigned per = 6u * g.sx + 6u * g.n1;
+  const unsigned q2 = q - 2u * slab;
+  k = GH + (int)(q2 / per);
+  unsigned r = q2 % per;
+  if (r < 3u * g.sx) {
+    j = (int)(r / g.sx);
+    i = (int)(r % g.sx);
+  } else if (r < 6u * g.sx) {
+    r -= 3u * g.sx;
+    j = GH + g.n1 + (int)(r / g.sx);
+    i = (int)(r % g.sx);
+  } else {
+    r -= 6u * g.sx;
+    j = GH + (int)(r / 6u);
+    const int c = (int)(r % 6u);
+    i = c < GH ? c : GH + g.n0 + (c - GH);
+  }
+}
+
+// RK4 stage combination modes of the fused stage kernel.  Classical RK4 as
+//   y_{n+1} = y_n + dt/6 (k1 + 2 k2 + 2 k3 + k4),
+// with y_n advanced in place once per step and the weighted sum of the k kept
+// in a k-sum register (a, b below already include dt):
+//   FIRST  out0 <- base + a k ; ksum <- k          (k = k1, source y_n)
+//   MID    out0 <- base + a k ; ksum <- ksum + 2 k  (k2, k3)
+//   LAST   yn   <- yn + b (ksum + k)                (k4, b = dt/6)
+// base is y_n (float64 path) or the float shadow of y_n (mixed path, where
+// LAST also refreshes that shadow into out0).  MODE_RHS writes k to rhs.
 enum StageMode : int {
-  MODE_RHS = 0,     // rhs <- k
-  MODE_FIRST = 1,   // out0 <- yn + a dt k ; acc <- yn + b dt k
-  MODE_MID = 2,     // out0 <- yn + a dt k ; acc <- acc + b dt k
-  MODE_LAST = 3,    // acc <- acc + b dt k ; out0 <- acc (mixed: float shadow of y_{n+1})
+  MODE_RHS = 0,
+  MODE_FIRST = 1,
+  MODE_MID = 2,
+  MODE_LAST = 3,
 };
 
 // Arguments of a fused stage.  S is the storage type of the stage buffers:
 // double on the float64 path; float on the mixed path, where every stage
-// buffer also carries W (field 0) in float64 in a separate array (w suffix).
+// buffer also carries W (field 0) in float64 in a separate array (w suffix)
+// and the float fields hold X - X0 (see background()).
 template <typename S>
 struct StageArgsT {
   const S* src;          // stage input state (stencil source)
   const double* srcw;    // mixed: float64 W of the stage input (else null)
-  const double* yn;      // y_n (float64)
+  const S* src0;         // base of the stage values: y_n (float64) / its float shadow (mixed)
+  const double* src0w;   // mixed: float64 W of the shadow
+  double* yn;            // y_n (float64), advanced in place by LAST
   S* out0;               // next stage state (FIRST/MID); mixed LAST: shadow of y_{n+1}
   double* out0w;         // mixed: float64 W of out0 (else null)
-  double* acc;           // accumulator (float64)
+  S* ksum;               // k1 + 2 k2 + 2 k3
+  double* ksumw;         // mixed: the same for W in float64
   double* rhs;           // MODE_RHS output (float64 register)
   S* kshell;             // if non-null: k at interior points next to the outer boundary
   double a_dt, b_dt;     // stage coefficients times dt
+  float a_dtf;           // a_dt as float (mixed stage values)
   double w_thr;          // mixed: W below this -> W right-hand side in float64
   int mode;
 };
@@ -72,8 +158,10 @@ using StageArgs = StageArgsT<double>;
 using StageArgsMixed = StageArgsT<float>;
 
 // Launch wrappers (defined in the .cu files); all return cudaError_t of the launch.
-cudaError_t launch_stage_fp64(const Grid& g, const StageArgs& a, cudaStream_t s);
-cudaError_t launch_stage_mixed(const Grid& g, const StageArgsMixed& a, cudaStream_t s);
+cudaError_t launch_stage_fp64(const Grid& g, const StageArgs& a, cudaStream_t s, int cfg = 0);
+cudaError_t launch_stage_mixed(const Grid& g, const StageArgsMixed& a, cudaStream_t s, int cfg = 0);
+int tile_config_count();
+const char* tile_config_name(int c);
 cudaError_t launch_sommerfeld(const Grid& g, const StageArgs& a, const double* kanchor,
                               cudaStream_t s);
 cudaError_t launch_sommerfeld_mixed(const Grid& g, const StageArgsMixed& a, const float* kanchor,
@@ -87,5 +175,11 @@ cudaError_t launch_constraints(const Grid& g, const double* y, const double* dpu
                                int npunct, double r_excise, double* partials, int nblocks,
                                double* dout16, cudaStream_t s);
 int constraints_blocks(const Grid& g);
+
+// Sets the message bssn_last_error() returns on the calling thread.
+void set_last_error(const std::string& msg);
+// Parameter validation and grid description shared by the context and batch paths.
+bool validate_params(const bssn_params* p, std::string& why);
+Grid grid_of(const bssn_params* p);
 
 }  // namespace bssn

@@ -1,0 +1,166 @@
+// Batched evolutions: one persistent launch per RK4 stage over the tiles of
+// every active member, and one launch for all their boundaries.
+//
+// Blocks stride over the global tile index; a tile's member is found by binary
+// search in the work-list prefix sums, its grid and stage arguments are staged
+// in shared memory, and each thread runs the same per-point stage function as
+// the single-grid kernels (stage_point.cuh) -- so a member's result does not
+// depend on which other members share the launch, or on the tile shape.
+#include <cuda_runtime.h>
+
+#include "batch_internal.cuh"
+#include "boundary_point.cuh"
+#include "stage_point.cuh"
+
+namespace bssn {
+
+__device__ __forceinline__ int find_member(const unsigned* base, int count, unsigned t) {
+  int lo = 0, hi = count;  // largest lo with base[lo] <= t
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (base[mid] <= t) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ int find_member64(const unsigned long long* base, int count,
+                                             unsigned long long t) {
+  int lo = 0, hi = count;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (base[mid] <= t) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+template <int TX, int TY, int TZ, int MINB, bool MIXED>
+__global__ void __launch_bounds__(TX * TY * TZ, MINB)
+    batch_stage_kernel(const MemberDev* __restrict__ mem, const BatchWork* __restrict__ wk, int stage) {
+  using Args = StageArgsT<typename std::conditional<MIXED, float, double>::type>;
+  __shared__ Grid sg;
+  __shared__ Args sa;
+  __shared__ int stile[3];
+  __shared__ unsigned slocal;
+  const int tid = threadIdx.x + TX * (threadIdx.y + TY * threadIdx.z);
+  const unsigned total = wk->total_tiles;
+  const int count = wk->count;
+  for (unsigned t = blockIdx.x; t < total; t += gridDim.x) {
+    __syncthreads();  // the previous tile is done with the shared arguments
+    if (tid == 0) {
+      const int slot = find_member(wk->tile_base, count, t);
+      const MemberDev& M = mem[wk->member[slot]];
+      sg = M.g;
+      if constexpr (MIXED) sa = M.amx[stage];
+      else sa = M.a64[stage];
+      stile[0] = M.tiles[0];
+      stile[1] = M.tiles[1];
+      stile[2] = M.tiles[2];
+      slocal = t - wk->tile_base[slot];
+    }
+    __syncthreads();
+    unsigned lt = slocal;
+    const int bx = (int)(lt % (unsigned)stile[0]);
+    lt /= (unsigned)stile[0];
+    const int by = (int)(lt % (unsigned)stile[1]);
+    const int bz = (int)(lt / (unsigned)stile[1]);
+    const int ii = bx * TX + threadIdx.x, jj = by * TY + threadIdx.y, kk = bz * TZ + threadIdx.z;
+    if (ii < sg.n0 && jj < sg.n1 && kk < sg.n2) {
+      if constexpr (MIXED) stage_point_mixed(sg, sa, ii, jj, kk);
+      else stage_point_fp64(sg, sa, ii, jj, kk);
+    }
+  }
+}
+
+template <bool MIXED>
+__global__ void batch_boundary_kernel(const MemberDev* __restrict__ mem, const BatchWork* __restrict__ wk,
+                                      int stage) {
+  const unsigned long long total = wk->total_bc;
+  const int count = wk->count;
+  for (unsigned long long t = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (unsigned long long)gridDim.x * blockDim.x) {
+    const int slot = find_member64(wk->bc_base, count, t);
+    const MemberDev& M = mem[wk->member[slot]];
+    const unsigned long long local = t - wk->bc_base[slot];
+    if (M.g.periodic) {
+      const unsigned q = (unsigned)local;
+      if constexpr (MIXED) {
+        const StageArgsMixed& a = M.amx[stage];
+        periodic_point<float>(M.g, a.out0, a.out0w, q);
+        if (a.mode == MODE_LAST) periodic_point<double>(M.g, a.yn, nullptr, q);
+      } else {
+        const StageArgs& a = M.a64[stage];
+        periodic_point<double>(M.g, a.mode == MODE_LAST ? a.yn : a.out0, nullptr, q);
+      }
+    } else if constexpr (MIXED) {
+      const unsigned ng = ghost_count(M.g);
+      const int f = (int)(local / ng);
+      const StageArgsMixed& a = M.amx[stage];
+      sommerfeld_point_mixed(M.g, a, a.kshell, (unsigned)(local - (unsigned long long)f * ng), f);
+    } else {
+      const StageArgs& a = M.a64[stage];
+      sommerfeld_point_fp64(M.g, a, a.kshell, (unsigned)local);
+    }
+  }
+}
+
+// ------------------------------------------------------------ dispatch
+struct BatchCfg {
+  const char* name;
+  int tx, ty, tz;
+  const void* k64;
+  const void* kmx;
+};
+
+#define BCFG(TX, TY, TZ, MINB)                                                       \
+  { #TX "x" #TY "x" #TZ "/" #MINB, TX, TY, TZ,                                      \
+    (const void*)batch_stage_kernel<TX, TY, TZ, MINB, false>,                       \
+    (const void*)batch_stage_kernel<TX, TY, TZ, MINB, true> }
+static const BatchCfg k_bcfg[] = {
+    BCFG(32, 8, 1, 1), BCFG(32, 2, 2, 2), BCFG(32, 4, 1, 3), BCFG(32, 4, 2, 1),
+};
+#undef BCFG
+
+int batch_tile_config_count() { return (int)(sizeof(k_bcfg) / sizeof(k_bcfg[0])); }
+const char* batch_tile_config_name(int c) {
+  return (c >= 0 && c < batch_tile_config_count()) ? k_bcfg[c].name : "";
+}
+void batch_tile_shape(int c, int& tx, int& ty, int& tz) {
+  if (c < 0 || c >= batch_tile_config_count()) c = 0;
+  tx = k_bcfg[c].tx;
+  ty = k_bcfg[c].ty;
+  tz = k_bcfg[c].tz;
+}
+
+cudaError_t launch_batch_stage(int cfg, bool mixed, const MemberDev* mem, const BatchWork* wk,
+                               int stage, cudaStream_t s) {
+  if (cfg < 0 || cfg >= batch_tile_config_count()) cfg = 0;
+  const BatchCfg& c = k_bcfg[cfg];
+  const void* fn = mixed ? c.kmx : c.k64;
+  const int threads = c.tx * c.ty * c.tz;
+  int dev = 0, sms = 0, per = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, threads, 0);
+  if (e != cudaSuccess) return e;
+  if (per < 1) per = 1;
+  dim3 block(c.tx, c.ty, c.tz);
+  dim3 grid((unsigned)(sms * per));
+  void* args[] = {(void*)&mem, (void*)&wk, (void*)&stage};
+  return cudaLaunchKernel(fn, grid, block, args, 0, s);
+}
+
+cudaError_t launch_batch_boundary(bool mixed, const MemberDev* mem, const BatchWork* wk, int stage,
+                                  cudaStream_t s) {
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  const dim3 grid((unsigned)(sms * 8)), block(256);
+  if (mixed) batch_boundary_kernel<true><<<grid, block, 0, s>>>(mem, wk, stage);
+  else batch_boundary_kernel<false><<<grid, block, 0, s>>>(mem, wk, stage);
+  return cudaGetLastError();
+}
+
+}  // namespace bssn

@@ -47,9 +47,9 @@ __device__ __forceinline__ void adm_at(const Grid& g, const double* __restrict__
 __device__ void constraints_point(const Grid& g, const double* __restrict__ y, long long id,
                                   double out[4]) {
   const long long sd[3] = {1, g.pitch, g.plane};
-  const double i12h = 1.0 / (12.0 * g.h);
-  const double i12h2 = 1.0 / (12.0 * g.h * g.h);
-  const double i144h2 = 1.0 / (144.0 * g.h * g.h);
+  const double i12h = g.i12h;
+  const double i12h2 = g.i12h2;
+  const double i144h2 = g.i144h2;
   double g0[6], k0[6];
   adm_at(g, y, id, g0, k0, true);
   double dg[3][6], dk[3][6], ddg[6][6];

@@ -56,60 +56,58 @@ __device__ __forceinline__ T dmu(const S* p, long long sa, long long sb) {
   return fmaT<T>(T(8), a, -b);
 }
 
-struct Adv {
-  long long s[3];  // signed stride toward the upwind side per axis
-};
+// Advection plus dissipation of every field as one 7-point stencil per axis.
+// Along axis d the upwinded advection beta^d d_d X (lopsided stencil on the
+// side the sign of beta^d selects) and the KO term eps/(64h) delta_d^6 X are
+// both linear in the values X(m s_d), m = -3..3, so their sum is
+//   sum_m w_d[m] X(m s_d),  w_d[m] = eps/(64h) c_KO[m] + |beta^d|/(12h) u_d[m]
+// with u_d = (0, 0, -3, -10, 18, -6, 1) for beta^d >= 0 and its mirror
+// (1, -6, 18, -10, -3, 0, 0) otherwise.  The weights are formed once per
+// point and shared by all fields; the centre weights of the three axes are
+// merged.
+__device__ __forceinline__ double up_coef(bool pos, int m) {
+  // u_d[m] for m in -3..3
+  const double cp[7] = {0.0, 0.0, -3.0, -10.0, 18.0, -6.0, 1.0};
+  const double cn[7] = {1.0, -6.0, 18.0, -10.0, -3.0, 0.0, 0.0};
+  return pos ? cp[m + 3] : cn[m + 3];
+}
 
-// Upwinded advection (times 12 h) plus KO sixth differences for one field.
-//   adv = sum_j |beta^j| (-3 f(-s) + 18 f(s) - 6 f(2s) + f(3s)) - 10 f0 sum_j |beta^j|
-//   ko  = sum_d (f-3 + f3) - 6 (f-2 + f2) + 15 (f-1 + f1) - 20 f0
-template <typename T, typename S>
-__device__ __forceinline__ void adv_ko(const S* p, const long long st[3], const Adv& up,
-                                       const T ab[3], T absum, T f0, T& adv, T& ko) {
-  T a = T(0);
-#pragma unroll
-  for (int d = 0; d < 3; d++) {
-    long long s = up.s[d];
-    T u = fmaT<T>(T(-3), ldg<T>(p - s),
-                  fmaT<T>(T(18), ldg<T>(p + s), fmaT<T>(T(-6), ldg<T>(p + 2 * s), ldg<T>(p + 3 * s))));
-    a = fmaT<T>(ab[d], u, a);
-  }
-  adv = fmaT<T>(T(-10) * absum, f0, a);
-  T s1 = T(0), s2 = T(0), s3 = T(0);
-#pragma unroll
-  for (int d = 0; d < 3; d++) {
-    long long s = st[d];
-    s1 += ldg<T>(p + s) + ldg<T>(p - s);
-    s2 += ldg<T>(p + 2 * s) + ldg<T>(p - 2 * s);
-    s3 += ldg<T>(p + 3 * s) + ldg<T>(p - 3 * s);
-  }
-  ko = fmaT<T>(T(-60), f0, fmaT<T>(T(15), s1, fmaT<T>(T(-6), s2, s3)));
+// Background value X0 of field f (1 for W, the diagonal of gt and alpha; 0
+// otherwise).  The float stage buffers of the mixed path hold X - X0, so that
+// float precision goes to the deviation; every stencil's weights sum to zero,
+// so derivatives of the deviation are the derivatives of X.
+__host__ __device__ __forceinline__ double background(const Grid& g, int f) {
+  return ((f == F_CHI && g.use_w) || f == F_GT + 0 || f == F_GT + 3 || f == F_GT + 5 || f == F_ALP)
+             ? 1.0 : 0.0;
 }
 
 // Right-hand side of all 24 fields at interior point (i, j, k) with linear
-// index id, reading the state register st (field stride g.fstride).
-template <typename T, typename S>
+// index id, reading the state register st (field stride g.fstride).  DEV: the
+// register holds X - X0 (mixed-path float buffers) instead of X.
+template <typename T, typename S, bool DEV = false>
 __device__ __forceinline__ void rhs_point(const Grid& g, const S* __restrict__ st, long long id,
                                           int i, int j, int k, T out[NF]) {
   const long long fs = g.fstride;
   const long long sd[3] = {1, g.pitch, g.plane};
-  const T hinv = T(1.0 / g.h);
-  const T i12h = T(1.0 / (12.0 * g.h));
-  const T i12h2 = T(1.0 / (12.0 * g.h * g.h));
-  const T i144h2 = T(1.0 / (144.0 * g.h * g.h));
-  (void)hinv;
+  const T i12h = gc<T>(g.i12h, g.i12hf);
+  const T i12h2 = gc<T>(g.i12h2, g.i12h2f);
+  const T i144h2 = gc<T>(g.i144h2, g.i144h2f);
 #define PF(f) (st + (long long)(f) * fs + id)
 
-  // ---- point values
-  T chi = ldg<T>(PF(F_CHI));
-  T gt[6], At[6];
+  // ---- point values (raw: as stored; chi, gt, alp: the field values)
+  const T chi_r = ldg<T>(PF(F_CHI));
+  T gt_r[6], gt[6], At[6];
 #pragma unroll
   for (int m = 0; m < 6; m++) {
-    gt[m] = ldg<T>(PF(F_GT + m));
+    gt_r[m] = ldg<T>(PF(F_GT + m));
     At[m] = ldg<T>(PF(F_AT + m));
   }
   T trK = ldg<T>(PF(F_TRK));
-  T alp = ldg<T>(PF(F_ALP));
+  const T alp_r = ldg<T>(PF(F_ALP));
+  const T chi = DEV && g.use_w ? chi_r + T(1) : chi_r;
+  const T alp = DEV ? alp_r + T(1) : alp_r;
+#pragma unroll
+  for (int m = 0; m < 6; m++) gt[m] = (DEV && (m == 0 || m == 3 || m == 5)) ? gt_r[m] + T(1) : gt_r[m];
   T beta[3], Bv[3];
 #pragma unroll
   for (int a = 0; a < 3; a++) {
@@ -168,9 +166,9 @@ __device__ __forceinline__ void rhs_point(const Grid& g, const S* __restrict__ s
         T dd[6];
         if (pa == pb) {
 #pragma unroll
-          for (int m = 0; m < 6; m++) dd[m] = d2u<T>(PF(F_GT + m), sd[pa], gt[m]) * i12h2;
-          ddchi[pq] = d2u<T>(PF(F_CHI), sd[pa], chi) * i12h2;
-          ddalp[pq] = d2u<T>(PF(F_ALP), sd[pa], alp) * i12h2;
+          for (int m = 0; m < 6; m++) dd[m] = d2u<T>(PF(F_GT + m), sd[pa], gt_r[m]) * i12h2;
+          ddchi[pq] = d2u<T>(PF(F_CHI), sd[pa], chi_r) * i12h2;
+          ddalp[pq] = d2u<T>(PF(F_ALP), sd[pa], alp_r) * i12h2;
         } else {
 #pragma unroll
           for (int m = 0; m < 6; m++) dd[m] = dmu<T>(PF(F_GT + m), sd[pa], sd[pb]) * i144h2;
@@ -198,7 +196,8 @@ __device__ __forceinline__ void rhs_point(const Grid& g, const S* __restrict__ s
   // ---- conformal factor
   T em4, dphi[3], ddphi[6];
   if (g.use_w) {
-    T Wd = chi > T(g.w_floor) ? chi : T(g.w_floor);
+    const T wf = gc<T>(g.w_floor, g.w_floorf);
+    T Wd = chi > wf ? chi : wf;
     T ih = T(0.5) / Wd;
     em4 = chi * chi;
 #pragma unroll
@@ -423,39 +422,54 @@ __device__ __forceinline__ void rhs_point(const Grid& g, const S* __restrict__ s
 #pragma unroll
     for (int a = 0; a < 3; a++) {
       out[F_BETA + a] = T(0.75) * Bv[a];
-      out[F_B + a] = gam_rhs[a] - T(g.eta) * q * Bv[a];
+      out[F_B + a] = gam_rhs[a] - gc<T>(g.eta, g.etaf) * q * Bv[a];
     }
   }
 
-  // ---- advection and dissipation, every field
-  Adv up;
-  T ab[3];
-#pragma unroll
-  for (int d = 0; d < 3; d++) {
-    up.s[d] = beta[d] >= T(0) ? sd[d] : -sd[d];
-    ab[d] = fabs(beta[d]);
-  }
-  const T absum = ab[0] + ab[1] + ab[2];
-  const T kos = T(g.ko_eps / (64.0 * g.h));
+  // ---- advection and dissipation, every field (one weighted stencil per axis)
   const int nf = frozen ? F_BETA : NF;
 #pragma unroll
-  for (int f = 0; f < NF; f++) {
-    if (f >= nf) {
-      out[f] = T(0);
-      continue;
+  for (int f = F_BETA; f < NF; f++)
+    if (f >= nf) out[f] = T(0);
+  {
+    const T kap = gc<T>(g.kos, g.kosf);
+    T bh[3];
+#pragma unroll
+    for (int d = 0; d < 3; d++) bh[d] = fabs(beta[d]) * i12h;
+    const T w0 = fmaT<T>(T(-10), bh[0] + bh[1] + bh[2], T(-60) * kap);
+#pragma unroll
+    for (int f = 0; f < NF; f++) {
+      if (f >= nf) break;
+      T f0;  // as stored: the stencil weights apply to stored values
+      if (f == F_CHI) f0 = chi_r;
+      else if (f >= F_GT && f < F_GT + 6) f0 = gt_r[f - F_GT];
+      else if (f == F_TRK) f0 = trK;
+      else if (f >= F_AT && f < F_AT + 6) f0 = At[f - F_AT];
+      else if (f == F_ALP) f0 = alp_r;
+      else if (f >= F_BETA && f < F_BETA + 3) f0 = beta[f - F_BETA];
+      else if (f >= F_B) f0 = Bv[f - F_B];
+      else f0 = ldg<T>(PF(f));
+      out[f] = fmaT<T>(w0, f0, out[f]);
     }
-    T f0;
-    if (f == F_CHI) f0 = chi;
-    else if (f >= F_GT && f < F_GT + 6) f0 = gt[f - F_GT];
-    else if (f == F_TRK) f0 = trK;
-    else if (f >= F_AT && f < F_AT + 6) f0 = At[f - F_AT];
-    else if (f == F_ALP) f0 = alp;
-    else if (f >= F_BETA && f < F_BETA + 3) f0 = beta[f - F_BETA];
-    else if (f >= F_B) f0 = Bv[f - F_B];
-    else f0 = ldg<T>(PF(f));
-    T adv, ko;
-    adv_ko<T>(PF(f), sd, up, ab, absum, f0, adv, ko);
-    out[f] = fmaT<T>(kos, ko, fmaT<T>(i12h, adv, out[f]));
+    const T cko[7] = {T(1), T(-6), T(15), T(-20), T(15), T(-6), T(1)};
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+      const bool pos = beta[d] >= T(0);
+      T w[7];
+#pragma unroll
+      for (int m = -3; m <= 3; m++)
+        if (m != 0) w[m + 3] = fmaT<T>(bh[d], T(up_coef(pos, m)), kap * cko[m + 3]);
+#pragma unroll
+      for (int f = 0; f < NF; f++) {
+        if (f >= nf) break;
+        const S* p = PF(f);
+        T acc = out[f];
+#pragma unroll
+        for (int m = -3; m <= 3; m++)
+          if (m != 0) acc = fmaT<T>(w[m + 3], ldg<T>(p + m * sd[d]), acc);
+        out[f] = acc;
+      }
+    }
   }
 #undef PF
 }

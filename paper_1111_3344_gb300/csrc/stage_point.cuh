@@ -1,0 +1,138 @@
+// Per-point fused stage (right-hand side + RK4 combine), shared by the
+// single-grid kernels (k_stage.cu) and the batched persistent kernels
+// (k_batch.cu) so that an evolution computes the same bits in either.
+#pragma once
+#include "bssn_internal.cuh"
+#include "rhs_point.cuh"
+
+namespace bssn {
+
+__device__ __forceinline__ bool on_shell(const Grid& g, int ii, int jj, int kk) {
+  return ii == 0 || jj == 0 || kk == 0 || ii == g.n0 - 1 || jj == g.n1 - 1 || kk == g.n2 - 1;
+}
+
+// Fused stage at interior point (ii, jj, kk) (interior indices), float64.
+__device__ __forceinline__ void stage_point_fp64(const Grid& g, const StageArgs& a, int ii, int jj,
+                                                 int kk) {
+  const int i = ii + GH, j = jj + GH, k = kk + GH;
+  const long long id = lin(g, i, j, k);
+  double r[NF];
+  rhs_point<double, double>(g, a.src, id, i, j, k, r);
+  const long long fs = g.fstride;
+  if (a.mode == MODE_RHS) {
+#pragma unroll
+    for (int f = 0; f < NF; f++) a.rhs[f * fs + id] = r[f];
+    return;
+  }
+  if (a.kshell && on_shell(g, ii, jj, kk)) {
+#pragma unroll
+    for (int f = 0; f < NF; f++) a.kshell[f * fs + id] = r[f];
+  }
+  if (a.mode == MODE_LAST) {
+#pragma unroll
+    for (int f = 0; f < NF; f++) {
+      const long long o = f * fs + id;
+      a.yn[o] = fma(a.b_dt, a.ksum[o] + r[f], a.yn[o]);
+    }
+    return;
+  }
+#pragma unroll
+  for (int f = 0; f < NF; f++) {
+    const long long o = f * fs + id;
+    a.out0[o] = fma(a.a_dt, r[f], a.src0[o]);
+    a.ksum[o] = a.mode == MODE_FIRST ? r[f] : fma(2.0, r[f], a.ksum[o]);
+  }
+}
+
+// ---------------------------------------------------------------- mixed
+
+// W (or phi) right-hand side in float64 from the float64 W of the stage input:
+// d_0 W = (W/3)(alpha K - d_k beta^k) (phi: -(alpha/6) K + d_k beta^k / 6),
+// plus upwinded advection and KO, as in rhs_point.
+__device__ __forceinline__ double chi_rhs_fp64(const Grid& g, const float* __restrict__ st,
+                               const double* __restrict__ w, long long id) {
+  const long long fs = g.fstride;
+  const long long sd[3] = {1, g.pitch, g.plane};
+  const double i12h = g.i12h;
+  const double chi = w[id];
+  const double alp = (double)__ldg(st + F_ALP * fs + id) + 1.0;  // stored as alpha - 1
+  const double trK = (double)__ldg(st + F_TRK * fs + id);
+  double beta[3], divb = 0.0;
+#pragma unroll
+  for (int d = 0; d < 3; d++) {
+    beta[d] = (double)__ldg(st + (F_BETA + d) * fs + id);
+    divb += d1u<double, float>(st + (F_BETA + d) * fs + id, sd[d]) * i12h;
+  }
+  double r = g.use_w ? (chi * (1.0 / 3.0)) * (alp * trK - divb)
+                     : (-1.0 / 6.0) * alp * trK + divb * (1.0 / 6.0);
+  const double kap = g.kos;
+  const double cko[7] = {1.0, -6.0, 15.0, -20.0, 15.0, -6.0, 1.0};
+  double bh[3];
+#pragma unroll
+  for (int d = 0; d < 3; d++) bh[d] = fabs(beta[d]) * i12h;
+  r = fma(fma(-10.0, bh[0] + bh[1] + bh[2], -60.0 * kap), chi, r);
+#pragma unroll
+  for (int d = 0; d < 3; d++) {
+    const bool pos = beta[d] >= 0.0;
+#pragma unroll
+    for (int m = -3; m <= 3; m++)
+      if (m != 0) r = fma(fma(bh[d], up_coef(pos, m), kap * cko[m + 3]), w[id + m * sd[d]], r);
+  }
+  return r;
+}
+
+// Fused stage at interior point (ii, jj, kk), mixed precision.
+__device__ __forceinline__ void stage_point_mixed(const Grid& g, const StageArgsMixed& a, int ii,
+                                                  int jj, int kk) {
+  const int i = ii + GH, j = jj + GH, k = kk + GH;
+  const long long id = lin(g, i, j, k);
+  float r[NF];
+  rhs_point<float, float, true>(g, a.src, id, i, j, k, r);
+  const long long fs = g.fstride;
+  // near a puncture the W update runs in float64
+  const double w0 = a.srcw[id];
+  const double wval = g.use_w ? w0 : exp(-2.0 * w0);
+  const double rchi = wval < a.w_thr ? chi_rhs_fp64(g, a.src, a.srcw, id) : (double)r[F_CHI];
+  if (a.mode == MODE_RHS) {
+    a.rhs[id] = rchi;
+#pragma unroll
+    for (int f = 1; f < NF; f++) a.rhs[f * fs + id] = (double)r[f];
+    return;
+  }
+  if (a.kshell && on_shell(g, ii, jj, kk)) {
+#pragma unroll
+    for (int f = 0; f < NF; f++) a.kshell[f * fs + id] = f == F_CHI ? (float)rchi : r[f];
+  }
+  if (a.mode == MODE_LAST) {
+    // y_{n+1} = y_n + dt/6 (k1 + 2 k2 + 2 k3 + k4), the only float64 update of the step
+    {
+      const double v = fma(a.b_dt, a.ksumw[id] + rchi, a.yn[id]);
+      a.yn[id] = v;
+      a.out0[id] = (float)(v - background(g, F_CHI));
+      a.out0w[id] = v;
+    }
+#pragma unroll
+    for (int f = 1; f < NF; f++) {
+      const long long o = f * fs + id;
+      const double v = fma(a.b_dt, (double)(a.ksum[o] + r[f]), a.yn[o]);
+      a.yn[o] = v;
+      a.out0[o] = (float)(v - background(g, f));
+    }
+    return;
+  }
+  const float af = a.a_dtf;
+  {
+    const double v = fma(a.a_dt, rchi, a.src0w[id]);
+    a.out0w[id] = v;
+    a.out0[id] = (float)(v - background(g, F_CHI));
+    a.ksumw[id] = a.mode == MODE_FIRST ? rchi : fma(2.0, rchi, a.ksumw[id]);
+  }
+#pragma unroll
+  for (int f = 1; f < NF; f++) {
+    const long long o = f * fs + id;
+    a.out0[o] = fmaf(af, r[f], a.src0[o]);
+    a.ksum[o] = a.mode == MODE_FIRST ? r[f] : fmaf(2.0f, r[f], a.ksum[o]);
+  }
+}
+
+}  // namespace bssn

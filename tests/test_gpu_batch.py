@@ -1,0 +1,220 @@
+"""Batched evolutions (one persistent launch per RK4 stage, CUDA graph) and the
+continuous-batching server.
+
+The bar: a member's state after n steps is bit-identical whether it runs alone
+in a batch or together with other members (the same kernel runs the same
+per-point arithmetic; the work-list only decides which block does which tile),
+and it matches the single-evolution path to the parity tolerance of the
+precision (float64: 1e-11 normwise; mixed: 1e-6)."""
+import time
+
+import numpy as np
+import pytest
+
+import oracle as O
+from cases import bl_params, gpu_params, normwise_errors, oracle_cfg
+from paper_1111_3344_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    return torch
+
+
+def _members(precision):
+    bl1 = dict(n=(24, 20, 28), xmin=(-3.0, -2.5, -3.5), h=0.25, boundary="sommerfeld", conformal="W",
+               slicing="1+log", shift="gamma-driver", eta=2.0, punctures=[(1.0, 0.05, 0.0, 0.0)],
+               precision=precision, w_fp64_threshold=0.3)
+    bl2 = dict(n=(33, 17, 21), xmin=(-4.0, -2.1, -2.6), h=0.25, boundary="sommerfeld", conformal="W",
+               slicing="1+log", shift="gamma-driver", eta=1.0,
+               punctures=[(0.6, 1.0, 0.0, 0.0), (0.4, -1.5, 0.0, 0.0)], precision=precision,
+               w_fp64_threshold=0.3)
+    gw = dict(n=(24, 24, 24), xmin=(-0.5,) * 3, h=1 / 24, boundary="periodic", conformal="phi",
+              slicing="harmonic", shift="frozen", precision=precision)
+    rnd = dict(n=(16, 12, 20), xmin=(0.0,) * 3, h=0.05, boundary="periodic", conformal="W",
+               slicing="geodesic", shift="gamma-driver", precision=precision, w_fp64_threshold=0.9)
+    return [bl1, bl2, gw, rnd]
+
+
+def _initial(case):
+    if case.get("punctures"):
+        return ("bl", bl_params(case))
+    if case["slicing"] == "harmonic":
+        return ("gauge_wave", [0.01, 1.0])
+    return ("state", inputs.random_state(5, case["n"], case["xmin"], case["h"], amp=0.05))
+
+
+def _load(batch, mid, case):
+    kind, p = _initial(case)
+    if kind == "state":
+        batch.set_state(mid, p, 0.0)
+    else:
+        batch.set_initial_data(mid, kind, p)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_alone_equals_in_the_mix(torch_cuda, precision):
+    from paper_1111_3344_gb300.bssn import Batch, Evolution
+    cases = _members(precision)
+    steps = 3
+    mix = Batch(precision, pool_bytes=1 << 30)
+    ids = [mix.add(gpu_params(c)) for c in cases]
+    for mid, c in zip(ids, cases):
+        _load(mix, mid, c)
+    mix.step(steps)
+    got_mix = [mix.get_state(m)[0] for m in ids]
+    norms_mix = [mix.constraints(m) for m in ids]
+    tile = 0
+    for c, gm, nm in zip(cases, got_mix, norms_mix):
+        alone = Batch(precision, pool_bytes=1 << 29)
+        mid = alone.add(gpu_params(c))
+        _load(alone, mid, c)
+        alone.step(steps)
+        ga, t = alone.get_state(mid)
+        assert np.array_equal(ga, gm)
+        assert np.array_equal(alone.constraints(mid), nm)
+        assert t == pytest.approx(steps * gpu_params(c).dt)
+        alone.close()
+        # and against the single-evolution path
+        evo = Evolution(gpu_params(c))
+        kind, p = _initial(c)
+        if kind == "state":
+            evo.set_state(p, 0.0)
+        else:
+            evo.set_initial_data(kind, p)
+        evo.rk4_step(steps)
+        e = normwise_errors(gm, evo.get_state()[0])
+        assert e.max() <= (1e-11 if precision == "fp64" else 1e-4), e.max()
+        evo.close()
+    mix.close()
+
+
+def test_batch_matches_oracle_fp64(torch_cuda):
+    from paper_1111_3344_gb300.bssn import Batch
+    c = _members("fp64")[1]
+    b = Batch("fp64", pool_bytes=1 << 28)
+    mid = b.add(gpu_params(c))
+    b.set_initial_data(mid, "bl", bl_params(c))
+    b.step(2)
+    got, _ = b.get_state(mid)
+    cfg = oracle_cfg(c)
+    want = O.rk4(cfg, O.initial_data(cfg, "bl", bl_params(c)), 2)
+    assert normwise_errors(got, want).max() <= 1e-11
+
+
+def test_membership_changes_between_steps(torch_cuda):
+    """Members join and leave between steps without re-capture; a member that
+    stays is unaffected by the others coming and going."""
+    from paper_1111_3344_gb300.bssn import Batch
+    cs = _members("mixed")
+    b = Batch("mixed", pool_bytes=1 << 30)
+    a = b.add(gpu_params(cs[0]))
+    _load(b, a, cs[0])
+    b.step(2)
+    x = b.add(gpu_params(cs[1]))
+    _load(b, x, cs[1])
+    b.step(2)
+    b.remove(x)
+    y = b.add(gpu_params(cs[2]))
+    _load(b, y, cs[2])
+    b.step(2)
+    got, t = b.get_state(a)
+    ref = Batch("mixed", pool_bytes=1 << 29)
+    r = ref.add(gpu_params(cs[0]))
+    _load(ref, r, cs[0])
+    ref.step(6)
+    assert np.array_equal(got, ref.get_state(r)[0])
+
+
+def test_pool_exhaustion_and_precision_mismatch(torch_cuda):
+    from paper_1111_3344_gb300.bssn import Batch, BssnError
+    c = _members("fp64")[0]
+    need = Batch.member_bytes(gpu_params(c))
+    b = Batch("fp64", pool_bytes=need + (2 << 20), max_members=4)
+    b.add(gpu_params(c))
+    with pytest.raises(BssnError) as e:
+        b.add(gpu_params(c))
+    assert e.value.status == 2
+    with pytest.raises(BssnError) as e:
+        b.add(gpu_params(dict(c, precision="mixed")))
+    assert e.value.status == 1
+
+
+def test_batch_autotune_keeps_results(torch_cuda):
+    from paper_1111_3344_gb300.bssn import Batch
+    cs = _members("mixed")
+    outs = []
+    for tune in (False, True):
+        b = Batch("mixed", pool_bytes=1 << 30)
+        ids = [b.add(gpu_params(c)) for c in cs]
+        for m, c in zip(ids, cs):
+            _load(b, m, c)
+        if tune:
+            best, times = b.autotune(reps=1)
+            assert len(times) >= 2
+        b.step(2)
+        outs.append([b.get_state(m)[0] for m in ids])
+    for x, y in zip(*outs):
+        assert normwise_errors(x, y).max() <= 1e-4
+
+
+# ------------------------------------------------------------------ server
+
+def _req(n, L=6.0, precision="mixed"):
+    from paper_1111_3344_gb300.bssn import Params
+    h = 2 * L / n
+    return Params(n=(n,) * 3, xmin=(-L,) * 3, h=h, boundary="sommerfeld", conformal="W",
+                  slicing="1+log", shift="gamma-driver", eta=2.0, dt=0.25 * h, precision=precision,
+                  w_fp64_threshold=0.2, r_excise=1.0)
+
+
+def test_server_results_same_alone_and_in_the_mix(torch_cuda):
+    from paper_1111_3344_gb300.bssn import Server
+    reqs = [(24, [1, 0.5, 0.3, 0.0, 0.0], 12), (32, [2, 0.6, 1.0, 0.0, 0.0, 0.4, -1.5, 0.0, 0.0], 5),
+            (20, [1, 1.0, 0.0, 0.0, 0.0], 20), (28, [1, 0.7, 0.0, 0.2, 0.0], 8)]
+    alone = {}
+    for i, (n, p, steps) in enumerate(reqs):
+        s = Server("mixed", budget_bytes=1 << 28)
+        t = s.submit(_req(n), "bl", p, steps)
+        st, norms, lat = s.wait(t)
+        assert st == 0 and lat > 0
+        alone[i] = norms
+        s.close()
+    s = Server("mixed", budget_bytes=1 << 29)
+    long_t = s.submit(_req(24), "bl", reqs[0][1], 400)   # keeps the batch busy
+    t0 = time.time()
+    while s.stats()["resident"] < 1 and time.time() - t0 < 30:
+        time.sleep(0.001)
+    tickets = [s.submit(_req(n), "bl", p, steps) for (n, p, steps) in reqs]  # arrive while it runs
+    res = [s.wait(t) for t in tickets]
+    assert s.poll(long_t) is None or s.poll(long_t)[0] == 0
+    for i, (st, norms, lat) in enumerate(res):
+        assert st == 0
+        assert np.array_equal(norms, alone[i]), i
+    st, _, _ = s.wait(long_t)
+    assert st == 0
+    stats = s.stats()
+    assert stats["completed"] == 5 and stats["failed"] == 0 and stats["point_updates"] > 0
+    s.close()
+
+
+def test_server_budget_and_failure_isolation(torch_cuda):
+    from paper_1111_3344_gb300.bssn import BssnError, Server
+    s = Server("mixed", budget_bytes=1 << 27)
+    with pytest.raises(BssnError) as e:   # larger than the whole budget
+        s.submit(_req(160), "bl", [1, 1.0, 0.0, 0.0, 0.0], 10)
+    assert e.value.status == 1
+    good = s.submit(_req(20), "bl", [1, 1.0, 0.0, 0.0, 0.0], 6)
+    bad = s.submit(_req(20), "bl", [1, float("nan"), 0.0, 0.0, 0.0], 6)
+    good2 = s.submit(_req(24), "bl", [1, 0.8, 0.1, 0.0, 0.0], 6)
+    assert s.wait(good)[0] == 0
+    assert s.wait(bad)[0] == 7          # BSSN_EFAILED, only for that request
+    assert s.wait(good2)[0] == 0
+    st = s.stats()
+    assert st["failed"] == 1 and st["completed"] == 3
+    s.close()
