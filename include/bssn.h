@@ -259,6 +259,31 @@ bssn_status bssn_server_destroy(bssn_server* s); /* stops the scheduler; synchro
  * out[2] = total boundary-kernel milliseconds, out[3] = boundary launches. */
 bssn_status bssn_profile(bssn_ctx* ctx, int32_t enable, double out[4]);
 
+/* Largest interior grid (n0 * n1 * n2) bssn_constraints_noalloc accepts. */
+#define BSSN_NOALLOC_MAX_POINTS 4194304
+
+/* Constraint norms without a bssn_alloc context and without allocating.  The
+ * paper has no counterpart: this exists for callers that may not allocate
+ * device memory themselves or hand the library a block -- a host that owns all
+ * of HBM through its own arena, a plug-in host that forbids its plug-ins to
+ * allocate, a real-time loop that must not call cudaMalloc (which can
+ * synchronise the device) -- yet hold a state buffer and want its norms.
+ *  p        grid and method parameters (as for bssn_alloc); at most
+ *           BSSN_NOALLOC_MAX_POINTS interior points, else EINVAL.
+ *  d_state  float64 register in the layout of bssn_layout_of(p), ghosts valid.
+ *  punct    host array of npunct x {m, x, y, z} (npunct 0..8) defining the
+ *           excised set, as set_initial_data does for Brill-Lindquist data.
+ *  out      host array of 16 doubles, same order as bssn_constraints.
+ * Synchronises cuda_stream.  The reduction scratch is a fixed static device
+ * array (2.25 MiB) that every GPU which loads the library holds until exit;
+ * its device address is looked up on the first call made on each device, so
+ * make that first call before any stream capture.  All calls on a device share
+ * that array: calls whose work overlaps on the GPU (other streams, other host
+ * threads) race and must be serialised by the caller.  No cudaMalloc,
+ * cudaFree or allocating library routine is called. */
+bssn_status bssn_constraints_noalloc(const bssn_params* p, const double* d_state,
+                                     const double* punct, int32_t npunct, void* cuda_stream,
+                                     double out[16]);
 
 #ifdef __cplusplus
 }

@@ -133,6 +133,9 @@ _SIGS = [
     ("bssn_set_tile", [ctypes.c_void_p, ctypes.c_int32], ctypes.c_int),
     ("bssn_autotune", [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
                        ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+    ("bssn_constraints_noalloc", [ctypes.POINTER(bssn_params), ctypes.c_void_p,
+                                  ctypes.POINTER(ctypes.c_double), ctypes.c_int32, ctypes.c_void_p,
+                                  ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
 ]
 
 
@@ -302,6 +305,18 @@ def bssn_profile(ctx: int, enable: bool):
     out = (ctypes.c_double * 4)()
     _check(load().bssn_profile(ctypes.c_void_p(ctx), 1 if enable else 0, out))
     return None if enable else (out[0], int(out[1]), out[2], int(out[3]))
+
+
+def bssn_constraints_noalloc(params: Params, d_state: int, punctures=(), stream: int = 0) -> np.ndarray:
+    """Constraint norms of a caller-held device state without a context and
+    without any device allocation (see include/bssn.h)."""
+    p = params.c()
+    flat = [float(v) for q in punctures for v in q]
+    arr = _dbl_array(flat)
+    out = (ctypes.c_double * 16)()
+    _check(load().bssn_constraints_noalloc(ctypes.byref(p), ctypes.c_void_p(d_state), arr,
+                                           len(punctures), ctypes.c_void_p(stream), out))
+    return np.array(out[:], dtype=np.float64)
 
 
 # ------------------------------------------------------- convenience class
