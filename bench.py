@@ -132,13 +132,23 @@ def barrier(world):
 
 
 def max_over_ranks(x, world):
+    """Max of a per-rank scalar over all ranks (the timing barrier's reduction;
+    the evolutions themselves exchange nothing)."""
     import torch
     if world == 1:
         return x
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def whole_job_rate(points_per_rank, steps, ms_local, world):
+    """Whole-job point-updates/s (millions): every rank advances its own replica
+    of the workload; the job takes as long as the slowest rank."""
+    ms = max_over_ranks(ms_local, world)
+    return points_per_rank * steps * world / (ms * 1e-3) / 1e6, ms
 
 
 def oracle_cpu_baseline(steps_budget_s=30.0):
@@ -225,9 +235,8 @@ def run_ours(args):
     ms_local = start.elapsed_time(stop)
     stage_ms, stage_n, bc_ms, bc_n = B.bssn_profile(evo.ctx, False)
     clk = clocks.stop()
-    ms = max_over_ranks(ms_local, world)
     pts = N_SIDE ** 3
-    value = pts * args.steps * world / (ms * 1e-3) / 1e6
+    value, ms = whole_job_rate(pts, args.steps, ms_local, world)
 
     # end to end through the C ABI with pinned host buffers: upload state,
     # one RK4 step, read the state back, every step
@@ -389,6 +398,50 @@ def run_served(args):
     print(json.dumps(line))
 
 
+def run_precision(args):
+    """Mixed precision against float64 on the same GPU: the puncture at
+    args.n^3 (256^3 by default for this mode) evolved args.steps RK4 steps
+    both ways; per-field L2/Linf of the state difference, relative difference
+    of every constraint norm, and the speedup."""
+    import torch
+
+    from paper_1111_3344_gb300 import bssn as B
+    torch.cuda.set_device(0)
+    out = {}
+    for prec in ("fp64", "mixed"):
+        evo = B.Evolution(workload_params(prec))
+        evo.set_initial_data("bl", BL_P)
+        B.bssn_autotune(evo.ctx, reps=2)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        evo.rk4_step(args.steps)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        st, _ = evo.get_state()
+        out[prec] = (st, evo.constraints(), dt)
+        evo.close()
+        del evo
+        torch.cuda.empty_cache()
+    s64, c64, t64 = out["fp64"]
+    smx, cmx, tmx = out["mixed"]
+    g = 3
+    d = (smx - s64)[:, g:-g, g:-g, g:-g].reshape(24, -1)
+    ref = np.abs(s64[:, g:-g, g:-g, g:-g]).reshape(24, -1).max(axis=1)
+    names = ["chi", "gt_xx", "gt_xy", "gt_xz", "gt_yy", "gt_yz", "gt_zz", "trK", "At_xx", "At_xy",
+             "At_xz", "At_yy", "At_yz", "At_zz", "Gt_x", "Gt_y", "Gt_z", "alpha", "beta_x", "beta_y",
+             "beta_z", "B_x", "B_y", "B_z"]
+    fields = {nm: {"L2": float(np.sqrt((d[f] ** 2).mean())), "Linf": float(np.abs(d[f]).max()),
+                   "max_abs_fp64": float(ref[f])} for f, nm in enumerate(names)}
+    cn = ["H", "Mx", "My", "Mz"]
+    keys = [f"{k}_{n}_{s}" for s in ("full", "excised") for k in ("L2", "Linf") for n in cn]
+    rel = {k: float(abs(a - b) / abs(b)) if b != 0 else None for k, a, b in zip(keys, cmx, c64)}
+    line = {"metric": "mixed vs float64: per-field state error and constraint-norm relative difference",
+            "grid": args.n, "steps": args.steps, "speedup_mixed_over_fp64": t64 / tmx,
+            "seconds": {"fp64": t64, "mixed": tmx}, "constraint_norms_fp64": dict(zip(keys, c64.tolist())),
+            "constraint_norm_rel_diff": rel, "fields": fields}
+    print(json.dumps(line))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -397,7 +450,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["puncture", "batched", "served"], default="puncture",
+    ap.add_argument("--workload", choices=["puncture", "batched", "served", "precision"],
+                    default="puncture",
                     help="puncture: the benchmark line (single 128^3 puncture); batched / served: "
                          "the multi-evolution workloads, reported on their own lines")
     ap.add_argument("--members", type=int, default=64)
@@ -419,6 +473,8 @@ def main():
         run_batched(args)
     elif args.workload == "served":
         run_served(args)
+    elif args.workload == "precision":
+        run_precision(args)
     else:
         run_ours(args)
 

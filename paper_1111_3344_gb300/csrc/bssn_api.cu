@@ -4,6 +4,7 @@
 // device memory happens here; registers and tables are carved from the block
 // given to bssn_alloc.
 #include <cmath>
+#include <math.h>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -87,7 +88,7 @@ Grid make_grid(const bssn_params* p) {
 // buffers m[0..2] (m[0] is the float shadow of y_n), each with a float64 W
 // array; the float k-sum with its float64 W; float anchors.
 struct Carve {
-  size_t reg, yn, ks, s1, s2, ksh, part, out16, total;
+  size_t reg, yn, ks, s1, s2, ksh, part, out16, err, total;
   size_t m32[3], mw[3], ks32, ksw;
   int nblocks;
 };
@@ -119,6 +120,7 @@ Carve carve(const bssn_params* p, const Grid& g) {
   c.nblocks = constraints_blocks(g);
   c.part = o; o += align_up((size_t)c.nblocks * 18 * sizeof(double));
   c.out16 = o; o += align_up(16 * sizeof(double));
+  c.err = o; o += align_up(sizeof(int));
   c.total = o;
   return c;
 }
@@ -147,6 +149,9 @@ struct bssn_ctx {
   float* ksh32;
   bool shadow_valid;
   int tile;  // stage-kernel tile configuration (see bssn_autotune)
+  CUtensorMap tmap[3];  // mixed: tensor maps of the float stage buffers (TMA kernel)
+  bool tmap_ok;
+  int* err;             // device error word (bounded waits that gave up)
   double* part;
   double* out16;
   double t;
@@ -246,6 +251,17 @@ bssn_status bssn_alloc(const bssn_params* p, void* d_mem, size_t bytes, void* cu
   ctx->t = 0.0;
   ctx->npunct = 0;
   ctx->prof = false;
+  ctx->err = (int*)(ctx->mem + c.err);
+  ctx->tmap_ok = false;
+  if (p->precision == BSSN_MIXED) {
+    bool ok = true;
+    for (int q = 0; q < 3 && ok; q++) ok = make_stage_tensor_map(g, ctx->m32[q], &ctx->tmap[q]) == cudaSuccess;
+    ctx->tmap_ok = ok;
+  }
+  if (cudaMemsetAsync(ctx->err, 0, sizeof(int), ctx->stream) != cudaSuccess) {
+    delete ctx;
+    return fail(BSSN_ECUDA, "error word init");
+  }
   *out = ctx;
   return BSSN_OK;
 }
@@ -386,7 +402,10 @@ static bssn_status run_stage_mixed(bssn_ctx* ctx, int src, int mode, int out, do
   a.mode = mode;
   cudaError_t e;
   if (ctx->prof && (e = prof_mark(ctx, ctx->ev_stage)) != cudaSuccess) return cuda_fail(e, "profile");
-  e = launch_stage_mixed(ctx->g, a, ctx->stream, ctx->tile);
+  if (ctx->tile == tile_config_count())
+    e = launch_stage_mixed_tma(ctx->g, a, ctx->tmap[src], ctx->err, ctx->stream);
+  else
+    e = launch_stage_mixed(ctx->g, a, ctx->stream, ctx->tile);
   if (e != cudaSuccess) return cuda_fail(e, "stage");
   if (ctx->prof && (e = prof_mark(ctx, ctx->ev_stage)) != cudaSuccess) return cuda_fail(e, "profile");
   if (ctx->prof && (e = prof_mark(ctx, ctx->ev_bc)) != cudaSuccess) return cuda_fail(e, "profile");
@@ -434,8 +453,11 @@ bssn_status bssn_rk4_step(bssn_ctx* ctx, int32_t nsteps) {
   return BSSN_OK;
 }
 
+static bssn_status check_err(bssn_ctx* ctx);
+
 bssn_status bssn_constraints(bssn_ctx* ctx, double out[16]) {
   if (!ctx || !out) return fail(BSSN_EINVAL, "NULL argument");
+  if (bssn_status es = check_err(ctx)) return es;
   cudaError_t e = launch_constraints(ctx->g, ctx->yn, &ctx->punct[0][0], ctx->npunct,
                                      ctx->p.r_excise, ctx->part, ctx->c.nblocks, ctx->out16,
                                      ctx->stream);
@@ -447,8 +469,22 @@ bssn_status bssn_constraints(bssn_ctx* ctx, double out[16]) {
   return BSSN_OK;
 }
 
+// Read and clear the device error word (a bounded wait in a kernel gave up).
+static bssn_status check_err(bssn_ctx* ctx) {
+  int h = 0;
+  cudaError_t e = cudaMemcpyAsync(&h, ctx->err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "error word");
+  if (h) {
+    cudaMemsetAsync(ctx->err, 0, sizeof(int), ctx->stream);
+    return fail(BSSN_ETIMEOUT, "a stage kernel gave up waiting for its shared-memory tile; the state is invalid");
+  }
+  return BSSN_OK;
+}
+
 bssn_status bssn_get_state(bssn_ctx* ctx, double* host, double* t) {
   if (!ctx || !host) return fail(BSSN_EINVAL, "NULL argument");
+  if (bssn_status es = check_err(ctx)) return es;
   const Grid& g = ctx->g;
   cudaError_t e = cudaMemcpy2DAsync(host, (size_t)g.sx * sizeof(double), ctx->yn,
                                     (size_t)g.pitch * sizeof(double), (size_t)g.sx * sizeof(double),
@@ -474,13 +510,24 @@ bssn_status bssn_set_state(bssn_ctx* ctx, const double* host, double t) {
   return BSSN_OK;
 }
 
-int32_t bssn_tile_count(void) { return tile_config_count(); }
+// Configurations: the plain tile shapes, then the TMA-staged mixed kernel.
+int32_t bssn_tile_count(void) { return tile_config_count() + 1; }
 
-const char* bssn_tile_name(int32_t cfg) { return tile_config_name(cfg); }
+const char* bssn_tile_name(int32_t cfg) {
+  if (cfg == tile_config_count()) return "tma32x4x1/2";
+  return tile_config_name(cfg);
+}
+
+static bool tile_usable(const bssn_ctx* ctx, int cfg) {
+  if (cfg < 0 || cfg > tile_config_count()) return false;
+  if (cfg == tile_config_count()) return ctx->p.precision == BSSN_MIXED && ctx->tmap_ok;
+  return true;
+}
 
 bssn_status bssn_set_tile(bssn_ctx* ctx, int32_t cfg) {
   if (!ctx) return fail(BSSN_EINVAL, "ctx is NULL");
-  if (cfg < 0 || cfg >= tile_config_count()) return fail(BSSN_EINVAL, "tile config out of range");
+  if (!tile_usable(ctx, cfg))
+    return fail(BSSN_EINVAL, "tile config out of range (the TMA kernel is for the mixed path)");
   ctx->tile = cfg;
   return BSSN_OK;
 }
@@ -497,12 +544,16 @@ bssn_status bssn_autotune(bssn_ctx* ctx, int32_t reps, int32_t* best, double* ms
   cudaError_t e;
   if ((e = cudaEventCreate(&e0)) != cudaSuccess) return cuda_fail(e, "event");
   if ((e = cudaEventCreate(&e1)) != cudaSuccess) { cudaEventDestroy(e0); return cuda_fail(e, "event"); }
-  const int ncfg = tile_config_count();
+  const int ncfg = tile_config_count() + 1;
   double best_ms = 1e300;
   int best_c = 0;
   bssn_status st = BSSN_OK;
   // the first stage leaves y_n (and its float shadow) unchanged
   for (int c = 0; c < ncfg && st == BSSN_OK; c++) {
+    if (!tile_usable(ctx, c)) {
+      if (ms_per_cfg) ms_per_cfg[c] = INFINITY;
+      continue;
+    }
     auto launch = [&]() -> cudaError_t {
       if (!mixed) {
         StageArgs a{};
@@ -515,6 +566,7 @@ bssn_status bssn_autotune(bssn_ctx* ctx, int32_t reps, int32_t* best, double* ms
       a.yn = ctx->yn; a.out0 = ctx->m32[1]; a.out0w = ctx->mw[1];
       a.ksum = ctx->ks32; a.ksumw = ctx->ksw; a.a_dt = 0.5 * ctx->p.dt; a.a_dtf = (float)a.a_dt;
       a.w_thr = ctx->p.w_fp64_threshold; a.mode = MODE_FIRST;
+      if (c == tile_config_count()) return launch_stage_mixed_tma(ctx->g, a, ctx->tmap[0], ctx->err, ctx->stream);
       return launch_stage_mixed(ctx->g, a, ctx->stream, c);
     };
     if ((e = launch()) != cudaSuccess) { st = cuda_fail(e, "autotune warm-up"); break; }

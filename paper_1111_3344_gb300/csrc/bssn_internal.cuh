@@ -3,6 +3,7 @@
 #pragma once
 #include <cstdint>
 #include <string>
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include "bssn.h"
@@ -162,6 +163,11 @@ cudaError_t launch_stage_fp64(const Grid& g, const StageArgs& a, cudaStream_t s,
 cudaError_t launch_stage_mixed(const Grid& g, const StageArgsMixed& a, cudaStream_t s, int cfg = 0);
 int tile_config_count();
 const char* tile_config_name(int c);
+// TMA-staged mixed stage kernel (k_stage_tma.cu); map describes the float
+// stage buffer that is the stencil source.
+cudaError_t make_stage_tensor_map(const Grid& g, const float* base, CUtensorMap* out);
+cudaError_t launch_stage_mixed_tma(const Grid& g, const StageArgsMixed& a, const CUtensorMap& map,
+                                   int* err, cudaStream_t s);
 cudaError_t launch_sommerfeld(const Grid& g, const StageArgs& a, const double* kanchor,
                               cudaStream_t s);
 cudaError_t launch_sommerfeld_mixed(const Grid& g, const StageArgsMixed& a, const float* kanchor,

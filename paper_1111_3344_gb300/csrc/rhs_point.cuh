@@ -34,26 +34,63 @@ __device__ __forceinline__ T ldg(const S* p) {
   return T(__ldg(p));
 }
 
+// Field access of rhs_point.  An accessor gives, for field f at the point,
+// a pointer, the strides of the three axes and a load; the compiler resolves
+// the field-dependent choices because f is a constant after unrolling.
+// GlobalAcc: every field read from the global register (read-only path).
+template <typename S>
+struct GlobalAcc {
+  const S* __restrict__ st;
+  long long id, fs, sd[3];
+  __device__ __forceinline__ GlobalAcc(const Grid& g, const S* __restrict__ st_, long long id_)
+      : st(st_), id(id_), fs(g.fstride), sd{1, g.pitch, g.plane} {}
+  __device__ __forceinline__ const S* ptr(int f) const { return st + (long long)f * fs + id; }
+  __device__ __forceinline__ long long s(int, int d) const { return sd[d]; }
+  template <typename T>
+  __device__ __forceinline__ T ld(int, const S* p) const { return T(__ldg(p)); }
+};
+
 // 8 (f1 - f-1) - (f2 - f-2): 12 h times the 4th-order first derivative.
-template <typename T, typename S>
-__device__ __forceinline__ T d1u(const S* p, long long s) {
-  T a = ldg<T>(p + s) - ldg<T>(p - s);
-  T b = ldg<T>(p + 2 * s) - ldg<T>(p - 2 * s);
+template <typename T, typename A, typename P>
+__device__ __forceinline__ T d1u(const A& acc, int f, const P* p, long long s) {
+  T a = acc.template ld<T>(f, p + s) - acc.template ld<T>(f, p - s);
+  T b = acc.template ld<T>(f, p + 2 * s) - acc.template ld<T>(f, p - 2 * s);
   return fmaT<T>(T(8), a, -b);
 }
 // 16 (f1 + f-1) - (f2 + f-2) - 30 f0: 12 h^2 times the 4th-order second derivative.
-template <typename T, typename S>
-__device__ __forceinline__ T d2u(const S* p, long long s, T f0) {
-  T a = ldg<T>(p + s) + ldg<T>(p - s);
-  T b = ldg<T>(p + 2 * s) + ldg<T>(p - 2 * s);
-  return fmaT<T>(T(-30), f0, fmaT<T>(T(16), a, -b));
+// In float the same sum is formed from differences to the centre value,
+// 16 ((f1 - f0) + (f-1 - f0)) - ((f2 - f0) + (f-2 - f0)): neighbour differences
+// are (nearly) exact, so the rounding scales with h f' instead of |f| (the
+// plain form loses |f| / (h^2 f'') of float's 24 bits).  Float64 keeps the
+// cheaper plain form.
+template <typename T, typename A, typename P>
+__device__ __forceinline__ T d2u(const A& acc, int f, const P* p, long long s, T f0) {
+  if constexpr (sizeof(T) == 4) {
+    T a = (acc.template ld<T>(f, p + s) - f0) + (acc.template ld<T>(f, p - s) - f0);
+    T b = (acc.template ld<T>(f, p + 2 * s) - f0) + (acc.template ld<T>(f, p - 2 * s) - f0);
+    return fmaT<T>(T(16), a, -b);
+  } else {
+    T a = acc.template ld<T>(f, p + s) + acc.template ld<T>(f, p - s);
+    T b = acc.template ld<T>(f, p + 2 * s) + acc.template ld<T>(f, p - 2 * s);
+    return fmaT<T>(T(-30), f0, fmaT<T>(T(16), a, -b));
+  }
 }
 // D1_a D1_b (a != b): 144 h^2 times the mixed derivative.
-template <typename T, typename S>
-__device__ __forceinline__ T dmu(const S* p, long long sa, long long sb) {
-  T a = d1u<T>(p + sa, sb) - d1u<T>(p - sa, sb);
-  T b = d1u<T>(p + 2 * sa, sb) - d1u<T>(p - 2 * sa, sb);
+template <typename T, typename A, typename P>
+__device__ __forceinline__ T dmu(const A& acc, int f, const P* p, long long sa, long long sb) {
+  T a = d1u<T>(acc, f, p + sa, sb) - d1u<T>(acc, f, p - sa, sb);
+  T b = d1u<T>(acc, f, p + 2 * sa, sb) - d1u<T>(acc, f, p - 2 * sa, sb);
   return fmaT<T>(T(8), a, -b);
+}
+// the same helpers over the plain read-only global path (one field)
+template <typename T, typename S>
+struct PlainAcc {
+  template <typename U>
+  __device__ __forceinline__ U ld(int, const S* p) const { return U(__ldg(p)); }
+};
+template <typename T, typename S>
+__device__ __forceinline__ T d1u(const S* p, long long s) {
+  return d1u<T>(PlainAcc<T, S>{}, 0, p, s);
 }
 
 // Advection plus dissipation of every field as one 7-point stencil per axis.
@@ -84,26 +121,26 @@ __host__ __device__ __forceinline__ double background(const Grid& g, int f) {
 // Right-hand side of all 24 fields at interior point (i, j, k) with linear
 // index id, reading the state register st (field stride g.fstride).  DEV: the
 // register holds X - X0 (mixed-path float buffers) instead of X.
-template <typename T, typename S, bool DEV = false>
-__device__ __forceinline__ void rhs_point(const Grid& g, const S* __restrict__ st, long long id,
-                                          int i, int j, int k, T out[NF]) {
-  const long long fs = g.fstride;
-  const long long sd[3] = {1, g.pitch, g.plane};
+template <typename T, typename S, bool DEV, typename A>
+__device__ __forceinline__ void rhs_point_acc(const Grid& g, const A& acc, int i, int j, int k,
+                                              T out[NF]) {
   const T i12h = gc<T>(g.i12h, g.i12hf);
   const T i12h2 = gc<T>(g.i12h2, g.i12h2f);
   const T i144h2 = gc<T>(g.i144h2, g.i144h2f);
-#define PF(f) (st + (long long)(f) * fs + id)
+#define PF(f) acc.ptr(f)
+#define SD(f, d) acc.s((f), (d))
+#define LD(f, p) acc.template ld<T>((f), (p))
 
   // ---- point values (raw: as stored; chi, gt, alp: the field values)
-  const T chi_r = ldg<T>(PF(F_CHI));
+  const T chi_r = LD(F_CHI, PF(F_CHI));
   T gt_r[6], gt[6], At[6];
 #pragma unroll
   for (int m = 0; m < 6; m++) {
-    gt_r[m] = ldg<T>(PF(F_GT + m));
-    At[m] = ldg<T>(PF(F_AT + m));
+    gt_r[m] = LD(F_GT + m, PF(F_GT + m));
+    At[m] = LD(F_AT + m, PF(F_AT + m));
   }
-  T trK = ldg<T>(PF(F_TRK));
-  const T alp_r = ldg<T>(PF(F_ALP));
+  T trK = LD(F_TRK, PF(F_TRK));
+  const T alp_r = LD(F_ALP, PF(F_ALP));
   const T chi = DEV && g.use_w ? chi_r + T(1) : chi_r;
   const T alp = DEV ? alp_r + T(1) : alp_r;
 #pragma unroll
@@ -111,8 +148,8 @@ __device__ __forceinline__ void rhs_point(const Grid& g, const S* __restrict__ s
   T beta[3], Bv[3];
 #pragma unroll
   for (int a = 0; a < 3; a++) {
-    beta[a] = ldg<T>(PF(F_BETA + a));
-    Bv[a] = ldg<T>(PF(F_B + a));
+    beta[a] = LD(F_BETA + a, PF(F_BETA + a));
+    Bv[a] = LD(F_B + a, PF(F_B + a));
   }
 
   // ---- inverse conformal metric (cofactors / det)
@@ -136,14 +173,14 @@ __device__ __forceinline__ void rhs_point(const Grid& g, const S* __restrict__ s
 #pragma unroll
   for (int d = 0; d < 3; d++) {
 #pragma unroll
-    for (int m = 0; m < 6; m++) dgt[d][m] = d1u<T>(PF(F_GT + m), sd[d]) * i12h;
-    dchi[d] = d1u<T>(PF(F_CHI), sd[d]) * i12h;
-    dalp[d] = d1u<T>(PF(F_ALP), sd[d]) * i12h;
-    dK[d] = d1u<T>(PF(F_TRK), sd[d]) * i12h;
+    for (int m = 0; m < 6; m++) dgt[d][m] = d1u<T>(acc, F_GT + m, PF(F_GT + m), SD(F_GT + m, d)) * i12h;
+    dchi[d] = d1u<T>(acc, F_CHI, PF(F_CHI), SD(F_CHI, d)) * i12h;
+    dalp[d] = d1u<T>(acc, F_ALP, PF(F_ALP), SD(F_ALP, d)) * i12h;
+    dK[d] = d1u<T>(acc, F_TRK, PF(F_TRK), SD(F_TRK, d)) * i12h;
 #pragma unroll
     for (int a = 0; a < 3; a++) {
-      db[d][a] = d1u<T>(PF(F_BETA + a), sd[d]) * i12h;
-      dG[d][a] = d1u<T>(PF(F_GAM + a), sd[d]) * i12h;
+      db[d][a] = d1u<T>(acc, F_BETA + a, PF(F_BETA + a), SD(F_BETA + a, d)) * i12h;
+      dG[d][a] = d1u<T>(acc, F_GAM + a, PF(F_GAM + a), SD(F_GAM + a, d)) * i12h;
     }
   }
 
@@ -166,14 +203,14 @@ __device__ __forceinline__ void rhs_point(const Grid& g, const S* __restrict__ s
         T dd[6];
         if (pa == pb) {
 #pragma unroll
-          for (int m = 0; m < 6; m++) dd[m] = d2u<T>(PF(F_GT + m), sd[pa], gt_r[m]) * i12h2;
-          ddchi[pq] = d2u<T>(PF(F_CHI), sd[pa], chi_r) * i12h2;
-          ddalp[pq] = d2u<T>(PF(F_ALP), sd[pa], alp_r) * i12h2;
+          for (int m = 0; m < 6; m++) dd[m] = d2u<T>(acc, F_GT + m, PF(F_GT + m), SD(F_GT + m, pa), gt_r[m]) * i12h2;
+          ddchi[pq] = d2u<T>(acc, F_CHI, PF(F_CHI), SD(F_CHI, pa), chi_r) * i12h2;
+          ddalp[pq] = d2u<T>(acc, F_ALP, PF(F_ALP), SD(F_ALP, pa), alp_r) * i12h2;
         } else {
 #pragma unroll
-          for (int m = 0; m < 6; m++) dd[m] = dmu<T>(PF(F_GT + m), sd[pa], sd[pb]) * i144h2;
-          ddchi[pq] = dmu<T>(PF(F_CHI), sd[pa], sd[pb]) * i144h2;
-          ddalp[pq] = dmu<T>(PF(F_ALP), sd[pa], sd[pb]) * i144h2;
+          for (int m = 0; m < 6; m++) dd[m] = dmu<T>(acc, F_GT + m, PF(F_GT + m), SD(F_GT + m, pa), SD(F_GT + m, pb)) * i144h2;
+          ddchi[pq] = dmu<T>(acc, F_CHI, PF(F_CHI), SD(F_CHI, pa), SD(F_CHI, pb)) * i144h2;
+          ddalp[pq] = dmu<T>(acc, F_ALP, PF(F_ALP), SD(F_ALP, pa), SD(F_ALP, pb)) * i144h2;
         }
 #pragma unroll
         for (int m = 0; m < 6; m++) Rdd[m] = fmaT<T>(w, dd[m], Rdd[m]);
@@ -182,8 +219,9 @@ __device__ __forceinline__ void rhs_point(const Grid& g, const S* __restrict__ s
         const T wb = (pa == pb) ? gu[pq] : T(2) * gu[pq];
 #pragma unroll
         for (int a = 0; a < 3; a++) {
-          T v = (pa == pb) ? d2u<T>(PF(F_BETA + a), sd[pa], beta[a]) * i12h2
-                           : dmu<T>(PF(F_BETA + a), sd[pa], sd[pb]) * i144h2;
+          T v = (pa == pb) ? d2u<T>(acc, F_BETA + a, PF(F_BETA + a), SD(F_BETA + a, pa), beta[a]) * i12h2
+                           : dmu<T>(acc, F_BETA + a, PF(F_BETA + a), SD(F_BETA + a, pa),
+                                    SD(F_BETA + a, pb)) * i144h2;
           lapb[a] = fmaT<T>(wb, v, lapb[a]);
           // d_pa d_pb beta^a contributes to gdiv[pa] when a == pb, gdiv[pb] when a == pa
           if (a == pb) gdiv[pa] += v;
@@ -433,6 +471,7 @@ __device__ __forceinline__ void rhs_point(const Grid& g, const S* __restrict__ s
     if (f >= nf) out[f] = T(0);
   {
     const T kap = gc<T>(g.kos, g.kosf);
+    T f0s[NF];  // centre values as stored (float: the stencil is applied to f_m - f0)
     T bh[3];
 #pragma unroll
     for (int d = 0; d < 3; d++) bh[d] = fabs(beta[d]) * i12h;
@@ -448,8 +487,9 @@ __device__ __forceinline__ void rhs_point(const Grid& g, const S* __restrict__ s
       else if (f == F_ALP) f0 = alp_r;
       else if (f >= F_BETA && f < F_BETA + 3) f0 = beta[f - F_BETA];
       else if (f >= F_B) f0 = Bv[f - F_B];
-      else f0 = ldg<T>(PF(f));
-      out[f] = fmaT<T>(w0, f0, out[f]);
+      else f0 = LD(f, PF(f));
+      if constexpr (sizeof(T) == 8) out[f] = fmaT<T>(w0, f0, out[f]);
+      f0s[f] = f0;
     }
     const T cko[7] = {T(1), T(-6), T(15), T(-20), T(15), T(-6), T(1)};
 #pragma unroll
@@ -462,16 +502,33 @@ __device__ __forceinline__ void rhs_point(const Grid& g, const S* __restrict__ s
 #pragma unroll
       for (int f = 0; f < NF; f++) {
         if (f >= nf) break;
-        const S* p = PF(f);
-        T acc = out[f];
+        const auto* p = PF(f);
+        T accv = out[f];
+        if constexpr (sizeof(T) == 4) {
+          // the weights sum to zero: apply them to differences to the centre
 #pragma unroll
-        for (int m = -3; m <= 3; m++)
-          if (m != 0) acc = fmaT<T>(w[m + 3], ldg<T>(p + m * sd[d]), acc);
-        out[f] = acc;
+          for (int m = -3; m <= 3; m++)
+            if (m != 0) accv = fmaT<T>(w[m + 3], LD(f, p + m * SD(f, d)) - f0s[f], accv);
+        } else {
+#pragma unroll
+          for (int m = -3; m <= 3; m++)
+            if (m != 0) accv = fmaT<T>(w[m + 3], LD(f, p + m * SD(f, d)), accv);
+        }
+        out[f] = accv;
       }
     }
   }
 #undef PF
+#undef SD
+#undef LD
+}
+
+// Right-hand side reading every field from the global register st.
+template <typename T, typename S, bool DEV = false>
+__device__ __forceinline__ void rhs_point(const Grid& g, const S* __restrict__ st, long long id,
+                                          int i, int j, int k, T out[NF]) {
+  const GlobalAcc<S> acc(g, st, id);
+  rhs_point_acc<T, S, DEV>(g, acc, i, j, k, out);
 }
 
 }  // namespace bssn

@@ -81,13 +81,15 @@ __device__ __forceinline__ double chi_rhs_fp64(const Grid& g, const float* __res
   return r;
 }
 
-// Fused stage at interior point (ii, jj, kk), mixed precision.
-__device__ __forceinline__ void stage_point_mixed(const Grid& g, const StageArgsMixed& a, int ii,
-                                                  int jj, int kk) {
+// Fused stage at interior point (ii, jj, kk), mixed precision; the accessor
+// says where each field of the stage input is read from.
+template <typename A>
+__device__ __forceinline__ void stage_point_mixed_acc(const Grid& g, const StageArgsMixed& a,
+                                                      const A& acc, int ii, int jj, int kk) {
   const int i = ii + GH, j = jj + GH, k = kk + GH;
   const long long id = lin(g, i, j, k);
   float r[NF];
-  rhs_point<float, float, true>(g, a.src, id, i, j, k, r);
+  rhs_point_acc<float, float, true>(g, acc, i, j, k, r);
   const long long fs = g.fstride;
   // near a puncture the W update runs in float64
   const double w0 = a.srcw[id];
@@ -133,6 +135,12 @@ __device__ __forceinline__ void stage_point_mixed(const Grid& g, const StageArgs
     a.out0[o] = fmaf(af, r[f], a.src0[o]);
     a.ksum[o] = a.mode == MODE_FIRST ? r[f] : fmaf(2.0f, r[f], a.ksum[o]);
   }
+}
+
+__device__ __forceinline__ void stage_point_mixed(const Grid& g, const StageArgsMixed& a, int ii,
+                                                  int jj, int kk) {
+  const GlobalAcc<float> acc(g, a.src, lin(g, ii + GH, jj + GH, kk + GH));
+  stage_point_mixed_acc(g, a, acc, ii, jj, kk);
 }
 
 }  // namespace bssn
