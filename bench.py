@@ -35,10 +35,10 @@ N_SIDE = 128
 DOMAIN = 8.0
 # Float64 work per interior point per fused stage launch (right-hand side plus
 # RK4 combine), from the ncu instruction counts of the stage kernel
-# (profiles/stage_fp64_bl64.md): 1032 DADD + 308 DMUL + 1530 DFMA.
-FLOP_PER_POINT_RHS = 4400.0        # DADD + DMUL + 2 DFMA
-DPINST_PER_POINT_RHS = 2870.0      # float64 instructions issued
-HBM_BYTES_PER_POINT_STEP = 3072.0  # 16 register passes x 24 fields x 8 B
+# (profiles/stage_fp64_bl64.md): 594 DADD + 301 DMUL + 1533 DFMA.
+FLOP_PER_POINT_RHS = 3961.0        # DADD + DMUL + 2 DFMA
+DPINST_PER_POINT_RHS = 2428.0      # float64 instructions issued
+HBM_BYTES_PER_POINT_STEP = 3264.0  # 17 register passes x 24 fields x 8 B
 FP64_PEAK_GFLOPS = 1250.0          # nominal GB300 FP64 rate
 FP64_MEASURED_GFLOPS = 1196.0      # dependent-chain DFMA microbenchmark on this pool
 
@@ -216,7 +216,11 @@ def run_ours(args):
     evo = B.Evolution(params)
     evo.set_initial_data("bl", BL_P)
     stream = evo.stream
-    tile, tile_ms = B.bssn_autotune(evo.ctx, reps=5)  # untimed: picks the stage-kernel tiles
+    if args.tile:  # a fixed configuration (profiling captures)
+        tile = [B.bssn_tile_name(c) for c in range(B.bssn_tile_count())].index(args.tile)
+        B.bssn_set_tile(evo.ctx, tile)
+    else:
+        tile, tile_ms = B.bssn_autotune(evo.ctx, reps=5)  # untimed: picks the stage-kernel tiles
     for _ in range(args.warmup):
         evo.rk4_step(1)
     barrier(world)
@@ -454,6 +458,7 @@ def main():
                     default="puncture",
                     help="puncture: the benchmark line (single 128^3 puncture); batched / served: "
                          "the multi-evolution workloads, reported on their own lines")
+    ap.add_argument("--tile", default=None, help="stage-kernel configuration name (default: autotune)")
     ap.add_argument("--members", type=int, default=64)
     ap.add_argument("--requests", type=int, default=64)
     ap.add_argument("--budget-gb", type=float, default=64.0)
