@@ -153,6 +153,21 @@ bssn_status bssn_state_ptr(bssn_ctx* ctx, double** d_state);
  * EINVAL on an unknown kind or too few parameters. */
 bssn_status bssn_set_initial_data(bssn_ctx* ctx, int32_t kind, const double* p, int32_t np);
 
+/* General initial data from ADM fields (Sec. "Initial Conditions"): host_adm
+ * holds 16 float64 fields in the unpadded host layout, (16, n2+6, n1+6, n0+6):
+ * alpha, beta^x, beta^y, beta^z, gamma_xx, gamma_xy, gamma_xz, gamma_yy,
+ * gamma_yz, gamma_zz, K_xx, ..., K_zz, at every stored point.  The BSSN
+ * variables follow by their definitions with B^i = 0; Gt^i = gt^jk Gt^i_jk
+ * from 4th-order first derivatives of gt_ij at interior points and, on the
+ * outer ghost layers, by cubic extrapolation along the summed outward normal
+ * (faces perpendicular, edges and corners diagonal), innermost layer first;
+ * periodic grids copy their ghosts instead.  Synchronises; sets t. */
+bssn_status bssn_set_adm(bssn_ctx* ctx, const double* host_adm, double t);
+
+/* Punctures {m, x, y, z} x npunct (npunct 0..8) that define the excised set of
+ * the constraint norms (set_initial_data with BSSN_ID_BL sets them too). */
+bssn_status bssn_set_punctures(bssn_ctx* ctx, const double* p, int32_t npunct);
+
 /* One right-hand side, interior points by the BSSN equations (4th-order
  * centred stencils, upwinded advection, KO dissipation), ghost points by the
  * Sommerfeld condition (or 0 when periodic).  d_state: a float64 register in

@@ -165,10 +165,18 @@ def _load():
     lib.oracle_initial_data.argtypes = [cp, ctypes.c_int, dp, ctypes.c_int, dp]
     lib.oracle_initial_data.restype = ctypes.c_int
     lib.oracle_adm_to_bssn.argtypes = [cp, dp, dp, dp, dp, dp]
+    lib.oracle_extrapolate_ghosts.argtypes = [cp, dp]
+    lib.oracle_adm_to_bssn_fd.argtypes = [cp, dp, dp]
+    lib.oracle_adm_to_bssn_fd.restype = ctypes.c_int
     lib.oracle_constraints.argtypes = [cp, dp, dp, dp, dp]
     lib.oracle_constraints.restype = ctypes.c_int
     lib.oracle_constraints_points.argtypes = [cp, dp, ctypes.c_int, ip, dp]
     lib.oracle_constraints_points.restype = ctypes.c_int
+    lib.oracle_adm_integrals.argtypes = [cp, dp, dp, dp]
+    lib.oracle_adm_integrals.restype = ctypes.c_int
+    lib.oracle_interp.argtypes = [cp, dp, dp]
+    lib.oracle_interp.restype = ctypes.c_double
+    lib.oracle_track_step.argtypes = [cp, dp, ctypes.c_int, dp, ctypes.c_double]
     _lib = lib
     return lib
 
@@ -275,6 +283,29 @@ def adm_to_bssn(cfg: Config, alpha, beta3, gam6, K6) -> np.ndarray:
     return st
 
 
+def extrapolate_ghosts(cfg: Config, f: np.ndarray) -> np.ndarray:
+    """Cubic extrapolation of a scalar grid's ghost points from its interior."""
+    lib = _load()
+    f = np.ascontiguousarray(f, dtype=np.float64).copy()
+    assert f.shape == cfg.shape[1:]
+    c = cfg._c()
+    lib.oracle_extrapolate_ghosts(ctypes.byref(c), _dp(f))
+    return f
+
+
+def adm_to_bssn_fd(cfg: Config, adm16: np.ndarray) -> np.ndarray:
+    """BSSN state from ADM grids (16, Z, Y, X): alpha, beta^i, gamma_ij (6),
+    K_ij (6); Gt^i by 4th-order differences inside, cubic extrapolation (or
+    periodic copy) on the ghost layers, B^i = 0."""
+    lib = _load()
+    adm16 = np.ascontiguousarray(adm16, dtype=np.float64)
+    assert adm16.shape == (16,) + cfg.shape[1:]
+    st = np.zeros(cfg.shape)
+    c = cfg._c()
+    lib.oracle_adm_to_bssn_fd(ctypes.byref(c), _dp(adm16), _dp(st))
+    return st
+
+
 def constraints(cfg: Config, st: np.ndarray):
     """(norms16, H, M): norms in the order L2 H,Mx,My,Mz, Linf H,Mx,My,Mz,
     full interior then excised; H (grid) and M (3, grid) at interior points."""
@@ -300,3 +331,35 @@ def constraints_points(cfg: Config, st: np.ndarray, ijk: np.ndarray) -> np.ndarr
                                      _dp(out)) != 0:
         raise MemoryError("oracle_constraints_points: allocation failed")
     return out
+
+
+def adm_integrals(cfg: Config, st: np.ndarray):
+    """(integrals8, dens): M, J_x, J_y, J_z as midpoint sums over all interior
+    points, then over the points farther than r_excise from every puncture;
+    dens (4, grid) holds the four integrands at interior points (0 elsewhere)."""
+    lib = _load()
+    st = _state(cfg, st)
+    out = np.zeros(8)
+    dens = np.zeros((4,) + cfg.shape[1:])
+    c = cfg._c()
+    lib.oracle_adm_integrals(ctypes.byref(c), _dp(st), _dp(out), _dp(dens))
+    return out, dens
+
+
+def interp(cfg: Config, f: np.ndarray, xyz) -> float:
+    """Tricubic Lagrange interpolation of one grid function at a point."""
+    lib = _load()
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    assert f.shape == cfg.shape[1:]
+    p = np.ascontiguousarray(xyz, dtype=np.float64)
+    return lib.oracle_interp(ctypes.byref(cfg._c()), _dp(f), _dp(p))
+
+
+def track_step(cfg: Config, st: np.ndarray, punctures, dt: float) -> np.ndarray:
+    """One forward-Euler step of dx/dt = -beta at every puncture; punctures is
+    (np, 4) rows {m, x, y, z}; returns the moved rows."""
+    lib = _load()
+    st = _state(cfg, st)
+    pos = np.array(punctures, dtype=np.float64).reshape(-1, 4).copy()
+    lib.oracle_track_step(ctypes.byref(cfg._c()), _dp(st), pos.shape[0], _dp(pos), float(dt))
+    return pos

@@ -823,6 +823,76 @@ void oracle_adm_to_bssn(const ocfg* c, const double* alpha, const double* beta3,
   }
 }
 
+/* ------------------------------------- ADM -> BSSN with Gt by differences
+ * Sec. "Initial Conditions": the BSSN variables from their definitions, with
+ * B^i = 0 and Gt^i = gt^{jk} Gt^i_jk from 4th-order first derivatives of gt_ij
+ * at interior points, and cubic extrapolation of Gt^i at the outer boundary:
+ * points on faces are extrapolated perpendicular to the face, points on edges
+ * and corners along the sum of the adjoining faces' normals, layer by layer
+ * from the innermost, each layer from the interior and the layers already set.
+ * Reading: the extrapolation through the four points b - n, ..., b - 4n is the
+ * cubic one, v(b) = 4 v(b-n) - 6 v(b-2n) + 4 v(b-3n) - v(b-4n). */
+
+/* Cubic extrapolation of a scalar grid's ghost points from its interior. */
+void oracle_extrapolate_ghosts(const ocfg* c, double* f) {
+  const int X = dimx(c, 0), Y = dimx(c, 1), Z = dimx(c, 2);
+  for (int L = 1; L <= GH; L++)
+    for (int k = 0; k < Z; k++)
+      for (int j = 0; j < Y; j++)
+        for (int i = 0; i < X; i++) {
+          int n[3];
+          if (layer_of(c, i, j, k, n) != L) continue;
+          double v[5];
+          for (int m = 1; m <= 4; m++) v[m] = f[pidx(c, i - m * n[0], j - m * n[1], k - m * n[2])];
+          f[pidx(c, i, j, k)] = 4.0 * v[1] - 6.0 * v[2] + 4.0 * v[3] - v[4];
+        }
+}
+
+/* adm16[q][k][j][i]: q = alpha, beta^x, beta^y, beta^z, gamma_xx..zz (6), K_xx..zz (6). */
+int oracle_adm_to_bssn_fd(const ocfg* c, const double* adm16, double* st) {
+  const size_t S = npts(c);
+  const ptrdiff_t str[3] = {1, dimx(c, 0), (ptrdiff_t)dimx(c, 0) * dimx(c, 1)};
+  for (size_t id = 0; id < S; id++) {
+    double g[3][3], K[3][3], b[3], Gt[3] = {0, 0, 0}, o[NF];
+    for (int a = 0; a < 3; a++)
+      for (int bb = 0; bb < 3; bb++) {
+        g[a][bb] = adm16[(size_t)(4 + SYM[a][bb]) * S + id];
+        K[a][bb] = adm16[(size_t)(10 + SYM[a][bb]) * S + id];
+      }
+    for (int a = 0; a < 3; a++) b[a] = adm16[(size_t)(1 + a) * S + id];
+    adm_to_bssn(c, adm16[id], b, g, K, Gt, o);
+    for (int f = 0; f < NF; f++) st[(size_t)f * S + id] = o[f];
+  }
+  /* Gt^i = gt^{jk} gt^{il} Gt_ljk at interior points */
+  for (int k = GH; k < GH + c->n[2]; k++)
+    for (int j = GH; j < GH + c->n[1]; j++)
+      for (int i = GH; i < GH + c->n[0]; i++) {
+        size_t id = pidx(c, i, j, k);
+        double g[3][3], gu[3][3], dg[3][3][3];
+        for (int a = 0; a < 3; a++)
+          for (int bb = 0; bb < 3; bb++) {
+            const double* p = st + (size_t)(F_GT + SYM[a][bb]) * S + id;
+            g[a][bb] = p[0];
+            for (int d = 0; d < 3; d++) dg[d][a][bb] = st_d1(p, str[d], c->h);
+          }
+        inv3(g, gu);
+        for (int a = 0; a < 3; a++) {
+          double s = 0.0;
+          for (int jj = 0; jj < 3; jj++)
+            for (int kk = 0; kk < 3; kk++)
+              for (int l = 0; l < 3; l++)
+                s += gu[jj][kk] * gu[a][l] * 0.5 * (dg[jj][l][kk] + dg[kk][l][jj] - dg[l][jj][kk]);
+          st[(size_t)(F_GAM + a) * S + id] = s;
+        }
+      }
+  if (c->periodic) {
+    oracle_fill_periodic(c, st);
+  } else {
+    for (int a = 0; a < 3; a++) oracle_extrapolate_ghosts(c, st + (size_t)(F_GAM + a) * S);
+  }
+  return 0;
+}
+
 /* -------------------------------------------------------- constraints
  * Sec. "Other analysis modules": H = R - K^i_j K^j_i + K^2 and
  * M_i = nabla_j K_i^j - nabla_i K (vacuum), from the ADM variables
@@ -1009,4 +1079,235 @@ int oracle_constraints_points(const ocfg* c, const double* st, int np, const int
   free(gam6);
   free(K6);
   return 0;
+}
+
+/* ------------------------------------------ ADM mass and angular momentum
+ * Sec. "Masses and Momenta" (volume-integral form of ML_ADMQuantities):
+ *   M   = 1/(16 pi) int d^3x [ e^{5 phi}(16 pi E + At_ij At^ij - (2/3) K^2)
+ *                              - e^{phi} Rt ]
+ *   J_i = 1/(8 pi) eps_ij^k int d^3x e^{6 phi} [ At^j_k + (2/3) x^j Dt_k K
+ *                              - (1/2) x^j At_ln d_k gt^{ln} + 8 pi x^j S_k ]
+ * in vacuum (E = S_k = 0).  Readings:
+ *  - Rt = gt^ij Rt_ij with the same Rt_ij as the right-hand side (the
+ *    evolved Gt^k in gt_k(i d_j) Gt^k, the metric-derived d_l gt^{lk}
+ *    elsewhere), from the same 4th-order stencils;
+ *  - Dt_k K = d_k K (a scalar), 4th-order centred;
+ *  - d_k gt^{ln} = -gt^{la} gt^{nb} d_k gt_ab (derivative of the inverse);
+ *  - At^j_k = gt^{jl} At_lk, At^ij = gt^ia gt^jb At_ab;
+ *  - eps_ij^k is the Levi-Civita symbol of the Cartesian grid coordinates,
+ *    and x^j the grid coordinates themselves (origin at x = 0);
+ *  - e^{phi} = W^{-1/2} in the W variant, with W floored at w_floor there
+ *    (the only place it divides);
+ *  - the integral is the midpoint sum h^3 sum over the interior points (each
+ *    point is the centre of a cell of the interior block), over all of them
+ *    and over the points farther than r_excise from every puncture.
+ * Pins: for exact vacuum data the integrands are divergences (the
+ * Hamiltonian and momentum constraints), -(1/2 pi) d_i(gt^ij d_j psi) and
+ * (1/8 pi) eps_ijk d_l(x^j psi^6 At^l_k) with psi = e^{phi}, which the tests
+ * evaluate exactly and compare at 4th order; the box sums converge to the
+ * corresponding surface integrals.
+ */
+static void adm_density_point(const ocfg* c, const double* st, int i, int j, int k,
+                              double out[4]) {
+  const size_t S = npts(c);
+  const size_t id = pidx(c, i, j, k);
+  const ptrdiff_t str[3] = {1, dimx(c, 0), (ptrdiff_t)dimx(c, 0) * dimx(c, 1)};
+  const double h = c->h;
+  const double* P0 = st + id;
+  double chi = P0[(size_t)F_CHI * S];
+  double trK = P0[(size_t)F_TRK * S];
+  double g[3][3], A[3][3];
+  for (int a = 0; a < 3; a++)
+    for (int b = 0; b < 3; b++) {
+      g[a][b] = P0[(size_t)(F_GT + SYM[a][b]) * S];
+      A[a][b] = P0[(size_t)(F_AT + SYM[a][b]) * S];
+    }
+  double dg[3][3][3], ddg[3][3][3][3], dGt[3][3], dK[3];
+  for (int kk = 0; kk < 3; kk++) {
+    for (int a = 0; a < 3; a++)
+      for (int b = 0; b < 3; b++) {
+        const double* p = P0 + (size_t)(F_GT + SYM[a][b]) * S;
+        dg[kk][a][b] = st_d1(p, str[kk], h);
+        for (int l = 0; l < 3; l++) ddg[kk][l][a][b] = st_dd(p, str, kk, l, h);
+      }
+    for (int a = 0; a < 3; a++) dGt[kk][a] = st_d1(P0 + (size_t)(F_GAM + a) * S, str[kk], h);
+    dK[kk] = st_d1(P0 + (size_t)F_TRK * S, str[kk], h);
+  }
+  double gu[3][3];
+  inv3(g, gu);
+  double G1[3][3][3], G2[3][3][3], dgu[3];
+  for (int kk = 0; kk < 3; kk++)
+    for (int a = 0; a < 3; a++)
+      for (int b = 0; b < 3; b++)
+        G1[kk][a][b] = 0.5 * (dg[a][kk][b] + dg[b][kk][a] - dg[kk][a][b]);
+  for (int kk = 0; kk < 3; kk++)
+    for (int a = 0; a < 3; a++)
+      for (int b = 0; b < 3; b++) {
+        double s = 0.0;
+        for (int l = 0; l < 3; l++) s += gu[kk][l] * G1[l][a][b];
+        G2[kk][a][b] = s;
+      }
+  for (int kk = 0; kk < 3; kk++) {
+    double s = 0.0;
+    for (int l = 0; l < 3; l++)
+      for (int a = 0; a < 3; a++)
+        for (int b = 0; b < 3; b++) s -= gu[l][a] * gu[kk][b] * dg[l][a][b];
+    dgu[kk] = s;
+  }
+  /* Rt_ij exactly as in the right-hand side, then its trace */
+  double Rt_trace = 0.0;
+  for (int a = 0; a < 3; a++)
+    for (int b = 0; b < 3; b++) {
+      double s = 0.0;
+      for (int kk = 0; kk < 3; kk++)
+        for (int l = 0; l < 3; l++) s += -0.5 * gu[kk][l] * ddg[kk][l][a][b];
+      for (int kk = 0; kk < 3; kk++)
+        s += 0.5 * (g[kk][a] * dGt[b][kk] + g[kk][b] * dGt[a][kk]);
+      for (int kk = 0; kk < 3; kk++)
+        s -= 0.5 * (G1[a][b][kk] + G1[b][a][kk]) * dgu[kk];
+      for (int l = 0; l < 3; l++)
+        for (int m = 0; m < 3; m++) {
+          double t = 0.0;
+          for (int kk = 0; kk < 3; kk++)
+            t += G2[kk][l][a] * G1[b][kk][m] + G2[kk][l][b] * G1[a][kk][m] +
+                 G2[kk][a][m] * G1[kk][l][b];
+          s += gu[l][m] * t;
+        }
+      Rt_trace += gu[a][b] * s;
+    }
+  /* e^{phi} */
+  double ephi;
+  if (c->use_w) {
+    double Wd = chi > c->w_floor ? chi : c->w_floor;
+    ephi = 1.0 / sqrt(Wd);
+  } else {
+    ephi = exp(chi);
+  }
+  double e5 = pow(ephi, 5.0), e6 = pow(ephi, 6.0);
+  /* At^ij, At^j_k, At_ij At^ij */
+  double Au[3][3], Am[3][3], AA = 0.0;
+  for (int a = 0; a < 3; a++)
+    for (int b = 0; b < 3; b++) {
+      double s = 0.0, m = 0.0;
+      for (int p = 0; p < 3; p++) {
+        m += gu[a][p] * A[p][b];
+        for (int q = 0; q < 3; q++) s += gu[a][p] * gu[b][q] * A[p][q];
+      }
+      Au[a][b] = s;
+      Am[a][b] = m;
+    }
+  for (int a = 0; a < 3; a++)
+    for (int b = 0; b < 3; b++) AA += A[a][b] * Au[a][b];
+  out[0] = (e5 * (AA - (2.0 / 3.0) * trK * trK) - ephi * Rt_trace) / (16.0 * M_PI);
+  /* d_k gt^{ln} and At_ln d_k gt^{ln} */
+  double AdG[3];
+  for (int kk = 0; kk < 3; kk++) {
+    double s = 0.0;
+    for (int l = 0; l < 3; l++)
+      for (int n = 0; n < 3; n++) {
+        double dgtu = 0.0;
+        for (int a = 0; a < 3; a++)
+          for (int b = 0; b < 3; b++) dgtu -= gu[l][a] * gu[n][b] * dg[kk][a][b];
+        s += A[l][n] * dgtu;
+      }
+    AdG[kk] = s;
+  }
+  const double x[3] = {coord(c, 0, i), coord(c, 1, j), coord(c, 2, k)};
+  for (int ii = 0; ii < 3; ii++) {
+    double s = 0.0;
+    for (int jj = 0; jj < 3; jj++)
+      for (int kk = 0; kk < 3; kk++) {
+        /* Levi-Civita symbol eps_{ii jj kk} */
+        double eps = (double)((ii - jj) * (jj - kk) * (kk - ii)) / 2.0;
+        if (eps == 0.0) continue;
+        double v = Am[jj][kk] + (2.0 / 3.0) * x[jj] * dK[kk] - 0.5 * x[jj] * AdG[kk];
+        s += eps * e6 * v;
+      }
+    out[1 + ii] = s / (8.0 * M_PI);
+  }
+}
+
+/* Volume integrals M, J_x, J_y, J_z over all interior points (out8[0..3])
+ * and over the points farther than r_excise from every puncture
+ * (out8[4..7]).  dens (may be NULL) receives the four integrands at every
+ * interior point, (4, stored points); other points are left untouched. */
+int oracle_adm_integrals(const ocfg* c, const double* st, double* out8, double* dens) {
+  const size_t S = npts(c);
+  double sum[2][4] = {{0}};
+  for (int k = GH; k < GH + c->n[2]; k++)
+    for (int j = GH; j < GH + c->n[1]; j++)
+      for (int i = GH; i < GH + c->n[0]; i++) {
+        double o[4];
+        adm_density_point(c, st, i, j, k, o);
+        size_t id = pidx(c, i, j, k);
+        if (dens)
+          for (int q = 0; q < 4; q++) dens[(size_t)q * S + id] = o[q];
+        double x = coord(c, 0, i), y = coord(c, 1, j), z = coord(c, 2, k);
+        int outside = 1;
+        for (int a = 0; a < c->npunct; a++) {
+          double dx = x - c->punct[a][1], dy = y - c->punct[a][2], dz = z - c->punct[a][3];
+          if (sqrt(dx * dx + dy * dy + dz * dz) <= c->r_excise) outside = 0;
+        }
+        for (int q = 0; q < 4; q++) {
+          sum[0][q] += o[q];
+          if (outside) sum[1][q] += o[q];
+        }
+      }
+  const double vol = c->h * c->h * c->h;
+  for (int set = 0; set < 2; set++)
+    for (int q = 0; q < 4; q++) out8[set * 4 + q] = sum[set][q] * vol;
+  return 0;
+}
+
+/* ------------------------------------------------------ puncture tracking
+ * Sec. "Object tracking": each puncture moves by dx^i/dt = -beta^i at its
+ * position, integrated by forward Euler, x_{n+1} = x_n - dt beta^i(t_n, x_n),
+ * with the shift of the state at the start of the step.  Readings: the
+ * shift is interpolated by the tensor product of 4-point Lagrange
+ * polynomials (cubic in each direction) on the stored points i0-1 .. i0+2,
+ * i0 the stored point at or below the position; the stencil is shifted to
+ * stay inside the stored block (then the polynomial extrapolates).
+ */
+static double lagrange4(int m, double u) {
+  /* basis polynomial of node m in {-1, 0, 1, 2}, evaluated at u */
+  double v = 1.0;
+  for (int n = -1; n <= 2; n++)
+    if (n != m) v *= (u - n) / (double)(m - n);
+  return v;
+}
+
+static void interp_setup(const ocfg* c, int d, double x, int* i0, double* u) {
+  double s = (x - coord(c, d, 0)) / c->h;  /* position in stored-index units */
+  int b = (int)floor(s);
+  if (b < 1) b = 1;
+  if (b > dimx(c, d) - 3) b = dimx(c, d) - 3;
+  *i0 = b;
+  *u = s - b;
+}
+
+/* Tricubic Lagrange interpolation of grid function f at (x, y, z). */
+double oracle_interp(const ocfg* c, const double* f, const double xyz[3]) {
+  int i0[3];
+  double u[3];
+  for (int d = 0; d < 3; d++) interp_setup(c, d, xyz[d], &i0[d], &u[d]);
+  double s = 0.0;
+  for (int mk = -1; mk <= 2; mk++)
+    for (int mj = -1; mj <= 2; mj++)
+      for (int mi = -1; mi <= 2; mi++)
+        s += lagrange4(mi, u[0]) * lagrange4(mj, u[1]) * lagrange4(mk, u[2]) *
+             f[pidx(c, i0[0] + mi, i0[1] + mj, i0[2] + mk)];
+  return s;
+}
+
+/* One Euler step of every puncture: pos[a] = {m, x, y, z}, a < np, updated in
+ * place from the shift of st. */
+void oracle_track_step(const ocfg* c, const double* st, int np, double* pos, double dt) {
+  const size_t S = npts(c);
+  for (int a = 0; a < np; a++) {
+    double* p = pos + 4 * a;
+    double xyz[3] = {p[1], p[2], p[3]};
+    double beta[3];
+    for (int d = 0; d < 3; d++) beta[d] = oracle_interp(c, st + (size_t)(F_BETA + d) * S, xyz);
+    for (int d = 0; d < 3; d++) p[1 + d] = xyz[d] - dt * beta[d];
+  }
 }

@@ -128,6 +128,8 @@ _SIGS = [
     ("bssn_get_state", [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     ("bssn_set_state", [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double], ctypes.c_int),
     ("bssn_profile", [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+    ("bssn_set_adm", [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double], ctypes.c_int),
+    ("bssn_set_punctures", [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int32], ctypes.c_int),
     ("bssn_tile_count", [], ctypes.c_int32),
     ("bssn_tile_name", [ctypes.c_int32], ctypes.c_char_p),
     ("bssn_set_tile", [ctypes.c_void_p, ctypes.c_int32], ctypes.c_int),
@@ -249,6 +251,16 @@ def bssn_state_ptr(ctx: int) -> int:
 def bssn_set_initial_data(ctx: int, kind: str, p=()):
     arr = _dbl_array(p)
     _check(load().bssn_set_initial_data(ctypes.c_void_p(ctx), ID_KIND[kind], arr, len(p)))
+
+
+def bssn_set_adm(ctx: int, host_adm: np.ndarray, t: float = 0.0):
+    assert host_adm.dtype == np.float64 and host_adm.flags.c_contiguous
+    _check(load().bssn_set_adm(ctypes.c_void_p(ctx), ctypes.c_void_p(host_adm.ctypes.data), float(t)))
+
+
+def bssn_set_punctures(ctx: int, punctures=()):
+    flat = [float(v) for q in punctures for v in q]
+    _check(load().bssn_set_punctures(ctypes.c_void_p(ctx), _dbl_array(flat), len(punctures)))
 
 
 def bssn_rhs(ctx: int, d_state, d_rhs: int):
@@ -399,6 +411,14 @@ class Evolution:
 
     def set_state(self, host: np.ndarray, t: float = 0.0):
         bssn_set_state(self.ctx, np.ascontiguousarray(host, dtype=np.float64), t)
+
+    def set_adm(self, adm16: np.ndarray, t: float = 0.0):
+        adm16 = np.ascontiguousarray(adm16, dtype=np.float64)
+        assert adm16.shape == (16,) + self.shape[1:]
+        bssn_set_adm(self.ctx, adm16, t)
+
+    def set_punctures(self, punctures=()):
+        bssn_set_punctures(self.ctx, punctures)
 
 
 # ---------------------------------------------------------------- batches

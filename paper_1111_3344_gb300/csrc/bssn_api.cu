@@ -312,6 +312,29 @@ bssn_status bssn_set_initial_data(bssn_ctx* ctx, int32_t kind, const double* p, 
   return BSSN_OK;
 }
 
+bssn_status bssn_set_adm(bssn_ctx* ctx, const double* host_adm, double t) {
+  if (!ctx || !host_adm) return fail(BSSN_EINVAL, "NULL argument");
+  const Grid& g = ctx->g;
+  cudaError_t e = cudaMemcpy2DAsync(ctx->yn, (size_t)g.pitch * sizeof(double), host_adm,
+                                    (size_t)g.sx * sizeof(double), (size_t)g.sx * sizeof(double),
+                                    (size_t)16 * g.sz * g.sy, cudaMemcpyHostToDevice, ctx->stream);
+  if (e == cudaSuccess) e = launch_adm_to_bssn(g, ctx->yn, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "set_adm");
+  ctx->t = t;
+  ctx->shadow_valid = false;
+  return BSSN_OK;
+}
+
+bssn_status bssn_set_punctures(bssn_ctx* ctx, const double* p, int32_t npunct) {
+  if (!ctx || npunct < 0 || npunct > 8 || (npunct > 0 && !p))
+    return fail(BSSN_EINVAL, "npunct must be 0..8 with 4 values {m, x, y, z} each");
+  ctx->npunct = npunct;
+  for (int a = 0; a < npunct; a++)
+    for (int q = 0; q < 4; q++) ctx->punct[a][q] = p[4 * a + q];
+  return BSSN_OK;
+}
+
 bssn_status bssn_rhs(bssn_ctx* ctx, const void* d_state, void* d_rhs) {
   if (!ctx || !d_rhs) return fail(BSSN_EINVAL, "NULL argument");
   const double* src = d_state ? (const double*)d_state : ctx->yn;

@@ -181,6 +181,9 @@ cudaError_t launch_constraints(const Grid& g, const double* y, const double* dpu
                                int npunct, double r_excise, double* partials, int nblocks,
                                double* dout16, cudaStream_t s);
 int constraints_blocks(const Grid& g);
+// y's first 16 field slots hold ADM data (alpha, beta^i, gamma_ij, K_ij);
+// converts it in place to the BSSN state (k_adm.cu).
+cudaError_t launch_adm_to_bssn(const Grid& g, double* y, cudaStream_t s);
 
 // Sets the message bssn_last_error() returns on the calling thread.
 void set_last_error(const std::string& msg);

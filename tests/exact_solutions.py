@@ -194,4 +194,33 @@ def evaluate(name: str, X, Y, Z, time=0.0, use_w=True):
         "Gt": np.stack([np.stack([dx(Gt[i], k).val for k in range(3)]) for i in range(3)]),
         "B": np.stack([np.stack([dx(Bv[i], k).val for k in range(3)]) for i in range(3)]),
     }
+    # Integrands of the ADM mass and angular momentum volume integrals: on
+    # exact vacuum data the Hamiltonian and momentum constraints make them
+    # divergences of the fluxes
+    #   F^i   = -(1/2 pi) gt^ij d_j psi                       (M)
+    #   G_i^l = (1/8 pi) eps_ijk x^j psi^6 gt^lm At_mk        (J_i)
+    # with psi = e^{phi} = det(gamma)^{1/12}; the exact integrands are
+    # d_i F^i and d_l G_i^l, and the box integrals are the outward fluxes.
+    psi = det ** (1.0 / 12.0)
+    psi6 = det ** 0.5
+    Fm = [sum((gtu[i][j] * dx(psi, j) for j in range(3)), Jet.const(0.0, shape)) * (-1.0 / (2 * np.pi))
+          for i in range(3)]
+    At3 = [[At[SYM6.index((min(a, b), max(a, b)))] for b in range(3)] for a in range(3)]
+    Amix = [[sum((gtu[l][m] * At3[m][k] for m in range(3)), Jet.const(0.0, shape)) for k in range(3)]
+            for l in range(3)]
+    G = [[Jet.const(0.0, shape) for _ in range(3)] for _ in range(3)]
+    for i in range(3):
+        for j in range(3):
+            for k in range(3):
+                eps = (i - j) * (j - k) * (k - i) / 2
+                if eps == 0:
+                    continue
+                for l in range(3):
+                    G[i][l] = G[i][l] + xs[j] * psi6 * Amix[l][k] * (eps / (8 * np.pi))
+    grad["M_dens"] = sum(dx(Fm[i], i).val for i in range(3))
+    grad["J_dens"] = np.stack([sum(dx(G[i][l], l).val for l in range(3)) for i in range(3)])
+    grad["M_flux"] = np.stack([f.val for f in Fm])
+    grad["J_flux"] = np.stack([np.stack([G[i][l].val for l in range(3)]) for i in range(3)])
+    grad["adm"] = np.stack([alpha.val] + [b.val for b in bu] +
+                           [gam[i][j].val for (i, j) in SYM6] + [Kij[i][j].val for (i, j) in SYM6])
     return np.ascontiguousarray(state), dts, grad

@@ -178,3 +178,39 @@ def test_tile_configs_agree_and_are_deterministic(torch_cuda, precision):
     assert best in runs
     evo.rk4_step(2)
     assert np.array_equal(evo.get_state()[0], runs[best])
+
+
+@pytest.mark.parametrize("name,box,periodic", [("ks_wavy", (1.5, 2.5), False), ("flat_wavy", (-0.5, 0.5), False),
+                                               ("gauge_wave", (-0.5, 0.5), True)])
+@pytest.mark.parametrize("conformal", ["W", "phi"])
+def test_set_adm_parity(torch_cuda, name, box, periodic, conformal):
+    """General ADM -> BSSN (Gt by differences, cubic extrapolation on the outer
+    layers) against the oracle, on exact-spacetime ADM data."""
+    import exact_solutions as E
+    lo, hi = box
+    n = (20, 17, 23)
+    case = dict(n=n, xmin=(lo, lo, lo), h=(hi - lo) / 20, boundary="periodic" if periodic else "sommerfeld",
+                conformal=conformal)
+    cfg = oracle_cfg(case)
+    Zc, Yc, Xc = np.meshgrid(cfg.coords(2), cfg.coords(1), cfg.coords(0), indexing="ij")
+    _, _, grad = E.evaluate(name, Xc, Yc, Zc, use_w=conformal == "W")
+    adm = np.ascontiguousarray(grad["adm"])
+    want = O.adm_to_bssn_fd(cfg, adm)
+    evo = _evo(case)
+    evo.set_adm(adm, 0.25)
+    got, t = evo.get_state()
+    # interior points: normwise per field within 1e-12
+    inner = (slice(None), slice(3, -3), slice(3, -3), slice(3, -3))
+    e = normwise_errors(got[inner], want[inner])
+    assert e.max() <= 1e-12, dict(zip(O.FIELD_NAMES, e))
+    # ghost layers: the cubic extrapolation v = 4 v1 - 6 v2 + 4 v3 - v4 carries
+    # an input error forward with gain |4|+|6|+|4|+|1| = 15 on the first layer,
+    # 4*15 + 11 = 71 on the second and 4*71 + 6*15 + 5 = 379 on the third, so
+    # the ghosts agree to 379 times the interior error plus the rounding of the
+    # sums themselves (a few ulp of the field's scale per layer).
+    d_in = np.abs(got[inner] - want[inner]).reshape(24, -1).max(axis=1)
+    d_all = np.abs(got - want).reshape(24, -1).max(axis=1)
+    scale = np.abs(want).reshape(24, -1).max(axis=1)
+    bound = 379.0 * d_in + 1e-13 * np.maximum(scale, 1e-3 * scale.max())
+    assert (d_all <= bound).all(), dict(zip(O.FIELD_NAMES, d_all / np.maximum(bound, 1e-300)))
+    assert t == 0.25
