@@ -41,6 +41,9 @@ DPINST_PER_POINT_RHS = 2428.0      # float64 instructions issued
 HBM_BYTES_PER_POINT_STEP = 3264.0  # 17 register passes x 24 fields x 8 B
 FP64_PEAK_GFLOPS = 1250.0          # nominal GB300 FP64 rate
 FP64_MEASURED_GFLOPS = 1196.0      # dependent-chain DFMA microbenchmark on this pool
+# Float64 work per interior point of the analysis kernels (DADD + DMUL + 2 DFMA
+# from ncu instruction counts; profiles/analysis_kernels_bl128.md).
+ANALYSIS_FLOP_PER_POINT = {"psi4": 0.0, "adm_integrals": 0.0, "constraints": 0.0}
 
 
 def workload_params(precision="fp64"):
@@ -446,6 +449,76 @@ def run_precision(args):
     print(json.dumps(line))
 
 
+def run_analysis(args):
+    """The analysis steps after the evolution on the benchmark puncture:
+    Weyl scalar Psi4, ADM mass / angular momentum volume integrals, constraint
+    norms (all float64), each timed over K launches with CUDA events on the
+    library's stream after W warm-up launches; and the puncture tracker's cost
+    per RK4 step (steps with and without tracking)."""
+    import torch
+
+    from paper_1111_3344_gb300 import bssn as B
+    torch.cuda.set_device(0)
+    evo = B.Evolution(workload_params("fp64"))
+    evo.set_initial_data("bl", BL_P)
+    B.bssn_autotune(evo.ctx, reps=2)
+    evo.rk4_step(4)  # a state with shift, B and K away from their initial zeros
+    pts = N_SIDE ** 3
+    psi4_out = evo.psi4()
+    stream = evo.stream
+    kernels = {"psi4": lambda: evo.psi4(psi4_out), "adm_integrals": lambda: evo.adm_integrals(),
+               "constraints": lambda: evo.constraints()}
+    clocks = ClockSampler(0)
+    clocks.start()
+    res = {}
+    for name, fn in kernels.items():
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            fn()
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        res[name] = {"ms": ms, "Mpoints_per_s": pts / ms / 1e3,
+                     "fp64_gflops": ANALYSIS_FLOP_PER_POINT[name] * pts / (ms * 1e-3) / 1e9}
+    # tracker: RK4 steps with and without it
+    times = {}
+    for track in (False, True):
+        evo.set_punctures([(1.0, 0.0, 0.0, 0.0)])
+        evo.track_punctures(track)
+        evo.rk4_step(1)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        evo.rk4_step(args.steps)
+        e1.record(stream)
+        e1.synchronize()
+        times[track] = e0.elapsed_time(e1) / args.steps
+    clk = clocks.stop()
+    evo.close()
+    top = res["psi4"]
+    line = {
+        "metric": "BSSN analysis point-evaluations/s (Psi4, Brill-Lindquist puncture 128^3)",
+        "value": top["Mpoints_per_s"], "unit": "Mpoints/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": top["ms"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "Psi4 / ADM integrals / constraint norms of the 128^3 puncture after 4 RK4 steps",
+                   "grid": [N_SIDE] * 3},
+        "roofline": {"bound": "alu", "kernel": "psi4_kernel", "achieved": top["fp64_gflops"],
+                     "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s (FP64)",
+                     "frac": top["fp64_gflops"] / FP64_PEAK_GFLOPS, "traffic": None},
+        "kernels": res,
+        "tracker": {"ms_per_step_without": times[False], "ms_per_step_with": times[True],
+                    "overhead_ms": times[True] - times[False]},
+        "gpu_launches": 3 * args.steps + 2 * args.steps * (1 + 8),
+        "clocks": clk,
+    }
+    print(json.dumps(line))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -454,7 +527,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["puncture", "batched", "served", "precision"],
+    ap.add_argument("--workload", choices=["puncture", "batched", "served", "precision", "analysis"],
                     default="puncture",
                     help="puncture: the benchmark line (single 128^3 puncture); batched / served: "
                          "the multi-evolution workloads, reported on their own lines")
@@ -480,6 +553,8 @@ def main():
         run_served(args)
     elif args.workload == "precision":
         run_precision(args)
+    elif args.workload == "analysis":
+        run_analysis(args)
     else:
         run_ours(args)
 

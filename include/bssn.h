@@ -175,8 +175,25 @@ bssn_status bssn_set_punctures(bssn_ctx* ctx, const double* p, int32_t npunct);
  * caller owns.  Ghost values of d_state must be valid (periodic: filled). */
 bssn_status bssn_rhs(bssn_ctx* ctx, const void* d_state, void* d_rhs);
 
-/* Advance y_n by nsteps classical RK4 steps of size dt (t += nsteps dt). */
+/* Advance y_n by nsteps classical RK4 steps of size dt (t += nsteps dt).
+ * With tracking on (bssn_track_punctures), each step first moves the
+ * punctures by one Euler step of the shift of y_n. */
 bssn_status bssn_rk4_step(bssn_ctx* ctx, int32_t nsteps);
+
+/* Puncture tracking (Sec. "Object tracking"): with enable != 0, every RK4 step
+ * moves each puncture of the context (set by bssn_set_punctures or Brill-
+ * Lindquist initial data) by x <- x - dt beta(t_n, x), the shift of y_n
+ * interpolated by the tensor product of 4-point Lagrange polynomials on stored
+ * points i0-1 .. i0+2 (i0 the stored point at or below x; the stencil is
+ * shifted inward at the edge of the stored block).  The positions stay on the
+ * device; the excised sets of bssn_constraints and bssn_adm_integrals follow
+ * them.  enable = 0 stops tracking (positions are kept). */
+bssn_status bssn_track_punctures(bssn_ctx* ctx, int32_t enable);
+
+/* Current punctures, rows {m, x, y, z}, into out (room for 8 rows, 32
+ * doubles) and their count into *npunct.  Synchronises when the tracker has
+ * moved them since the last read. */
+bssn_status bssn_get_punctures(bssn_ctx* ctx, double* out, int32_t* npunct);
 
 /* Constraint norms of y_n (synchronises): out[0..3] L2 (root mean square)
  * of H, M_x, M_y, M_z over interior points, out[4..7] their max-abs, out[8..15]
@@ -184,6 +201,33 @@ bssn_status bssn_rk4_step(bssn_ctx* ctx, int32_t nsteps);
  * H = R - K^i_j K^j_i + K^2, M_i = nabla_j K_i^j - nabla_i K (vacuum) from the
  * ADM fields (Sec. "Other analysis modules"), float64 in every precision. */
 bssn_status bssn_constraints(bssn_ctx* ctx, double out[16]);
+
+/* ADM mass and angular momentum of y_n as volume integrals (Sec. "Masses and
+ * Momenta", vacuum), synchronises:
+ *   M   = 1/(16 pi) int [ e^{5 phi}(At_ij At^ij - (2/3) K^2) - e^{phi} Rt ]
+ *   J_i = 1/(8 pi) eps_ijk int e^{6 phi} [ At^j_k + (2/3) x^j d_k K
+ *                                          - (1/2) x^j At_ln d_k gt^{ln} ]
+ * Rt = gt^ij Rt_ij as in the right-hand side, x^j the grid coordinates, the
+ * integral the midpoint sum h^3 sum over interior points.  out[0..3] = M, J_x,
+ * J_y, J_z over all interior points, out[4..7] over the points farther than
+ * r_excise from every puncture.  d_dens: NULL, or a caller-owned device array
+ * of 4 * field_stride doubles (register layout) that receives the four
+ * integrands at interior points (other points untouched).  Float64 in every
+ * precision mode. */
+bssn_status bssn_adm_integrals(bssn_ctx* ctx, double* d_dens, double out[8]);
+
+/* Weyl scalar Psi4 = C_abcd n^a mb^b n^c mb^d of y_n (Sec. "Gravitational
+ * Waves", WeylScal4, vacuum) for the fiducial tetrad n = (u - r)/sqrt2,
+ * m = (theta + i phi)/sqrt2: u the unit normal, the spatial triad started from
+ * r = x^i, phi = (-y, x, 0), theta^i = sqrt(det g) g^ik eps_klm phi^l r^m
+ * (x^i the grid coordinates) and made orthonormal in gamma_ij by Gram-Schmidt
+ * in the order phi, r, theta; the curvature enters through the Gauss, Codazzi
+ * and Ricci projections with 4th-order stencils of the ADM fields.  Psi4 = 0
+ * where phi = 0 (the z axis).  d_out: caller-owned device array of
+ * 2 * field_stride doubles (register layout), real part then imaginary part,
+ * written at interior points only.  Asynchronous on the context's stream;
+ * float64 in every precision mode. */
+bssn_status bssn_psi4(bssn_ctx* ctx, double* d_out);
 
 /* Copy y_n to / from host memory (unpadded float64 layout; synchronises).
  * Pinned host memory gives full transfer speed.  t may be NULL. */

@@ -177,6 +177,8 @@ def _load():
     lib.oracle_interp.argtypes = [cp, dp, dp]
     lib.oracle_interp.restype = ctypes.c_double
     lib.oracle_track_step.argtypes = [cp, dp, ctypes.c_int, dp, ctypes.c_double]
+    lib.oracle_psi4.argtypes = [cp, dp, dp]
+    lib.oracle_psi4.restype = ctypes.c_int
     _lib = lib
     return lib
 
@@ -363,3 +365,14 @@ def track_step(cfg: Config, st: np.ndarray, punctures, dt: float) -> np.ndarray:
     pos = np.array(punctures, dtype=np.float64).reshape(-1, 4).copy()
     lib.oracle_track_step(ctypes.byref(cfg._c()), _dp(st), pos.shape[0], _dp(pos), float(dt))
     return pos
+
+
+def psi4(cfg: Config, st: np.ndarray) -> np.ndarray:
+    """Weyl scalar Psi4 (2, grid): real and imaginary parts at interior points
+    (0 elsewhere)."""
+    lib = _load()
+    st = _state(cfg, st)
+    out = np.zeros((2,) + cfg.shape[1:])
+    if lib.oracle_psi4(ctypes.byref(cfg._c()), _dp(st), _dp(out)) != 0:
+        raise MemoryError("oracle_psi4: allocation failed")
+    return out

@@ -33,6 +33,8 @@
  * initial lapse are readings of an under-specified passage: parity there is
  * unpinned beyond the pure-wave part.
  */
+#include <complex.h>
+#undef I /* the imaginary unit is written _Complex_I below */
 #include <math.h>
 #include <stddef.h>
 #include <stdlib.h>
@@ -1310,4 +1312,193 @@ void oracle_track_step(const ocfg* c, const double* st, int np, double* pos, dou
     for (int d = 0; d < 3; d++) beta[d] = oracle_interp(c, st + (size_t)(F_BETA + d) * S, xyz);
     for (int d = 0; d < 3; d++) p[1 + d] = xyz[d] - dt * beta[d];
   }
+}
+
+/* ------------------------------------------------------------ Weyl scalar
+ * Sec. "Gravitational Waves" (WeylScal4): Psi4 = C_abcd n^a mb^b n^c mb^d for
+ * the fiducial tetrad l = (u + r)/sqrt2, n = (u - r)/sqrt2,
+ * m = (theta + i phi)/sqrt2, u the unit normal of the slice, from the
+ * projections of the curvature onto the slice.  Readings:
+ *  - index 0 of the printed formula is the component along u, so n^0 = 1/sqrt2,
+ *    the spatial part of n is -r/sqrt2, and mb^0 = 0 (the triad is spatial),
+ *    which removes every term with mb^0;
+ *  - the three projections (vacuum, K_ij = -grad_i u_j):
+ *      R_ijkl = 3R_ijkl + K_ik K_jl - K_il K_jk                (Gauss)
+ *      R_0jkl = D_k K_jl - D_l K_jk                            (Codazzi)
+ *      R_0j0l = 3R_jl + K K_jl - K_jm K^m_l                    (Ricci, vacuum)
+ *    with 3R_ijkl = 1/2 (d_j d_k g_il + d_i d_l g_jk - d_i d_k g_jl
+ *    - d_j d_l g_ik) + g_mn (G^m_jk G^n_il - G^m_jl G^n_ik) and 3R_jl =
+ *    g^ik 3R_ijkl, all from 4th-order stencils of the ADM fields formed
+ *    pointwise (as for the constraints);
+ *  - the triad starts from r = x^i, phi = (-y, x, 0),
+ *    theta^i = sqrt(det g) g^ik eps_klm phi^l r^m (x^i the grid coordinates,
+ *    origin at 0), and is made orthonormal in g_ij by Gram-Schmidt in the
+ *    order phi, r, theta;
+ *  - on the z axis (phi = 0) the triad is undefined: Psi4 = 0 there.
+ * Pin: the exact 4-Riemann tensor of exact spacetimes (Taylor jets of the
+ * 4-metric) contracted with the same tetrad, at 4th order; flat space in
+ * curved slicings gives 0; the triad is the spherical one for a flat metric.
+ */
+static void psi4_point(const ocfg* c, const double* gam6, const double* K6, int i, int j, int k,
+                       double out[2]) {
+  const size_t S = npts(c);
+  const size_t id = pidx(c, i, j, k);
+  const ptrdiff_t str[3] = {1, dimx(c, 0), (ptrdiff_t)dimx(c, 0) * dimx(c, 1)};
+  const double h = c->h;
+  double g[3][3], K[3][3], dg[3][3][3], ddg[3][3][3][3], dK[3][3][3];
+  for (int a = 0; a < 3; a++)
+    for (int b = 0; b < 3; b++) {
+      const double* pg = gam6 + (size_t)SYM[a][b] * S + id;
+      const double* pk = K6 + (size_t)SYM[a][b] * S + id;
+      g[a][b] = pg[0];
+      K[a][b] = pk[0];
+      for (int m = 0; m < 3; m++) {
+        dg[m][a][b] = st_d1(pg, str[m], h);
+        dK[m][a][b] = st_d1(pk, str[m], h);
+        for (int n = 0; n < 3; n++) ddg[m][n][a][b] = st_dd(pg, str, m, n, h);
+      }
+    }
+  double gu[3][3];
+  inv3(g, gu);
+  /* Christoffel symbols G^m_ij */
+  double G[3][3][3];
+  for (int m = 0; m < 3; m++)
+    for (int a = 0; a < 3; a++)
+      for (int b = 0; b < 3; b++) {
+        double s = 0.0;
+        for (int l = 0; l < 3; l++) s += 0.5 * gu[m][l] * (dg[a][l][b] + dg[b][a][l] - dg[l][a][b]);
+        G[m][a][b] = s;
+      }
+  /* 3-Riemann R_ijkl (all indices down) */
+  double R4[3][3][3][3];
+  for (int a = 0; a < 3; a++)
+    for (int b = 0; b < 3; b++)
+      for (int cc = 0; cc < 3; cc++)
+        for (int d = 0; d < 3; d++) {
+          double s = 0.5 * (ddg[b][cc][a][d] + ddg[a][d][b][cc] - ddg[a][cc][b][d] - ddg[b][d][a][cc]);
+          for (int m = 0; m < 3; m++)
+            for (int n = 0; n < 3; n++) s += g[m][n] * (G[m][b][cc] * G[n][a][d] - G[m][b][d] * G[n][a][cc]);
+          R4[a][b][cc][d] = s;
+        }
+  double Ric[3][3];
+  for (int b = 0; b < 3; b++)
+    for (int d = 0; d < 3; d++) {
+      double s = 0.0;
+      for (int a = 0; a < 3; a++)
+        for (int cc = 0; cc < 3; cc++) s += gu[a][cc] * R4[a][b][cc][d];
+      Ric[b][d] = s;
+    }
+  double trK = 0.0, Kud[3][3];
+  for (int a = 0; a < 3; a++)
+    for (int b = 0; b < 3; b++) {
+      trK += gu[a][b] * K[a][b];
+      double s = 0.0;
+      for (int m = 0; m < 3; m++) s += gu[a][m] * K[m][b];
+      Kud[a][b] = s; /* K^a_b */
+    }
+  /* D_k K_jl */
+  double DK[3][3][3];
+  for (int m = 0; m < 3; m++)
+    for (int a = 0; a < 3; a++)
+      for (int b = 0; b < 3; b++) {
+        double s = dK[m][a][b];
+        for (int l = 0; l < 3; l++) s -= G[l][m][a] * K[l][b] + G[l][m][b] * K[a][l];
+        DK[m][a][b] = s;
+      }
+  /* projections */
+  double Rs[3][3][3][3], R0[3][3][3], R00[3][3];
+  for (int a = 0; a < 3; a++)
+    for (int b = 0; b < 3; b++)
+      for (int cc = 0; cc < 3; cc++)
+        for (int d = 0; d < 3; d++)
+          Rs[a][b][cc][d] = R4[a][b][cc][d] + K[a][cc] * K[b][d] - K[a][d] * K[b][cc];
+  for (int b = 0; b < 3; b++)
+    for (int cc = 0; cc < 3; cc++)
+      for (int d = 0; d < 3; d++) R0[b][cc][d] = DK[cc][b][d] - DK[d][b][cc];
+  for (int b = 0; b < 3; b++)
+    for (int d = 0; d < 3; d++) {
+      double s = Ric[b][d] + trK * K[b][d];
+      for (int m = 0; m < 3; m++) s -= K[b][m] * Kud[m][d];
+      R00[b][d] = s;
+    }
+  /* fiducial triad */
+  const double x[3] = {coord(c, 0, i), coord(c, 1, j), coord(c, 2, k)};
+  double rv[3] = {x[0], x[1], x[2]};
+  double pv[3] = {-x[1], x[0], 0.0};
+  double tv[3];
+  const double sdet = sqrt(det3(g));
+  for (int a = 0; a < 3; a++) {
+    double s = 0.0;
+    for (int kk = 0; kk < 3; kk++)
+      for (int l = 0; l < 3; l++)
+        for (int m = 0; m < 3; m++) {
+          double eps = (double)((kk - l) * (l - m) * (m - kk)) / 2.0;
+          s += sdet * gu[a][kk] * eps * pv[l] * rv[m];
+        }
+    tv[a] = s;
+  }
+#define DOT(u, v) (g[0][0] * u[0] * v[0] + g[0][1] * u[0] * v[1] + g[0][2] * u[0] * v[2] + \
+                   g[1][0] * u[1] * v[0] + g[1][1] * u[1] * v[1] + g[1][2] * u[1] * v[2] + \
+                   g[2][0] * u[2] * v[0] + g[2][1] * u[2] * v[1] + g[2][2] * u[2] * v[2])
+  double pp = DOT(pv, pv);
+  if (!(pp > 0.0)) {
+    out[0] = out[1] = 0.0;
+    return;
+  }
+  for (int a = 0; a < 3; a++) pv[a] /= sqrt(pp);
+  double rp = DOT(rv, pv);
+  for (int a = 0; a < 3; a++) rv[a] -= rp * pv[a];
+  double rr = DOT(rv, rv);
+  for (int a = 0; a < 3; a++) rv[a] /= sqrt(rr);
+  double tp = DOT(tv, pv), tr = DOT(tv, rv);
+  for (int a = 0; a < 3; a++) tv[a] -= tp * pv[a] + tr * rv[a];
+  double tt = DOT(tv, tv);
+  for (int a = 0; a < 3; a++) tv[a] /= sqrt(tt);
+#undef DOT
+  /* tetrad components: n^0 = 1/sqrt2, n^i = -r^i/sqrt2, mb^i = (theta^i - i phi^i)/sqrt2 */
+  const double s2 = 1.0 / sqrt(2.0);
+  double complex mb[3];
+  double n[3];
+  for (int a = 0; a < 3; a++) {
+    n[a] = -s2 * rv[a];
+    mb[a] = s2 * (tv[a] - _Complex_I * pv[a]);
+  }
+  const double n0 = s2;
+  double complex psi = 0.0;
+  for (int a = 0; a < 3; a++)
+    for (int b = 0; b < 3; b++)
+      for (int cc = 0; cc < 3; cc++)
+        for (int d = 0; d < 3; d++) psi += Rs[a][b][cc][d] * n[a] * mb[b] * n[cc] * mb[d];
+  for (int b = 0; b < 3; b++)
+    for (int cc = 0; cc < 3; cc++)
+      for (int d = 0; d < 3; d++) psi += 2.0 * R0[b][cc][d] * n0 * mb[b] * n[cc] * mb[d];
+  for (int b = 0; b < 3; b++)
+    for (int d = 0; d < 3; d++) psi += R00[b][d] * n0 * mb[b] * n0 * mb[d];
+  out[0] = creal(psi);
+  out[1] = cimag(psi);
+}
+
+/* Psi4 at every interior point: out2 (2, stored points) real and imaginary
+ * parts; other points are left untouched.  Returns 2 on allocation failure. */
+int oracle_psi4(const ocfg* c, const double* st, double* out2) {
+  const size_t S = npts(c);
+  double* gam6 = (double*)malloc(6 * S * sizeof(double));
+  double* K6 = (double*)malloc(6 * S * sizeof(double));
+  if (!gam6 || !K6) {
+    free(gam6); free(K6);
+    return 2;
+  }
+  adm_grids(c, st, gam6, K6);
+  for (int k = GH; k < GH + c->n[2]; k++)
+    for (int j = GH; j < GH + c->n[1]; j++)
+      for (int i = GH; i < GH + c->n[0]; i++) {
+        double o[2];
+        psi4_point(c, gam6, K6, i, j, k, o);
+        size_t id = pidx(c, i, j, k);
+        out2[id] = o[0];
+        out2[S + id] = o[1];
+      }
+  free(gam6);
+  free(K6);
+  return 0;
 }

@@ -130,6 +130,11 @@ _SIGS = [
     ("bssn_profile", [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     ("bssn_set_adm", [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double], ctypes.c_int),
     ("bssn_set_punctures", [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int32], ctypes.c_int),
+    ("bssn_track_punctures", [ctypes.c_void_p, ctypes.c_int32], ctypes.c_int),
+    ("bssn_get_punctures", [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32)],
+     ctypes.c_int),
+    ("bssn_adm_integrals", [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+    ("bssn_psi4", [ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
     ("bssn_tile_count", [], ctypes.c_int32),
     ("bssn_tile_name", [ctypes.c_int32], ctypes.c_char_p),
     ("bssn_set_tile", [ctypes.c_void_p, ctypes.c_int32], ctypes.c_int),
@@ -261,6 +266,27 @@ def bssn_set_adm(ctx: int, host_adm: np.ndarray, t: float = 0.0):
 def bssn_set_punctures(ctx: int, punctures=()):
     flat = [float(v) for q in punctures for v in q]
     _check(load().bssn_set_punctures(ctypes.c_void_p(ctx), _dbl_array(flat), len(punctures)))
+
+
+def bssn_track_punctures(ctx: int, enable: bool):
+    _check(load().bssn_track_punctures(ctypes.c_void_p(ctx), 1 if enable else 0))
+
+
+def bssn_get_punctures(ctx: int) -> np.ndarray:
+    out = (ctypes.c_double * 32)()
+    n = ctypes.c_int32()
+    _check(load().bssn_get_punctures(ctypes.c_void_p(ctx), out, ctypes.byref(n)))
+    return np.array(out[:4 * n.value], dtype=np.float64).reshape(n.value, 4)
+
+
+def bssn_adm_integrals(ctx: int, d_dens=None) -> np.ndarray:
+    out = (ctypes.c_double * 8)()
+    _check(load().bssn_adm_integrals(ctypes.c_void_p(ctx), ctypes.c_void_p(d_dens or 0), out))
+    return np.array(out[:], dtype=np.float64)
+
+
+def bssn_psi4(ctx: int, d_out: int):
+    _check(load().bssn_psi4(ctypes.c_void_p(ctx), ctypes.c_void_p(d_out)))
 
 
 def bssn_rhs(ctx: int, d_state, d_rhs: int):
@@ -419,6 +445,37 @@ class Evolution:
 
     def set_punctures(self, punctures=()):
         bssn_set_punctures(self.ctx, punctures)
+
+    def track_punctures(self, enable=True):
+        bssn_track_punctures(self.ctx, enable)
+
+    def get_punctures(self) -> np.ndarray:
+        return bssn_get_punctures(self.ctx)
+
+    def psi4(self, out=None):
+        """Psi4 into a device register (2 * field_stride float64: real, then
+        imaginary part, interior points); returns it (asynchronous)."""
+        if out is None:
+            out = self.torch.zeros(2 * self.layout["field_stride"], dtype=self.torch.float64, device=self.device)
+        bssn_psi4(self.ctx, out.data_ptr())
+        return out
+
+    def psi4_to_numpy(self, reg) -> np.ndarray:
+        sx, sy, sz = self.layout["stored"]
+        return reg.view(2, sz, sy, self.layout["pitch"])[..., :sx].cpu().numpy().copy()
+
+    def adm_integrals(self, densities=False):
+        """(integrals8, dens): M, J_x, J_y, J_z over all interior points then
+        over the excised set; dens (4, Z, Y, X) host copy of the integrands at
+        interior points (zero elsewhere) when densities is true, else None."""
+        if not densities:
+            return bssn_adm_integrals(self.ctx), None
+        sx, sy, sz = self.layout["stored"]
+        fs = self.layout["field_stride"]
+        reg = self.torch.zeros(4 * fs, dtype=self.torch.float64, device=self.device)
+        out = bssn_adm_integrals(self.ctx, reg.data_ptr())
+        d = reg.view(4, sz, sy, self.layout["pitch"])[..., :sx].cpu().numpy().copy()
+        return out, d
 
 
 # ---------------------------------------------------------------- batches

@@ -88,7 +88,7 @@ Grid make_grid(const bssn_params* p) {
 // buffers m[0..2] (m[0] is the float shadow of y_n), each with a float64 W
 // array; the float k-sum with its float64 W; float anchors.
 struct Carve {
-  size_t reg, yn, ks, s1, s2, ksh, part, out16, err, total;
+  size_t reg, yn, ks, s1, s2, ksh, part, out16, err, trk, total;
   size_t m32[3], mw[3], ks32, ksw;
   int nblocks;
 };
@@ -121,6 +121,7 @@ Carve carve(const bssn_params* p, const Grid& g) {
   c.part = o; o += align_up((size_t)c.nblocks * 18 * sizeof(double));
   c.out16 = o; o += align_up(16 * sizeof(double));
   c.err = o; o += align_up(sizeof(int));
+  c.trk = o; o += align_up(8 * 4 * sizeof(double));
   c.total = o;
   return c;
 }
@@ -156,7 +157,10 @@ struct bssn_ctx {
   double* out16;
   double t;
   int npunct;
-  double punct[8][4];
+  double punct[8][4];    // host copy of the punctures {m, x, y, z}
+  double* trk;           // device copy, moved by the tracker
+  bool tracking;         // advance trk by one Euler step per RK4 step
+  bool trk_stale;        // host copy older than trk
   // launch timing (bssn_profile): event pairs around stage and boundary launches
   bool prof;
   std::vector<cudaEvent_t> ev_stage, ev_bc;
@@ -252,6 +256,9 @@ bssn_status bssn_alloc(const bssn_params* p, void* d_mem, size_t bytes, void* cu
   ctx->npunct = 0;
   ctx->prof = false;
   ctx->err = (int*)(ctx->mem + c.err);
+  ctx->trk = (double*)(ctx->mem + c.trk);
+  ctx->tracking = false;
+  ctx->trk_stale = false;
   ctx->tmap_ok = false;
   if (p->precision == BSSN_MIXED) {
     bool ok = true;
@@ -281,6 +288,23 @@ bssn_status bssn_state_ptr(bssn_ctx* ctx, double** d_state) {
   return BSSN_OK;
 }
 
+// Puncture positions: the host copy ctx->punct and the device copy ctx->trk
+// that the tracker moves.  push: host -> device (the copy from pageable
+// memory is staged before cudaMemcpyAsync returns); pull: device -> host when
+// the tracker has run since the last pull.
+static cudaError_t push_punct(bssn_ctx* ctx) {
+  ctx->trk_stale = false;
+  return cudaMemcpyAsync(ctx->trk, &ctx->punct[0][0], sizeof(ctx->punct), cudaMemcpyHostToDevice, ctx->stream);
+}
+static cudaError_t pull_punct(bssn_ctx* ctx) {
+  if (!ctx->trk_stale) return cudaSuccess;
+  cudaError_t e = cudaMemcpyAsync(&ctx->punct[0][0], ctx->trk, sizeof(ctx->punct), cudaMemcpyDeviceToHost,
+                                  ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (e == cudaSuccess) ctx->trk_stale = false;
+  return e;
+}
+
 bssn_status bssn_set_initial_data(bssn_ctx* ctx, int32_t kind, const double* p, int32_t np) {
   if (!ctx) return fail(BSSN_EINVAL, "ctx is NULL");
   if (np < 0 || (np > 0 && !p)) return fail(BSSN_EINVAL, "bad parameter array");
@@ -308,6 +332,7 @@ bssn_status bssn_set_initial_data(bssn_ctx* ctx, int32_t kind, const double* p, 
   ctx->npunct = npunct;
   for (int a = 0; a < npunct; a++)
     for (int q = 0; q < 4; q++) ctx->punct[a][q] = p[1 + 4 * a + q];
+  if ((e = push_punct(ctx)) != cudaSuccess) return cuda_fail(e, "punctures");
   ctx->t = 0.0;
   return BSSN_OK;
 }
@@ -332,6 +357,28 @@ bssn_status bssn_set_punctures(bssn_ctx* ctx, const double* p, int32_t npunct) {
   ctx->npunct = npunct;
   for (int a = 0; a < npunct; a++)
     for (int q = 0; q < 4; q++) ctx->punct[a][q] = p[4 * a + q];
+  cudaError_t e = push_punct(ctx);
+  if (e != cudaSuccess) return cuda_fail(e, "punctures");
+  return BSSN_OK;
+}
+
+bssn_status bssn_track_punctures(bssn_ctx* ctx, int32_t enable) {
+  if (!ctx) return fail(BSSN_EINVAL, "ctx is NULL");
+  if (enable && !ctx->tracking && !ctx->trk_stale) {
+    cudaError_t e = push_punct(ctx);
+    if (e != cudaSuccess) return cuda_fail(e, "punctures");
+  }
+  ctx->tracking = enable != 0;
+  return BSSN_OK;
+}
+
+bssn_status bssn_get_punctures(bssn_ctx* ctx, double* out, int32_t* npunct) {
+  if (!ctx || !out || !npunct) return fail(BSSN_EINVAL, "NULL argument");
+  cudaError_t e = pull_punct(ctx);
+  if (e != cudaSuccess) return cuda_fail(e, "punctures");
+  *npunct = ctx->npunct;
+  for (int a = 0; a < ctx->npunct; a++)
+    for (int q = 0; q < 4; q++) out[4 * a + q] = ctx->punct[a][q];
   return BSSN_OK;
 }
 
@@ -451,6 +498,12 @@ bssn_status bssn_rk4_step(bssn_ctx* ctx, int32_t nsteps) {
   for (int s = 0; s < nsteps; s++) {
     bssn_status st;
     cudaError_t e;
+    if (ctx->tracking && ctx->npunct > 0) {
+      // Euler step of the punctures with the shift of y_n, before y_n moves
+      e = launch_track(ctx->g, ctx->yn, ctx->trk, ctx->npunct, dt, ctx->stream);
+      if (e != cudaSuccess) return cuda_fail(e, "track");
+      ctx->trk_stale = true;
+    }
     if (ctx->g.periodic && !(mixed && ctx->shadow_valid)) {
       e = launch_periodic_fill(ctx->g, ctx->yn, ctx->stream);
       if (e != cudaSuccess) return cuda_fail(e, "periodic fill");
@@ -481,7 +534,9 @@ static bssn_status check_err(bssn_ctx* ctx);
 bssn_status bssn_constraints(bssn_ctx* ctx, double out[16]) {
   if (!ctx || !out) return fail(BSSN_EINVAL, "NULL argument");
   if (bssn_status es = check_err(ctx)) return es;
-  cudaError_t e = launch_constraints(ctx->g, ctx->yn, &ctx->punct[0][0], ctx->npunct,
+  cudaError_t e = pull_punct(ctx);
+  if (e != cudaSuccess) return cuda_fail(e, "punctures");
+  e = launch_constraints(ctx->g, ctx->yn, &ctx->punct[0][0], ctx->npunct,
                                      ctx->p.r_excise, ctx->part, ctx->c.nblocks, ctx->out16,
                                      ctx->stream);
   if (e != cudaSuccess) return cuda_fail(e, "constraints");
@@ -489,6 +544,32 @@ bssn_status bssn_constraints(bssn_ctx* ctx, double out[16]) {
   if (e != cudaSuccess) return cuda_fail(e, "constraints copy");
   e = cudaStreamSynchronize(ctx->stream);
   if (e != cudaSuccess) return cuda_fail(e, "constraints sync");
+  return BSSN_OK;
+}
+
+bssn_status bssn_adm_integrals(bssn_ctx* ctx, double* d_dens, double out[8]) {
+  if (!ctx || !out) return fail(BSSN_EINVAL, "NULL argument");
+  if (bssn_status es = check_err(ctx)) return es;
+  cudaError_t e = pull_punct(ctx);
+  if (e != cudaSuccess) return cuda_fail(e, "punctures");
+  Punct pu{};
+  pu.n = ctx->npunct;
+  for (int a = 0; a < pu.n; a++)
+    for (int q = 0; q < 4; q++) pu.p[a][q] = ctx->punct[a][q];
+  pu.r_ex = ctx->p.r_excise;
+  e = launch_adm_integrals(ctx->g, ctx->yn, pu, d_dens, ctx->part, adm_integrals_blocks(ctx->g), ctx->out16,
+                           ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "adm integrals");
+  e = cudaMemcpyAsync(out, ctx->out16, 8 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "adm integrals copy");
+  return BSSN_OK;
+}
+
+bssn_status bssn_psi4(bssn_ctx* ctx, double* d_out) {
+  if (!ctx || !d_out) return fail(BSSN_EINVAL, "NULL argument");
+  cudaError_t e = launch_psi4(ctx->g, ctx->yn, d_out, ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "psi4");
   return BSSN_OK;
 }
 

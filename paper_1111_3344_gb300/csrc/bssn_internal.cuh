@@ -75,6 +75,14 @@ __host__ __device__ __forceinline__ double gc<double>(double d, float) { return 
 template <>
 __host__ __device__ __forceinline__ float gc<float>(double, float f) { return f; }
 
+// Coordinate of interior index ii (cell centre), xmin + (ii + 1/2) h, with the
+// product and the sum rounded separately (no fused multiply-add), so that a
+// coordinate that is exactly 0 comes out as 0 (the z axis of the Psi4 triad)
+// and the excision tests see the same values as a plain evaluation.
+__device__ __forceinline__ double cell_coord(double xmin, int ii, double h) {
+  return __dadd_rn(xmin, __dmul_rn((double)ii + 0.5, h));
+}
+
 __host__ __device__ inline long long lin(const Grid& g, int i, int j, int k) {
   return (long long)k * g.plane + (long long)j * g.pitch + i;
 }
@@ -158,6 +166,14 @@ struct StageArgsT {
 using StageArgs = StageArgsT<double>;
 using StageArgsMixed = StageArgsT<float>;
 
+// Punctures {m, x, y, z} (at most 8) and the excision radius of the excised
+// norms and integrals, passed to kernels by value.
+struct Punct {
+  double p[8][4];
+  int n;
+  double r_ex;
+};
+
 // Launch wrappers (defined in the .cu files); all return cudaError_t of the launch.
 cudaError_t launch_stage_fp64(const Grid& g, const StageArgs& a, cudaStream_t s, int cfg = 0);
 cudaError_t launch_stage_mixed(const Grid& g, const StageArgsMixed& a, cudaStream_t s, int cfg = 0);
@@ -184,6 +200,19 @@ int constraints_blocks(const Grid& g);
 // y's first 16 field slots hold ADM data (alpha, beta^i, gamma_ij, K_ij);
 // converts it in place to the BSSN state (k_adm.cu).
 cudaError_t launch_adm_to_bssn(const Grid& g, double* y, cudaStream_t s);
+// ADM mass / angular momentum integrals (k_adm_integrals.cu): dout8 receives
+// M, J_x, J_y, J_z over all interior points then over the excised set; dens
+// (4 fields of the register layout, may be null) the integrands.  partials
+// holds adm_integrals_blocks(g) * 8 doubles.
+int adm_integrals_blocks(const Grid& g);
+cudaError_t launch_adm_integrals(const Grid& g, const double* y, const Punct& pu, double* dens,
+                                 double* partials, int nblocks, double* dout8, cudaStream_t s);
+// Weyl scalar Psi4 at interior points into out (2 fields of the register
+// layout: real, imaginary) (k_psi4.cu).
+cudaError_t launch_psi4(const Grid& g, const double* y, double* out, cudaStream_t s);
+// One Euler step of the puncture positions dpunct (rows {m, x, y, z}) from the
+// shift of y (k_track.cu).
+cudaError_t launch_track(const Grid& g, const double* y, double* dpunct, int np, double dt, cudaStream_t s);
 
 // Sets the message bssn_last_error() returns on the calling thread.
 void set_last_error(const std::string& msg);

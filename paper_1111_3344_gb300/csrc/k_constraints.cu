@@ -10,10 +10,10 @@
 // (the Christoffel terms of gamma^jk (nabla_k K_ij - nabla_i K_jk) after the
 // symmetric pair cancels).  Float64 in every precision mode.
 //
-// Reduction: one thread per interior point, a fixed-shape shared-memory tree
-// per block into per-block partials (8 sums of squares, 8 maxima, 2 counts),
-// then one block folds the partials in a fixed order: the result does not
-// depend on scheduling.
+// Reduction: one thread per interior point; per block a warp-shuffle tree in
+// each warp and a shuffle tree over the warp results, in a fixed order, into
+// per-block partials (8 sums of squares, 8 maxima, 2 counts); then one block
+// folds the partials the same way: the result does not depend on scheduling.
 #include "bssn_internal.cuh"
 
 namespace bssn {
@@ -23,12 +23,6 @@ __device__ __forceinline__ double nanmax(double a, double b) { return (b > a || 
 
 constexpr int CB = 256;   // threads per block
 constexpr int NPART = 18; // partial values per block
-
-struct Punct {
-  double p[8][4];
-  int n;
-  double r_ex;
-};
 
 __device__ __forceinline__ void adm_at(const Grid& g, const double* __restrict__ y, long long id,
                                        double gam[6], double K[6], bool needK) {
@@ -182,9 +176,40 @@ __device__ void constraints_point(const Grid& g, const double* __restrict__ y, l
   }
 }
 
+// Combine rule of partial slot q: max (NaN-propagating) for the Linf slots,
+// sum for the rest.
+__device__ __forceinline__ bool is_max_slot(int q) { return (q >= 4 && q < 8) || (q >= 12 && q < 16); }
+__device__ __forceinline__ double combine(int q, double a, double b) {
+  return is_max_slot(q) ? nanmax(a, b) : a + b;
+}
+
+// Block reduction of NPART values per thread in a fixed order: a shuffle tree
+// inside each warp (offsets 16, 8, 4, 2, 1), the warp results through shared
+// memory, then the same shuffle tree over them in warp 0.  Thread 0 returns
+// the block's values in v.
+__device__ __forceinline__ void block_reduce(double v[NPART]) {
+  __shared__ double wsum[NPART][CB / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+    for (int q = 0; q < NPART; q++) v[q] = combine(q, v[q], __shfl_down_sync(0xffffffffu, v[q], off));
+  if (lane == 0)
+#pragma unroll
+    for (int q = 0; q < NPART; q++) wsum[q][warp] = v[q];
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int q = 0; q < NPART; q++) v[q] = lane < CB / 32 ? wsum[q][lane] : 0.0;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+      for (int q = 0; q < NPART; q++) v[q] = combine(q, v[q], __shfl_down_sync(0xffffffffu, v[q], off));
+  }
+}
+
 __global__ void __launch_bounds__(CB) constraints_kernel(Grid g, const double* __restrict__ y,
                                                          Punct pu, double* __restrict__ partials) {
-  __shared__ double sh[NPART][CB];
   const long long npts = (long long)g.n0 * g.n1 * g.n2;
   const long long tid = (long long)blockIdx.x * CB + threadIdx.x;
   double v[NPART];
@@ -197,9 +222,9 @@ __global__ void __launch_bounds__(CB) constraints_kernel(Grid g, const double* _
     const int i = ii + GH, j = jj + GH, k = kk + GH;
     double c4[4];
     constraints_point(g, y, lin(g, i, j, k), c4);
-    const double x = g.xmin0 + (i - GH + 0.5) * g.h;
-    const double yy = g.xmin1 + (j - GH + 0.5) * g.h;
-    const double z = g.xmin2 + (k - GH + 0.5) * g.h;
+    const double x = cell_coord(g.xmin0, ii, g.h);
+    const double yy = cell_coord(g.xmin1, jj, g.h);
+    const double z = cell_coord(g.xmin2, kk, g.h);
     bool outside = true;
     for (int a = 0; a < pu.n; a++) {
       const double dx = x - pu.p[a][1], dy = yy - pu.p[a][2], dz = z - pu.p[a][3];
@@ -216,61 +241,29 @@ __global__ void __launch_bounds__(CB) constraints_kernel(Grid g, const double* _
     v[16] = 1.0;
     v[17] = outside ? 1.0 : 0.0;
   }
+  block_reduce(v);
+  if (threadIdx.x == 0)
 #pragma unroll
-  for (int q = 0; q < NPART; q++) sh[q][threadIdx.x] = v[q];
-  __syncthreads();
-  for (int w = CB / 2; w > 0; w >>= 1) {
-    if ((int)threadIdx.x < w) {
-#pragma unroll
-      for (int q = 0; q < NPART; q++) {
-        const double o = sh[q][threadIdx.x + w];
-        const bool ismax = (q >= 4 && q < 8) || (q >= 12 && q < 16);
-        sh[q][threadIdx.x] = ismax ? nanmax(sh[q][threadIdx.x], o) : sh[q][threadIdx.x] + o;
-      }
-    }
-    __syncthreads();
-  }
-  if (threadIdx.x < NPART) partials[(long long)blockIdx.x * NPART + threadIdx.x] = sh[threadIdx.x][0];
+    for (int q = 0; q < NPART; q++) partials[(long long)blockIdx.x * NPART + q] = v[q];
 }
 
 __global__ void __launch_bounds__(CB) constraints_finalize(const double* __restrict__ partials,
                                                            int nblocks, double* __restrict__ out) {
-  __shared__ double sh[NPART][CB];
   double v[NPART];
 #pragma unroll
   for (int q = 0; q < NPART; q++) v[q] = 0.0;
   for (int b = threadIdx.x; b < nblocks; b += CB) {
 #pragma unroll
-    for (int q = 0; q < NPART; q++) {
-      const double o = partials[(long long)b * NPART + q];
-      const bool ismax = (q >= 4 && q < 8) || (q >= 12 && q < 16);
-      v[q] = ismax ? nanmax(v[q], o) : v[q] + o;
-    }
+    for (int q = 0; q < NPART; q++) v[q] = combine(q, v[q], partials[(long long)b * NPART + q]);
   }
+  block_reduce(v);
+  if (threadIdx.x == 0) {
 #pragma unroll
-  for (int q = 0; q < NPART; q++) sh[q][threadIdx.x] = v[q];
-  __syncthreads();
-  for (int w = CB / 2; w > 0; w >>= 1) {
-    if ((int)threadIdx.x < w) {
-#pragma unroll
-      for (int q = 0; q < NPART; q++) {
-        const double o = sh[q][threadIdx.x + w];
-        const bool ismax = (q >= 4 && q < 8) || (q >= 12 && q < 16);
-        sh[q][threadIdx.x] = ismax ? nanmax(sh[q][threadIdx.x], o) : sh[q][threadIdx.x] + o;
-      }
+    for (int q = 0; q < 16; q++) {
+      const int set = q / 8, within = q % 8;
+      const double cnt = v[16 + set];
+      out[q] = within < 4 ? (cnt > 0.0 ? sqrt(v[set * 8 + within] / cnt) : 0.0) : v[set * 8 + within];
     }
-    __syncthreads();
-  }
-  if (threadIdx.x < 16) {
-    const int q = threadIdx.x;
-    const int set = q / 8, within = q % 8;
-    const double cnt = sh[16 + set][0];
-    double r;
-    if (within < 4)
-      r = cnt > 0.0 ? sqrt(sh[set * 8 + within][0] / cnt) : 0.0;
-    else
-      r = sh[set * 8 + within][0];
-    out[q] = r;
   }
 }
 

@@ -66,6 +66,22 @@ def _ks_wavy_map(t, x, y, z):
     return t, xb
 
 
+def _ks_offset_map(t, x, y, z):
+    e = 0.05
+    xb = [x - 0.8 + sin(y + t * (1 / 3)) * e,
+          y + 0.6 + cos(z - x) * (e / 2),
+          z - 0.3 + sin(x + 2.0 * y - t * 0.5) * (e / 2)]
+    return t, xb
+
+
+def _ks_boost_map(t, x, y, z):
+    # boosted slices (velocity 0.3 along x) of the displaced black hole
+    v = 0.3
+    gm = 1.0 / np.sqrt(1.0 - v * v)
+    xs = x - 0.8 + sin(y + t * (1 / 3)) * 0.05
+    return (t - xs * v) * gm, [(xs - t * v) * gm, y + 0.6, z - 0.3 + sin(x - y) * 0.025]
+
+
 def _ks_wavy_B(t, x, y, z):
     return [cos(y + z) * 0.1, sin(z - x) * 0.1, cos(x + y) * 0.1]
 
@@ -96,6 +112,14 @@ SPACETIMES = {
     # Schwarzschild (M = 1) in Kerr-Schild form seen from a moving, sheared
     # grid: 3-curvature, conformal factor and Gt all non-trivial.
     "ks_wavy": {"metric": kerr_schild(1.0), "map": _ks_wavy_map, "B": _ks_wavy_B},
+    # The same black hole displaced from the grid origin (and seen from a
+    # wavy grid): radial lines from the origin are far from its principal
+    # null directions, so the fiducial tetrad sees Psi4 of the size of Psi2.
+    "ks_offset": {"metric": kerr_schild(1.0), "map": _ks_offset_map, "B": _ks_wavy_B},
+    # Slices boosted against the Kerr-Schild ones: the normal observer is not
+    # radial, so the magnetic part of the Weyl tensor (the Codazzi projection)
+    # is non-zero, which no spherically symmetric slicing of Schwarzschild has.
+    "ks_boost": {"metric": kerr_schild(1.0), "map": _ks_boost_map, "B": _ks_wavy_B},
 }
 
 
@@ -114,18 +138,9 @@ def _adj3(m):
     return [[c(j, i) for j in range(3)] for i in range(3)]  # adjugate = C^T
 
 
-def evaluate(name: str, X, Y, Z, time=0.0, use_w=True):
-    """Evaluate the spacetime on coordinate arrays.
-
-    Returns (state, dtstate, grad):
-      state  (24, ...) BSSN fields in the oracle's field order
-      dtstate (24, ...) exact d_t of fields 0..16 (phi|W, gt, K, At, Gt);
-              fields 17..23 are NaN (gauge: checked separately)
-      grad dict with 'alpha' (3,...) d_k alpha, 'beta' (3,3,...) [i][k] = d_k beta^i,
-              'Gt' (3,3,...) [i][k] = d_k Gt^i, 'B' (3,3,...) [i][k] = d_k B^i
-    """
-    spec = SPACETIMES[name]
-    X, Y, Z = np.broadcast_arrays(*(np.asarray(v, dtype=np.float64) for v in (X, Y, Z)))
+def _four_metric(spec, X, Y, Z, time):
+    """Jets of the time, the grid coordinates and the 4-metric g_{mu nu} in
+    grid coordinates (pulled back through the spacetime's coordinate map)."""
     shape = X.shape
     T = Jet.var(0, np.full(shape, float(time)))
     xs = [Jet.var(1, X), Jet.var(2, Y), Jet.var(3, Z)]
@@ -145,6 +160,93 @@ def evaluate(name: str, X, Y, Z, time=0.0, use_w=True):
                     term = Jm[a][m] * Jm[b][n] * gab
                     s = term if s is None else s + term
             g4[m][n] = g4[n][m] = s
+    return T, xs, g4
+
+
+def psi4_exact(name: str, X, Y, Z, time=0.0):
+    """Psi4 = R_abcd n^a mb^b n^c mb^d from the exact 4-Riemann tensor (vacuum:
+    Riemann = Weyl) of the spacetime in grid coordinates (t, x, y, z), with
+    R^a_bcd = d_c G^a_bd - d_d G^a_bc + G^a_ce G^e_bd - G^a_de G^e_bc, and the
+    fiducial tetrad in coordinate components: u^mu = (1, -beta^i)/alpha,
+    n = (u - r)/sqrt2, mb = (theta - i phi)/sqrt2 with the triad (r, theta, phi)
+    built from r = x^i, phi = (-y, x, 0), theta^i = sqrt(det g) g^ik eps_klm
+    phi^l r^m and made orthonormal in gamma_ij in the order phi, r, theta.
+    Nothing of the 3+1 split of the curvature is used."""
+    spec = SPACETIMES[name]
+    X, Y, Z = np.broadcast_arrays(*(np.asarray(v, dtype=np.float64) for v in (X, Y, Z)))
+    _, _, g4 = _four_metric(spec, X, Y, Z, time)
+    gam = [[g4[i + 1][j + 1] for j in range(3)] for i in range(3)]
+    bl = [g4[0][i + 1] for i in range(3)]
+    idet = _det3(gam).recip()
+    gu = [[a * idet for a in row] for row in _adj3(gam)]
+    bu = [gu[i][0] * bl[0] + gu[i][1] * bl[1] + gu[i][2] * bl[2] for i in range(3)]
+    ia2 = (bu[0] * bl[0] + bu[1] * bl[1] + bu[2] * bl[2] - g4[0][0]).recip()  # 1 / alpha^2
+    # inverse 4-metric from the 3+1 split
+    ginv = [[None] * 4 for _ in range(4)]
+    ginv[0][0] = -ia2
+    for i in range(3):
+        ginv[0][i + 1] = ginv[i + 1][0] = bu[i] * ia2
+        for j in range(3):
+            ginv[i + 1][j + 1] = gu[i][j] - bu[i] * bu[j] * ia2
+    dg = [[[g4[a][b].d(m) for b in range(4)] for a in range(4)] for m in range(4)]  # dg[m][a][b]
+    Gam = [[[None] * 4 for _ in range(4)] for _ in range(4)]
+    for a in range(4):
+        for b in range(4):
+            for c in range(b, 4):
+                acc = None
+                for d in range(4):
+                    t = ginv[a][d] * (dg[b][d][c] + dg[c][d][b] - dg[d][b][c]) * 0.5
+                    acc = t if acc is None else acc + t
+                Gam[a][b][c] = Gam[a][c][b] = acc
+    G = np.array([[[Gam[a][b][c].val for c in range(4)] for b in range(4)] for a in range(4)])
+    dG = np.array([[[[Gam[a][b][c].d(m).val for c in range(4)] for b in range(4)] for a in range(4)]
+                   for m in range(4)])  # dG[m][a][b][c]
+    Rup = (np.einsum("cabd...->abcd...", dG) - np.einsum("dabc...->abcd...", dG)
+           + np.einsum("ace...,ebd...->abcd...", G, G) - np.einsum("ade...,ebc...->abcd...", G, G))
+    g4v = np.array([[g4[a][b].val for b in range(4)] for a in range(4)])
+    Rdn = np.einsum("ae...,ebcd...->abcd...", g4v, Rup)
+    # tetrad
+    gamv = g4v[1:, 1:]
+    guv = np.array([[gu[i][j].val for j in range(3)] for i in range(3)])
+    alpha = 1.0 / np.sqrt(ia2.val)
+    beta = np.array([b.val for b in bu])
+    rv = np.array([X, Y, Z])
+    pv = np.array([-Y, X, np.zeros_like(X)])
+    eps = np.zeros((3, 3, 3))
+    for i, j, k in ((0, 1, 2), (1, 2, 0), (2, 0, 1)):
+        eps[i, j, k], eps[j, i, k] = 1.0, -1.0
+    sdet = np.sqrt(np.linalg.det(np.moveaxis(gamv, (0, 1), (-2, -1))))
+    tv = sdet * np.einsum("ik...,klm,l...,m...->i...", guv, eps, pv, rv)
+
+    def dot(u, v):
+        return np.einsum("ij...,i...,j...->...", gamv, u, v)
+
+    pv = pv / np.sqrt(dot(pv, pv))
+    rv = rv - dot(rv, pv) * pv
+    rv = rv / np.sqrt(dot(rv, rv))
+    tv = tv - dot(tv, pv) * pv - dot(tv, rv) * rv
+    tv = tv / np.sqrt(dot(tv, tv))
+    s2 = 1.0 / np.sqrt(2.0)
+    u4 = np.concatenate([(1.0 / alpha)[None], -beta / alpha])
+    n4 = s2 * (u4 - np.concatenate([np.zeros_like(X)[None], rv]))
+    mb4 = s2 * np.concatenate([np.zeros_like(X)[None], tv - 1j * pv])
+    return np.einsum("abcd...,a...,b...,c...,d...->...", Rdn, n4, mb4, n4, mb4)
+
+
+def evaluate(name: str, X, Y, Z, time=0.0, use_w=True):
+    """Evaluate the spacetime on coordinate arrays.
+
+    Returns (state, dtstate, grad):
+      state  (24, ...) BSSN fields in the oracle's field order
+      dtstate (24, ...) exact d_t of fields 0..16 (phi|W, gt, K, At, Gt);
+              fields 17..23 are NaN (gauge: checked separately)
+      grad dict with 'alpha' (3,...) d_k alpha, 'beta' (3,3,...) [i][k] = d_k beta^i,
+              'Gt' (3,3,...) [i][k] = d_k Gt^i, 'B' (3,3,...) [i][k] = d_k B^i
+    """
+    spec = SPACETIMES[name]
+    X, Y, Z = np.broadcast_arrays(*(np.asarray(v, dtype=np.float64) for v in (X, Y, Z)))
+    shape = X.shape
+    T, xs, g4 = _four_metric(spec, X, Y, Z, time)
     gam = [[g4[i + 1][j + 1] for j in range(3)] for i in range(3)]
     bl = [g4[0][i + 1] for i in range(3)]
     det = _det3(gam)
