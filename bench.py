@@ -42,8 +42,8 @@ HBM_BYTES_PER_POINT_STEP = 3264.0  # 17 register passes x 24 fields x 8 B
 FP64_PEAK_GFLOPS = 1250.0          # nominal GB300 FP64 rate
 FP64_MEASURED_GFLOPS = 1196.0      # dependent-chain DFMA microbenchmark on this pool
 # Float64 work per interior point of the analysis kernels (DADD + DMUL + 2 DFMA
-# from ncu instruction counts; profiles/analysis_kernels_bl128.md).
-ANALYSIS_FLOP_PER_POINT = {"psi4": 0.0, "adm_integrals": 0.0, "constraints": 0.0}
+# from ncu instruction counts; profiles/analysis_kernels_bl96.md).
+ANALYSIS_FLOP_PER_POINT = {"psi4": 4888.0, "adm_integrals": 1858.0, "constraints": 3508.0}
 
 
 def workload_params(precision="fp64"):

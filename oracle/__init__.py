@@ -29,7 +29,7 @@ import os
 import subprocess
 import threading
 from dataclasses import dataclass, field
-from typing import Sequence
+from typing import Optional, Sequence
 
 import numpy as np
 
@@ -73,6 +73,7 @@ class _OCfg(ctypes.Structure):
         ("r_excise", ctypes.c_double),
         ("npunct", ctypes.c_int),
         ("punct", (ctypes.c_double * 4) * 8),
+        ("tmunu", ctypes.POINTER(ctypes.c_double)),
     ]
 
 
@@ -93,6 +94,9 @@ class Config:
     w_floor: float = 1e-10
     r_excise: float = 1.0
     punctures: list = field(default_factory=list)  # [(m, x, y, z), ...]
+    # stress-energy tensor T_{mu nu} (10, grid): T_00, T_0x, T_0y, T_0z, T_xx,
+    # T_xy, T_xz, T_yy, T_yz, T_zz at every stored point; None = vacuum
+    tmunu: Optional[np.ndarray] = None
 
     @property
     def shape(self):
@@ -120,6 +124,12 @@ class Config:
         for a, p in enumerate(self.punctures):
             for q in range(4):
                 c.punct[a][q] = float(p[q])
+        if self.tmunu is not None:
+            t = self.tmunu
+            if not (isinstance(t, np.ndarray) and t.dtype == np.float64 and t.flags.c_contiguous
+                    and t.shape == (10,) + self.shape[1:]):
+                raise ValueError("tmunu must be a C-contiguous float64 array of shape (10, Z, Y, X)")
+            c.tmunu = t.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
         return c
 
     def coords(self, axis: int) -> np.ndarray:

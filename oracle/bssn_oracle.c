@@ -70,6 +70,8 @@ typedef struct {
   double r_excise;   /* constraint-norm excision radius around punctures */
   int npunct;        /* punctures (for excision) */
   double punct[8][4];/* m, x, y, z */
+  const double* tmunu; /* NULL (vacuum) or T_{mu nu}, 10 grids: T_00, T_0x,
+                          T_0y, T_0z, T_xx, T_xy, T_xz, T_yy, T_yz, T_zz */
 } ocfg;
 
 /* ------------------------------------------------------------------ grid */
@@ -186,6 +188,42 @@ static void inv3(const double g[3][3], double gu[3][3]) {
   gu[2][2] = (g[0][0] * g[1][1] - g[0][1] * g[1][0]) / d;
 }
 
+/* ------------------------------------------------------ matter sources
+ * Sec. "Spacetime Curvature Evolution", the projections of the
+ * stress-energy tensor T_{mu nu} (Sec. "TmunuBase") on the slice:
+ *   E   = (T_00 - 2 beta^i T_0i + beta^i beta^j T_ij) / alpha^2
+ *   S_i = -(T_0i - beta^j T_ij) / alpha
+ *   S_ij = T_ij,  S = gamma^ij S_ij
+ * (the printed T^{ij} in E is read as T_ij: E = n^mu n^nu T_{mu nu} with
+ * n^mu = (1, -beta^i)/alpha).  gu_phys is gamma^ij. */
+static void matter_projections(const ocfg* c, size_t id, double alpha, const double beta[3],
+                               const double gu_phys[3][3], double* E, double Si[3],
+                               double Sij[3][3], double* S) {
+  const size_t S_ = npts(c);
+  const double* T = c->tmunu;
+  double T00 = T[id], T0[3], Tij[3][3];
+  for (int a = 0; a < 3; a++) T0[a] = T[(size_t)(1 + a) * S_ + id];
+  for (int a = 0; a < 3; a++)
+    for (int b = 0; b < 3; b++) Tij[a][b] = T[(size_t)(4 + SYM[a][b]) * S_ + id];
+  double e = T00;
+  for (int a = 0; a < 3; a++) e -= 2.0 * beta[a] * T0[a];
+  for (int a = 0; a < 3; a++)
+    for (int b = 0; b < 3; b++) e += beta[a] * beta[b] * Tij[a][b];
+  *E = e / (alpha * alpha);
+  for (int a = 0; a < 3; a++) {
+    double s = T0[a];
+    for (int b = 0; b < 3; b++) s -= beta[b] * Tij[b][a];
+    Si[a] = -s / alpha;
+  }
+  double tr = 0.0;
+  for (int a = 0; a < 3; a++)
+    for (int b = 0; b < 3; b++) {
+      Sij[a][b] = Tij[a][b];
+      tr += gu_phys[a][b] * Tij[a][b];
+    }
+  *S = tr;
+}
+
 /* ------------------------------------------------------------ BSSN RHS
  * Interior right-hand side at one point, Sec. "Spacetime Curvature
  * Evolution", equations for d_0 alpha, K, beta, B, phi, gt, At, Gt with
@@ -209,6 +247,12 @@ static void inv3(const double g[3][3], double gu[3][3]) {
  *    d_0 W = (W/3)(alpha K - d_k beta^k); W is floored at w_floor only where
  *    it divides.
  *  - Frozen shift: the beta and B right-hand sides are identically zero.
+ *  - Matter (when T_{mu nu} is given): the printed source terms -alpha S,
+ *    -alpha e^{-4 phi} Shat_ij and -S^i are read in the normalisation of
+ *    Einstein's equations G = 8 pi T that the paper's ADM mass integrand
+ *    (16 pi E) uses: d_0 K gets +4 pi alpha (E + S), d_0 At_ij gets
+ *    -8 pi alpha e^{-4 phi} [S_ij]^TF, d_0 Gt^i gets -16 pi alpha gt^ij S_j
+ *    (and so does the Gamma-driver through d_0 Gt^i).
  */
 static double q_of_r(const ocfg* c, double r) {
   if (!(c->q_R > 0.0) || isinf(c->q_R)) return 1.0;
@@ -378,6 +422,15 @@ static void rhs_interior_point(const ocfg* c, const double* st, int i, int j, in
     for (int b = 0; b < 3; b++) AA += Auu[a][b] * A[a][b];
   double divb = db[0][0] + db[1][1] + db[2][2];
 
+  /* --- matter projections (zero in vacuum) --- */
+  double Em = 0.0, Sm = 0.0, Smi[3] = {0.0, 0.0, 0.0}, Smij[3][3] = {{0.0}};
+  if (c->tmunu) {
+    double gphys[3][3];
+    for (int a = 0; a < 3; a++)
+      for (int b = 0; b < 3; b++) gphys[a][b] = em4phi * gu[a][b];
+    matter_projections(c, id, alpha, beta, gphys, &Em, Smi, Smij, &Sm);
+  }
+
   double r[NF];
   for (int f = 0; f < NF; f++) r[f] = 0.0;
 
@@ -404,7 +457,8 @@ static void rhs_interior_point(const ocfg* c, const double* st, int i, int j, in
         lap_alp += gu[a][b] * DDalp[a][b];
         dphi_dalp += gu[a][b] * dphi[a] * dalp[b];
       }
-    r[F_TRK] = -em4phi * (lap_alp + 2.0 * dphi_dalp) + alpha * (AA + trK * trK / 3.0);
+    r[F_TRK] = -em4phi * (lap_alp + 2.0 * dphi_dalp) + alpha * (AA + trK * trK / 3.0) +
+               4.0 * M_PI * alpha * (Em + Sm);
   }
 
   /* d_0 At_ij = e^{-4phi}[alpha Rt + alpha Rphi - DtDt alpha + 4 d_(i phi Dt_j) alpha]^TF
@@ -426,6 +480,13 @@ static void rhs_interior_point(const ocfg* c, const double* st, int i, int j, in
         for (int kk = 0; kk < 3; kk++) s -= 2.0 * alpha * A[a][kk] * Aud[kk][b];
         for (int kk = 0; kk < 3; kk++) s += A[kk][a] * db[b][kk] + A[kk][b] * db[a][kk];
         s -= (2.0 / 3.0) * A[a][b] * divb;
+        if (c->tmunu) {
+          /* [S_ij]^TF = S_ij - (1/3) gamma_ij S = S_ij - (1/3) gt_ij gt^kl S_kl */
+          double trs = 0.0;
+          for (int kk = 0; kk < 3; kk++)
+            for (int l = 0; l < 3; l++) trs += gu[kk][l] * Smij[kk][l];
+          s -= 8.0 * M_PI * alpha * em4phi * (Smij[a][b] - g[a][b] * trs / 3.0);
+        }
         r[F_AT + SYM[a][b]] = s;
       }
   }
@@ -450,6 +511,7 @@ static void rhs_interior_point(const ocfg* c, const double* st, int i, int j, in
       for (int l = 0; l < 3; l++) br += G2[a][kk][l] * Auu[kk][l];
     for (int jj = 0; jj < 3; jj++) br += 6.0 * Auu[a][jj] * dphi[jj];
     s += 2.0 * alpha * br;
+    for (int jj = 0; jj < 3; jj++) s -= 16.0 * M_PI * alpha * gu[a][jj] * Smi[jj];
     gam_rhs[a] = s;
     r[F_GAM + a] = s;
   }
@@ -1015,6 +1077,19 @@ static void constraints_point(const ocfg* c, const double* gam6, const double* K
   }
 }
 
+/* Matter terms of the constraints (Sec. "Other analysis modules" with the
+ * normalisation of the ADM mass integrand): H gets -16 pi E, M_i gets
+ * -8 pi S_i, with alpha and beta^i of the state at the point. */
+static void constraint_sources(const ocfg* c, const double* st, size_t id, double o[4]) {
+  if (!c->tmunu) return;
+  const size_t S = npts(c);
+  double alpha = st[(size_t)F_ALP * S + id], beta[3], gdummy[3][3] = {{0.0}}, E, Si[3], Sij[3][3], Sm;
+  for (int a = 0; a < 3; a++) beta[a] = st[(size_t)(F_BETA + a) * S + id];
+  matter_projections(c, id, alpha, beta, gdummy, &E, Si, Sij, &Sm);
+  o[0] -= 16.0 * M_PI * E;
+  for (int a = 0; a < 3; a++) o[1 + a] -= 8.0 * M_PI * Si[a];
+}
+
 /* Constraint norms over interior points.  out16: L2 H, Mx, My, Mz, Linf H,
  * Mx, My, Mz over all interior points, then the same over points farther
  * than r_excise from every puncture.  L2 is the root mean square.  Hgrid and
@@ -1037,6 +1112,7 @@ int oracle_constraints(const ocfg* c, const double* st, double* out16, double* H
         double o[4];
         constraints_point(c, gam6, K6, i, j, k, o);
         size_t id = pidx(c, i, j, k);
+        constraint_sources(c, st, id, o);
         if (Hgrid) Hgrid[id] = o[0];
         if (Mgrid)
           for (int a = 0; a < 3; a++) Mgrid[(size_t)a * S + id] = o[1 + a];
@@ -1077,7 +1153,10 @@ int oracle_constraints_points(const ocfg* c, const double* st, int np, const int
   }
   adm_grids(c, st, gam6, K6);
   for (int p = 0; p < np; p++)
+  {
     constraints_point(c, gam6, K6, ijk[3 * p], ijk[3 * p + 1], ijk[3 * p + 2], out + 4 * p);
+    constraint_sources(c, st, pidx(c, ijk[3 * p], ijk[3 * p + 1], ijk[3 * p + 2]), out + 4 * p);
+  }
   free(gam6);
   free(K6);
   return 0;
@@ -1089,7 +1168,8 @@ int oracle_constraints_points(const ocfg* c, const double* st, int np, const int
  *                              - e^{phi} Rt ]
  *   J_i = 1/(8 pi) eps_ij^k int d^3x e^{6 phi} [ At^j_k + (2/3) x^j Dt_k K
  *                              - (1/2) x^j At_ln d_k gt^{ln} + 8 pi x^j S_k ]
- * in vacuum (E = S_k = 0).  Readings:
+ * with E and S_k the matter projections when T_{mu nu} is given (else 0).
+ * Readings:
  *  - Rt = gt^ij Rt_ij with the same Rt_ij as the right-hand side (the
  *    evolved Gt^k in gt_k(i d_j) Gt^k, the metric-derived d_l gt^{lk}
  *    elsewhere), from the same 4th-order stencils;
@@ -1200,7 +1280,14 @@ static void adm_density_point(const ocfg* c, const double* st, int i, int j, int
     }
   for (int a = 0; a < 3; a++)
     for (int b = 0; b < 3; b++) AA += A[a][b] * Au[a][b];
-  out[0] = (e5 * (AA - (2.0 / 3.0) * trK * trK) - ephi * Rt_trace) / (16.0 * M_PI);
+  /* matter: E and S_k (zero in vacuum) */
+  double Em = 0.0, Sk[3] = {0.0, 0.0, 0.0};
+  if (c->tmunu) {
+    double alpha = P0[(size_t)F_ALP * S], beta[3], gdummy[3][3] = {{0.0}}, Sij[3][3], Sm;
+    for (int a = 0; a < 3; a++) beta[a] = P0[(size_t)(F_BETA + a) * S];
+    matter_projections(c, id, alpha, beta, gdummy, &Em, Sk, Sij, &Sm);
+  }
+  out[0] = (e5 * (16.0 * M_PI * Em + AA - (2.0 / 3.0) * trK * trK) - ephi * Rt_trace) / (16.0 * M_PI);
   /* d_k gt^{ln} and At_ln d_k gt^{ln} */
   double AdG[3];
   for (int kk = 0; kk < 3; kk++) {
@@ -1222,7 +1309,8 @@ static void adm_density_point(const ocfg* c, const double* st, int i, int j, int
         /* Levi-Civita symbol eps_{ii jj kk} */
         double eps = (double)((ii - jj) * (jj - kk) * (kk - ii)) / 2.0;
         if (eps == 0.0) continue;
-        double v = Am[jj][kk] + (2.0 / 3.0) * x[jj] * dK[kk] - 0.5 * x[jj] * AdG[kk];
+        double v = Am[jj][kk] + (2.0 / 3.0) * x[jj] * dK[kk] - 0.5 * x[jj] * AdG[kk] +
+                   8.0 * M_PI * x[jj] * Sk[kk];
         s += eps * e6 * v;
       }
     out[1 + ii] = s / (8.0 * M_PI);

@@ -103,6 +103,40 @@ def _zero_B(t, x, y, z):
     return [x * 0.0, x * 0.0, x * 0.0]
 
 
+def flrw(w, t0=1.0):
+    """Spatially flat FLRW with a perfect fluid P = w rho:
+    ds^2 = -dt^2 + a(t)^2 dx^2, a = (t/t0)^p, p = 2/(3(1+w)); returns the
+    metric and the stress-energy tensor T_ab = (rho + P) u_a u_b + P g_ab with
+    u = d_t, rho = 3 H^2/(8 pi), H = p/t (Friedmann's equations for G = 1)."""
+    p = 2.0 / (3.0 * (1.0 + w))
+
+    def a2(tb):
+        return (tb * (1.0 / t0)) ** (2.0 * p)
+
+    def metric(tb, xb):
+        A = a2(tb)
+        return [[-1.0, 0.0, 0.0, 0.0], [0.0, A, 0.0, 0.0], [0.0, 0.0, A, 0.0], [0.0, 0.0, 0.0, A]]
+
+    def tmunu(tb, xb):
+        H = tb.recip() * p
+        rho = H * H * (3.0 / (8.0 * np.pi))
+        P = rho * w
+        A = a2(tb)
+        z = tb * 0.0
+        return [[rho, z, z, z], [z, P * A, z, z], [z, z, P * A, z], [z, z, z, P * A]]
+    return metric, tmunu
+
+
+def _flrw_wavy_map(t, x, y, z):
+    # t0 + t with tilted, curved slices and a sheared, time-dependent grid
+    e = 0.04
+    tb = t + 1.0 + sin((x - 2.0 * y + z) * (2 * np.pi / 3) + t) * (e / 2)
+    xb = [x + sin((y + z) * (2 * np.pi / 3) + t * 0.5) * e,
+          y + cos((z - x) * (2 * np.pi / 3) - t) * (e / 2),
+          z + sin((x - y) * (2 * np.pi / 3)) * cos(t) * (e / 2)]
+    return tb, xb
+
+
 SPACETIMES = {
     "gauge_wave": {"metric": _gauge_wave_metric(0.01, 1.0), "map": _identity_map, "B": _zero_B},
     # Flat space in a time-dependent, curl-carrying, anisotropic coordinate
@@ -120,6 +154,12 @@ SPACETIMES = {
     # radial, so the magnetic part of the Weyl tensor (the Codazzi projection)
     # is non-zero, which no spherically symmetric slicing of Schwarzschild has.
     "ks_boost": {"metric": kerr_schild(1.0), "map": _ks_boost_map, "B": _ks_wavy_B},
+    # Matter: dust and radiation FLRW universes seen from tilted, curved,
+    # time-dependent coordinates (E, S, S_i and the trace-free S_ij all
+    # non-zero on the slices).
+    "flrw_dust": {"metric": flrw(0.0)[0], "tmunu": flrw(0.0)[1], "map": _flrw_wavy_map, "B": _flat_wavy_B},
+    "flrw_rad": {"metric": flrw(1.0 / 3.0)[0], "tmunu": flrw(1.0 / 3.0)[1], "map": _flrw_wavy_map,
+                 "B": _flat_wavy_B},
 }
 
 
@@ -138,9 +178,11 @@ def _adj3(m):
     return [[c(j, i) for j in range(3)] for i in range(3)]  # adjugate = C^T
 
 
-def _four_metric(spec, X, Y, Z, time):
+def _four_metric(spec, X, Y, Z, time, want_jac=False):
     """Jets of the time, the grid coordinates and the 4-metric g_{mu nu} in
-    grid coordinates (pulled back through the spacetime's coordinate map)."""
+    grid coordinates (pulled back through the spacetime's coordinate map);
+    with want_jac also the base coordinates and the Jacobian
+    Jm[a][m] = d base^a / d x^m."""
     shape = X.shape
     T = Jet.var(0, np.full(shape, float(time)))
     xs = [Jet.var(1, X), Jet.var(2, Y), Jet.var(3, Z)]
@@ -160,7 +202,11 @@ def _four_metric(spec, X, Y, Z, time):
                     term = Jm[a][m] * Jm[b][n] * gab
                     s = term if s is None else s + term
             g4[m][n] = g4[n][m] = s
+    if want_jac:
+        return T, xs, g4, tb, xb, Jm
     return T, xs, g4
+
+
 
 
 def psi4_exact(name: str, X, Y, Z, time=0.0):
@@ -246,7 +292,7 @@ def evaluate(name: str, X, Y, Z, time=0.0, use_w=True):
     spec = SPACETIMES[name]
     X, Y, Z = np.broadcast_arrays(*(np.asarray(v, dtype=np.float64) for v in (X, Y, Z)))
     shape = X.shape
-    T, xs, g4 = _four_metric(spec, X, Y, Z, time)
+    T, xs, g4, tb, xb, Jm = _four_metric(spec, X, Y, Z, time, want_jac=True)
     gam = [[g4[i + 1][j + 1] for j in range(3)] for i in range(3)]
     bl = [g4[0][i + 1] for i in range(3)]
     det = _det3(gam)
@@ -323,6 +369,19 @@ def evaluate(name: str, X, Y, Z, time=0.0, use_w=True):
     grad["J_dens"] = np.stack([sum(dx(G[i][l], l).val for l in range(3)) for i in range(3)])
     grad["M_flux"] = np.stack([f.val for f in Fm])
     grad["J_flux"] = np.stack([np.stack([G[i][l].val for l in range(3)]) for i in range(3)])
+    if "tmunu" in spec:
+        # T_{mu nu} in grid coordinates: J^a_mu J^b_nu T_ab, rows T_00, T_0x,
+        # T_0y, T_0z, T_xx, T_xy, T_xz, T_yy, T_yz, T_zz
+        Tb = spec["tmunu"](tb, xb)
+        order = [(0, 0), (0, 1), (0, 2), (0, 3), (1, 1), (1, 2), (1, 3), (2, 2), (2, 3), (3, 3)]
+        tm = []
+        for (m, n) in order:
+            acc = np.zeros(shape)
+            for a in range(4):
+                for b in range(4):
+                    acc = acc + Jm[a][m].val * Jm[b][n].val * Tb[a][b].val
+            tm.append(acc)
+        grad["tmunu"] = np.stack(tm)
     grad["adm"] = np.stack([alpha.val] + [b.val for b in bu] +
                            [gam[i][j].val for (i, j) in SYM6] + [Kij[i][j].val for (i, j) in SYM6])
     return np.ascontiguousarray(state), dts, grad
