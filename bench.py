@@ -285,7 +285,8 @@ def run_ours(args):
                      "hbm_frac": (HBM_BYTES_PER_POINT_STEP * pts * args.steps / (ms * 1e-3)) / 6764e9},
         "e2e": {"value": e2e_value, "unit": "Mpoint-updates/s", "h2d_bytes_per_step": nbytes,
                 "d2h_bytes_per_step": nbytes, "steps": e2e_steps},
-        "gpu_launches": stage_n + bc_n,
+        # the split mixed stage is two kernels per stage (stencils, algebra)
+        "gpu_launches": stage_n * (2 if B.bssn_tile_name(tile).startswith("split") else 1) + bc_n,
         "clocks": clk,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -180,6 +180,23 @@ bssn_status bssn_rhs(bssn_ctx* ctx, const void* d_state, void* d_rhs);
  * punctures by one Euler step of the shift of y_n. */
 bssn_status bssn_rk4_step(bssn_ctx* ctx, int32_t nsteps);
 
+/* Matter coupling (Sec. "Spacetime Curvature Evolution" source terms,
+ * Sec. "TmunuBase"): d_tmunu is a caller-owned device array of
+ * 10 * field_stride doubles in the register layout holding T_{mu nu} at every
+ * stored point, in the order T_00, T_0x, T_0y, T_0z, T_xx, T_xy, T_xz, T_yy,
+ * T_yz, T_zz; NULL returns to vacuum.  From the projections
+ * E = (T_00 - 2 beta^i T_0i + beta^i beta^j T_ij)/alpha^2,
+ * S_i = -(T_0i - beta^j T_ij)/alpha, S_ij = T_ij, S = gamma^ij S_ij, every
+ * later right-hand side gets d_0 K += 4 pi alpha (E + S),
+ * d_0 At_ij -= 8 pi alpha e^{-4 phi} [S_ij]^TF and d_0 Gt^i -= 16 pi alpha
+ * gt^ij S_j (the B^i equation through d_0 Gt^i); bssn_constraints subtracts
+ * 16 pi E from H and 8 pi S_i from M_i, and bssn_adm_integrals adds 16 pi E
+ * and 8 pi x^j S_k to its integrands.  T_{mu nu} is read as given during every
+ * stage of a step (constant over the step; the matter evolution itself is the
+ * caller's) and must stay valid while set.  bssn_psi4 keeps the vacuum
+ * projections.  Batches and the server evolve vacuum only. */
+bssn_status bssn_set_matter(bssn_ctx* ctx, const double* d_tmunu);
+
 /* Puncture tracking (Sec. "Object tracking"): with enable != 0, every RK4 step
  * moves each puncture of the context (set by bssn_set_punctures or Brill-
  * Lindquist initial data) by x <- x - dt beta(t_n, x), the shift of y_n
@@ -235,8 +252,12 @@ bssn_status bssn_get_state(bssn_ctx* ctx, double* host_state, double* t);
 bssn_status bssn_set_state(bssn_ctx* ctx, const double* host_state, double t);
 
 /* Stage-kernel tile configurations: block shape (points along x, y, z) and the
- * minimum resident blocks per SM given to the compiler.  Every configuration
- * evaluates the same per-point arithmetic, so results do not depend on it. */
+ * minimum resident blocks per SM given to the compiler.  The last ones are for
+ * the mixed path only: "tma32x4x1/2" stages the second-differenced fields in
+ * shared memory by TMA; "split32x4x1/B" (B = 2, 3, 4) run the stencils as one
+ * pass per field into a derivative register and the algebra as a second pass.
+ * Every configuration evaluates the same per-point arithmetic, so results agree
+ * to rounding and each configuration is reproducible bit for bit. */
 int32_t bssn_tile_count(void);
 const char* bssn_tile_name(int32_t cfg); /* e.g. "32x8x1/1"; "" when out of range */
 bssn_status bssn_set_tile(bssn_ctx* ctx, int32_t cfg);

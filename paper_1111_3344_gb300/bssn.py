@@ -135,6 +135,7 @@ _SIGS = [
      ctypes.c_int),
     ("bssn_adm_integrals", [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     ("bssn_psi4", [ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
+    ("bssn_set_matter", [ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
     ("bssn_tile_count", [], ctypes.c_int32),
     ("bssn_tile_name", [ctypes.c_int32], ctypes.c_char_p),
     ("bssn_set_tile", [ctypes.c_void_p, ctypes.c_int32], ctypes.c_int),
@@ -283,6 +284,10 @@ def bssn_adm_integrals(ctx: int, d_dens=None) -> np.ndarray:
     out = (ctypes.c_double * 8)()
     _check(load().bssn_adm_integrals(ctypes.c_void_p(ctx), ctypes.c_void_p(d_dens or 0), out))
     return np.array(out[:], dtype=np.float64)
+
+
+def bssn_set_matter(ctx: int, d_tmunu):
+    _check(load().bssn_set_matter(ctypes.c_void_p(ctx), ctypes.c_void_p(d_tmunu or 0)))
 
 
 def bssn_psi4(ctx: int, d_out: int):
@@ -451,6 +456,23 @@ class Evolution:
 
     def get_punctures(self) -> np.ndarray:
         return bssn_get_punctures(self.ctx)
+
+    def set_matter(self, tmunu=None):
+        """Stress-energy tensor T_{mu nu}: a host array (10, Z, Y, X) in the order
+        T_00, T_0x, T_0y, T_0z, T_xx, T_xy, T_xz, T_yy, T_yz, T_zz, copied to a
+        device register this object keeps alive; None returns to vacuum."""
+        if tmunu is None:
+            bssn_set_matter(self.ctx, None)
+            self._tmunu = None
+            return
+        sx, sy, sz = self.layout["stored"]
+        t = np.ascontiguousarray(tmunu, dtype=np.float64)
+        assert t.shape == (10, sz, sy, sx)
+        reg = self.torch.zeros(10 * self.layout["field_stride"], dtype=self.torch.float64, device=self.device)
+        reg.view(10, sz, sy, self.layout["pitch"])[..., :sx] = self.torch.from_numpy(t).to(self.device)
+        self.torch.cuda.current_stream(self.device).synchronize()
+        self._tmunu = reg
+        bssn_set_matter(self.ctx, reg.data_ptr())
 
     def psi4(self, out=None):
         """Psi4 into a device register (2 * field_stride float64: real, then

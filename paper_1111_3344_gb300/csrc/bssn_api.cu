@@ -86,10 +86,11 @@ Grid make_grid(const bssn_params* p) {
 // Device block layout.  float64: y_n, k-sum, s1, s2 (+ anchor buffer for
 // Sommerfeld).  mixed: y_n in float64 (advanced in place); three float stage
 // buffers m[0..2] (m[0] is the float shadow of y_n), each with a float64 W
-// array; the float k-sum with its float64 W; float anchors.
+// array; the float k-sum with its float64 W; float anchors; the derivative
+// register of the split stage (135 float fields).
 struct Carve {
   size_t reg, yn, ks, s1, s2, ksh, part, out16, err, trk, total;
-  size_t m32[3], mw[3], ks32, ksw;
+  size_t m32[3], mw[3], ks32, ksw, dr;
   int nblocks;
 };
 
@@ -116,6 +117,7 @@ Carve carve(const bssn_params* p, const Grid& g) {
     c.ksw = o; o += wb;
     c.ksh = o;
     if (p->boundary == BSSN_BC_SOMMERFELD) o += reg32;
+    c.dr = o; o += align_up((size_t)split_slot_count() * (size_t)g.fstride * sizeof(float));
   }
   c.nblocks = constraints_blocks(g);
   c.part = o; o += align_up((size_t)c.nblocks * 18 * sizeof(double));
@@ -148,6 +150,7 @@ struct bssn_ctx {
   float* ks32;
   double* ksw;
   float* ksh32;
+  float* dr;  // mixed: derivative register of the split stage
   bool shadow_valid;
   int tile;  // stage-kernel tile configuration (see bssn_autotune)
   CUtensorMap tmap[3];  // mixed: tensor maps of the float stage buffers (TMA kernel)
@@ -247,6 +250,7 @@ bssn_status bssn_alloc(const bssn_params* p, void* d_mem, size_t bytes, void* cu
     ctx->ks32 = (float*)(ctx->mem + c.ks32);
     ctx->ksw = (double*)(ctx->mem + c.ksw);
     ctx->ksh32 = som ? (float*)(ctx->mem + c.ksh) : nullptr;
+    ctx->dr = (float*)(ctx->mem + c.dr);
   }
   ctx->shadow_valid = false;
   ctx->tile = 0;
@@ -362,6 +366,13 @@ bssn_status bssn_set_punctures(bssn_ctx* ctx, const double* p, int32_t npunct) {
   return BSSN_OK;
 }
 
+bssn_status bssn_set_matter(bssn_ctx* ctx, const double* d_tmunu) {
+  if (!ctx) return fail(BSSN_EINVAL, "ctx is NULL");
+  if (((uintptr_t)d_tmunu) % sizeof(double)) return fail(BSSN_EINVAL, "d_tmunu must be 8-byte aligned");
+  ctx->g.tmunu = d_tmunu;
+  return BSSN_OK;
+}
+
 bssn_status bssn_track_punctures(bssn_ctx* ctx, int32_t enable) {
   if (!ctx) return fail(BSSN_EINVAL, "ctx is NULL");
   if (enable && !ctx->tracking && !ctx->trk_stale) {
@@ -413,7 +424,10 @@ bssn_status bssn_rhs(bssn_ctx* ctx, const void* d_state, void* d_rhs) {
   a.rhs = out;
   a.w_thr = ctx->p.w_fp64_threshold;
   a.mode = MODE_RHS;
-  e = launch_stage_mixed(ctx->g, a, ctx->stream, ctx->tile);
+  if (ctx->tile > tile_config_count())
+    e = launch_stage_mixed_split(ctx->g, a, ctx->dr, ctx->stream, ctx->tile - tile_config_count() - 1);
+  else
+    e = launch_stage_mixed(ctx->g, a, ctx->stream, ctx->tile < tile_config_count() ? ctx->tile : 0);
   if (e != cudaSuccess) return cuda_fail(e, "bssn_rhs interior");
   if (!ctx->g.periodic) {
     e = launch_sommerfeld_mixed(ctx->g, a, nullptr, ctx->stream);
@@ -474,6 +488,8 @@ static bssn_status run_stage_mixed(bssn_ctx* ctx, int src, int mode, int out, do
   if (ctx->prof && (e = prof_mark(ctx, ctx->ev_stage)) != cudaSuccess) return cuda_fail(e, "profile");
   if (ctx->tile == tile_config_count())
     e = launch_stage_mixed_tma(ctx->g, a, ctx->tmap[src], ctx->err, ctx->stream);
+  else if (ctx->tile > tile_config_count())
+    e = launch_stage_mixed_split(ctx->g, a, ctx->dr, ctx->stream, ctx->tile - tile_config_count() - 1);
   else
     e = launch_stage_mixed(ctx->g, a, ctx->stream, ctx->tile);
   if (e != cudaSuccess) return cuda_fail(e, "stage");
@@ -615,23 +631,27 @@ bssn_status bssn_set_state(bssn_ctx* ctx, const double* host, double t) {
 }
 
 // Configurations: the plain tile shapes, then the TMA-staged mixed kernel.
-int32_t bssn_tile_count(void) { return tile_config_count() + 1; }
+// configurations: [0, tile_config_count()) fused kernels; tile_config_count()
+// the TMA kernel; then the split-stage variants
+int32_t bssn_tile_count(void) { return tile_config_count() + 1 + split_config_count(); }
 
 const char* bssn_tile_name(int32_t cfg) {
   if (cfg == tile_config_count()) return "tma32x4x1/2";
+  if (cfg > tile_config_count()) return split_config_name(cfg - tile_config_count() - 1);
   return tile_config_name(cfg);
 }
 
 static bool tile_usable(const bssn_ctx* ctx, int cfg) {
-  if (cfg < 0 || cfg > tile_config_count()) return false;
+  if (cfg < 0 || cfg >= bssn_tile_count()) return false;
   if (cfg == tile_config_count()) return ctx->p.precision == BSSN_MIXED && ctx->tmap_ok;
+  if (cfg > tile_config_count()) return ctx->p.precision == BSSN_MIXED;
   return true;
 }
 
 bssn_status bssn_set_tile(bssn_ctx* ctx, int32_t cfg) {
   if (!ctx) return fail(BSSN_EINVAL, "ctx is NULL");
   if (!tile_usable(ctx, cfg))
-    return fail(BSSN_EINVAL, "tile config out of range (the TMA kernel is for the mixed path)");
+    return fail(BSSN_EINVAL, "tile config out of range (the TMA and split kernels are for the mixed path)");
   ctx->tile = cfg;
   return BSSN_OK;
 }
@@ -648,7 +668,7 @@ bssn_status bssn_autotune(bssn_ctx* ctx, int32_t reps, int32_t* best, double* ms
   cudaError_t e;
   if ((e = cudaEventCreate(&e0)) != cudaSuccess) return cuda_fail(e, "event");
   if ((e = cudaEventCreate(&e1)) != cudaSuccess) { cudaEventDestroy(e0); return cuda_fail(e, "event"); }
-  const int ncfg = tile_config_count() + 1;
+  const int ncfg = bssn_tile_count();
   double best_ms = 1e300;
   int best_c = 0;
   bssn_status st = BSSN_OK;
@@ -671,6 +691,8 @@ bssn_status bssn_autotune(bssn_ctx* ctx, int32_t reps, int32_t* best, double* ms
       a.ksum = ctx->ks32; a.ksumw = ctx->ksw; a.a_dt = 0.5 * ctx->p.dt; a.a_dtf = (float)a.a_dt;
       a.w_thr = ctx->p.w_fp64_threshold; a.mode = MODE_FIRST;
       if (c == tile_config_count()) return launch_stage_mixed_tma(ctx->g, a, ctx->tmap[0], ctx->err, ctx->stream);
+      if (c > tile_config_count())
+        return launch_stage_mixed_split(ctx->g, a, ctx->dr, ctx->stream, c - tile_config_count() - 1);
       return launch_stage_mixed(ctx->g, a, ctx->stream, c);
     };
     if ((e = launch()) != cudaSuccess) { st = cuda_fail(e, "autotune warm-up"); break; }

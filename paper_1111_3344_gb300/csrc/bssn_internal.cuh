@@ -45,6 +45,9 @@ struct Grid {
   double i12h, i12h2, i144h2, kos, i2h;  // 1/(12h), 1/(12h^2), 1/(144h^2), eps/(64h), 1/(2h)
   float i12hf, i12h2f, i144h2f, kosf, i2hf, w_floorf, etaf, hf;
   float xminf[3];
+  // stress-energy tensor T_{mu nu} (10 fields in the register layout: T_00,
+  // T_0x, T_0y, T_0z, T_xx, T_xy, T_xz, T_yy, T_yz, T_zz), or null (vacuum)
+  const double* tmunu;
 };
 
 // Host-side fill of the derived constants of a Grid.
@@ -74,6 +77,38 @@ template <>
 __host__ __device__ __forceinline__ double gc<double>(double d, float) { return d; }
 template <>
 __host__ __device__ __forceinline__ float gc<float>(double, float f) { return f; }
+
+// Matter projections of T_{mu nu} at linear index id (Sec. "Spacetime Curvature
+// Evolution"): E = (T_00 - 2 beta^i T_0i + beta^i beta^j T_ij)/alpha^2,
+// S_i = -(T_0i - beta^j T_ij)/alpha, S_ij = T_ij (6 components), in type T.
+template <typename T>
+__device__ __forceinline__ void matter_at(const Grid& g, long long id, T alp, const T beta[3], T& E, T Si[3],
+                                          T Sij[6]) {
+  const double* p = g.tmunu + id;
+  const long long fs = g.fstride;
+  const T T00 = T(__ldg(p));
+  T T0[3];
+#pragma unroll
+  for (int a = 0; a < 3; a++) T0[a] = T(__ldg(p + (1 + a) * fs));
+#pragma unroll
+  for (int m = 0; m < 6; m++) Sij[m] = T(__ldg(p + (4 + m) * fs));
+  T e = T00;
+#pragma unroll
+  for (int a = 0; a < 3; a++) e -= T(2) * beta[a] * T0[a];
+#pragma unroll
+  for (int a = 0; a < 3; a++)
+#pragma unroll
+    for (int b = 0; b < 3; b++) e += beta[a] * beta[b] * Sij[sym(a, b)];
+  const T ia = T(1) / alp;
+  E = e * ia * ia;
+#pragma unroll
+  for (int a = 0; a < 3; a++) {
+    T s = T0[a];
+#pragma unroll
+    for (int b = 0; b < 3; b++) s -= beta[b] * Sij[sym(b, a)];
+    Si[a] = -s * ia;
+  }
+}
 
 // Coordinate of interior index ii (cell centre), xmin + (ii + 1/2) h, with the
 // product and the sum rounded separately (no fused multiply-add), so that a
@@ -184,6 +219,14 @@ const char* tile_config_name(int c);
 cudaError_t make_stage_tensor_map(const Grid& g, const float* base, CUtensorMap* out);
 cudaError_t launch_stage_mixed_tma(const Grid& g, const StageArgsMixed& a, const CUtensorMap& map,
                                    int* err, cudaStream_t s);
+// Split mixed stage (k_stage_split.cu): a stencil pass into the derivative
+// register dr (split_slot_count() float fields of the register layout) and an
+// algebra pass.
+int split_slot_count();
+int split_config_count();
+const char* split_config_name(int v);
+cudaError_t launch_stage_mixed_split(const Grid& g, const StageArgsMixed& a, float* dr, cudaStream_t s,
+                                     int variant);
 cudaError_t launch_sommerfeld(const Grid& g, const StageArgs& a, const double* kanchor,
                               cudaStream_t s);
 cudaError_t launch_sommerfeld_mixed(const Grid& g, const StageArgsMixed& a, const float* kanchor,

@@ -1,8 +1,9 @@
 // ADM mass and angular momentum as volume integrals (arXiv:1111.3344, Sec.
-// "Masses and Momenta", the ML_ADMQuantities form), in vacuum:
-//   M   = 1/(16 pi) int [ e^{5 phi}(At_ij At^ij - (2/3) K^2) - e^{phi} Rt ]
+// "Masses and Momenta", the ML_ADMQuantities form):
+//   M   = 1/(16 pi) int [ e^{5 phi}(16 pi E + At_ij At^ij - (2/3) K^2) - e^{phi} Rt ]
 //   J_i = 1/(8 pi) eps_ijk int e^{6 phi} [ At^j_k + (2/3) x^j d_k K
-//                                          - (1/2) x^j At_ln d_k gt^{ln} ]
+//                                          - (1/2) x^j At_ln d_k gt^{ln} + 8 pi x^j S_k ]
+// (E = S_k = 0 unless a stress-energy tensor is given)
 // with Rt = gt^ij Rt_ij built from the same pieces as the right-hand side
 // (the evolved Gt in gt_k(i d_j) Gt^k, d_l gt^{lk} from the metric stencils
 // elsewhere), d_k gt^{ln} = -gt^{la} gt^{nb} d_k gt_ab, so that
@@ -171,7 +172,16 @@ __device__ void adm_density(const Grid& g, const double* __restrict__ y, long lo
   for (int a = 0; a < 3; a++)
 #pragma unroll
     for (int b = 0; b < 3; b++) AA = fma(At[sym(a, b)], Au[sym(a, b)], AA);
-  out[0] = (e5 * (AA - (2.0 / 3.0) * trK * trK) - ephi * Rtr) * (1.0 / (16.0 * M_PI));
+  // matter: E and S_k (zero in vacuum)
+  double Em = 0.0, Sk[3] = {0.0, 0.0, 0.0};
+  if (g.tmunu) {
+    const double alp = __ldg(y + F_ALP * g.fstride + id);
+    const double beta[3] = {__ldg(y + F_BETA * g.fstride + id), __ldg(y + (F_BETA + 1) * g.fstride + id),
+                            __ldg(y + (F_BETA + 2) * g.fstride + id)};
+    double Sij[6];
+    matter_at<double>(g, id, alp, beta, Em, Sk, Sij);
+  }
+  out[0] = (e5 * (16.0 * M_PI * Em + AA - (2.0 / 3.0) * trK * trK) - ephi * Rtr) * (1.0 / (16.0 * M_PI));
   // At_ln d_k gt^{ln} = -At^{ab} d_k gt_ab
   double AdG[3];
 #pragma unroll
@@ -187,7 +197,8 @@ __device__ void adm_density(const Grid& g, const double* __restrict__ y, long lo
 #pragma unroll
   for (int jj = 0; jj < 3; jj++)
 #pragma unroll
-    for (int kk = 0; kk < 3; kk++) v[jj][kk] = fma(x[jj], (2.0 / 3.0) * dK[kk] - 0.5 * AdG[kk], Am[jj][kk]);
+    for (int kk = 0; kk < 3; kk++)
+      v[jj][kk] = fma(x[jj], (2.0 / 3.0) * dK[kk] - 0.5 * AdG[kk] + 8.0 * M_PI * Sk[kk], Am[jj][kk]);
   const double c = e6 * (1.0 / (8.0 * M_PI));
   out[1] = c * (v[1][2] - v[2][1]);
   out[2] = c * (v[2][0] - v[0][2]);

@@ -8,7 +8,8 @@
 //          + gamma^kl (Gamma^m_il Gamma_mkj - Gamma^m_ij Gamma_mkl)
 //   M_i  = gamma^jk (d_k K_ij - d_i K_jk) - Gamma^l K_il + Gamma^l_ij K_l^j
 // (the Christoffel terms of gamma^jk (nabla_k K_ij - nabla_i K_jk) after the
-// symmetric pair cancels).  Float64 in every precision mode.
+// symmetric pair cancels).  With a stress-energy tensor, H gets -16 pi E and
+// M_i gets -8 pi S_i.  Float64 in every precision mode.
 //
 // Reduction: one thread per interior point; per block a warp-shuffle tree in
 // each warp and a shuffle tree over the warp results, in a fixed order, into
@@ -173,6 +174,18 @@ __device__ void constraints_point(const Grid& g, const double* __restrict__ y, l
       for (int j = 0; j < 3; j++) s = fma(G2[l][sym(i, j)], Kud[j][l], s);
     }
     out[1 + i] = s;
+  }
+  if (g.tmunu) {
+    // matter: H -= 16 pi E, M_i -= 8 pi S_i
+    const long long fs = g.fstride;
+    const double alp = __ldg(y + F_ALP * fs + id);
+    const double beta[3] = {__ldg(y + F_BETA * fs + id), __ldg(y + (F_BETA + 1) * fs + id),
+                            __ldg(y + (F_BETA + 2) * fs + id)};
+    double E, Si[3], Sij[6];
+    matter_at<double>(g, id, alp, beta, E, Si, Sij);
+    out[0] -= 16.0 * M_PI * E;
+#pragma unroll
+    for (int q = 0; q < 3; q++) out[1 + q] -= 8.0 * M_PI * Si[q];
   }
 }
 

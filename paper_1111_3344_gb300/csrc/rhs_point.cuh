@@ -50,6 +50,15 @@ struct GlobalAcc {
   __device__ __forceinline__ T ld(int, const S* p) const { return T(__ldg(p)); }
 };
 
+// Accessors whose derivatives and advection/dissipation sums were computed
+// beforehand (the split mixed stage, k_stage_split.cu) say so here; the
+// right-hand side then adds acc.advko(f) instead of applying the 7-point
+// stencils itself.
+template <typename A>
+struct is_precomputed {
+  static constexpr bool value = false;
+};
+
 // 8 (f1 - f-1) - (f2 - f-2): 12 h times the 4th-order first derivative.
 template <typename T, typename A, typename P>
 __device__ __forceinline__ T d1u(const A& acc, int f, const P* p, long long s) {
@@ -379,6 +388,29 @@ __device__ __forceinline__ void rhs_point_acc(const Grid& g, const A& acc, int i
     for (int b = 0; b < 3; b++) AA = fmaT<T>(Auu[sym(a, b)], At[sym(a, b)], AA);
   const T divb = db[0][0] + db[1][1] + db[2][2];
 
+  // ---- matter sources, when a stress-energy tensor is given: the paper's
+  // -alpha S, -alpha e^{-4 phi} Shat_ij and -S^i in the normalisation G = 8 pi T,
+  // i.e. d_0 K += 4 pi alpha (E + S), d_0 At_ij -= 8 pi alpha e^{-4 phi} [S_ij]^TF,
+  // d_0 Gt^i -= 16 pi alpha gt^ij S_j (and the Gamma-driver through d_0 Gt^i)
+  const bool matter = g.tmunu != nullptr;
+  T mK = T(0), mA = T(0), mG[3] = {T(0), T(0), T(0)}, Stf[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
+  if (matter) {
+    T Em, Smi[3];
+    matter_at<T>(g, lin(g, i, j, k), alp, beta, Em, Smi, Stf);
+    T trs = T(0);
+#pragma unroll
+    for (int a = 0; a < 3; a++)
+#pragma unroll
+      for (int b = 0; b < 3; b++) trs = fmaT<T>(gu[sym(a, b)], Stf[sym(a, b)], trs);
+#pragma unroll
+    for (int m = 0; m < 6; m++) Stf[m] -= gt[m] * trs * T(1.0 / 3.0);  // [S_ij]^TF (gt_ij gt^kl = gamma_ij gamma^kl)
+    mK = T(4.0 * M_PI) * alp * (Em + em4 * trs);
+    mA = T(-8.0 * M_PI) * alp * em4;
+#pragma unroll
+    for (int a = 0; a < 3; a++)
+      mG[a] = T(-16.0 * M_PI) * alp * (gu[sym(a, 0)] * Smi[0] + gu[sym(a, 1)] * Smi[1] + gu[sym(a, 2)] * Smi[2]);
+  }
+
   // ---- assemble
   if (g.use_w)
     out[F_CHI] = (chi * T(1.0 / 3.0)) * (alp * trK - divb);
@@ -409,11 +441,11 @@ __device__ __forceinline__ void rhs_point_acc(const Grid& g, const A& acc, int i
           sa = fmaT<T>(At[sym(kk, b)], db[a][kk], sa);
         }
         out[F_GT + ab] = sg;
-        out[F_AT + ab] = sa;
+        out[F_AT + ab] = matter ? fmaT<T>(mA, Stf[ab], sa) : sa;
       }
   }
 
-  out[F_TRK] = -em4 * (lap_alp + T(2) * dphi_dalp) + alp * (AA + trK * trK * T(1.0 / 3.0));
+  out[F_TRK] = -em4 * (lap_alp + T(2) * dphi_dalp) + alp * (AA + trK * trK * T(1.0 / 3.0)) + mK;
 
   T gam_rhs[3];
 #pragma unroll
@@ -436,7 +468,7 @@ __device__ __forceinline__ void rhs_point_acc(const Grid& g, const A& acc, int i
     for (int kk = 0; kk < 3; kk++)
 #pragma unroll
       for (int l = 0; l < 3; l++) br = fmaT<T>(G2[a][sym(kk, l)], Auu[sym(kk, l)], br);
-    s = fmaT<T>(T(2) * alp, br, s);
+    s = fmaT<T>(T(2) * alp, br, s) + mG[a];
     gam_rhs[a] = s;
     out[F_GAM + a] = s;
   }
@@ -469,7 +501,11 @@ __device__ __forceinline__ void rhs_point_acc(const Grid& g, const A& acc, int i
 #pragma unroll
   for (int f = F_BETA; f < NF; f++)
     if (f >= nf) out[f] = T(0);
-  {
+  if constexpr (is_precomputed<A>::value) {
+#pragma unroll
+    for (int f = 0; f < NF; f++)
+      if (f < nf) out[f] += acc.template advko<T>(f);
+  } else {
     const T kap = gc<T>(g.kos, g.kosf);
     T f0s[NF];  // centre values as stored (float: the stencil is applied to f_m - f0)
     T bh[3];

@@ -59,6 +59,22 @@ def random_state(seed, n, xmin, h, amp=0.1, background=None):
     return np.ascontiguousarray(st)
 
 
+def random_tmunu(seed, n, xmin, h, amp=0.01):
+    """A smooth random stress-energy tensor T_{mu nu} on all stored points,
+    (10, Z, Y, X) in the order T_00, T_0x, T_0y, T_0z, T_xx, T_xy, T_xz, T_yy,
+    T_yz, T_zz: a positive energy density amp (1 + 0.5 p) and momentum and
+    stress components of size amp/2 (plain seeded numbers, no physics)."""
+    rng = np.random.default_rng(seed)
+    xs = grid_coords(n, xmin, h)
+    Z, Y, X = np.meshgrid(xs[2], xs[1], xs[0], indexing="ij")
+    L = max(n) * h
+    t = np.empty((10,) + X.shape)
+    t[0] = amp * (1.0 + 0.5 * smooth_field(rng, X, Y, Z, L))
+    for q in range(1, 10):
+        t[q] = smooth_field(rng, X, Y, Z, L, amp=0.5 * amp)
+    return np.ascontiguousarray(t)
+
+
 # ---- workload recipes (plain numbers)
 def single_puncture_128():
     """Brill-Lindquist M = 1 on [-8, 8]^3 at 128^3: the origin sits on a cell

@@ -150,9 +150,9 @@ def test_tile_configs_agree_and_are_deterministic(torch_cuda, precision):
     st = _state_for("bl", case)
     runs = {}
     for cfg in range(B.bssn_tile_count()):
-        if precision == "fp64" and B.bssn_tile_name(cfg).startswith("tma"):
+        if precision == "fp64" and B.bssn_tile_name(cfg).startswith(("tma", "split")):
             evo = _evo(case)
-            with pytest.raises(B.BssnError):  # the TMA-staged kernel is mixed-only
+            with pytest.raises(B.BssnError):  # the TMA-staged and split kernels are mixed-only
                 B.bssn_set_tile(evo.ctx, cfg)
             evo.close()
             continue
