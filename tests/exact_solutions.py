@@ -23,6 +23,8 @@ their defining equations evaluated with exact values.
 """
 from __future__ import annotations
 
+import functools
+
 import numpy as np
 
 from jets import Jet, cos, sin, sqrt
@@ -385,3 +387,26 @@ def evaluate(name: str, X, Y, Z, time=0.0, use_w=True):
     grad["adm"] = np.stack([alpha.val] + [b.val for b in bu] +
                            [gam[i][j].val for (i, j) in SYM6] + [Kij[i][j].val for (i, j) in SYM6])
     return np.ascontiguousarray(state), dts, grad
+
+
+@functools.lru_cache(maxsize=48)
+def _on_grid_w(name, n, lo, hi):
+    h = (hi - lo) / n[0]
+    xs = [lo + (np.arange(n[d] + 6) - 3 + 0.5) * h for d in range(3)]
+    Z, Y, X = np.meshgrid(xs[2], xs[1], xs[0], indexing="ij")
+    return evaluate(name, X, Y, Z, use_w=True)
+
+
+def on_grid(name, n, lo, hi, use_w=True):
+    """evaluate() on the cell-centred grid of n = (n0, n1, n2) interior points
+    with spacing (hi - lo)/n0 from xmin = (lo, lo, lo), three ghost layers;
+    cached (the jets are the slow part of the pins), returned as copies.  The
+    phi variant is derived from W: phi = -ln(W)/2, d_t phi = -d_t W / (2 W)."""
+    st, dts, grad = _on_grid_w(name, tuple(n), float(lo), float(hi))
+    st, dts = st.copy(), dts.copy()
+    grad = {k: np.array(v, copy=True) for k, v in grad.items()}
+    if not use_w:
+        W = st[0].copy()
+        st[0] = -0.5 * np.log(W)
+        dts[0] = -0.5 * dts[0] / W
+    return st, dts, grad

@@ -53,7 +53,7 @@ def test_adm_to_bssn_fd_on_exact_solutions(name, box):
         lo, hi = box
         cfg = O.Config(n=(n, n, n), h=(hi - lo) / n, xmin=(lo,) * 3, periodic=False, use_w=True)
         X, Y, Z = _mesh(cfg)
-        st_exact, _, grad = E.evaluate(name, X, Y, Z)
+        st_exact, _, grad = E.on_grid(name, (n, n, n), lo, hi)
         st = O.adm_to_bssn_fd(cfg, grad["adm"])
         # all non-Gt fields by the definitions, exactly; B^i = 0
         others = [f for f in range(O.F_B) if not O.F_GAM <= f < O.F_GAM + 3]

@@ -34,8 +34,7 @@ def _case(name, n, use_w, box):
     lo, hi = box
     cfg = O.Config(n=(n, n, n), h=(hi - lo) / n, xmin=(lo,) * 3, periodic=name == "gauge_wave",
                    use_w=use_w)
-    X, Y, Z = _mesh(cfg)
-    st, _, grad = E.evaluate(name, X, Y, Z, use_w=use_w)
+    st, _, grad = E.on_grid(name, (n, n, n), lo, hi, use_w=use_w)
     return cfg, st, grad
 
 
@@ -63,7 +62,7 @@ def test_integrands_fourth_order(name, use_w):
     assert (e1[live] < 1e-3 * scales[1][live]).all(), (e1, scales[1])
 
 
-def _gauss_faces(lo, hi, m=12):
+def _gauss_faces(lo, hi, m=10):
     """Points and weights of an m x m Gauss-Legendre rule on each face of the
     cube [lo, hi]^3, with the face's outward normal axis and sign."""
     t, w = np.polynomial.legendre.leggauss(m)

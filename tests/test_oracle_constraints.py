@@ -94,8 +94,7 @@ def test_constraints_vanish_on_exact_solutions(name, box):
     for n in (12, 24):
         lo, hi = box
         cfg = O.Config(n=(n, n, n), h=(hi - lo) / n, xmin=(lo,) * 3, use_w=True)
-        X, Y, Z = _mesh(cfg)
-        st, _, _ = E.evaluate(name, X, Y, Z)
+        st, _, _ = E.on_grid(name, (n, n, n), lo, hi)
         _, H, M = O.constraints(cfg, st)
         errs.append([np.abs(_int(cfg, H)).max()] + [np.abs(_int(cfg, M[i])).max() for i in range(3)])
     errs = np.array(errs)

@@ -26,7 +26,7 @@ def _setup(name, n, use_w, **kw):
     h = (hi - lo) / n
     cfg = O.Config(n=(n, n, n), h=h, xmin=(lo, lo, lo), periodic=True, use_w=use_w, **kw)
     Zc, Yc, Xc = np.meshgrid(cfg.coords(2), cfg.coords(1), cfg.coords(0), indexing="ij")
-    state, dts, grad = E.evaluate(name, Xc, Yc, Zc, use_w=use_w)
+    state, dts, grad = E.on_grid(name, (n, n, n), lo, hi, use_w=use_w)
     return cfg, state, dts, grad, (Xc, Yc, Zc)
 
 

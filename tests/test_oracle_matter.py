@@ -28,8 +28,7 @@ import oracle as O
 def _setup(name, n, use_w):
     lo, hi = -0.5, 0.5
     cfg = O.Config(n=(n, n, n), h=(hi - lo) / n, xmin=(lo,) * 3, periodic=False, use_w=use_w)
-    Zc, Yc, Xc = np.meshgrid(cfg.coords(2), cfg.coords(1), cfg.coords(0), indexing="ij")
-    state, dts, grad = E.evaluate(name, Xc, Yc, Zc, use_w=use_w)
+    state, dts, grad = E.on_grid(name, (n, n, n), lo, hi, use_w=use_w)
     return cfg, state, dts, grad
 
 
