@@ -39,8 +39,20 @@ DOMAIN = 8.0
 FLOP_PER_POINT_RHS = 3961.0        # DADD + DMUL + 2 DFMA
 DPINST_PER_POINT_RHS = 2428.0      # float64 instructions issued
 HBM_BYTES_PER_POINT_STEP = 3264.0  # 17 register passes x 24 fields x 8 B
+# mixed: float stage buffers (24 x 4 B) each with a float64 W (8 B), 104 B a
+# buffer pass; per RK4 step: stage 1 reads m0, writes m1 and the k-sum (312 B);
+# stages 2-3 read src, m0 and the k-sum and write out and the k-sum (520 B
+# each); stage 4 reads src and the k-sum, reads and writes y_n (2 x 192 B) and
+# writes the new shadow m0 (696 B)
+HBM_BYTES_PER_POINT_STEP_MIXED = 312.0 + 2 * 520.0 + 696.0   # 2048
+HBM_MEASURED_GBS = 6764.0          # STREAM-style copy on this pool
 FP64_PEAK_GFLOPS = 1250.0          # nominal GB300 FP64 rate
 FP64_MEASURED_GFLOPS = 1196.0      # dependent-chain DFMA microbenchmark on this pool
+# DRAM bytes (read + write) per interior point of one stage launch, from the
+# ncu capture of the current kernels on the 64^3 case (traffic grows with the
+# points; profiles/stage_traffic_bl64.md); None until captured.
+FP64_TRAFFIC_PER_POINT = 1248.2    # (93.1 + 234.0) MB / 262,144 points, stage_fp64_kernel 32x2x2/2
+MIXED_TRAFFIC_PER_POINT = 282.0    # (50.5 + 23.4) MB / 262,144 points, stage_mixed_tma_kernel
 # Float64 work per interior point of the analysis kernels (DADD + DMUL + 2 DFMA
 # from ncu instruction counts; profiles/analysis_kernels_bl96.md).
 ANALYSIS_FLOP_PER_POINT = {"psi4": 4888.0, "adm_integrals": 1858.0, "constraints": 3508.0}
@@ -264,8 +276,30 @@ def run_ours(args):
     flop_launch = FLOP_PER_POINT_RHS * pts
     stage_launch_ms = stage_ms / max(stage_n, 1)
     achieved = flop_launch / (stage_launch_ms * 1e-3) / 1e12
+    mixed = args.precision == "mixed"
+    if mixed:
+        # HBM-bound form: algorithmic bytes per stage launch over its duration
+        bytes_launch = HBM_BYTES_PER_POINT_STEP_MIXED / 4.0 * pts
+        gbs = bytes_launch / (stage_launch_ms * 1e-3) / 1e9
+        roofline = {"bound": "hbm", "kernel": B.bssn_tile_name(tile), "achieved": gbs,
+                    "peak": HBM_MEASURED_GBS, "unit": "GB/s", "frac": gbs / HBM_MEASURED_GBS,
+                    "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)",
+                    "algorithmic_bytes_per_launch": bytes_launch,
+                    "traffic": MIXED_TRAFFIC_PER_POINT * pts if MIXED_TRAFFIC_PER_POINT else None,
+                    "launch_ms": stage_launch_ms, "launches": stage_n}
+    else:
+        roofline = {"bound": "alu", "kernel": "stage_fp64_kernel", "achieved": achieved * 1e3,
+                    "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s (FP64)",
+                    "frac": achieved * 1e3 / FP64_PEAK_GFLOPS,
+                    "frac_of_measured_dfma": achieved * 1e3 / FP64_MEASURED_GFLOPS,
+                    "fp64_issue_frac": DPINST_PER_POINT_RHS * pts / (stage_launch_ms * 1e-3)
+                                       / (FP64_MEASURED_GFLOPS * 1e9 / 2),
+                    "traffic": FP64_TRAFFIC_PER_POINT * pts if FP64_TRAFFIC_PER_POINT else None,
+                    "launch_ms": stage_launch_ms, "launches": stage_n,
+                    "hbm_frac": (HBM_BYTES_PER_POINT_STEP * pts * args.steps / (ms * 1e-3)) / HBM_MEASURED_GBS / 1e9}
     line = {
-        "metric": "BSSN RK4 point-updates/s (FP64, Brill-Lindquist puncture 128^3)",
+        "metric": ("BSSN RK4 point-updates/s (mixed FP32 RHS / FP64 state, Brill-Lindquist puncture 128^3)"
+                   if mixed else "BSSN RK4 point-updates/s (FP64, Brill-Lindquist puncture 128^3)"),
         "value": value, "unit": "Mpoint-updates/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f64",
@@ -275,14 +309,7 @@ def run_ours(args):
                    "global_batch": world, "grid": [N_SIDE] * 3, "parallelism": f"replicas{world}",
                    "precision": args.precision, "tile": B.bssn_tile_name(tile),
                    "l2": "inputs larger than L2 (4 float64 registers of 469 MB each)"},
-        "roofline": {"bound": "alu", "kernel": "stage_fp64_kernel", "achieved": achieved * 1e3,
-                     "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s (FP64)",
-                     "frac": achieved * 1e3 / FP64_PEAK_GFLOPS,
-                     "frac_of_measured_dfma": achieved * 1e3 / FP64_MEASURED_GFLOPS,
-                     "fp64_issue_frac": DPINST_PER_POINT_RHS * pts / (stage_launch_ms * 1e-3)
-                                        / (FP64_MEASURED_GFLOPS * 1e9 / 2),
-                     "traffic": None, "launch_ms": stage_launch_ms, "launches": stage_n,
-                     "hbm_frac": (HBM_BYTES_PER_POINT_STEP * pts * args.steps / (ms * 1e-3)) / 6764e9},
+        "roofline": roofline,
         "e2e": {"value": e2e_value, "unit": "Mpoint-updates/s", "h2d_bytes_per_step": nbytes,
                 "d2h_bytes_per_step": nbytes, "steps": e2e_steps},
         # the split mixed stage is two kernels per stage (stencils, algebra)

@@ -424,10 +424,13 @@ bssn_status bssn_rhs(bssn_ctx* ctx, const void* d_state, void* d_rhs) {
   a.rhs = out;
   a.w_thr = ctx->p.w_fp64_threshold;
   a.mode = MODE_RHS;
+  // the selected stage kernel, TMA-staged included (tmap[2] describes m32[2])
   if (ctx->tile > tile_config_count())
     e = launch_stage_mixed_split(ctx->g, a, ctx->dr, ctx->stream, ctx->tile - tile_config_count() - 1);
+  else if (ctx->tile == tile_config_count())
+    e = launch_stage_mixed_tma(ctx->g, a, ctx->tmap[2], ctx->err, ctx->stream);
   else
-    e = launch_stage_mixed(ctx->g, a, ctx->stream, ctx->tile < tile_config_count() ? ctx->tile : 0);
+    e = launch_stage_mixed(ctx->g, a, ctx->stream, ctx->tile);
   if (e != cudaSuccess) return cuda_fail(e, "bssn_rhs interior");
   if (!ctx->g.periodic) {
     e = launch_sommerfeld_mixed(ctx->g, a, nullptr, ctx->stream);
@@ -547,6 +550,14 @@ bssn_status bssn_rk4_step(bssn_ctx* ctx, int32_t nsteps) {
 
 static bssn_status check_err(bssn_ctx* ctx);
 
+// Scratch for the 12 ADM fields of the analysis kernels: a stage buffer that
+// holds nothing between RK4 steps (float64: s1; mixed: the float stage buffer
+// m[1], 24 floats = 12 doubles per point).  Stream order keeps a following
+// step from overwriting it early.
+static double* adm_scratch(bssn_ctx* ctx) {
+  return ctx->p.precision == BSSN_FP64 ? ctx->s1 : (double*)ctx->m32[1];
+}
+
 bssn_status bssn_constraints(bssn_ctx* ctx, double out[16]) {
   if (!ctx || !out) return fail(BSSN_EINVAL, "NULL argument");
   if (bssn_status es = check_err(ctx)) return es;
@@ -554,7 +565,7 @@ bssn_status bssn_constraints(bssn_ctx* ctx, double out[16]) {
   if (e != cudaSuccess) return cuda_fail(e, "punctures");
   e = launch_constraints(ctx->g, ctx->yn, &ctx->punct[0][0], ctx->npunct,
                                      ctx->p.r_excise, ctx->part, ctx->c.nblocks, ctx->out16,
-                                     ctx->stream);
+                                     ctx->stream, adm_scratch(ctx));
   if (e != cudaSuccess) return cuda_fail(e, "constraints");
   e = cudaMemcpyAsync(out, ctx->out16, 16 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
   if (e != cudaSuccess) return cuda_fail(e, "constraints copy");
@@ -584,7 +595,7 @@ bssn_status bssn_adm_integrals(bssn_ctx* ctx, double* d_dens, double out[8]) {
 
 bssn_status bssn_psi4(bssn_ctx* ctx, double* d_out) {
   if (!ctx || !d_out) return fail(BSSN_EINVAL, "NULL argument");
-  cudaError_t e = launch_psi4(ctx->g, ctx->yn, d_out, ctx->stream);
+  cudaError_t e = launch_psi4(ctx->g, ctx->yn, d_out, ctx->stream, adm_scratch(ctx));
   if (e != cudaSuccess) return cuda_fail(e, "psi4");
   return BSSN_OK;
 }

@@ -236,9 +236,14 @@ cudaError_t launch_periodic_fill_mixed(const Grid& g, float* y, double* w, cudaS
 cudaError_t launch_shadow(const Grid& g, const double* y, float* s32, double* w, cudaStream_t s);
 cudaError_t launch_initial_data(const Grid& g, int kind, const double* dparams, int np,
                                 double* y, cudaStream_t s);
+// adm_scratch (may be null): 12 * fstride doubles; when given, the ADM fields
+// are formed once per stored point there (launch_adm_fields) instead of at
+// every stencil point.
 cudaError_t launch_constraints(const Grid& g, const double* y, const double* dpunct,
                                int npunct, double r_excise, double* partials, int nblocks,
-                               double* dout16, cudaStream_t s);
+                               double* dout16, cudaStream_t s, double* adm_scratch = nullptr);
+// gamma_ij and K_ij (12 fields) at every stored point of y (k_constraints.cu).
+cudaError_t launch_adm_fields(const Grid& g, const double* y, double* adm, cudaStream_t s);
 int constraints_blocks(const Grid& g);
 // y's first 16 field slots hold ADM data (alpha, beta^i, gamma_ij, K_ij);
 // converts it in place to the BSSN state (k_adm.cu).
@@ -252,7 +257,8 @@ cudaError_t launch_adm_integrals(const Grid& g, const double* y, const Punct& pu
                                  double* partials, int nblocks, double* dout8, cudaStream_t s);
 // Weyl scalar Psi4 at interior points into out (2 fields of the register
 // layout: real, imaginary) (k_psi4.cu).
-cudaError_t launch_psi4(const Grid& g, const double* y, double* out, cudaStream_t s);
+cudaError_t launch_psi4(const Grid& g, const double* y, double* out, cudaStream_t s,
+                        double* adm_scratch = nullptr);
 // One Euler step of the puncture positions dpunct (rows {m, x, y, z}) from the
 // shift of y (k_track.cu).
 cudaError_t launch_track(const Grid& g, const double* y, double* dpunct, int np, double dt, cudaStream_t s);

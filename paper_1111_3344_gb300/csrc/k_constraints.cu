@@ -25,9 +25,22 @@ __device__ __forceinline__ double nanmax(double a, double b) { return (b > a || 
 constexpr int CB = 256;   // threads per block
 constexpr int NPART = 18; // partial values per block
 
-__device__ __forceinline__ void adm_at(const Grid& g, const double* __restrict__ y, long long id,
-                                       double gam[6], double K[6], bool needK) {
+// ADM fields at one stored point, formed from the state (PRE = false) or read
+// from a buffer of 12 fields gamma_ij, K_ij filled by adm_fields_kernel with
+// the same operations (PRE = true), so both give the same bits.
+template <bool PRE>
+__device__ __forceinline__ void adm_at(const Grid& g, const double* __restrict__ y,
+                                       const double* __restrict__ adm, long long id, double gam[6],
+                                       double K[6], bool needK) {
   const long long fs = g.fstride;
+  if constexpr (PRE) {
+#pragma unroll
+    for (int m = 0; m < 6; m++) {
+      gam[m] = __ldg(adm + m * fs + id);
+      if (needK) K[m] = __ldg(adm + (6 + m) * fs + id);
+    }
+    return;
+  }
   const double chi = __ldg(y + F_CHI * fs + id);
   const double e4 = g.use_w ? 1.0 / (chi * chi) : exp(4.0 * chi);
   const double tr3 = needK ? __ldg(y + F_TRK * fs + id) * (1.0 / 3.0) : 0.0;
@@ -39,22 +52,23 @@ __device__ __forceinline__ void adm_at(const Grid& g, const double* __restrict__
   }
 }
 
-__device__ void constraints_point(const Grid& g, const double* __restrict__ y, long long id,
-                                  double out[4]) {
+template <bool PRE>
+__device__ void constraints_point(const Grid& g, const double* __restrict__ y,
+                                  const double* __restrict__ adm, long long id, double out[4]) {
   const long long sd[3] = {1, g.pitch, g.plane};
   const double i12h = g.i12h;
   const double i12h2 = g.i12h2;
   const double i144h2 = g.i144h2;
   double g0[6], k0[6];
-  adm_at(g, y, id, g0, k0, true);
+  adm_at<PRE>(g, y, adm, id, g0, k0, true);
   double dg[3][6], dk[3][6], ddg[6][6];
 #pragma unroll
   for (int d = 0; d < 3; d++) {
     double gp1[6], gm1[6], gp2[6], gm2[6], kp1[6], km1[6], kp2[6], km2[6];
-    adm_at(g, y, id + sd[d], gp1, kp1, true);
-    adm_at(g, y, id - sd[d], gm1, km1, true);
-    adm_at(g, y, id + 2 * sd[d], gp2, kp2, true);
-    adm_at(g, y, id - 2 * sd[d], gm2, km2, true);
+    adm_at<PRE>(g, y, adm, id + sd[d], gp1, kp1, true);
+    adm_at<PRE>(g, y, adm, id - sd[d], gm1, km1, true);
+    adm_at<PRE>(g, y, adm, id + 2 * sd[d], gp2, kp2, true);
+    adm_at<PRE>(g, y, adm, id - 2 * sd[d], gm2, km2, true);
 #pragma unroll
     for (int m = 0; m < 6; m++) {
       dg[d][m] = fma(8.0, gp1[m] - gm1[m], -(gp2[m] - gm2[m])) * i12h;
@@ -75,7 +89,7 @@ __device__ void constraints_point(const Grid& g, const double* __restrict__ y, l
 #pragma unroll
         for (int q = 0; q < 4; q++) {
           double gv[6];
-          adm_at(g, y, id + off[p] * sd[a] + off[q] * sd[b], gv, dummy, false);
+          adm_at<PRE>(g, y, adm, id + off[p] * sd[a] + off[q] * sd[b], gv, dummy, false);
           const double w = c[p] * c[q];
 #pragma unroll
           for (int m = 0; m < 6; m++) acc[m] = fma(w, gv[m], acc[m]);
@@ -221,8 +235,10 @@ __device__ __forceinline__ void block_reduce(double v[NPART]) {
   }
 }
 
+template <bool PRE>
 __global__ void __launch_bounds__(CB) constraints_kernel(Grid g, const double* __restrict__ y,
-                                                         Punct pu, double* __restrict__ partials) {
+                                                         const double* __restrict__ adm, Punct pu,
+                                                         double* __restrict__ partials) {
   const long long npts = (long long)g.n0 * g.n1 * g.n2;
   const long long tid = (long long)blockIdx.x * CB + threadIdx.x;
   double v[NPART];
@@ -234,7 +250,7 @@ __global__ void __launch_bounds__(CB) constraints_kernel(Grid g, const double* _
     const int kk = (int)(tid / ((long long)g.n0 * g.n1));
     const int i = ii + GH, j = jj + GH, k = kk + GH;
     double c4[4];
-    constraints_point(g, y, lin(g, i, j, k), c4);
+    constraints_point<PRE>(g, y, adm, lin(g, i, j, k), c4);
     const double x = cell_coord(g.xmin0, ii, g.h);
     const double yy = cell_coord(g.xmin1, jj, g.h);
     const double z = cell_coord(g.xmin2, kk, g.h);
@@ -285,16 +301,48 @@ int constraints_blocks(const Grid& g) {
   return (int)((npts + CB - 1) / CB);
 }
 
+// gamma_ij = e^{4 phi} gt_ij and K_ij = e^{4 phi}(At_ij + gt_ij K/3) at every
+// stored point into adm (12 fields of the register layout), with the
+// operations of adm_at<false>.
+__global__ void adm_fields_kernel(Grid g, const double* __restrict__ y, double* __restrict__ adm) {
+  const long long n = g.fstride;
+  for (long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x; id < n;
+       id += (long long)gridDim.x * blockDim.x) {
+    double gam[6], K[6];
+    adm_at<false>(g, y, nullptr, id, gam, K, true);
+#pragma unroll
+    for (int m = 0; m < 6; m++) {
+      adm[m * n + id] = gam[m];
+      adm[(6 + m) * n + id] = K[m];
+    }
+  }
+}
+
+cudaError_t launch_adm_fields(const Grid& g, const double* y, double* adm, cudaStream_t s) {
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  adm_fields_kernel<<<sms * 8, 256, 0, s>>>(g, y, adm);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_constraints(const Grid& g, const double* y, const double* punct4, int npunct,
                                double r_excise, double* partials, int nblocks, double* dout16,
-                               cudaStream_t s) {
+                               cudaStream_t s, double* adm_scratch) {
   Punct pu{};
   pu.n = npunct < 8 ? npunct : 8;
   for (int a = 0; a < pu.n; a++)
     for (int q = 0; q < 4; q++) pu.p[a][q] = punct4[4 * a + q];
   pu.r_ex = r_excise;
-  constraints_kernel<<<nblocks, CB, 0, s>>>(g, y, pu, partials);
-  cudaError_t e = cudaGetLastError();
+  cudaError_t e;
+  if (adm_scratch) {
+    if ((e = launch_adm_fields(g, y, adm_scratch, s)) != cudaSuccess) return e;
+    constraints_kernel<true><<<nblocks, CB, 0, s>>>(g, y, adm_scratch, pu, partials);
+  } else {
+    constraints_kernel<false><<<nblocks, CB, 0, s>>>(g, y, nullptr, pu, partials);
+  }
+  e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   constraints_finalize<<<1, CB, 0, s>>>(partials, nblocks, dout16);
   return cudaGetLastError();

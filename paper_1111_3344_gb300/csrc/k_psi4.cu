@@ -30,9 +30,19 @@ namespace {
 
 constexpr int PB = 128;  // threads per block
 
-__device__ __forceinline__ void adm_fields(const Grid& g, const double* __restrict__ y, long long id,
-                                           double gam[6], double K[6], bool needK) {
+template <bool PRE>
+__device__ __forceinline__ void adm_fields(const Grid& g, const double* __restrict__ y,
+                                           const double* __restrict__ adm, long long id, double gam[6],
+                                           double K[6], bool needK) {
   const long long fs = g.fstride;
+  if constexpr (PRE) {  // precomputed by launch_adm_fields with the operations below
+#pragma unroll
+    for (int m = 0; m < 6; m++) {
+      gam[m] = __ldg(adm + m * fs + id);
+      if (needK) K[m] = __ldg(adm + (6 + m) * fs + id);
+    }
+    return;
+  }
   const double chi = __ldg(y + F_CHI * fs + id);
   const double e4 = g.use_w ? 1.0 / (chi * chi) : exp(4.0 * chi);
   const double tr3 = needK ? __ldg(y + F_TRK * fs + id) * (1.0 / 3.0) : 0.0;
@@ -54,20 +64,21 @@ __device__ __forceinline__ double bil(const double T[6], const double a[3], cons
   return s;
 }
 
-__device__ void psi4_point(const Grid& g, const double* __restrict__ y, long long id, const double x[3],
-                           double out[2]) {
+template <bool PRE>
+__device__ void psi4_point(const Grid& g, const double* __restrict__ y, const double* __restrict__ adm,
+                           long long id, const double x[3], double out[2]) {
   const long long sd[3] = {1, g.pitch, g.plane};
   const double i12h = g.i12h, i12h2 = g.i12h2, i144h2 = g.i144h2;
   double g0[6], k0[6];
-  adm_fields(g, y, id, g0, k0, true);
+  adm_fields<PRE>(g, y, adm, id, g0, k0, true);
   double dg[3][6], dk[3][6], ddg[6][6];
 #pragma unroll
   for (int d = 0; d < 3; d++) {
     double gp1[6], gm1[6], gp2[6], gm2[6], kp1[6], km1[6], kp2[6], km2[6];
-    adm_fields(g, y, id + sd[d], gp1, kp1, true);
-    adm_fields(g, y, id - sd[d], gm1, km1, true);
-    adm_fields(g, y, id + 2 * sd[d], gp2, kp2, true);
-    adm_fields(g, y, id - 2 * sd[d], gm2, km2, true);
+    adm_fields<PRE>(g, y, adm, id + sd[d], gp1, kp1, true);
+    adm_fields<PRE>(g, y, adm, id - sd[d], gm1, km1, true);
+    adm_fields<PRE>(g, y, adm, id + 2 * sd[d], gp2, kp2, true);
+    adm_fields<PRE>(g, y, adm, id - 2 * sd[d], gm2, km2, true);
 #pragma unroll
     for (int m = 0; m < 6; m++) {
       dg[d][m] = fma(8.0, gp1[m] - gm1[m], -(gp2[m] - gm2[m])) * i12h;
@@ -89,7 +100,7 @@ __device__ void psi4_point(const Grid& g, const double* __restrict__ y, long lon
 #pragma unroll
           for (int q = 0; q < 4; q++) {
             double gv[6];
-            adm_fields(g, y, id + off[p] * sd[a] + off[q] * sd[b], gv, dummy, false);
+            adm_fields<PRE>(g, y, adm, id + off[p] * sd[a] + off[q] * sd[b], gv, dummy, false);
             const double w = c[p] * c[q];
 #pragma unroll
             for (int m = 0; m < 6; m++) acc[m] = fma(w, gv[m], acc[m]);
@@ -241,7 +252,9 @@ __device__ void psi4_point(const Grid& g, const double* __restrict__ y, long lon
   out[1] = im;
 }
 
-__global__ void __launch_bounds__(PB) psi4_kernel(Grid g, const double* __restrict__ y, double* __restrict__ out) {
+template <bool PRE>
+__global__ void __launch_bounds__(PB) psi4_kernel(Grid g, const double* __restrict__ y,
+                                                  const double* __restrict__ adm, double* __restrict__ out) {
   const long long npts = (long long)g.n0 * g.n1 * g.n2;
   const long long tid = (long long)blockIdx.x * PB + threadIdx.x;
   if (tid >= npts) return;
@@ -251,17 +264,23 @@ __global__ void __launch_bounds__(PB) psi4_kernel(Grid g, const double* __restri
   const long long id = lin(g, ii + GH, jj + GH, kk + GH);
   const double x[3] = {cell_coord(g.xmin0, ii, g.h), cell_coord(g.xmin1, jj, g.h), cell_coord(g.xmin2, kk, g.h)};
   double o[2];
-  psi4_point(g, y, id, x, o);
+  psi4_point<PRE>(g, y, adm, id, x, o);
   out[id] = o[0];
   out[g.fstride + id] = o[1];
 }
 
 }  // namespace
 
-cudaError_t launch_psi4(const Grid& g, const double* y, double* out, cudaStream_t s) {
+cudaError_t launch_psi4(const Grid& g, const double* y, double* out, cudaStream_t s, double* adm_scratch) {
   const long long npts = (long long)g.n0 * g.n1 * g.n2;
   const unsigned blocks = (unsigned)((npts + PB - 1) / PB);
-  psi4_kernel<<<blocks, PB, 0, s>>>(g, y, out);
+  if (adm_scratch) {
+    cudaError_t e = launch_adm_fields(g, y, adm_scratch, s);
+    if (e != cudaSuccess) return e;
+    psi4_kernel<true><<<blocks, PB, 0, s>>>(g, y, adm_scratch, out);
+  } else {
+    psi4_kernel<false><<<blocks, PB, 0, s>>>(g, y, nullptr, out);
+  }
   return cudaGetLastError();
 }
 
