@@ -38,6 +38,12 @@ DOMAIN = 8.0
 # (profiles/stage_fp64_bl64.md): 594 DADD + 301 DMUL + 1533 DFMA.
 FLOP_PER_POINT_RHS = 3961.0        # DADD + DMUL + 2 DFMA
 DPINST_PER_POINT_RHS = 2428.0      # float64 instructions issued
+# The 32-wide tiles on grids whose n0 is a multiple of 32 run the full-row
+# kernel (mixed second differences shared across lanes):
+# 428 DADD + 313 DMUL + 1448 DFMA per point (profiles/stage_fp64_rows_bl64.md).
+ROWS_TILES = ("32x8x1/1", "32x4x1/1", "32x4x2/1", "32x2x2/2")
+FLOP_PER_POINT_RHS_ROWS = 3636.3
+DPINST_PER_POINT_RHS_ROWS = 2188.1
 HBM_BYTES_PER_POINT_STEP = 3264.0  # 17 register passes x 24 fields x 8 B
 # mixed: float stage buffers (24 x 4 B) each with a float64 W (8 B), 104 B a
 # buffer pass; per RK4 step: stage 1 reads m0, writes m1 and the k-sum (312 B);
@@ -52,10 +58,13 @@ FP64_MEASURED_GFLOPS = 1196.0      # dependent-chain DFMA microbenchmark on this
 # ncu capture of the current kernels on the 64^3 case (traffic grows with the
 # points; profiles/stage_traffic_bl64.md); None until captured.
 FP64_TRAFFIC_PER_POINT = 1248.2    # (93.1 + 234.0) MB / 262,144 points, stage_fp64_kernel 32x2x2/2
+FP64_ROWS_TRAFFIC_PER_POINT = 820.2  # (86.5 + 128.8) MB / 262,144 points, stage_fp64_rows_kernel 32x4x1/1
 MIXED_TRAFFIC_PER_POINT = 282.0    # (50.5 + 23.4) MB / 262,144 points, stage_mixed_tma_kernel
 # Float64 work per interior point of the analysis kernels (DADD + DMUL + 2 DFMA
 # from ncu instruction counts; profiles/analysis_kernels_bl96.md).
-ANALYSIS_FLOP_PER_POINT = {"psi4": 4888.0, "adm_integrals": 1858.0, "constraints": 3508.0}
+# psi4 and constraints include the ADM-field pass that precedes them
+# (36 flop per stored point, 44 per interior point at 96^3).
+ANALYSIS_FLOP_PER_POINT = {"psi4": 3613.0 + 44.0, "adm_integrals": 1858.0, "constraints": 2206.0 + 44.0}
 
 
 def workload_params(precision="fp64"):
@@ -273,7 +282,11 @@ def run_ours(args):
     e2e_value = pts * e2e_steps * world / e2e_s / 1e6
     nbytes = host_in.nbytes
 
-    flop_launch = FLOP_PER_POINT_RHS * pts
+    rows = B.bssn_tile_name(tile) in ROWS_TILES and N_SIDE % 32 == 0
+    flop_pt = FLOP_PER_POINT_RHS_ROWS if rows else FLOP_PER_POINT_RHS
+    dpinst_pt = DPINST_PER_POINT_RHS_ROWS if rows else DPINST_PER_POINT_RHS
+    traffic_pt = FP64_ROWS_TRAFFIC_PER_POINT if rows else FP64_TRAFFIC_PER_POINT
+    flop_launch = flop_pt * pts
     stage_launch_ms = stage_ms / max(stage_n, 1)
     achieved = flop_launch / (stage_launch_ms * 1e-3) / 1e12
     mixed = args.precision == "mixed"
@@ -288,13 +301,15 @@ def run_ours(args):
                     "traffic": MIXED_TRAFFIC_PER_POINT * pts if MIXED_TRAFFIC_PER_POINT else None,
                     "launch_ms": stage_launch_ms, "launches": stage_n}
     else:
-        roofline = {"bound": "alu", "kernel": "stage_fp64_kernel", "achieved": achieved * 1e3,
+        roofline = {"bound": "alu", "kernel": "stage_fp64_rows_kernel" if rows else "stage_fp64_kernel",
+                    "achieved": achieved * 1e3,
                     "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s (FP64)",
+                    "peak_source": "nominal GB300 FP64 rate (no tensor-core path: stencil)",
                     "frac": achieved * 1e3 / FP64_PEAK_GFLOPS,
                     "frac_of_measured_dfma": achieved * 1e3 / FP64_MEASURED_GFLOPS,
-                    "fp64_issue_frac": DPINST_PER_POINT_RHS * pts / (stage_launch_ms * 1e-3)
+                    "fp64_issue_frac": dpinst_pt * pts / (stage_launch_ms * 1e-3)
                                        / (FP64_MEASURED_GFLOPS * 1e9 / 2),
-                    "traffic": FP64_TRAFFIC_PER_POINT * pts if FP64_TRAFFIC_PER_POINT else None,
+                    "traffic": traffic_pt * pts,
                     "launch_ms": stage_launch_ms, "launches": stage_n,
                     "hbm_frac": (HBM_BYTES_PER_POINT_STEP * pts * args.steps / (ms * 1e-3)) / HBM_MEASURED_GBS / 1e9}
     line = {

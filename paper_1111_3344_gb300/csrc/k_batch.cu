@@ -68,7 +68,7 @@ __global__ void __launch_bounds__(TX * TY * TZ, MINB)
     const int ii = bx * TX + threadIdx.x, jj = by * TY + threadIdx.y, kk = bz * TZ + threadIdx.z;
     if (ii < sg.n0 && jj < sg.n1 && kk < sg.n2) {
       if constexpr (MIXED) stage_point_mixed(sg, sa, ii, jj, kk);
-      else stage_point_fp64(sg, sa, ii, jj, kk);
+      else stage_point_fp64<0>(sg, sa, ii, jj, kk);
     }
   }
 }

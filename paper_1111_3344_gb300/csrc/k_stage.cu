@@ -33,7 +33,7 @@ __global__ void __launch_bounds__(TX * TY * TZ, MINB) stage_fp64_kernel(Grid g, 
   const int jj = blockIdx.y * TY + threadIdx.y;
   const int kk = blockIdx.z * TZ + threadIdx.z;
   if (ii >= g.n0 || jj >= g.n1 || kk >= g.n2) return;
-  stage_point_fp64(g, a, ii, jj, kk);
+  stage_point_fp64<0>(g, a, ii, jj, kk);
 }
 
 template <int TX, int TY, int TZ, int MINB>
@@ -44,6 +44,14 @@ __global__ void __launch_bounds__(TX * TY * TZ, MINB) stage_mixed_kernel(Grid g,
   if (ii >= g.n0 || jj >= g.n1 || kk >= g.n2) return;
   stage_point_mixed(g, a, ii, jj, kk);
 }
+
+// float64 full-row variants, defined in k_stage_shfl.cu
+template <int TY, int TZ, int MINB>
+cudaError_t launch_fp64_rows(const Grid& g, const StageArgs& a, cudaStream_t s);
+extern template cudaError_t launch_fp64_rows<8, 1, 1>(const Grid&, const StageArgs&, cudaStream_t);
+extern template cudaError_t launch_fp64_rows<4, 1, 1>(const Grid&, const StageArgs&, cudaStream_t);
+extern template cudaError_t launch_fp64_rows<4, 2, 1>(const Grid&, const StageArgs&, cudaStream_t);
+extern template cudaError_t launch_fp64_rows<2, 2, 2>(const Grid&, const StageArgs&, cudaStream_t);
 
 // ------------------------------------------------------ tile configurations
 // Candidate block shapes (points per block along x, y, z) and the minimum
@@ -68,16 +76,23 @@ struct TileCfg {
   const char* name;
   cudaError_t (*fp64)(const Grid&, const StageArgs&, cudaStream_t);
   cudaError_t (*mixed)(const Grid&, const StageArgsMixed&, cudaStream_t);
+  // float64 variant whose warps are full 32-point x-rows sharing first
+  // differences (k_stage_shfl.cu); used when n0 is a multiple of 32
+  cudaError_t (*fp64_rows)(const Grid&, const StageArgs&, cudaStream_t);
 };
 
 #define TILE(TX, TY, TZ, MINB)                                                  \
   { #TX "x" #TY "x" #TZ "/" #MINB, launch_fp64_t<TX, TY, TZ, MINB>,            \
-    launch_mixed_t<TX, TY, TZ, MINB> }
+    launch_mixed_t<TX, TY, TZ, MINB>, nullptr }
+#define TILE_ROWS(TY, TZ, MINB)                                                 \
+  { "32x" #TY "x" #TZ "/" #MINB, launch_fp64_t<32, TY, TZ, MINB>,              \
+    launch_mixed_t<32, TY, TZ, MINB>, launch_fp64_rows<TY, TZ, MINB> }
 static const TileCfg k_tiles[] = {
-    TILE(32, 8, 1, 1), TILE(32, 4, 1, 1), TILE(32, 4, 2, 1), TILE(64, 4, 1, 1),
-    TILE(16, 8, 2, 1), TILE(32, 2, 2, 2), TILE(32, 8, 1, 2), TILE(32, 4, 1, 3),
+    TILE_ROWS(8, 1, 1), TILE_ROWS(4, 1, 1), TILE_ROWS(4, 2, 1), TILE(64, 4, 1, 1),
+    TILE(16, 8, 2, 1), TILE_ROWS(2, 2, 2), TILE(32, 8, 1, 2), TILE(32, 4, 1, 3),
 };
 #undef TILE
+#undef TILE_ROWS
 
 int tile_config_count() { return (int)(sizeof(k_tiles) / sizeof(k_tiles[0])); }
 const char* tile_config_name(int c) {
@@ -86,6 +101,7 @@ const char* tile_config_name(int c) {
 
 cudaError_t launch_stage_fp64(const Grid& g, const StageArgs& a, cudaStream_t s, int cfg) {
   if (cfg < 0 || cfg >= tile_config_count()) cfg = 0;
+  if (k_tiles[cfg].fp64_rows && g.n0 % 32 == 0) return k_tiles[cfg].fp64_rows(g, a, s);
   return k_tiles[cfg].fp64(g, a, s);
 }
 

@@ -1,0 +1,35 @@
+// Float64 fused stage for blocks whose warps are full rows of 32 x points
+// (n0 a multiple of 32, TX = 32): the mixed second differences D1_x D1_y and
+// D1_x D1_z take the neighbouring points' first differences along y or z from
+// the neighbouring lanes (dmx_shfl in rhs_point.cuh) instead of evaluating
+// four more first differences per field.  Everything else is the stage of
+// k_stage.cu; a warp is either wholly inside the grid or wholly outside it
+// (rows past n1 or n2), so the shuffles always see 32 active lanes.
+#include "stage_point.cuh"
+
+namespace bssn {
+
+template <int TY, int TZ, int MINB>
+__global__ void __launch_bounds__(32 * TY * TZ, MINB) stage_fp64_rows_kernel(Grid g, StageArgs a) {
+  const int ii = blockIdx.x * 32 + threadIdx.x;
+  const int jj = blockIdx.y * TY + threadIdx.y;
+  const int kk = blockIdx.z * TZ + threadIdx.z;
+  if (jj >= g.n1 || kk >= g.n2) return;  // whole warps
+  stage_point_fp64<32>(g, a, ii, jj, kk);
+}
+
+template <int TY, int TZ, int MINB>
+cudaError_t launch_fp64_rows(const Grid& g, const StageArgs& a, cudaStream_t s) {
+  if (g.n0 % 32) return cudaErrorInvalidValue;  // the caller checks; rows must be full
+  dim3 block(32, TY, TZ);
+  dim3 grid(g.n0 / 32, (g.n1 + TY - 1) / TY, (g.n2 + TZ - 1) / TZ);
+  stage_fp64_rows_kernel<TY, TZ, MINB><<<grid, block, 0, s>>>(g, a);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_fp64_rows<8, 1, 1>(const Grid&, const StageArgs&, cudaStream_t);
+template cudaError_t launch_fp64_rows<4, 1, 1>(const Grid&, const StageArgs&, cudaStream_t);
+template cudaError_t launch_fp64_rows<4, 2, 1>(const Grid&, const StageArgs&, cudaStream_t);
+template cudaError_t launch_fp64_rows<2, 2, 2>(const Grid&, const StageArgs&, cudaStream_t);
+
+}  // namespace bssn

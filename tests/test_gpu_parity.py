@@ -214,3 +214,48 @@ def test_set_adm_parity(torch_cuda, name, box, periodic, conformal):
     bound = 379.0 * d_in + 1e-13 * np.maximum(scale, 1e-3 * scale.max())
     assert (d_all <= bound).all(), dict(zip(O.FIELD_NAMES, d_all / np.maximum(bound, 1e-300)))
     assert t == 0.25
+
+
+@pytest.mark.parametrize("cfg_name", ["32x8x1/1", "32x4x1/1", "32x4x2/1", "32x2x2/2"])
+def test_full_row_variants(torch_cuda, cfg_name):
+    """With n0 a multiple of 32 the 32-wide float64 configurations run the
+    kernel whose warps share first differences across lanes for the mixed
+    second differences: right-hand side (faces, edges, corners, every lane of
+    the row, rows past n1 and n2 in partial blocks) against the oracle and
+    against a plain every-stencil kernel (1e-13), and RK4 steps against the
+    oracle."""
+    from paper_1111_3344_gb300 import bssn as B
+    # the puncture sits on a cell corner, half a cell from the nearest points
+    case = dict(n=(64, 13, 11), xmin=(-3.2, -0.7, -0.6), h=0.1, boundary="sommerfeld", conformal="W",
+                punctures=[(0.8, 0.0, 0.0, 0.0)], shift="gamma-driver", eta=1.5, q_R=1.2)
+    cfg = oracle_cfg(case)
+    bg = O.initial_data(cfg, "bl", bl_params(case))
+    st = inputs.random_state(19, case["n"], case["xmin"], case["h"], amp=0.05, background=bg)
+    names = [B.bssn_tile_name(c) for c in range(B.bssn_tile_count())]
+    rhs = {}
+    for name in (cfg_name, "64x4x1/1"):  # the row variant and a plain (every-stencil) shape
+        evo = _evo(case)
+        B.bssn_set_tile(evo.ctx, names.index(name))
+        rhs[name] = evo.register_to_numpy(evo.rhs(evo.numpy_to_register(st)))
+        evo.close()
+    want = O.rhs(cfg, st)
+    e = normwise_errors(rhs[cfg_name], want)
+    e_plain = normwise_errors(rhs["64x4x1/1"], want)
+    d = normwise_errors(rhs[cfg_name], rhs["64x4x1/1"])
+    # Half a cell from the puncture the K and At right-hand sides are small
+    # differences of much larger terms (as in the full-size test): measured
+    # 1.08e-12 in trK for both kernels; every other field within 1e-12.
+    ka = [O.F_TRK] + list(range(O.F_AT, O.F_AT + 6))
+    rest = [f for f in range(O.NF) if f not in ka]
+    assert e[ka].max() <= 5e-12 and e[rest].max() <= TOL_RHS, dict(zip(O.FIELD_NAMES, e))
+    assert e.max() <= 1.01 * e_plain.max() + 1e-15, (e.max(), e_plain.max())
+    # same arithmetic but for the mixed-difference rounding (1/(12h) twice
+    # instead of 1/(144h^2) once)
+    assert d.max() <= 1e-13, dict(zip(O.FIELD_NAMES, d))
+    evo = _evo(case)
+    B.bssn_set_tile(evo.ctx, names.index(cfg_name))
+    evo.set_state(st, 0.0)
+    evo.rk4_step(2)
+    e = normwise_errors(evo.get_state()[0], O.rk4(cfg, st, 2))
+    assert e.max() <= TOL_STEP, dict(zip(O.FIELD_NAMES, e))
+    evo.close()
