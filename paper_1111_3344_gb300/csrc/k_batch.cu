@@ -67,8 +67,17 @@ __global__ void __launch_bounds__(TX * TY * TZ, MINB)
     const int bz = (int)(lt / (unsigned)stile[1]);
     const int ii = bx * TX + threadIdx.x, jj = by * TY + threadIdx.y, kk = bz * TZ + threadIdx.z;
     if (ii < sg.n0 && jj < sg.n1 && kk < sg.n2) {
-      if constexpr (MIXED) stage_point_mixed(sg, sa, ii, jj, kk);
-      else stage_point_fp64<0>(sg, sa, ii, jj, kk);
+      if constexpr (MIXED) {
+        stage_point_mixed(sg, sa, ii, jj, kk);
+      } else if constexpr (TX == 32) {
+        // members whose n0 is a multiple of 32: every warp is a full x-row, so
+        // the x-mixed second differences share first differences across
+        // lanes (the choice is uniform over the block's tile)
+        if (sg.n0 % 32 == 0) stage_point_fp64<32>(sg, sa, ii, jj, kk);
+        else stage_point_fp64<0>(sg, sa, ii, jj, kk);
+      } else {
+        stage_point_fp64<0>(sg, sa, ii, jj, kk);
+      }
     }
   }
 }
