@@ -613,13 +613,43 @@ static bssn_status check_err(bssn_ctx* ctx) {
   return BSSN_OK;
 }
 
+// Staging area for the host copies of the state: a stage buffer that holds
+// nothing between RK4 steps (float64: s1, 24 fields; mixed: the float stage
+// buffer m[1], 12 fields of doubles).  Host copies are contiguous blocks of
+// whole fields, repacked into the pitched layout on the device.
+static double* stage_area(bssn_ctx* ctx, int* fields) {
+  if (ctx->p.precision == BSSN_FP64) {
+    *fields = NF;
+    return ctx->s1;
+  }
+  *fields = NF / 2;
+  return (double*)ctx->m32[1];
+}
+
+static cudaError_t copy_state(bssn_ctx* ctx, double* host, bool to_device) {
+  const Grid& g = ctx->g;
+  const size_t per = (size_t)g.sx * g.sy * g.sz;
+  int chunk = 0;
+  double* area = stage_area(ctx, &chunk);
+  cudaError_t e = cudaSuccess;
+  for (int f0 = 0; f0 < NF && e == cudaSuccess; f0 += chunk) {
+    const int nf = f0 + chunk <= NF ? chunk : NF - f0;
+    const size_t bytes = per * nf * sizeof(double);
+    if (to_device) {
+      e = cudaMemcpyAsync(area, host + per * f0, bytes, cudaMemcpyHostToDevice, ctx->stream);
+      if (e == cudaSuccess) e = launch_repack(g, area, ctx->yn, f0, nf, true, ctx->stream);
+    } else {
+      e = launch_repack(g, area, ctx->yn, f0, nf, false, ctx->stream);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(host + per * f0, area, bytes, cudaMemcpyDeviceToHost, ctx->stream);
+    }
+  }
+  return e;
+}
+
 bssn_status bssn_get_state(bssn_ctx* ctx, double* host, double* t) {
   if (!ctx || !host) return fail(BSSN_EINVAL, "NULL argument");
   if (bssn_status es = check_err(ctx)) return es;
-  const Grid& g = ctx->g;
-  cudaError_t e = cudaMemcpy2DAsync(host, (size_t)g.sx * sizeof(double), ctx->yn,
-                                    (size_t)g.pitch * sizeof(double), (size_t)g.sx * sizeof(double),
-                                    (size_t)NF * g.sz * g.sy, cudaMemcpyDeviceToHost, ctx->stream);
+  cudaError_t e = copy_state(ctx, host, false);
   if (e != cudaSuccess) return cuda_fail(e, "get_state copy");
   e = cudaStreamSynchronize(ctx->stream);
   if (e != cudaSuccess) return cuda_fail(e, "get_state sync");
@@ -629,10 +659,7 @@ bssn_status bssn_get_state(bssn_ctx* ctx, double* host, double* t) {
 
 bssn_status bssn_set_state(bssn_ctx* ctx, const double* host, double t) {
   if (!ctx || !host) return fail(BSSN_EINVAL, "NULL argument");
-  const Grid& g = ctx->g;
-  cudaError_t e = cudaMemcpy2DAsync(ctx->yn, (size_t)g.pitch * sizeof(double), host,
-                                    (size_t)g.sx * sizeof(double), (size_t)g.sx * sizeof(double),
-                                    (size_t)NF * g.sz * g.sy, cudaMemcpyHostToDevice, ctx->stream);
+  cudaError_t e = copy_state(ctx, const_cast<double*>(host), true);
   if (e != cudaSuccess) return cuda_fail(e, "set_state copy");
   e = cudaStreamSynchronize(ctx->stream);
   if (e != cudaSuccess) return cuda_fail(e, "set_state sync");
@@ -641,9 +668,9 @@ bssn_status bssn_set_state(bssn_ctx* ctx, const double* host, double t) {
   return BSSN_OK;
 }
 
-// Configurations: the plain tile shapes, then the TMA-staged mixed kernel.
-// configurations: [0, tile_config_count()) fused kernels; tile_config_count()
-// the TMA kernel; then the split-stage variants
+// Configurations: [0, tile_config_count()) the fused kernels;
+// tile_config_count() the TMA-staged mixed kernel; then the split-stage
+// variants.
 int32_t bssn_tile_count(void) { return tile_config_count() + 1 + split_config_count(); }
 
 const char* bssn_tile_name(int32_t cfg) {

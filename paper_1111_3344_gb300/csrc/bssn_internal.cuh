@@ -234,6 +234,9 @@ cudaError_t launch_sommerfeld_mixed(const Grid& g, const StageArgsMixed& a, cons
 cudaError_t launch_periodic_fill(const Grid& g, double* y, cudaStream_t s);
 cudaError_t launch_periodic_fill_mixed(const Grid& g, float* y, double* w, cudaStream_t s);
 cudaError_t launch_shadow(const Grid& g, const double* y, float* s32, double* w, cudaStream_t s);
+// Copy fields f0 .. f0+nf-1 between a contiguous unpadded block flat and the
+// pitched register reg (to_reg: flat -> reg) (k_boundary.cu).
+cudaError_t launch_repack(const Grid& g, double* flat, double* reg, int f0, int nf, bool to_reg, cudaStream_t s);
 cudaError_t launch_initial_data(const Grid& g, int kind, const double* dparams, int np,
                                 double* y, cudaStream_t s);
 // adm_scratch (may be null): 12 * fstride doubles; when given, the ADM fields

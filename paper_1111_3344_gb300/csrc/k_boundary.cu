@@ -66,4 +66,36 @@ cudaError_t launch_periodic_fill_mixed(const Grid& g, float* y, double* w, cudaS
   return cudaGetLastError();
 }
 
+// Repacking between the unpadded host layout (nf fields of sz x sy x sx
+// doubles, contiguous) and the pitched register layout, fields f0 .. f0+nf-1:
+// the host copies then move one contiguous block at full link speed.
+__global__ void unpack_fields_kernel(Grid g, const double* __restrict__ flat, double* __restrict__ reg, int f0,
+                                     int nf) {
+  const long long per = (long long)g.sx * g.sy * g.sz;
+  const long long n = per * nf;
+  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n;
+       q += (long long)gridDim.x * blockDim.x) {
+    const long long f = q / per, r = q - f * per;
+    const long long row = r / g.sx, i = r - row * g.sx;  // row = k sy + j
+    reg[(f0 + f) * g.fstride + row * g.pitch + i] = flat[q];
+  }
+}
+__global__ void pack_fields_kernel(Grid g, const double* __restrict__ reg, double* __restrict__ flat, int f0,
+                                   int nf) {
+  const long long per = (long long)g.sx * g.sy * g.sz;
+  const long long n = per * nf;
+  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n;
+       q += (long long)gridDim.x * blockDim.x) {
+    const long long f = q / per, r = q - f * per;
+    const long long row = r / g.sx, i = r - row * g.sx;
+    flat[q] = reg[(f0 + f) * g.fstride + row * g.pitch + i];
+  }
+}
+
+cudaError_t launch_repack(const Grid& g, double* flat, double* reg, int f0, int nf, bool to_reg, cudaStream_t s) {
+  if (to_reg) unpack_fields_kernel<<<152 * 8, 256, 0, s>>>(g, flat, reg, f0, nf);
+  else pack_fields_kernel<<<152 * 8, 256, 0, s>>>(g, reg, flat, f0, nf);
+  return cudaGetLastError();
+}
+
 }  // namespace bssn
