@@ -38,12 +38,14 @@ DOMAIN = 8.0
 # (profiles/stage_fp64_bl64.md): 594 DADD + 301 DMUL + 1533 DFMA.
 FLOP_PER_POINT_RHS = 3961.0        # DADD + DMUL + 2 DFMA
 DPINST_PER_POINT_RHS = 2428.0      # float64 instructions issued
-# The 32-wide tiles on grids whose n0 is a multiple of 32 run the full-row
-# kernel (mixed second differences shared across lanes):
-# 428 DADD + 313 DMUL + 1448 DFMA per point (profiles/stage_fp64_rows_bl64.md).
+# The 32-wide tiles on grids whose n0 is a multiple of 32 and whose n1, n2
+# fill the blocks (the benchmark grid) run the full-block kernel: x-mixed
+# second differences shared across lanes, D_y D_z across rows through shared
+# memory; 362 DADD + 317 DMUL + 1415 DFMA per point
+# (profiles/stage_fp64_rows_bl64.md).
 ROWS_TILES = ("32x8x1/1", "32x4x1/1", "32x4x2/1", "32x2x2/2")
-FLOP_PER_POINT_RHS_ROWS = 3636.3
-DPINST_PER_POINT_RHS_ROWS = 2188.1
+FLOP_PER_POINT_RHS_ROWS = 3507.7
+DPINST_PER_POINT_RHS_ROWS = 2093.0
 HBM_BYTES_PER_POINT_STEP = 3264.0  # 17 register passes x 24 fields x 8 B
 # mixed: float stage buffers (24 x 4 B) each with a float64 W (8 B), 104 B a
 # buffer pass; per RK4 step: stage 1 reads m0, writes m1 and the k-sum (312 B);
@@ -58,7 +60,7 @@ FP64_MEASURED_GFLOPS = 1196.0      # dependent-chain DFMA microbenchmark on this
 # ncu capture of the current kernels on the 64^3 case (traffic grows with the
 # points; profiles/stage_traffic_bl64.md); None until captured.
 FP64_TRAFFIC_PER_POINT = 1248.2    # (93.1 + 234.0) MB / 262,144 points, stage_fp64_kernel 32x2x2/2
-FP64_ROWS_TRAFFIC_PER_POINT = 820.2  # (86.5 + 128.8) MB / 262,144 points, stage_fp64_rows_kernel 32x4x1/1
+FP64_ROWS_TRAFFIC_PER_POINT = 635.9  # (83.2 + 83.5) MB / 262,144 points, stage_fp64_blocks_kernel 32x4x1/1
 MIXED_TRAFFIC_PER_POINT = 282.0    # (50.5 + 23.4) MB / 262,144 points, stage_mixed_tma_kernel
 # Float64 work per interior point of the analysis kernels (DADD + DMUL + 2 DFMA
 # from ncu instruction counts; profiles/analysis_kernels_bl96.md).
@@ -323,7 +325,7 @@ def run_ours(args):
                     "traffic": MIXED_TRAFFIC_PER_POINT * pts if MIXED_TRAFFIC_PER_POINT else None,
                     "launch_ms": stage_launch_ms, "launches": stage_n}
     else:
-        roofline = {"bound": "alu", "kernel": "stage_fp64_rows_kernel" if rows else "stage_fp64_kernel",
+        roofline = {"bound": "alu", "kernel": "stage_fp64_blocks_kernel" if rows else "stage_fp64_kernel",
                     "achieved": achieved * 1e3,
                     "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s (FP64)",
                     "peak_source": "nominal GB300 FP64 rate (no tensor-core path: stencil)",

@@ -18,12 +18,28 @@ __global__ void __launch_bounds__(32 * TY * TZ, MINB) stage_fp64_rows_kernel(Gri
   stage_point_fp64<32>(g, a, ii, jj, kk);
 }
 
+// Full blocks (n1 % TY == 0 and n2 % TZ == 0 as well): every thread is inside
+// the grid, so the block can also exchange first differences along z through
+// shared memory for D_y D_z.
+template <int TY, int TZ, int MINB>
+__global__ void __launch_bounds__(32 * TY * TZ, MINB) stage_fp64_blocks_kernel(Grid g, StageArgs a) {
+  const int ii = blockIdx.x * 32 + threadIdx.x;
+  const int jj = blockIdx.y * TY + threadIdx.y;
+  const int kk = blockIdx.z * TZ + threadIdx.z;
+  stage_point_fp64<32, TY, TZ>(g, a, ii, jj, kk);
+}
+
 template <int TY, int TZ, int MINB>
 cudaError_t launch_fp64_rows(const Grid& g, const StageArgs& a, cudaStream_t s) {
   if (g.n0 % 32) return cudaErrorInvalidValue;  // the caller checks; rows must be full
   dim3 block(32, TY, TZ);
   dim3 grid(g.n0 / 32, (g.n1 + TY - 1) / TY, (g.n2 + TZ - 1) / TZ);
-  stage_fp64_rows_kernel<TY, TZ, MINB><<<grid, block, 0, s>>>(g, a);
+  if (g.n1 % TY == 0 && g.n2 % TZ == 0 && TY >= 2) {
+    const int smem = 11 * (TY + 4) * TZ * 32 * (int)sizeof(double);
+    stage_fp64_blocks_kernel<TY, TZ, MINB><<<grid, block, smem, s>>>(g, a);
+  } else {
+    stage_fp64_rows_kernel<TY, TZ, MINB><<<grid, block, 0, s>>>(g, a);
+  }
   return cudaGetLastError();
 }
 

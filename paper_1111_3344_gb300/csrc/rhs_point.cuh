@@ -161,7 +161,11 @@ __host__ __device__ __forceinline__ double background(const Grid& g, int f) {
 // XSEG = 32: the calling warp is one full x-row of 32 points (float64 only);
 // the mixed second differences involving x then share first differences
 // across lanes (dmx_shfl).  XSEG = 0: every stencil evaluated by the thread.
-template <typename T, typename S, bool DEV, typename A, int XSEG = 0>
+// YROWS > 0 (with XSEG = 32): the block is 32 x YROWS x ZS points, every
+// thread inside the grid, and D_y D_z takes the neighbouring rows' first
+// differences along z from shared memory (11 fields x (YROWS + 4) rows x ZS x
+// 32 doubles of dynamic shared memory; one barrier).
+template <typename T, typename S, bool DEV, typename A, int XSEG = 0, int YROWS = 0, int ZS = 1>
 __device__ __forceinline__ void rhs_point_acc(const Grid& g, const A& acc, int i, int j, int k,
                                               T out[NF]) {
   const T i12h = gc<T>(g.i12h, g.i12hf);
@@ -224,6 +228,34 @@ __device__ __forceinline__ void rhs_point_acc(const Grid& g, const A& acc, int i
     }
   }
 
+  // ---- D_y D_z through shared memory (full blocks of full rows)
+  [[maybe_unused]] T dyz[11];  // gt_ij (6), phi|W, alpha, beta^i (3)
+  if constexpr (YROWS > 0 && XSEG == 32 && sizeof(T) == 8) {
+    extern __shared__ double yz_smem[];
+    constexpr int ROWS = YROWS + 4;
+    const int ty = threadIdx.y, tz = threadIdx.z, lane = threadIdx.x;
+    auto at = [&](int q, int row) -> double& { return yz_smem[((q * ROWS + row) * ZS + tz) * 32 + lane]; };
+    auto dz_of = [&](int q) -> T {
+      return q < 6 ? dgt[2][q] : (q == 6 ? dchi[2] : (q == 7 ? dalp[2] : db[2][q - 8]));
+    };
+    auto field_of = [](int q) { return q < 6 ? F_GT + q : (q == 6 ? F_CHI : (q == 7 ? F_ALP : F_BETA + (q - 8))); };
+    const long long sy = SD(F_CHI, 1), sz = SD(F_CHI, 2);
+#pragma unroll
+    for (int q = 0; q < 11; q++) at(q, ty + 2) = dz_of(q);
+    if (ty < 2) {  // rows y0-2, y0-1 below the block
+#pragma unroll
+      for (int q = 0; q < 11; q++) at(q, ty) = d1u<T>(acc, field_of(q), PF(field_of(q)) - 2 * sy, sz) * i12h;
+    }
+    if (ty >= YROWS - 2) {  // rows y0+YROWS, y0+YROWS+1 above it
+#pragma unroll
+      for (int q = 0; q < 11; q++) at(q, ty + 4) = d1u<T>(acc, field_of(q), PF(field_of(q)) + 2 * sy, sz) * i12h;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 11; q++)
+      dyz[q] = fmaT<T>(T(8), at(q, ty + 3) - at(q, ty + 1), -(at(q, ty + 4) - at(q, ty))) * i12h;
+  }
+
   // ---- second derivatives, consumed pair by pair
   T Rdd[6];      // -1/2 gt^{kl} d_k d_l gt_ij
   T lapb[3];     // gt^{kl} d_k d_l beta^i
@@ -253,6 +285,11 @@ __device__ __forceinline__ void rhs_point_acc(const Grid& g, const A& acc, int i
               dd[m] = dmx_shfl<XSEG>(acc, F_GT + m, PF(F_GT + m), SD(F_GT + m, pb), dgt[pb][m], i12h);
             ddchi[pq] = dmx_shfl<XSEG>(acc, F_CHI, PF(F_CHI), SD(F_CHI, pb), dchi[pb], i12h);
             ddalp[pq] = dmx_shfl<XSEG>(acc, F_ALP, PF(F_ALP), SD(F_ALP, pb), dalp[pb], i12h);
+          } else if constexpr (YROWS > 0) {  // (1, 2)
+#pragma unroll
+            for (int m = 0; m < 6; m++) dd[m] = dyz[m];
+            ddchi[pq] = dyz[6];
+            ddalp[pq] = dyz[7];
           } else {
 #pragma unroll
             for (int m = 0; m < 6; m++) dd[m] = dmu<T>(acc, F_GT + m, PF(F_GT + m), SD(F_GT + m, pa), SD(F_GT + m, pb)) * i144h2;
@@ -276,8 +313,12 @@ __device__ __forceinline__ void rhs_point_acc(const Grid& g, const A& acc, int i
           if (pa == pb) {
             v = d2u<T>(acc, F_BETA + a, PF(F_BETA + a), SD(F_BETA + a, pa), beta[a]) * i12h2;
           } else if constexpr (XSEG > 0 && sizeof(T) == 8) {
-            v = pa == 0 ? dmx_shfl<XSEG>(acc, F_BETA + a, PF(F_BETA + a), SD(F_BETA + a, pb), db[pb][a], i12h)
-                        : dmu<T>(acc, F_BETA + a, PF(F_BETA + a), SD(F_BETA + a, pa), SD(F_BETA + a, pb)) * i144h2;
+            if (pa == 0)
+              v = dmx_shfl<XSEG>(acc, F_BETA + a, PF(F_BETA + a), SD(F_BETA + a, pb), db[pb][a], i12h);
+            else if constexpr (YROWS > 0)
+              v = dyz[8 + a];
+            else
+              v = dmu<T>(acc, F_BETA + a, PF(F_BETA + a), SD(F_BETA + a, pa), SD(F_BETA + a, pb)) * i144h2;
           } else {
             v = dmu<T>(acc, F_BETA + a, PF(F_BETA + a), SD(F_BETA + a, pa), SD(F_BETA + a, pb)) * i144h2;
           }
@@ -610,11 +651,11 @@ __device__ __forceinline__ void rhs_point_acc(const Grid& g, const A& acc, int i
 }
 
 // Right-hand side reading every field from the global register st.
-template <typename T, typename S, bool DEV = false, int XSEG = 0>
+template <typename T, typename S, bool DEV = false, int XSEG = 0, int YROWS = 0, int ZS = 1>
 __device__ __forceinline__ void rhs_point(const Grid& g, const S* __restrict__ st, long long id,
                                           int i, int j, int k, T out[NF]) {
   const GlobalAcc<S> acc(g, st, id);
-  rhs_point_acc<T, S, DEV, GlobalAcc<S>, XSEG>(g, acc, i, j, k, out);
+  rhs_point_acc<T, S, DEV, GlobalAcc<S>, XSEG, YROWS, ZS>(g, acc, i, j, k, out);
 }
 
 }  // namespace bssn

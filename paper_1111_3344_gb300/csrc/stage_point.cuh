@@ -12,14 +12,16 @@ __device__ __forceinline__ bool on_shell(const Grid& g, int ii, int jj, int kk) 
 }
 
 // Fused stage at interior point (ii, jj, kk) (interior indices), float64.
-// XSEG = 32: the calling warp is one full row of 32 x points (see dmx_shfl).
-template <int XSEG = 0>
+// XSEG = 32: the calling warp is one full row of 32 x points (see dmx_shfl);
+// YROWS > 0: also every thread of the block is inside the grid (D_y D_z
+// through shared memory, see rhs_point_acc).
+template <int XSEG = 0, int YROWS = 0, int ZS = 1>
 __device__ __forceinline__ void stage_point_fp64(const Grid& g, const StageArgs& a, int ii, int jj,
                                                  int kk) {
   const int i = ii + GH, j = jj + GH, k = kk + GH;
   const long long id = lin(g, i, j, k);
   double r[NF];
-  rhs_point<double, double, false, XSEG>(g, a.src, id, i, j, k, r);
+  rhs_point<double, double, false, XSEG, YROWS, ZS>(g, a.src, id, i, j, k, r);
   const long long fs = g.fstride;
   if (a.mode == MODE_RHS) {
 #pragma unroll

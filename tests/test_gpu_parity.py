@@ -216,18 +216,23 @@ def test_set_adm_parity(torch_cuda, name, box, periodic, conformal):
     assert t == 0.25
 
 
+@pytest.mark.parametrize("shape", [(64, 13, 11), (64, 16, 12)])
 @pytest.mark.parametrize("cfg_name", ["32x8x1/1", "32x4x1/1", "32x4x2/1", "32x2x2/2"])
-def test_full_row_variants(torch_cuda, cfg_name):
+def test_full_row_variants(torch_cuda, cfg_name, shape):
     """With n0 a multiple of 32 the 32-wide float64 configurations run the
     kernel whose warps share first differences across lanes for the mixed
-    second differences: right-hand side (faces, edges, corners, every lane of
-    the row, rows past n1 and n2 in partial blocks) against the oracle and
-    against a plain every-stencil kernel (1e-13), and RK4 steps against the
-    oracle."""
+    second differences (and, when n1 and n2 fill the blocks, rows share them
+    through shared memory for D_y D_z): right-hand side (faces, edges,
+    corners, every lane of the row, rows past n1 and n2 in partial blocks)
+    against the oracle and against a plain every-stencil kernel (1e-13), and
+    RK4 steps against the oracle."""
     from paper_1111_3344_gb300 import bssn as B
-    # the puncture sits on a cell corner, half a cell from the nearest points
-    case = dict(n=(64, 13, 11), xmin=(-3.2, -0.7, -0.6), h=0.1, boundary="sommerfeld", conformal="W",
-                punctures=[(0.8, 0.0, 0.0, 0.0)], shift="gamma-driver", eta=1.5, q_R=1.2)
+    # the puncture sits on a cell corner, half a cell from the nearest points;
+    # (64, 16, 12) fills every block of every 32-wide shape, so the kernel
+    # also shares first differences along z between rows (D_y D_z)
+    h = 0.1
+    case = dict(n=shape, xmin=(-3.2, -h * (shape[1] // 2), -h * (shape[2] // 2)), h=h, boundary="sommerfeld",
+                conformal="W", punctures=[(0.8, 0.0, 0.0, 0.0)], shift="gamma-driver", eta=1.5, q_R=1.2)
     cfg = oracle_cfg(case)
     bg = O.initial_data(cfg, "bl", bl_params(case))
     st = inputs.random_state(19, case["n"], case["xmin"], case["h"], amp=0.05, background=bg)
