@@ -92,9 +92,29 @@ __device__ __forceinline__ void stage_point_mixed_acc(const Grid& g, const Stage
                                                       const A& acc, int ii, int jj, int kk) {
   const int i = ii + GH, j = jj + GH, k = kk + GH;
   const long long id = lin(g, i, j, k);
+  const long long fs = g.fstride;
+  // The combine's inputs (stages 2-3: base and k-sum; stage 4: k-sum and
+  // y_n) are loaded before the right-hand side: issued after it, at 255
+  // registers and 8 warps per SM, their latency was exposed (a third of the
+  // step).  What the compiler cannot keep in registers it spills to local
+  // memory, which comes back from L1.
+  float pk[NF], ps[NF];
+  double py[NF];
+  if (a.mode == MODE_MID) {
+#pragma unroll
+    for (int f = 1; f < NF; f++) {
+      ps[f] = a.src0[f * fs + id];
+      pk[f] = a.ksum[f * fs + id];
+    }
+  } else if (a.mode == MODE_LAST) {
+#pragma unroll
+    for (int f = 1; f < NF; f++) {
+      pk[f] = a.ksum[f * fs + id];
+      py[f] = a.yn[f * fs + id];
+    }
+  }
   float r[NF];
   rhs_point_acc<float, float, true>(g, acc, i, j, k, r);
-  const long long fs = g.fstride;
   // near a puncture the W update runs in float64
   const double w0 = a.srcw[id];
   const double wval = g.use_w ? w0 : exp(-2.0 * w0);
@@ -120,7 +140,7 @@ __device__ __forceinline__ void stage_point_mixed_acc(const Grid& g, const Stage
 #pragma unroll
     for (int f = 1; f < NF; f++) {
       const long long o = f * fs + id;
-      const double v = fma(a.b_dt, (double)(a.ksum[o] + r[f]), a.yn[o]);
+      const double v = fma(a.b_dt, (double)(pk[f] + r[f]), py[f]);
       a.yn[o] = v;
       a.out0[o] = (float)(v - background(g, f));
     }
@@ -136,8 +156,8 @@ __device__ __forceinline__ void stage_point_mixed_acc(const Grid& g, const Stage
 #pragma unroll
   for (int f = 1; f < NF; f++) {
     const long long o = f * fs + id;
-    a.out0[o] = fmaf(af, r[f], a.src0[o]);
-    a.ksum[o] = a.mode == MODE_FIRST ? r[f] : fmaf(2.0f, r[f], a.ksum[o]);
+    a.out0[o] = fmaf(af, r[f], a.mode == MODE_FIRST ? a.src0[o] : ps[f]);
+    a.ksum[o] = a.mode == MODE_FIRST ? r[f] : fmaf(2.0f, r[f], pk[f]);
   }
 }
 
