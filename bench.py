@@ -61,7 +61,7 @@ FP64_MEASURED_GFLOPS = 1196.0      # dependent-chain DFMA microbenchmark on this
 # points; profiles/stage_traffic_bl64.md); None until captured.
 FP64_TRAFFIC_PER_POINT = 1248.2    # (93.1 + 234.0) MB / 262,144 points, stage_fp64_kernel 32x2x2/2
 FP64_ROWS_TRAFFIC_PER_POINT = 635.9  # (83.2 + 83.5) MB / 262,144 points, stage_fp64_blocks_kernel 32x4x1/1
-MIXED_TRAFFIC_PER_POINT = 282.0    # (50.5 + 23.4) MB / 262,144 points, stage_mixed_tma_kernel
+MIXED_TRAFFIC_PER_POINT = 488.0    # mean over the 4 stages of stage_mixed_tma_kernel: 282, 501, 492, 677 B
 # Float64 work per interior point of the analysis kernels (DADD + DMUL + 2 DFMA
 # from ncu instruction counts; profiles/analysis_kernels_bl96.md).
 # psi4 and constraints include the ADM-field pass that precedes them
