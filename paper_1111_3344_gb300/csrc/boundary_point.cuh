@@ -180,6 +180,54 @@ __device__ __forceinline__ void sommerfeld_point_mixed(const Grid& g, const Stag
   }
 }
 
+// mixed path, ghost point q, every field: the same per-field arithmetic as
+// sommerfeld_point_mixed with the geometry (index decode, anchor,
+// coordinates, normals) formed once for the 23 float fields.
+__device__ __forceinline__ void sommerfeld_point_mixed_all(const Grid& g, const StageArgsMixed& a,
+                                                           const float* __restrict__ kanchor, unsigned q) {
+  sommerfeld_point_mixed(g, a, kanchor, q, F_CHI);  // W: float64 geometry and arithmetic
+  const long long fs = g.fstride;
+  const int nf = g.shift == BSSN_SHIFT_FROZEN ? F_BETA : NF;
+  int I[3], A[3];
+  ghost_decode(g, q, I[0], I[1], I[2]);
+  const int n[3] = {g.n0, g.n1, g.n2};
+#pragma unroll
+  for (int d = 0; d < 3; d++) A[d] = I[d] < GH ? GH : (I[d] >= GH + n[d] ? GH + n[d] - 1 : I[d]);
+  const long long ib = lin(g, I[0], I[1], I[2]);
+  const long long ia = lin(g, A[0], A[1], A[2]);
+  float xb[3], xa[3];
+#pragma unroll
+  for (int d = 0; d < 3; d++) {
+    xb[d] = fmaf((float)(I[d] - GH) + 0.5f, g.hf, g.xminf[d]);
+    xa[d] = fmaf((float)(A[d] - GH) + 0.5f, g.hf, g.xminf[d]);
+  }
+  const float irb = rsqrtf(xb[0] * xb[0] + xb[1] * xb[1] + xb[2] * xb[2]);
+  const float ira = rsqrtf(xa[0] * xa[0] + xa[1] * xa[1] + xa[2] * xa[2]);
+  const float nb[3] = {xb[0] * irb, xb[1] * irb, xb[2] * irb};
+  const float na[3] = {xa[0] * ira, xa[1] * ira, xa[2] * ira};
+  const float fac = (irb / ira) * (irb / ira);
+  for (int f = 1; f < NF; f++) {
+    const long long o = f * fs + ib;
+    float rhs = 0.0f;
+    if (f < nf) {
+      const float radb = rad_at<float, float, true>(g, a.src + o, f, I, nb, irb);
+      const float rada = rad_at<float, float, true>(g, a.src + f * fs + ia, f, A, na, ira);
+      const float ka = (a.mode == MODE_RHS) ? (float)a.rhs[f * fs + ia] : kanchor[f * fs + ia];
+      rhs = fmaf(fac, ka - rada, radb);
+    }
+    if (a.mode == MODE_RHS) {
+      a.rhs[o] = (double)rhs;
+    } else if (a.mode == MODE_LAST) {
+      const double v = fma(a.b_dt, (double)(a.ksum[o] + rhs), a.yn[o]);
+      a.yn[o] = v;
+      a.out0[o] = (float)(v - background(g, f));
+    } else {
+      a.out0[o] = fmaf(a.a_dtf, rhs, a.src0[o]);
+      a.ksum[o] = a.mode == MODE_FIRST ? rhs : fmaf(2.0f, rhs, a.ksum[o]);
+    }
+  }
+}
+
 // Periodic ghosts: copy from the wrapped interior point, all fields (and the
 // float64 W array of a mixed stage buffer when w is non-null).
 template <typename S>

@@ -24,11 +24,11 @@ __global__ void sommerfeld_fp64_kernel(Grid g, StageArgs a, const double* __rest
   sommerfeld_point_fp64(g, a, kanchor, q);
 }
 
-// one thread per (ghost point, field): x over ghost points, y over fields
+// one thread per ghost point, every field (geometry formed once)
 __global__ void sommerfeld_mixed_kernel(Grid g, StageArgsMixed a, const float* __restrict__ kanchor) {
   const unsigned q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= ghost_count(g)) return;
-  sommerfeld_point_mixed(g, a, kanchor, q, (int)blockIdx.y);
+  sommerfeld_point_mixed_all(g, a, kanchor, q);
 }
 
 template <typename S>
@@ -48,8 +48,8 @@ cudaError_t launch_sommerfeld(const Grid& g, const StageArgs& a, const double* k
 cudaError_t launch_sommerfeld_mixed(const Grid& g, const StageArgsMixed& a, const float* kanchor,
                                     cudaStream_t s) {
   const unsigned total = ghost_count(g);
-  const int bs = 256;
-  sommerfeld_mixed_kernel<<<dim3((total + bs - 1) / bs, NF), bs, 0, s>>>(g, a, kanchor);
+  const int bs = 128;
+  sommerfeld_mixed_kernel<<<(total + bs - 1) / bs, bs, 0, s>>>(g, a, kanchor);
   return cudaGetLastError();
 }
 
