@@ -41,11 +41,11 @@ DPINST_PER_POINT_RHS = 2428.0      # float64 instructions issued
 # The 32-wide tiles on grids whose n0 is a multiple of 32 and whose n1, n2
 # fill the blocks (the benchmark grid) run the full-block kernel: x-mixed
 # second differences shared across lanes, D_y D_z across rows through shared
-# memory; 362 DADD + 317 DMUL + 1415 DFMA per point
+# memory; 302.5 DADD + 251.8 DMUL + 1366.8 DFMA per point
 # (profiles/stage_fp64_rows_bl64.md).
 ROWS_TILES = ("32x8x1/1", "32x4x1/1", "32x4x2/1", "32x2x2/2")
-FLOP_PER_POINT_RHS_ROWS = 3507.7
-DPINST_PER_POINT_RHS_ROWS = 2093.0
+FLOP_PER_POINT_RHS_ROWS = 3287.9
+DPINST_PER_POINT_RHS_ROWS = 1921.1
 HBM_BYTES_PER_POINT_STEP = 3264.0  # 17 register passes x 24 fields x 8 B
 # mixed: float stage buffers (24 x 4 B) each with a float64 W (8 B), 104 B a
 # buffer pass; per RK4 step: stage 1 reads m0, writes m1 and the k-sum (312 B);
@@ -60,7 +60,7 @@ FP64_MEASURED_GFLOPS = 1196.0      # dependent-chain DFMA microbenchmark on this
 # ncu capture of the current kernels on the 64^3 case (traffic grows with the
 # points; profiles/stage_traffic_bl64.md); None until captured.
 FP64_TRAFFIC_PER_POINT = 1248.2    # (93.1 + 234.0) MB / 262,144 points, stage_fp64_kernel 32x2x2/2
-FP64_ROWS_TRAFFIC_PER_POINT = 635.9  # (83.2 + 83.5) MB / 262,144 points, stage_fp64_blocks_kernel 32x4x1/1
+FP64_ROWS_TRAFFIC_PER_POINT = 620.3  # (83.2 + 79.4) MB / 262,144 points, stage_fp64_blocks_kernel 32x4x1/1
 MIXED_TRAFFIC_PER_POINT = 488.0    # mean over the 4 stages of stage_mixed_tma_kernel: 282, 501, 492, 677 B
 # Float64 work per interior point of the analysis kernels (DADD + DMUL + 2 DFMA
 # from ncu instruction counts; profiles/analysis_kernels_bl96.md).
@@ -468,7 +468,7 @@ def run_served(args):
             "p50_s": float(np.percentile(lats, 50)), "p99_s": float(np.percentile(lats, 99)),
             "failed": int(fails), "wall_s": wall, "busy_s": stats["busy_s"],
             "config": {"workload": f"{len(reqs)} Poisson-arrival Brill-Lindquist binaries, grids 32^3..192^3, "
-                                   f"50..400 steps, seed 3344", "lambda_per_s": lam,
+                                   f"50..400 steps, seed 3344", "precision": args.precision, "lambda_per_s": lam,
                        "budget_gb": args.budget_gb, "point_updates": work}}
     print(json.dumps(line))
 
@@ -593,7 +593,8 @@ def main():
     ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
+    ap.add_argument("--precision", choices=["fp64", "mixed"], default=None,
+                    help="default: mixed for the served workload (its configuration), float64 otherwise")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", choices=["puncture", "batched", "served", "precision", "analysis"],
                     default="puncture",
@@ -603,12 +604,17 @@ def main():
     ap.add_argument("--members", type=int, default=64)
     ap.add_argument("--requests", type=int, default=64)
     ap.add_argument("--budget-gb", type=float, default=64.0)
-    ap.add_argument("--capacity-mpts", type=float, default=250.0,
-                    help="served: throughput estimate (M point-updates/s) that sets the arrival rate")
+    ap.add_argument("--capacity-mpts", type=float, default=None,
+                    help="served: throughput estimate (M point-updates/s) that sets the arrival rate "
+                         "(default 250 mixed, 50 float64)")
     ap.add_argument("--n", type=int, default=128,
                     help="grid points per side (128 is the benchmark workload; smaller sizes are "
                          "for profiling captures only)")
     args = ap.parse_args()
+    if args.precision is None:
+        args.precision = "mixed" if args.workload == "served" else "fp64"
+    if args.capacity_mpts is None:
+        args.capacity_mpts = 250.0 if args.precision == "mixed" else 50.0
     global N_SIDE
     N_SIDE = args.n
     if args.warmup < 3 and args.impl == "ours":

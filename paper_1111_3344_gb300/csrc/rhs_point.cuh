@@ -96,8 +96,8 @@ __device__ __forceinline__ T dmu(const A& acc, int f, const P* p, long long sa, 
 // (already formed, scaled by 1/(12h)); the lanes x-1, x+1, x-2, x+2 hold
 // theirs, so only the two lanes at each end of the row form one more
 // (at x -+ 2), and the mixed difference costs 3 float64 operations instead
-// of 15.  Same stencil as dmu (D1 along x applied to D1 along b), scaled by
-// 1/(12h) twice instead of by 1/(144 h^2) once.
+// of 15.  Same stencil as dmu (D1 along x applied to D1 along b); the result
+// is 12 h times the mixed derivative (v already carries 1/(12h)).
 template <int W, typename A, typename P>
 __device__ __forceinline__ double dmx_shfl(const A& acc, int f, const P* p, long long sb, double v,
                                            double i12h) {
@@ -116,7 +116,7 @@ __device__ __forceinline__ double dmx_shfl(const A& acc, int f, const P* p, long
   const double vm1 = lane >= 1 ? sm1 : e1;
   const double vp1 = lane <= W - 2 ? sp1 : ew;
   const double vp2 = lane <= W - 3 ? sp2 : ve;
-  return fma(8.0, vp1 - vm1, -(vp2 - vm2)) * i12h;
+  return fma(8.0, vp1 - vm1, -(vp2 - vm2));
 }
 
 // the same helpers over the plain read-only global path (one field)
@@ -196,14 +196,24 @@ __device__ __forceinline__ void rhs_point_acc(const Grid& g, const A& acc, int i
     Bv[a] = LD(F_B + a, PF(F_B + a));
   }
 
-  // ---- inverse conformal metric (cofactors / det)
-  T gu[6];
+  // ---- inverse conformal metric (cofactors / det); in the W variant one
+  // division gives both 1/det and 1/(2W) (W floored where it divides)
+  T gu[6], ihW = T(0);
   {
     T c00 = gt[3] * gt[5] - gt[4] * gt[4];
     T c01 = gt[2] * gt[4] - gt[1] * gt[5];
     T c02 = gt[1] * gt[4] - gt[2] * gt[3];
     T det = gt[0] * c00 + gt[1] * c01 + gt[2] * c02;
-    T idet = T(1) / det;
+    T idet;
+    if (g.use_w) {
+      const T wf = gc<T>(g.w_floor, g.w_floorf);
+      const T Wd = chi > wf ? chi : wf;
+      const T r = T(1) / (det * Wd);
+      idet = Wd * r;
+      ihW = T(0.5) * det * r;
+    } else {
+      idet = T(1) / det;
+    }
     gu[0] = c00 * idet;
     gu[1] = c01 * idet;
     gu[2] = c02 * idet;
@@ -253,14 +263,21 @@ __device__ __forceinline__ void rhs_point_acc(const Grid& g, const A& acc, int i
     __syncthreads();
 #pragma unroll
     for (int q = 0; q < 11; q++)
-      dyz[q] = fmaT<T>(T(8), at(q, ty + 3) - at(q, ty + 1), -(at(q, ty + 4) - at(q, ty))) * i12h;
+      dyz[q] = fmaT<T>(T(8), at(q, ty + 3) - at(q, ty + 1), -(at(q, ty + 4) - at(q, ty)));  // x 1/(12h)
   }
 
-  // ---- second derivatives, consumed pair by pair
+  // ---- second derivatives, consumed pair by pair.  Each is formed unscaled
+  // (12 h^2, 12 h or 144 h^2 times the derivative, by stencil) and its scale
+  // sc goes into the weight of the contraction that takes it.
   T Rdd[6];      // -1/2 gt^{kl} d_k d_l gt_ij
   T lapb[3];     // gt^{kl} d_k d_l beta^i
   T gdiv[3];     // d_j d_k beta^k
-  T ddchi[6], ddalp[6];
+  T ddchi[6];    // d_a d_b (phi|W)
+  T ddalp[6];    // d_a d_b alpha, unscaled; times sc2[pq]
+  T sc2[6];
+  T g2u[6];      // gt^{ab} with the off-diagonal entries doubled (symmetric contractions)
+#pragma unroll
+  for (int m = 0; m < 6; m++) g2u[m] = (m == 0 || m == 3 || m == 5) ? gu[m] : T(2) * gu[m];
 #pragma unroll
   for (int m = 0; m < 6; m++) Rdd[m] = T(0);
 #pragma unroll
@@ -271,61 +288,68 @@ __device__ __forceinline__ void rhs_point_acc(const Grid& g, const A& acc, int i
 #pragma unroll
       for (int pb = pa; pb < 3; pb++) {
         const int pq = sym(pa, pb);
-        const T w = (pa == pb) ? T(-0.5) * gu[pq] : -gu[pq];  // -1/2 gt^{kl}, both orders
         T dd[6];
+        T sc;
         if (pa == pb) {
+          sc = i12h2;
 #pragma unroll
-          for (int m = 0; m < 6; m++) dd[m] = d2u<T>(acc, F_GT + m, PF(F_GT + m), SD(F_GT + m, pa), gt_r[m]) * i12h2;
+          for (int m = 0; m < 6; m++) dd[m] = d2u<T>(acc, F_GT + m, PF(F_GT + m), SD(F_GT + m, pa), gt_r[m]);
           ddchi[pq] = d2u<T>(acc, F_CHI, PF(F_CHI), SD(F_CHI, pa), chi_r) * i12h2;
-          ddalp[pq] = d2u<T>(acc, F_ALP, PF(F_ALP), SD(F_ALP, pa), alp_r) * i12h2;
+          ddalp[pq] = d2u<T>(acc, F_ALP, PF(F_ALP), SD(F_ALP, pa), alp_r);
         } else if constexpr (XSEG > 0 && sizeof(T) == 8) {
           if (pa == 0) {
+            sc = i12h;
 #pragma unroll
             for (int m = 0; m < 6; m++)
               dd[m] = dmx_shfl<XSEG>(acc, F_GT + m, PF(F_GT + m), SD(F_GT + m, pb), dgt[pb][m], i12h);
-            ddchi[pq] = dmx_shfl<XSEG>(acc, F_CHI, PF(F_CHI), SD(F_CHI, pb), dchi[pb], i12h);
+            ddchi[pq] = dmx_shfl<XSEG>(acc, F_CHI, PF(F_CHI), SD(F_CHI, pb), dchi[pb], i12h) * i12h;
             ddalp[pq] = dmx_shfl<XSEG>(acc, F_ALP, PF(F_ALP), SD(F_ALP, pb), dalp[pb], i12h);
           } else if constexpr (YROWS > 0) {  // (1, 2)
+            sc = i12h;
 #pragma unroll
             for (int m = 0; m < 6; m++) dd[m] = dyz[m];
-            ddchi[pq] = dyz[6];
+            ddchi[pq] = dyz[6] * i12h;
             ddalp[pq] = dyz[7];
           } else {
+            sc = i144h2;
 #pragma unroll
-            for (int m = 0; m < 6; m++) dd[m] = dmu<T>(acc, F_GT + m, PF(F_GT + m), SD(F_GT + m, pa), SD(F_GT + m, pb)) * i144h2;
+            for (int m = 0; m < 6; m++) dd[m] = dmu<T>(acc, F_GT + m, PF(F_GT + m), SD(F_GT + m, pa), SD(F_GT + m, pb));
             ddchi[pq] = dmu<T>(acc, F_CHI, PF(F_CHI), SD(F_CHI, pa), SD(F_CHI, pb)) * i144h2;
-            ddalp[pq] = dmu<T>(acc, F_ALP, PF(F_ALP), SD(F_ALP, pa), SD(F_ALP, pb)) * i144h2;
+            ddalp[pq] = dmu<T>(acc, F_ALP, PF(F_ALP), SD(F_ALP, pa), SD(F_ALP, pb));
           }
         } else {
+          sc = i144h2;
 #pragma unroll
-          for (int m = 0; m < 6; m++) dd[m] = dmu<T>(acc, F_GT + m, PF(F_GT + m), SD(F_GT + m, pa), SD(F_GT + m, pb)) * i144h2;
+          for (int m = 0; m < 6; m++) dd[m] = dmu<T>(acc, F_GT + m, PF(F_GT + m), SD(F_GT + m, pa), SD(F_GT + m, pb));
           ddchi[pq] = dmu<T>(acc, F_CHI, PF(F_CHI), SD(F_CHI, pa), SD(F_CHI, pb)) * i144h2;
-          ddalp[pq] = dmu<T>(acc, F_ALP, PF(F_ALP), SD(F_ALP, pa), SD(F_ALP, pb)) * i144h2;
+          ddalp[pq] = dmu<T>(acc, F_ALP, PF(F_ALP), SD(F_ALP, pa), SD(F_ALP, pb));
         }
+        sc2[pq] = sc;
+        const T wb = sc * g2u[pq];       // gt^{kl} over both orders of (k, l)
+        const T w = T(-0.5) * wb;        // -1/2 gt^{kl}
 #pragma unroll
         for (int m = 0; m < 6; m++) Rdd[m] = fmaT<T>(w, dd[m], Rdd[m]);
         // shift second derivatives enter the Gt equation even when the shift
         // itself is frozen
-        const T wb = (pa == pb) ? gu[pq] : T(2) * gu[pq];
 #pragma unroll
         for (int a = 0; a < 3; a++) {
           T v;
           if (pa == pb) {
-            v = d2u<T>(acc, F_BETA + a, PF(F_BETA + a), SD(F_BETA + a, pa), beta[a]) * i12h2;
+            v = d2u<T>(acc, F_BETA + a, PF(F_BETA + a), SD(F_BETA + a, pa), beta[a]);
           } else if constexpr (XSEG > 0 && sizeof(T) == 8) {
             if (pa == 0)
               v = dmx_shfl<XSEG>(acc, F_BETA + a, PF(F_BETA + a), SD(F_BETA + a, pb), db[pb][a], i12h);
             else if constexpr (YROWS > 0)
               v = dyz[8 + a];
             else
-              v = dmu<T>(acc, F_BETA + a, PF(F_BETA + a), SD(F_BETA + a, pa), SD(F_BETA + a, pb)) * i144h2;
+              v = dmu<T>(acc, F_BETA + a, PF(F_BETA + a), SD(F_BETA + a, pa), SD(F_BETA + a, pb));
           } else {
-            v = dmu<T>(acc, F_BETA + a, PF(F_BETA + a), SD(F_BETA + a, pa), SD(F_BETA + a, pb)) * i144h2;
+            v = dmu<T>(acc, F_BETA + a, PF(F_BETA + a), SD(F_BETA + a, pa), SD(F_BETA + a, pb));
           }
           lapb[a] = fmaT<T>(wb, v, lapb[a]);
           // d_pa d_pb beta^a contributes to gdiv[pa] when a == pb, gdiv[pb] when a == pa
-          if (a == pb) gdiv[pa] += v;
-          if (pa != pb && a == pa) gdiv[pb] += v;
+          if (a == pb) gdiv[pa] = fmaT<T>(sc, v, gdiv[pa]);
+          if (pa != pb && a == pa) gdiv[pb] = fmaT<T>(sc, v, gdiv[pb]);
         }
       }
     }
@@ -334,9 +358,7 @@ __device__ __forceinline__ void rhs_point_acc(const Grid& g, const A& acc, int i
   // ---- conformal factor
   T em4, dphi[3], ddphi[6];
   if (g.use_w) {
-    const T wf = gc<T>(g.w_floor, g.w_floorf);
-    T Wd = chi > wf ? chi : wf;
-    T ih = T(0.5) / Wd;
+    const T ih = ihW;
     em4 = chi * chi;
 #pragma unroll
     for (int a = 0; a < 3; a++) dphi[a] = -dchi[a] * ih;
@@ -353,15 +375,28 @@ __device__ __forceinline__ void rhs_point_acc(const Grid& g, const A& acc, int i
     for (int m = 0; m < 6; m++) ddphi[m] = ddchi[m];
   }
 
-  // ---- Christoffel symbols: first kind G1[k][ij] = (d_i g_kj + d_j g_ki - d_k g_ij)/2
+  // ---- Christoffel symbols: first kind G1[k][ij] = (d_i g_kj + d_j g_ki - d_k g_ij)/2,
+  // with the terms that cancel identically left out (k = i or k = j, i = j)
   T G1[3][6], G2[3][6];
 #pragma unroll
   for (int kk = 0; kk < 3; kk++)
 #pragma unroll
     for (int a = 0; a < 3; a++)
 #pragma unroll
-      for (int b = a; b < 3; b++)
-        G1[kk][sym(a, b)] = T(0.5) * (dgt[a][sym(kk, b)] + dgt[b][sym(kk, a)] - dgt[kk][sym(a, b)]);
+      for (int b = a; b < 3; b++) {
+        T v;
+        if (a == b && kk == a)
+          v = T(0.5) * dgt[a][sym(a, a)];
+        else if (a == b)
+          v = fmaT<T>(T(-0.5), dgt[kk][sym(a, a)], dgt[a][sym(kk, a)]);
+        else if (kk == a)
+          v = T(0.5) * dgt[b][sym(a, a)];
+        else if (kk == b)
+          v = T(0.5) * dgt[a][sym(b, b)];
+        else
+          v = T(0.5) * (dgt[a][sym(kk, b)] + dgt[b][sym(kk, a)] - dgt[kk][sym(a, b)]);
+        G1[kk][sym(a, b)] = v;
+      }
 #pragma unroll
   for (int kk = 0; kk < 3; kk++)
 #pragma unroll
@@ -405,22 +440,38 @@ __device__ __forceinline__ void rhs_point_acc(const Grid& g, const A& acc, int i
       for (int b = a; b < 3; b++) {
         const int ab = sym(a, b);
         T s = Rdd[ab];
+        // gt_k(a d_b) Gt^k + Gt^k Gt_(ab)k with Gt^k = -d_l gt^{lk} and
+        // Gt_akb + Gt_bka = d_k gt_ab
         T t = T(0);
 #pragma unroll
         for (int kk = 0; kk < 3; kk++) {
           t = fmaT<T>(gt[sym(kk, a)], dG[b][kk], t);
           t = fmaT<T>(gt[sym(kk, b)], dG[a][kk], t);
-          t = fmaT<T>(-(G1[a][sym(b, kk)] + G1[b][sym(a, kk)]), dgu[kk], t);
+          t = fmaT<T>(-dgt[kk][ab], dgu[kk], t);
         }
         s = fmaT<T>(T(0.5), t, s);
+        // gt^{lm} (Gt^k_la Gt_bkm + Gt^k_lb Gt_akm + Gt^k_am Gt_klb); the first
+        // two coincide on the diagonal
+        if (a == b) {
+          T q = T(0);
 #pragma unroll
-        for (int kk = 0; kk < 3; kk++)
+          for (int kk = 0; kk < 3; kk++)
 #pragma unroll
-          for (int l = 0; l < 3; l++) {
-            s = fmaT<T>(G2[kk][sym(l, a)], G1u[b][kk][l], s);
-            s = fmaT<T>(G2[kk][sym(l, b)], G1u[a][kk][l], s);
-            s = fmaT<T>(G2[kk][sym(a, l)], G1u[kk][b][l], s);
-          }
+            for (int l = 0; l < 3; l++) {
+              q = fmaT<T>(G2[kk][sym(l, a)], G1u[a][kk][l], q);
+              s = fmaT<T>(G2[kk][sym(a, l)], G1u[kk][a][l], s);
+            }
+          s = fmaT<T>(T(2), q, s);
+        } else {
+#pragma unroll
+          for (int kk = 0; kk < 3; kk++)
+#pragma unroll
+            for (int l = 0; l < 3; l++) {
+              s = fmaT<T>(G2[kk][sym(l, a)], G1u[b][kk][l], s);
+              s = fmaT<T>(G2[kk][sym(l, b)], G1u[a][kk][l], s);
+              s = fmaT<T>(G2[kk][sym(a, l)], G1u[kk][b][l], s);
+            }
+        }
         Rt[ab] = s;
       }
   }
@@ -433,34 +484,35 @@ __device__ __forceinline__ void rhs_point_acc(const Grid& g, const A& acc, int i
 #pragma unroll
     for (int m = 0; m < 6; m++) {
       DDphi[m] = ddphi[m] - (G2[0][m] * dphi[0] + G2[1][m] * dphi[1] + G2[2][m] * dphi[2]);
-      DDalp[m] = ddalp[m] - (G2[0][m] * dalp[0] + G2[1][m] * dalp[1] + G2[2][m] * dalp[2]);
+      DDalp[m] = fmaT<T>(sc2[m], ddalp[m], -(G2[0][m] * dalp[0] + G2[1][m] * dalp[1] + G2[2][m] * dalp[2]));
     }
-    T lap_phi = T(0), grad2 = T(0);
+    T lap_phi = T(0);
     lap_alp = T(0);
-    dphi_dalp = T(0);
 #pragma unroll
-    for (int a = 0; a < 3; a++)
+    for (int m = 0; m < 6; m++) {
+      lap_phi = fmaT<T>(g2u[m], DDphi[m], lap_phi);
+      lap_alp = fmaT<T>(g2u[m], DDalp[m], lap_alp);
+    }
+    T uphi[3];  // gt^{ab} d_b phi
 #pragma unroll
-      for (int b = 0; b < 3; b++) {
-        const T gab = gu[sym(a, b)];
-        lap_phi = fmaT<T>(gab, DDphi[sym(a, b)], lap_phi);
-        lap_alp = fmaT<T>(gab, DDalp[sym(a, b)], lap_alp);
-        grad2 = fmaT<T>(gab, dphi[a] * dphi[b], grad2);
-        dphi_dalp = fmaT<T>(gab, dphi[a] * dalp[b], dphi_dalp);
-      }
+    for (int a = 0; a < 3; a++) uphi[a] = gu[sym(a, 0)] * dphi[0] + gu[sym(a, 1)] * dphi[1] + gu[sym(a, 2)] * dphi[2];
+    const T grad2 = uphi[0] * dphi[0] + uphi[1] * dphi[1] + uphi[2] * dphi[2];
+    dphi_dalp = uphi[0] * dalp[0] + uphi[1] * dalp[1] + uphi[2] * dalp[2];
+    // Rphi_ab = -2 DD_ab phi + 4 d_a phi d_b phi - gt_ab (2 lap phi + 4 |d phi|^2)
+    const T cg = fmaT<T>(T(4), grad2, T(2) * lap_phi);
 #pragma unroll
     for (int a = 0; a < 3; a++)
 #pragma unroll
       for (int b = a; b < 3; b++) {
         const int ab = sym(a, b);
-        T rphi = T(-2) * DDphi[ab] - T(2) * gt[ab] * lap_phi + T(4) * dphi[a] * dphi[b] -
-                 T(4) * gt[ab] * grad2;
-        X[ab] = alp * (Rt[ab] + rphi) - DDalp[ab] + T(2) * (dphi[a] * dalp[b] + dphi[b] * dalp[a]);
+        const T rphi = fmaT<T>(T(-2), DDphi[ab], fmaT<T>(T(4) * dphi[a], dphi[b], -gt[ab] * cg));
+        const T cross = fmaT<T>(dphi[a], dalp[b], dphi[b] * dalp[a]);
+        X[ab] = fmaT<T>(T(2), cross, fmaT<T>(alp, Rt[ab] + rphi, -DDalp[ab]));
       }
   }
 
   // ---- At with raised indices
-  T Aud[3][3], Auu[6];
+  T Aud[3][3], Auu[6], Auu2[6];
 #pragma unroll
   for (int a = 0; a < 3; a++)
 #pragma unroll
@@ -472,11 +524,11 @@ __device__ __forceinline__ void rhs_point_acc(const Grid& g, const A& acc, int i
 #pragma unroll
     for (int b = a; b < 3; b++)
       Auu[sym(a, b)] = Aud[a][0] * gu[sym(0, b)] + Aud[a][1] * gu[sym(1, b)] + Aud[a][2] * gu[sym(2, b)];
+#pragma unroll
+  for (int m = 0; m < 6; m++) Auu2[m] = (m == 0 || m == 3 || m == 5) ? Auu[m] : T(2) * Auu[m];
   T AA = T(0);
 #pragma unroll
-  for (int a = 0; a < 3; a++)
-#pragma unroll
-    for (int b = 0; b < 3; b++) AA = fmaT<T>(Auu[sym(a, b)], At[sym(a, b)], AA);
+  for (int m = 0; m < 6; m++) AA = fmaT<T>(Auu2[m], At[m], AA);
   const T divb = db[0][0] + db[1][1] + db[2][2];
 
   // ---- matter sources, when a stress-energy tensor is given: the paper's
@@ -490,9 +542,7 @@ __device__ __forceinline__ void rhs_point_acc(const Grid& g, const A& acc, int i
     matter_at<T>(g, lin(g, i, j, k), alp, beta, Em, Smi, Stf);
     T trs = T(0);
 #pragma unroll
-    for (int a = 0; a < 3; a++)
-#pragma unroll
-      for (int b = 0; b < 3; b++) trs = fmaT<T>(gu[sym(a, b)], Stf[sym(a, b)], trs);
+    for (int m = 0; m < 6; m++) trs = fmaT<T>(g2u[m], Stf[m], trs);
 #pragma unroll
     for (int m = 0; m < 6; m++) Stf[m] -= gt[m] * trs * T(1.0 / 3.0);  // [S_ij]^TF (gt_ij gt^kl = gamma_ij gamma^kl)
     mK = T(4.0 * M_PI) * alp * (Em + em4 * trs);
@@ -508,21 +558,20 @@ __device__ __forceinline__ void rhs_point_acc(const Grid& g, const A& acc, int i
   else
     out[F_CHI] = T(-1.0 / 6.0) * alp * trK + divb * T(1.0 / 6.0);
 
+  const T divb23 = T(2.0 / 3.0) * divb;
   {
     T trX = T(0);
 #pragma unroll
-    for (int a = 0; a < 3; a++)
-#pragma unroll
-      for (int b = 0; b < 3; b++) trX = fmaT<T>(gu[sym(a, b)], X[sym(a, b)], trX);
+    for (int m = 0; m < 6; m++) trX = fmaT<T>(g2u[m], X[m], trX);
     const T trX3 = trX * T(1.0 / 3.0);
-    const T divb23 = T(2.0 / 3.0) * divb;
+    const T akd = fmaT<T>(alp, trK, -divb23);  // alpha K - 2/3 d_k beta^k
 #pragma unroll
     for (int a = 0; a < 3; a++)
 #pragma unroll
       for (int b = a; b < 3; b++) {
         const int ab = sym(a, b);
         T sg = T(-2) * alp * At[ab] - gt[ab] * divb23;
-        T sa = em4 * (X[ab] - gt[ab] * trX3) + alp * trK * At[ab] - At[ab] * divb23;
+        T sa = fmaT<T>(akd, At[ab], em4 * fmaT<T>(-gt[ab], trX3, X[ab]));
 #pragma unroll
         for (int kk = 0; kk < 3; kk++) {
           sg = fmaT<T>(gt[sym(kk, a)], db[b][kk], sg);
@@ -539,29 +588,37 @@ __device__ __forceinline__ void rhs_point_acc(const Grid& g, const A& acc, int i
   out[F_TRK] = -em4 * (lap_alp + T(2) * dphi_dalp) + alp * (AA + trK * trK * T(1.0 / 3.0)) + mK;
 
   T gam_rhs[3];
+  {
+    // -2 At^{aj} d_j alpha + 12 alpha At^{aj} d_j phi = At^{aj} vj_j
+    T vj[3], dKu[3], gdu[3];
+    const T a12 = T(12) * alp;
 #pragma unroll
-  for (int a = 0; a < 3; a++) {
-    T s = lapb[a];
-    s = fmaT<T>(T(1.0 / 3.0),
-                gu[sym(a, 0)] * gdiv[0] + gu[sym(a, 1)] * gdiv[1] + gu[sym(a, 2)] * gdiv[2], s);
-    s = fmaT<T>(dgu[0], db[0][a], s);
-    s = fmaT<T>(dgu[1], db[1][a], s);
-    s = fmaT<T>(dgu[2], db[2][a], s);
-    s = fmaT<T>(T(-2.0 / 3.0) * dgu[a], divb, s);
-    T br = T(0);
+    for (int jj = 0; jj < 3; jj++) vj[jj] = fmaT<T>(a12, dphi[jj], T(-2) * dalp[jj]);
 #pragma unroll
-    for (int jj = 0; jj < 3; jj++) {
-      s = fmaT<T>(T(-2) * Auu[sym(a, jj)], dalp[jj], s);
-      br = fmaT<T>(T(-2.0 / 3.0) * gu[sym(a, jj)], dK[jj], br);
-      br = fmaT<T>(T(6) * Auu[sym(a, jj)], dphi[jj], br);
+    for (int a = 0; a < 3; a++) {
+      dKu[a] = gu[sym(a, 0)] * dK[0] + gu[sym(a, 1)] * dK[1] + gu[sym(a, 2)] * dK[2];
+      gdu[a] = gu[sym(a, 0)] * gdiv[0] + gu[sym(a, 1)] * gdiv[1] + gu[sym(a, 2)] * gdiv[2];
     }
+    const T m23divb = T(-2.0 / 3.0) * divb;
+    const T alp2 = T(2) * alp;
 #pragma unroll
-    for (int kk = 0; kk < 3; kk++)
+    for (int a = 0; a < 3; a++) {
+      T s = fmaT<T>(T(1.0 / 3.0), gdu[a], lapb[a]);
+      s = fmaT<T>(dgu[0], db[0][a], s);
+      s = fmaT<T>(dgu[1], db[1][a], s);
+      s = fmaT<T>(dgu[2], db[2][a], s);
+      s = fmaT<T>(m23divb, dgu[a], s);
 #pragma unroll
-      for (int l = 0; l < 3; l++) br = fmaT<T>(G2[a][sym(kk, l)], Auu[sym(kk, l)], br);
-    s = fmaT<T>(T(2) * alp, br, s) + mG[a];
-    gam_rhs[a] = s;
-    out[F_GAM + a] = s;
+      for (int jj = 0; jj < 3; jj++) s = fmaT<T>(Auu[sym(a, jj)], vj[jj], s);
+      // Gt^a_kl At^kl - 2/3 gt^aj d_j K
+      T br = T(-2.0 / 3.0) * dKu[a];
+#pragma unroll
+      for (int m = 0; m < 6; m++) br = fmaT<T>(G2[a][m], Auu2[m], br);
+      s = fmaT<T>(alp2, br, s);
+      if (matter) s += mG[a];
+      gam_rhs[a] = s;
+      out[F_GAM + a] = s;
+    }
   }
 
   if (g.slicing == BSSN_1PLUSLOG)

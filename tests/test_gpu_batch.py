@@ -218,3 +218,34 @@ def test_server_budget_and_failure_isolation(torch_cuda):
     st = s.stats()
     assert st["failed"] == 1 and st["completed"] == 3
     s.close()
+
+
+def test_batch_full_rows_fp64(torch_cuda):
+    """A float64 member whose x extent is a multiple of 32 takes the full-row
+    point function (first differences shared across the warp's lanes); next to
+    a member with a ragged x extent it still matches the oracle and itself
+    alone, bit for bit."""
+    from paper_1111_3344_gb300.bssn import Batch
+    rows = dict(n=(64, 12, 16), xmin=(-8.0, -1.5, -2.0), h=0.25, boundary="sommerfeld", conformal="W",
+                slicing="1+log", shift="gamma-driver", eta=2.0, punctures=[(1.0, 0.05, 0.0, 0.0)],
+                precision="fp64", w_fp64_threshold=0.3)
+    ragged = _members("fp64")[1]
+    mix = Batch("fp64", pool_bytes=1 << 29)
+    ids = [mix.add(gpu_params(c)) for c in (rows, ragged)]
+    for mid, c in zip(ids, (rows, ragged)):
+        mix.set_initial_data(mid, "bl", bl_params(c))
+    mix.step(2)
+    got = mix.get_state(ids[0])[0]
+    alone = Batch("fp64", pool_bytes=1 << 28)
+    aid = alone.add(gpu_params(rows))
+    alone.set_initial_data(aid, "bl", bl_params(rows))
+    alone.step(2)
+    assert np.array_equal(alone.get_state(aid)[0], got)
+    alone.close()
+    cfg = oracle_cfg(rows)
+    want = O.rk4(cfg, O.initial_data(cfg, "bl", bl_params(rows)), 2)
+    assert normwise_errors(got, want).max() <= 1e-11
+    cfg = oracle_cfg(ragged)
+    want = O.rk4(cfg, O.initial_data(cfg, "bl", bl_params(ragged)), 2)
+    assert normwise_errors(mix.get_state(ids[1])[0], want).max() <= 1e-11
+    mix.close()
