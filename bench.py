@@ -35,9 +35,9 @@ N_SIDE = 128
 DOMAIN = 8.0
 # Float64 work per interior point per fused stage launch (right-hand side plus
 # RK4 combine), from the ncu instruction counts of the stage kernel
-# (profiles/stage_fp64_bl64.md): 594 DADD + 301 DMUL + 1533 DFMA.
-FLOP_PER_POINT_RHS = 3961.0        # DADD + DMUL + 2 DFMA
-DPINST_PER_POINT_RHS = 2428.0      # float64 instructions issued
+# (profiles/stage_fp64_bl64.md): 535 DADD + 239 DMUL + 1485 DFMA.
+FLOP_PER_POINT_RHS = 3744.0        # DADD + DMUL + 2 DFMA
+DPINST_PER_POINT_RHS = 2259.0      # float64 instructions issued
 # The 32-wide tiles on grids whose n0 is a multiple of 32 and whose n1, n2
 # fill the blocks (the benchmark grid) run the full-block kernel: x-mixed
 # second differences shared across lanes, D_y D_z across rows through shared
@@ -59,7 +59,7 @@ FP64_MEASURED_GFLOPS = 1196.0      # dependent-chain DFMA microbenchmark on this
 # DRAM bytes (read + write) per interior point of one stage launch, from the
 # ncu capture of the current kernels on the 64^3 case (traffic grows with the
 # points; profiles/stage_traffic_bl64.md); None until captured.
-FP64_TRAFFIC_PER_POINT = 1248.2    # (93.1 + 234.0) MB / 262,144 points, stage_fp64_kernel 32x2x2/2
+FP64_TRAFFIC_PER_POINT = 1587.9    # (100.8 + 315.4) MB / 262,144 points, stage_fp64_kernel 64x4x1/1
 FP64_ROWS_TRAFFIC_PER_POINT = 620.3  # (83.2 + 79.4) MB / 262,144 points, stage_fp64_blocks_kernel 32x4x1/1
 MIXED_TRAFFIC_PER_POINT = 488.0    # mean over the 4 stages of stage_mixed_tma_kernel: 282, 501, 492, 677 B
 # Float64 work per interior point of the analysis kernels (DADD + DMUL + 2 DFMA
