@@ -251,6 +251,33 @@ bssn_status bssn_psi4(bssn_ctx* ctx, double* d_out);
 bssn_status bssn_get_state(bssn_ctx* ctx, double* host_state, double* t);
 bssn_status bssn_set_state(bssn_ctx* ctx, const double* host_state, double t);
 
+/* The same copies without waiting for them (no counterpart in the paper: a
+ * host loop that uploads a state, steps and reads it back every step).
+ * The layout, arguments and errors are those of bssn_get_state / bssn_set_state.
+ *
+ * bssn_set_state_async:
+ *  - Enqueues the upload on the context's stream.
+ *  - host_state must be pinned, and must stay unchanged until the stream has
+ *    passed the copy (bssn_wait_state, or any later synchronising call).
+ *
+ * bssn_get_state_async:
+ *  - Repacks y_n on the context's stream into a read-back area that later uploads
+ *    do not use.
+ *  - Copies it to host_state on a copy stream of the library, so that the copy
+ *    can overlap the next bssn_set_state_async.
+ *  - host_state must be pinned, and is valid after bssn_wait_state.
+ *  - The next call that may overwrite the read-back area first waits, on the
+ *    device, for that copy: the next bssn_get_state_async, bssn_rk4_step,
+ *    bssn_rhs, the initial-data and analysis calls, and bssn_autotune.
+ *  - *t (if t is not NULL) is the time of the state read.
+ *
+ * bssn_wait_state:
+ *  - Synchronises both streams.
+ *  - Returns BSSN_ETIMEOUT if a stage kernel gave up waiting (see bssn_rk4_step). */
+bssn_status bssn_set_state_async(bssn_ctx* ctx, const double* host_state, double t);
+bssn_status bssn_get_state_async(bssn_ctx* ctx, double* host_state, double* t);
+bssn_status bssn_wait_state(bssn_ctx* ctx);
+
 /* Stage-kernel tile configurations: block shape (points along x, y, z) and the
  * minimum resident blocks per SM given to the compiler.  The last ones are for
  * the mixed path only: "tma32x4x1/2" stages the second-differenced fields in

@@ -127,6 +127,9 @@ _SIGS = [
     ("bssn_constraints", [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     ("bssn_get_state", [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     ("bssn_set_state", [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double], ctypes.c_int),
+    ("bssn_get_state_async", [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+    ("bssn_set_state_async", [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double], ctypes.c_int),
+    ("bssn_wait_state", [ctypes.c_void_p], ctypes.c_int),
     ("bssn_profile", [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     ("bssn_set_adm", [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double], ctypes.c_int),
     ("bssn_set_punctures", [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int32], ctypes.c_int),
@@ -318,6 +321,24 @@ def bssn_get_state(ctx: int, host: np.ndarray) -> float:
 def bssn_set_state(ctx: int, host: np.ndarray, t: float = 0.0):
     assert host.dtype == np.float64 and host.flags.c_contiguous
     _check(load().bssn_set_state(ctypes.c_void_p(ctx), ctypes.c_void_p(host.ctypes.data), float(t)))
+
+
+def bssn_get_state_async(ctx: int, host: np.ndarray) -> float:
+    """host: pinned, float64, C-contiguous; valid after bssn_wait_state."""
+    assert host.dtype == np.float64 and host.flags.c_contiguous
+    t = ctypes.c_double()
+    _check(load().bssn_get_state_async(ctypes.c_void_p(ctx), ctypes.c_void_p(host.ctypes.data), ctypes.byref(t)))
+    return t.value
+
+
+def bssn_set_state_async(ctx: int, host: np.ndarray, t: float = 0.0):
+    """host: pinned, float64, C-contiguous; unchanged until bssn_wait_state."""
+    assert host.dtype == np.float64 and host.flags.c_contiguous
+    _check(load().bssn_set_state_async(ctypes.c_void_p(ctx), ctypes.c_void_p(host.ctypes.data), float(t)))
+
+
+def bssn_wait_state(ctx: int):
+    _check(load().bssn_wait_state(ctypes.c_void_p(ctx)))
 
 
 def bssn_tile_count() -> int:

@@ -167,6 +167,12 @@ struct bssn_ctx {
   // launch timing (bssn_profile): event pairs around stage and boundary launches
   bool prof;
   std::vector<cudaEvent_t> ev_stage, ev_bc;
+  // asynchronous state read-back (bssn_get_state_async): a copy stream, the
+  // event after the repack into the read-back area, the event after the copy
+  // to the host, and whether that copy may still be running
+  cudaStream_t cstream;
+  cudaEvent_t ev_out_ready, ev_out_done;
+  bool out_pending;
 };
 
 namespace {
@@ -269,18 +275,40 @@ bssn_status bssn_alloc(const bssn_params* p, void* d_mem, size_t bytes, void* cu
     for (int q = 0; q < 3 && ok; q++) ok = make_stage_tensor_map(g, ctx->m32[q], &ctx->tmap[q]) == cudaSuccess;
     ctx->tmap_ok = ok;
   }
-  if (cudaMemsetAsync(ctx->err, 0, sizeof(int), ctx->stream) != cudaSuccess) {
+  ctx->cstream = nullptr;
+  ctx->ev_out_ready = ctx->ev_out_done = nullptr;
+  ctx->out_pending = false;
+  if (cudaStreamCreateWithFlags(&ctx->cstream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->ev_out_ready, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->ev_out_done, cudaEventDisableTiming) != cudaSuccess ||
+      cudaMemsetAsync(ctx->err, 0, sizeof(int), ctx->stream) != cudaSuccess) {
+    if (ctx->ev_out_done) cudaEventDestroy(ctx->ev_out_done);
+    if (ctx->ev_out_ready) cudaEventDestroy(ctx->ev_out_ready);
+    if (ctx->cstream) cudaStreamDestroy(ctx->cstream);
     delete ctx;
-    return fail(BSSN_ECUDA, "error word init");
+    return fail(BSSN_ECUDA, "stream, events or error word init");
   }
   *out = ctx;
   return BSSN_OK;
 }
 
+// Work on the library stream that may overwrite the read-back area first
+// waits (on the device) for a pending asynchronous copy out of it.
+static cudaError_t drain_out(bssn_ctx* ctx) {
+  if (!ctx->out_pending) return cudaSuccess;
+  ctx->out_pending = false;
+  return cudaStreamWaitEvent(ctx->stream, ctx->ev_out_done, 0);
+}
+
 bssn_status bssn_free(bssn_ctx* ctx) {
   if (!ctx) return fail(BSSN_EINVAL, "ctx is NULL");
   cudaError_t e = cudaStreamSynchronize(ctx->stream);
+  cudaError_t e2 = cudaStreamSynchronize(ctx->cstream);
+  if (e == cudaSuccess) e = e2;
   prof_clear(ctx);
+  cudaEventDestroy(ctx->ev_out_done);
+  cudaEventDestroy(ctx->ev_out_ready);
+  cudaStreamDestroy(ctx->cstream);
   delete ctx;
   if (e != cudaSuccess) return cuda_fail(e, "bssn_free");
   return BSSN_OK;
@@ -312,6 +340,7 @@ static cudaError_t pull_punct(bssn_ctx* ctx) {
 bssn_status bssn_set_initial_data(bssn_ctx* ctx, int32_t kind, const double* p, int32_t np) {
   if (!ctx) return fail(BSSN_EINVAL, "ctx is NULL");
   if (np < 0 || (np > 0 && !p)) return fail(BSSN_EINVAL, "bad parameter array");
+  if (cudaError_t ed = drain_out(ctx)) return cuda_fail(ed, "wait for the state read-back");
   double buf[33] = {0};
   int npunct = 0;
   if (kind == BSSN_ID_FLAT) {
@@ -343,6 +372,7 @@ bssn_status bssn_set_initial_data(bssn_ctx* ctx, int32_t kind, const double* p, 
 
 bssn_status bssn_set_adm(bssn_ctx* ctx, const double* host_adm, double t) {
   if (!ctx || !host_adm) return fail(BSSN_EINVAL, "NULL argument");
+  if (cudaError_t ed = drain_out(ctx)) return cuda_fail(ed, "wait for the state read-back");
   const Grid& g = ctx->g;
   cudaError_t e = cudaMemcpy2DAsync(ctx->yn, (size_t)g.pitch * sizeof(double), host_adm,
                                     (size_t)g.sx * sizeof(double), (size_t)g.sx * sizeof(double),
@@ -395,6 +425,7 @@ bssn_status bssn_get_punctures(bssn_ctx* ctx, double* out, int32_t* npunct) {
 
 bssn_status bssn_rhs(bssn_ctx* ctx, const void* d_state, void* d_rhs) {
   if (!ctx || !d_rhs) return fail(BSSN_EINVAL, "NULL argument");
+  if (cudaError_t ed = drain_out(ctx)) return cuda_fail(ed, "wait for the state read-back");
   const double* src = d_state ? (const double*)d_state : ctx->yn;
   double* out = (double*)d_rhs;
   cudaError_t e;
@@ -512,6 +543,7 @@ static bssn_status run_stage_mixed(bssn_ctx* ctx, int src, int mode, int out, do
 bssn_status bssn_rk4_step(bssn_ctx* ctx, int32_t nsteps) {
   if (!ctx) return fail(BSSN_EINVAL, "ctx is NULL");
   if (nsteps < 0) return fail(BSSN_EINVAL, "nsteps < 0");
+  if (cudaError_t ed = drain_out(ctx)) return cuda_fail(ed, "wait for the state read-back");
   const double dt = ctx->p.dt;
   const bool mixed = ctx->p.precision == BSSN_MIXED;
   for (int s = 0; s < nsteps; s++) {
@@ -560,6 +592,7 @@ static double* adm_scratch(bssn_ctx* ctx) {
 
 bssn_status bssn_constraints(bssn_ctx* ctx, double out[16]) {
   if (!ctx || !out) return fail(BSSN_EINVAL, "NULL argument");
+  if (cudaError_t ed = drain_out(ctx)) return cuda_fail(ed, "wait for the state read-back");
   if (bssn_status es = check_err(ctx)) return es;
   cudaError_t e = pull_punct(ctx);
   if (e != cudaSuccess) return cuda_fail(e, "punctures");
@@ -576,6 +609,7 @@ bssn_status bssn_constraints(bssn_ctx* ctx, double out[16]) {
 
 bssn_status bssn_adm_integrals(bssn_ctx* ctx, double* d_dens, double out[8]) {
   if (!ctx || !out) return fail(BSSN_EINVAL, "NULL argument");
+  if (cudaError_t ed = drain_out(ctx)) return cuda_fail(ed, "wait for the state read-back");
   if (bssn_status es = check_err(ctx)) return es;
   cudaError_t e = pull_punct(ctx);
   if (e != cudaSuccess) return cuda_fail(e, "punctures");
@@ -595,6 +629,7 @@ bssn_status bssn_adm_integrals(bssn_ctx* ctx, double* d_dens, double out[8]) {
 
 bssn_status bssn_psi4(bssn_ctx* ctx, double* d_out) {
   if (!ctx || !d_out) return fail(BSSN_EINVAL, "NULL argument");
+  if (cudaError_t ed = drain_out(ctx)) return cuda_fail(ed, "wait for the state read-back");
   cudaError_t e = launch_psi4(ctx->g, ctx->yn, d_out, ctx->stream, adm_scratch(ctx));
   if (e != cudaSuccess) return cuda_fail(e, "psi4");
   return BSSN_OK;
@@ -646,10 +681,28 @@ static cudaError_t copy_state(bssn_ctx* ctx, double* host, bool to_device) {
   return e;
 }
 
+// Read-back area of bssn_get_state_async, disjoint from the staging area of
+// the uploads (so that a copy out and the next upload can run at the same
+// time): float64: s2; mixed: the float buffers m[2] and m[0] (12 fields of
+// doubles each; m[0], the float shadow of y_n, is rebuilt before the next
+// step).  Returns the number of areas (1 or 2) and their field counts.
+static int out_areas(bssn_ctx* ctx, double* area[2], int nf[2]) {
+  if (ctx->p.precision == BSSN_FP64) {
+    area[0] = ctx->s2;
+    nf[0] = NF;
+    return 1;
+  }
+  area[0] = (double*)ctx->m32[2];
+  area[1] = (double*)ctx->m32[0];
+  nf[0] = nf[1] = NF / 2;
+  return 2;
+}
+
 bssn_status bssn_get_state(bssn_ctx* ctx, double* host, double* t) {
   if (!ctx || !host) return fail(BSSN_EINVAL, "NULL argument");
   if (bssn_status es = check_err(ctx)) return es;
-  cudaError_t e = copy_state(ctx, host, false);
+  cudaError_t e = drain_out(ctx);
+  if (e == cudaSuccess) e = copy_state(ctx, host, false);
   if (e != cudaSuccess) return cuda_fail(e, "get_state copy");
   e = cudaStreamSynchronize(ctx->stream);
   if (e != cudaSuccess) return cuda_fail(e, "get_state sync");
@@ -658,14 +711,52 @@ bssn_status bssn_get_state(bssn_ctx* ctx, double* host, double* t) {
 }
 
 bssn_status bssn_set_state(bssn_ctx* ctx, const double* host, double t) {
+  bssn_status st = bssn_set_state_async(ctx, host, t);
+  if (st != BSSN_OK) return st;
+  cudaError_t e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "set_state sync");
+  return BSSN_OK;
+}
+
+bssn_status bssn_set_state_async(bssn_ctx* ctx, const double* host, double t) {
   if (!ctx || !host) return fail(BSSN_EINVAL, "NULL argument");
   cudaError_t e = copy_state(ctx, const_cast<double*>(host), true);
   if (e != cudaSuccess) return cuda_fail(e, "set_state copy");
-  e = cudaStreamSynchronize(ctx->stream);
-  if (e != cudaSuccess) return cuda_fail(e, "set_state sync");
   ctx->t = t;
   ctx->shadow_valid = false;
   return BSSN_OK;
+}
+
+bssn_status bssn_get_state_async(bssn_ctx* ctx, double* host, double* t) {
+  if (!ctx || !host) return fail(BSSN_EINVAL, "NULL argument");
+  const Grid& g = ctx->g;
+  const size_t per = (size_t)g.sx * g.sy * g.sz;
+  double* area[2];
+  int nf[2];
+  const int na = out_areas(ctx, area, nf);
+  cudaError_t e = drain_out(ctx);  // the previous copy out of these areas is done
+  for (int q = 0, f0 = 0; q < na && e == cudaSuccess; f0 += nf[q], q++)
+    e = launch_repack(g, area[q], ctx->yn, f0, nf[q], false, ctx->stream);
+  if (ctx->p.precision == BSSN_MIXED) ctx->shadow_valid = false;
+  if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_out_ready, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->cstream, ctx->ev_out_ready, 0);
+  for (int q = 0, f0 = 0; q < na && e == cudaSuccess; f0 += nf[q], q++)
+    e = cudaMemcpyAsync(host + per * f0, area[q], per * nf[q] * sizeof(double), cudaMemcpyDeviceToHost,
+                        ctx->cstream);
+  if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_out_done, ctx->cstream);
+  if (e != cudaSuccess) return cuda_fail(e, "get_state_async");
+  ctx->out_pending = true;
+  if (t) *t = ctx->t;
+  return BSSN_OK;
+}
+
+bssn_status bssn_wait_state(bssn_ctx* ctx) {
+  if (!ctx) return fail(BSSN_EINVAL, "ctx is NULL");
+  cudaError_t e = cudaStreamSynchronize(ctx->stream);
+  cudaError_t e2 = cudaStreamSynchronize(ctx->cstream);
+  if (e == cudaSuccess) e = e2;
+  if (e != cudaSuccess) return cuda_fail(e, "wait_state");
+  return check_err(ctx);
 }
 
 // Configurations: [0, tile_config_count()) the fused kernels;
@@ -696,6 +787,7 @@ bssn_status bssn_set_tile(bssn_ctx* ctx, int32_t cfg) {
 
 bssn_status bssn_autotune(bssn_ctx* ctx, int32_t reps, int32_t* best, double* ms_per_cfg) {
   if (!ctx || reps < 1) return fail(BSSN_EINVAL, "bad argument");
+  if (cudaError_t ed = drain_out(ctx)) return cuda_fail(ed, "wait for the state read-back");
   const bool mixed = ctx->p.precision == BSSN_MIXED;
   if (mixed && !ctx->shadow_valid) {
     cudaError_t e = launch_shadow(ctx->g, ctx->yn, ctx->m32[0], ctx->mw[0], ctx->stream);
