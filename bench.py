@@ -606,7 +606,7 @@ def main():
                          "the multi-evolution workloads, reported on their own lines")
     ap.add_argument("--tile", default=None, help="stage-kernel configuration name (default: autotune)")
     ap.add_argument("--members", type=int, default=64)
-    ap.add_argument("--requests", type=int, default=64)
+    ap.add_argument("--requests", type=int, default=256)
     ap.add_argument("--budget-gb", type=float, default=64.0)
     ap.add_argument("--capacity-mpts", type=float, default=None,
                     help="served: throughput estimate (M point-updates/s) that sets the arrival rate "

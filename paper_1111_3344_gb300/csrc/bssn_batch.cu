@@ -229,7 +229,7 @@ cudaError_t rebuild_work(bssn_batch* b) {
     W.bc_base[W.count] = bb;
     tb += (unsigned)D.tiles[0] * D.tiles[1] * D.tiles[2];
     const unsigned long long ng = ghost_count(M.g);
-    bb += (b->precision == BSSN_MIXED && !M.g.periodic) ? ng * NF : ng;
+    bb += ng;  // one thread per ghost point (every field)
     W.count++;
   }
   W.tile_base[W.count] = tb;

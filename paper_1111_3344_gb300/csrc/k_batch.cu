@@ -70,11 +70,16 @@ __global__ void __launch_bounds__(TX * TY * TZ, MINB)
       if constexpr (MIXED) {
         stage_point_mixed(sg, sa, ii, jj, kk);
       } else if constexpr (TX == 32) {
-        // members whose n0 is a multiple of 32: every warp is a full x-row, so
-        // the x-mixed second differences share first differences across
-        // lanes (the choice is uniform over the block's tile)
-        if (sg.n0 % 32 == 0) stage_point_fp64<32>(sg, sa, ii, jj, kk);
-        else stage_point_fp64<0>(sg, sa, ii, jj, kk);
+        // members whose tiles are all full (n0 a multiple of 32, n1 of TY, n2
+        // of TZ): every warp is a full x-row and every thread of the block is
+        // inside the grid, so the x-mixed second differences share first
+        // differences across lanes and D_y D_z across rows through shared
+        // memory (one barrier, reached by the whole block: the choice is
+        // uniform over the member)
+        if (sg.n0 % 32 == 0 && sg.n1 % TY == 0 && sg.n2 % TZ == 0)
+          stage_point_fp64<32, TY, TZ>(sg, sa, ii, jj, kk);
+        else
+          stage_point_fp64<0>(sg, sa, ii, jj, kk);
       } else {
         stage_point_fp64<0>(sg, sa, ii, jj, kk);
       }
@@ -103,10 +108,8 @@ __global__ void batch_boundary_kernel(const MemberDev* __restrict__ mem, const B
         periodic_point<double>(M.g, a.mode == MODE_LAST ? a.yn : a.out0, nullptr, q);
       }
     } else if constexpr (MIXED) {
-      const unsigned ng = ghost_count(M.g);
-      const int f = (int)(local / ng);
       const StageArgsMixed& a = M.amx[stage];
-      sommerfeld_point_mixed(M.g, a, a.kshell, (unsigned)(local - (unsigned long long)f * ng), f);
+      sommerfeld_point_mixed_all(M.g, a, a.kshell, (unsigned)local);
     } else {
       const StageArgs& a = M.a64[stage];
       sommerfeld_point_fp64(M.g, a, a.kshell, (unsigned)local);
@@ -148,16 +151,19 @@ cudaError_t launch_batch_stage(int cfg, bool mixed, const MemberDev* mem, const 
   const BatchCfg& c = k_bcfg[cfg];
   const void* fn = mixed ? c.kmx : c.k64;
   const int threads = c.tx * c.ty * c.tz;
+  // float64 full-block tiles exchange the first differences along z of 11
+  // fields over the block's rows and two halo rows on each side
+  const size_t smem = (!mixed && c.tx == 32) ? (size_t)11 * (c.ty + 4) * c.tz * 32 * sizeof(double) : 0;
   int dev = 0, sms = 0, per = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, threads, 0);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, threads, smem);
   if (e != cudaSuccess) return e;
   if (per < 1) per = 1;
   dim3 block(c.tx, c.ty, c.tz);
   dim3 grid((unsigned)(sms * per));
   void* args[] = {(void*)&mem, (void*)&wk, (void*)&stage};
-  return cudaLaunchKernel(fn, grid, block, args, 0, s);
+  return cudaLaunchKernel(fn, grid, block, args, smem, s);
 }
 
 cudaError_t launch_batch_boundary(bool mixed, const MemberDev* mem, const BatchWork* wk, int stage,

@@ -221,12 +221,13 @@ def test_server_budget_and_failure_isolation(torch_cuda):
 
 
 def test_batch_full_rows_fp64(torch_cuda):
-    """A float64 member whose x extent is a multiple of 32 takes the full-row
-    point function (first differences shared across the warp's lanes); next to
-    a member with a ragged x extent it still matches the oracle and itself
-    alone, bit for bit."""
+    """A float64 member whose tiles are all full (x extent a multiple of 32,
+    y and z of every tile shape) takes the full-block point function (first
+    differences shared across the warp's lanes and across rows through shared
+    memory); next to a member with ragged tiles it still matches the oracle and
+    itself alone, bit for bit."""
     from paper_1111_3344_gb300.bssn import Batch
-    rows = dict(n=(64, 12, 16), xmin=(-8.0, -1.5, -2.0), h=0.25, boundary="sommerfeld", conformal="W",
+    rows = dict(n=(64, 16, 12), xmin=(-8.0, -2.0, -1.5), h=0.25, boundary="sommerfeld", conformal="W",
                 slicing="1+log", shift="gamma-driver", eta=2.0, punctures=[(1.0, 0.05, 0.0, 0.0)],
                 precision="fp64", w_fp64_threshold=0.3)
     ragged = _members("fp64")[1]
