@@ -398,6 +398,9 @@ def run_batched(args):
         batch.set_initial_data(mid, "bl", bl)
         ids.append(mid)
     best, tile_ms = batch.autotune(reps=2)
+    if args.tile:
+        best = list(tile_ms).index(args.tile)
+        batch.set_tile(best)
     batch.step(args.warmup)
     batch.synchronize()
     start = torch.cuda.Event(enable_timing=True)
@@ -415,6 +418,7 @@ def run_batched(args):
             "dtype": "f64" if args.precision == "fp64" else "f32+f64", "data": "synthetic",
             "config": {"workload": f"{len(params)} Brill-Lindquist binaries, grids {{48,64,96,128}}^3, seed 1111",
                        "interior_points": pts, "tile": list(tile_ms)[best],
+                       "autotune_ms_stage1": {k: round(v, 3) for k, v in tile_ms.items() if v >= 0},
                        "launches_per_step": 8, "graph": True}}
     print(json.dumps(line))
     batch.close()

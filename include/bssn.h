@@ -290,10 +290,12 @@ const char* bssn_tile_name(int32_t cfg); /* e.g. "32x8x1/1"; "" when out of rang
 bssn_status bssn_set_tile(bssn_ctx* ctx, int32_t cfg);
 
 /* Autotuner: time every tile configuration on this evolution's live state
- * (reps launches of the first RK4 stage each, which leaves y_n unchanged),
- * select the fastest for the context and return it in *best; ms_per_cfg (may be
- * NULL, else bssn_tile_count() entries) receives the mean milliseconds per
- * launch.  Synchronises the stream. */
+ * (reps launches each of the first two RK4 stages, which leave y_n unchanged;
+ * the next step overwrites the stage buffers and k-sum they write), select the
+ * fastest for the context and return it in *best; ms_per_cfg (may be NULL,
+ * else bssn_tile_count() entries) receives the mean milliseconds per stage
+ * launch (INFINITY for configurations this context cannot use).  Synchronises
+ * the stream. */
 bssn_status bssn_autotune(bssn_ctx* ctx, int32_t reps, int32_t* best, double* ms_per_cfg);
 
 /* ------------------------------------------------------------ batches
@@ -327,12 +329,19 @@ bssn_status bssn_batch_get_state(bssn_batch* b, int32_t member, double* host, do
 /* Advance every active member nsteps RK4 steps (asynchronous). */
 bssn_status bssn_batch_step(bssn_batch* b, int32_t nsteps);
 bssn_status bssn_batch_constraints(bssn_batch* b, int32_t member, double out[16]); /* synchronises */
+/* Tile configurations of the persistent stage kernel.  The last one,
+ * "tma32x4x1/2", stages W, gt_ij and alpha of each 32x4x1 tile in shared
+ * memory by tensor loads (mixed batches only; BSSN_EINVAL for float64).  A
+ * tensor-load wait that gives up (bounded) makes the next
+ * bssn_batch_get_state or bssn_batch_constraints return BSSN_ETIMEOUT. */
 int32_t bssn_batch_tile_count(void);
 const char* bssn_batch_tile_name(int32_t cfg);
 bssn_status bssn_batch_set_tile(bssn_batch* b, int32_t cfg);
-/* Autotuner for the persistent stage kernel: times each tile shape on the
- * batch's live members (first-stage launches, which leave y_n unchanged) and
- * selects the fastest. */
+/* Autotuner for the persistent stage kernel: times each usable tile shape on
+ * the batch's live members (launches of the first two stages, which leave y_n
+ * unchanged) and selects the fastest; ms_per_cfg (bssn_batch_tile_count
+ * entries, may be NULL) gets the mean milliseconds per stage launch, -1 for
+ * the configurations the batch cannot use. */
 bssn_status bssn_batch_autotune(bssn_batch* b, int32_t reps, int32_t* best, double* ms_per_cfg);
 
 /* ------------------------------------------------------------- server

@@ -13,6 +13,9 @@ struct MemberDev {
   StageArgs a64[4];
   StageArgsMixed amx[4];
   int tiles[3];  // stage tiles per axis for the batch's current tile shape
+  // mixed: tensor map of each stage's input float buffer (TMA-staged batch
+  // kernel); 64-byte aligned, as the tensor loads require
+  CUtensorMap tmap[4];
 };
 
 // The active members and prefix sums of their work (rebuilt on the host when
@@ -26,12 +29,22 @@ struct BatchWork {
   unsigned long long bc_base[BATCH_MAX + 1];
 };
 
+// Tile configurations of the batched stage: [0, count - 1) fused kernels
+// (both precisions); count - 1 the TMA-staged kernel (mixed only).
 int batch_tile_config_count();
 const char* batch_tile_config_name(int c);
 void batch_tile_shape(int c, int& tx, int& ty, int& tz);
+bool batch_tile_is_tma(int c);
+int batch_default_tile(bool mixed);
 // Persistent stage kernel over every active member's tiles (grid = blocks).
+// err: device error word (a bounded wait of the TMA kernel gave up).
 cudaError_t launch_batch_stage(int cfg, bool mixed, const MemberDev* mem, const BatchWork* wk,
-                               int stage, cudaStream_t s);
+                               int stage, int* err, cudaStream_t s);
+// TMA-staged form (k_batch_tma.cu)
+void batch_tma_tile_shape(int& tx, int& ty, int& tz);
+cudaError_t prepare_batch_stage_tma();
+cudaError_t launch_batch_stage_tma(const MemberDev* mem, const BatchWork* wk, int stage, int* err,
+                                   cudaStream_t s);
 // Boundary of every active member after a stage (Sommerfeld or periodic).
 cudaError_t launch_batch_boundary(bool mixed, const MemberDev* mem, const BatchWork* wk, int stage,
                                   cudaStream_t s);

@@ -802,28 +802,39 @@ bssn_status bssn_autotune(bssn_ctx* ctx, int32_t reps, int32_t* best, double* ms
   double best_ms = 1e300;
   int best_c = 0;
   bssn_status st = BSSN_OK;
-  // the first stage leaves y_n (and its float shadow) unchanged
+  // Each repetition times the first two stages (first: y_n -> stage buffer 1
+  // and k-sum; second: stage buffer 1 -> stage buffer 2, k-sum accumulated),
+  // which leave y_n (and its float shadow) unchanged; the next step
+  // overwrites what they wrote.  The second stage carries the combine's extra
+  // loads, which the first alone would not weigh.
   for (int c = 0; c < ncfg && st == BSSN_OK; c++) {
     if (!tile_usable(ctx, c)) {
       if (ms_per_cfg) ms_per_cfg[c] = INFINITY;
       continue;
     }
-    auto launch = [&]() -> cudaError_t {
+    auto launch1 = [&](int stage) -> cudaError_t {
+      const bool second = stage == 1;
       if (!mixed) {
         StageArgs a{};
-        a.src = ctx->yn; a.src0 = ctx->yn; a.yn = ctx->yn; a.out0 = ctx->s1; a.ksum = ctx->ks;
-        a.a_dt = 0.5 * ctx->p.dt; a.mode = MODE_FIRST;
+        a.src = second ? ctx->s1 : ctx->yn; a.src0 = ctx->yn; a.yn = ctx->yn;
+        a.out0 = second ? ctx->s2 : ctx->s1; a.ksum = ctx->ks;
+        a.a_dt = 0.5 * ctx->p.dt; a.mode = second ? MODE_MID : MODE_FIRST;
         return launch_stage_fp64(ctx->g, a, ctx->stream, c);
       }
+      const int q = second ? 1 : 0, o = second ? 2 : 1;
       StageArgsMixed a{};
-      a.src = ctx->m32[0]; a.srcw = ctx->mw[0]; a.src0 = ctx->m32[0]; a.src0w = ctx->mw[0];
-      a.yn = ctx->yn; a.out0 = ctx->m32[1]; a.out0w = ctx->mw[1];
+      a.src = ctx->m32[q]; a.srcw = ctx->mw[q]; a.src0 = ctx->m32[0]; a.src0w = ctx->mw[0];
+      a.yn = ctx->yn; a.out0 = ctx->m32[o]; a.out0w = ctx->mw[o];
       a.ksum = ctx->ks32; a.ksumw = ctx->ksw; a.a_dt = 0.5 * ctx->p.dt; a.a_dtf = (float)a.a_dt;
-      a.w_thr = ctx->p.w_fp64_threshold; a.mode = MODE_FIRST;
-      if (c == tile_config_count()) return launch_stage_mixed_tma(ctx->g, a, ctx->tmap[0], ctx->err, ctx->stream);
+      a.w_thr = ctx->p.w_fp64_threshold; a.mode = second ? MODE_MID : MODE_FIRST;
+      if (c == tile_config_count()) return launch_stage_mixed_tma(ctx->g, a, ctx->tmap[q], ctx->err, ctx->stream);
       if (c > tile_config_count())
         return launch_stage_mixed_split(ctx->g, a, ctx->dr, ctx->stream, c - tile_config_count() - 1);
       return launch_stage_mixed(ctx->g, a, ctx->stream, c);
+    };
+    auto launch = [&]() -> cudaError_t {
+      cudaError_t r = launch1(0);
+      return r == cudaSuccess ? launch1(1) : r;
     };
     if ((e = launch()) != cudaSuccess) { st = cuda_fail(e, "autotune warm-up"); break; }
     cudaEventRecord(e0, ctx->stream);
@@ -833,7 +844,7 @@ bssn_status bssn_autotune(bssn_ctx* ctx, int32_t reps, int32_t* best, double* ms
     if (e != cudaSuccess) { st = cuda_fail(e, "autotune"); break; }
     float ms = 0.f;
     cudaEventElapsedTime(&ms, e0, e1);
-    const double per = ms / reps;
+    const double per = ms / (2.0 * reps);  // per stage launch
     if (ms_per_cfg) ms_per_cfg[c] = per;
     if (per < best_ms) { best_ms = per; best_c = c; }
   }

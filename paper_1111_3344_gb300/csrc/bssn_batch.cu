@@ -139,6 +139,8 @@ struct bssn_batch {
   std::vector<Member> m;
   MemberDev* d_mem;
   BatchWork* d_work;
+  int* d_err;          // error word of the TMA-staged kernel's bounded waits
+  bool tma_ok = true;  // every member's tensor maps could be encoded
   std::vector<MemberDev> h_mem;
   BatchWork h_work;
   bool work_dirty = true;
@@ -204,6 +206,7 @@ void fill_member_dev(bssn_batch* b, int id) {
       a.b_dt = b_dt[s];
       a.w_thr = M.p.w_fp64_threshold;
       a.mode = mode[s];
+      if (make_stage_tensor_map(M.g, a.src, &D.tmap[s]) != cudaSuccess) b->tma_ok = false;
     }
   }
 }
@@ -253,7 +256,7 @@ cudaError_t capture(bssn_batch* b) {
   if (e != cudaSuccess) return e;
   const bool mixed = b->precision == BSSN_MIXED;
   for (int s = 0; s < 4 && e == cudaSuccess; s++) {
-    e = launch_batch_stage(b->cfg, mixed, b->d_mem, b->d_work, s, b->stream);
+    e = launch_batch_stage(b->cfg, mixed, b->d_mem, b->d_work, s, b->d_err, b->stream);
     if (e == cudaSuccess) e = launch_batch_boundary(mixed, b->d_mem, b->d_work, s, b->stream);
   }
   cudaGraph_t g = nullptr;
@@ -280,6 +283,47 @@ cudaError_t after_state(bssn_batch* b, Member& M) {
 
 bool member_ok(bssn_batch* b, int id) { return b && id >= 0 && id < b->maxm && b->m[id].used; }
 
+bool tile_usable(const bssn_batch* b, int c) {
+  return !batch_tile_is_tma(c) || (b->precision == BSSN_MIXED && b->tma_ok);
+}
+
+// Switch the batch to tile configuration cfg (stream idle): member tables
+// refilled and uploaded, work list and graph rebuilt at the next step.
+cudaError_t apply_cfg(bssn_batch* b, int cfg) {
+  cudaError_t e = batch_tile_is_tma(cfg) ? prepare_batch_stage_tma() : cudaSuccess;
+  if (e != cudaSuccess) return e;
+  b->cfg = cfg;
+  for (int id = 0; id < b->maxm && e == cudaSuccess; id++)
+    if (b->m[id].used) {
+      fill_member_dev(b, id);
+      e = upload_member(b, id);
+    }
+  b->work_dirty = true;
+  if (b->exec) {
+    cudaGraphExecDestroy(b->exec);
+    b->exec = nullptr;
+  }
+  if (b->graph) {
+    cudaGraphDestroy(b->graph);
+    b->graph = nullptr;
+  }
+  return e;
+}
+
+// After a synchronisation: did a stage kernel give up waiting for its tile?
+// (the states it touched are invalid); the word is cleared.
+bssn_status check_batch_err(bssn_batch* b) {
+  int h = 0;
+  cudaError_t e = cudaMemcpyAsync(&h, b->d_err, sizeof(int), cudaMemcpyDeviceToHost, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) return bcuda(e, "batch error word");
+  if (h) {
+    cudaMemsetAsync(b->d_err, 0, sizeof(int), b->stream);
+    return bfail(BSSN_ETIMEOUT, "a batched stage kernel gave up waiting for its shared-memory tile; the states are invalid");
+  }
+  return BSSN_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -296,7 +340,7 @@ size_t bssn_batch_member_bytes(const bssn_params* p) {
 
 size_t bssn_batch_table_bytes(int32_t max_members) {
   if (max_members < 1 || max_members > BATCH_MAX) return 0;
-  return aup(sizeof(MemberDev) * (size_t)max_members) + aup(sizeof(BatchWork));
+  return aup(sizeof(MemberDev) * (size_t)max_members) + aup(sizeof(BatchWork)) + aup(sizeof(int));
 }
 
 bssn_status bssn_batch_create(int32_t precision, int32_t max_members, void* d_pool, size_t pool_bytes,
@@ -323,7 +367,11 @@ bssn_status bssn_batch_create(int32_t precision, int32_t max_members, void* d_po
   memset(&b->h_work, 0, sizeof(BatchWork));
   b->d_mem = (MemberDev*)b->pool;
   b->d_work = (BatchWork*)(b->pool + aup(sizeof(MemberDev) * (size_t)max_members));
-  cudaError_t e = rebuild_work(b);
+  b->d_err = (int*)((char*)b->d_work + aup(sizeof(BatchWork)));
+  b->cfg = batch_default_tile(precision == BSSN_MIXED);
+  cudaError_t e = batch_tile_is_tma(b->cfg) ? prepare_batch_stage_tma() : cudaSuccess;
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->d_err, 0, sizeof(int), b->stream);
+  if (e == cudaSuccess) e = rebuild_work(b);
   if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
   if (e != cudaSuccess) {
     delete b;
@@ -363,6 +411,11 @@ bssn_status bssn_batch_add(bssn_batch* b, const bssn_params* p, int32_t* member)
   b->m[id] = M;
   fill_member_dev(b, id);
   cudaError_t e = upload_member(b, id);
+  // a member whose tensor maps could not be encoded: fall back to a fused tile
+  if (e == cudaSuccess && !b->tma_ok && batch_tile_is_tma(b->cfg)) {
+    e = cudaStreamSynchronize(b->stream);
+    if (e == cudaSuccess) e = apply_cfg(b, 0);
+  }
   if (e != cudaSuccess) return bcuda(e, "batch add");
   *member = id;
   return BSSN_OK;
@@ -446,6 +499,7 @@ bssn_status bssn_batch_get_state(bssn_batch* b, int32_t id, double* host, double
                                     (size_t)NF * g.sz * g.sy, cudaMemcpyDeviceToHost, b->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
   if (e != cudaSuccess) return bcuda(e, "batch get_state");
+  if (bssn_status es = check_batch_err(b)) return es;
   if (t) *t = M.t;
   return BSSN_OK;
 }
@@ -485,7 +539,7 @@ bssn_status bssn_batch_constraints(bssn_batch* b, int32_t id, double out[16]) {
   if (e == cudaSuccess) e = cudaMemcpyAsync(out, dout, 16 * sizeof(double), cudaMemcpyDeviceToHost, b->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
   if (e != cudaSuccess) return bcuda(e, "batch constraints");
-  return BSSN_OK;
+  return check_batch_err(b);
 }
 
 int32_t bssn_batch_tile_count(void) { return batch_tile_config_count(); }
@@ -495,23 +549,10 @@ bssn_status bssn_batch_set_tile(bssn_batch* b, int32_t cfg) {
   if (!b) return bfail(BSSN_EINVAL, "batch is NULL");
   std::lock_guard<std::mutex> lk(b->mu);
   if (cfg < 0 || cfg >= batch_tile_config_count()) return bfail(BSSN_EINVAL, "tile config out of range");
+  if (!tile_usable(b, cfg)) return bfail(BSSN_EINVAL, "the TMA-staged tile is for mixed batches");
   cudaError_t e = cudaStreamSynchronize(b->stream);
+  if (e == cudaSuccess) e = apply_cfg(b, cfg);
   if (e != cudaSuccess) return bcuda(e, "set tile");
-  b->cfg = cfg;
-  for (int id = 0; id < b->maxm; id++)
-    if (b->m[id].used) {
-      fill_member_dev(b, id);
-      if ((e = upload_member(b, id)) != cudaSuccess) return bcuda(e, "set tile upload");
-    }
-  b->work_dirty = true;
-  if (b->exec) {
-    cudaGraphExecDestroy(b->exec);
-    b->exec = nullptr;
-  }
-  if (b->graph) {
-    cudaGraphDestroy(b->graph);
-    b->graph = nullptr;
-  }
   return BSSN_OK;
 }
 
@@ -529,22 +570,32 @@ bssn_status bssn_batch_autotune(bssn_batch* b, int32_t reps, int32_t* best, doub
   }
   bssn_status st = BSSN_OK;
   for (int c = 0; c < n && st == BSSN_OK; c++) {
+    if (!tile_usable(b, c)) {
+      if (ms_per_cfg) ms_per_cfg[c] = -1.0;
+      continue;
+    }
     if ((st = bssn_batch_set_tile(b, c)) != BSSN_OK) break;
     std::lock_guard<std::mutex> lk(b->mu);
     if (b->work_dirty && (e = rebuild_work(b)) != cudaSuccess) { st = bcuda(e, "autotune"); break; }
-    // stage 0 writes only stage buffers and the k-sum: y_n is left unchanged
+    // stages 0 and 1 write only stage buffers and the k-sum (y_n is left
+    // unchanged, the next step overwrites them); the second stage carries the
+    // combine's extra loads, which the first alone would not weigh
     const bool mixed = b->precision == BSSN_MIXED;
-    e = launch_batch_stage(c, mixed, b->d_mem, b->d_work, 0, b->stream);
+    auto pair = [&]() -> cudaError_t {
+      cudaError_t r = launch_batch_stage(c, mixed, b->d_mem, b->d_work, 0, b->d_err, b->stream);
+      return r == cudaSuccess ? launch_batch_stage(c, mixed, b->d_mem, b->d_work, 1, b->d_err, b->stream) : r;
+    };
+    e = pair();
     cudaEventRecord(e0, b->stream);
-    for (int r = 0; r < reps && e == cudaSuccess; r++)
-      e = launch_batch_stage(c, mixed, b->d_mem, b->d_work, 0, b->stream);
+    for (int r = 0; r < reps && e == cudaSuccess; r++) e = pair();
     cudaEventRecord(e1, b->stream);
     if (e == cudaSuccess) e = cudaEventSynchronize(e1);
     if (e != cudaSuccess) { st = bcuda(e, "autotune"); break; }
     float ms = 0.f;
     cudaEventElapsedTime(&ms, e0, e1);
-    if (ms_per_cfg) ms_per_cfg[c] = ms / reps;
-    if (ms / reps < best_ms) { best_ms = ms / reps; best_c = c; }
+    const double per = ms / (2.0 * reps);  // per stage launch
+    if (ms_per_cfg) ms_per_cfg[c] = per;
+    if (per < best_ms) { best_ms = per; best_c = c; }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);

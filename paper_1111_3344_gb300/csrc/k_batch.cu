@@ -46,18 +46,26 @@ __global__ void __launch_bounds__(TX * TY * TZ, MINB)
   const int tid = threadIdx.x + TX * (threadIdx.y + TY * threadIdx.z);
   const unsigned total = wk->total_tiles;
   const int count = wk->count;
+  // thread 0: tile range [t_lo, t_hi) of the member whose arguments are in
+  // shared memory (a block's next tile, gridDim.x further on, is nearly
+  // always in the same member: no search and no copy then)
+  unsigned t_lo = 1u, t_hi = 0u;
   for (unsigned t = blockIdx.x; t < total; t += gridDim.x) {
     __syncthreads();  // the previous tile is done with the shared arguments
     if (tid == 0) {
-      const int slot = find_member(wk->tile_base, count, t);
-      const MemberDev& M = mem[wk->member[slot]];
-      sg = M.g;
-      if constexpr (MIXED) sa = M.amx[stage];
-      else sa = M.a64[stage];
-      stile[0] = M.tiles[0];
-      stile[1] = M.tiles[1];
-      stile[2] = M.tiles[2];
-      slocal = t - wk->tile_base[slot];
+      if (t < t_lo || t >= t_hi) {
+        const int slot = find_member(wk->tile_base, count, t);
+        const MemberDev& M = mem[wk->member[slot]];
+        sg = M.g;
+        if constexpr (MIXED) sa = M.amx[stage];
+        else sa = M.a64[stage];
+        stile[0] = M.tiles[0];
+        stile[1] = M.tiles[1];
+        stile[2] = M.tiles[2];
+        t_lo = wk->tile_base[slot];
+        t_hi = wk->tile_base[slot + 1];
+      }
+      slocal = t - t_lo;
     }
     __syncthreads();
     unsigned lt = slocal;
@@ -134,20 +142,33 @@ static const BatchCfg k_bcfg[] = {
 };
 #undef BCFG
 
-int batch_tile_config_count() { return (int)(sizeof(k_bcfg) / sizeof(k_bcfg[0])); }
+constexpr int N_FUSED = (int)(sizeof(k_bcfg) / sizeof(k_bcfg[0]));
+
+int batch_tile_config_count() { return N_FUSED + 1; }
+// Default tile of a new batch (the serving loop keeps it): the fastest
+// configuration of the 64-binary batched workload on GB300 -- the TMA-staged
+// kernel for mixed batches, 32x4x1/3 for float64 ones.
+int batch_default_tile(bool mixed) { return mixed ? N_FUSED : 2; }
+bool batch_tile_is_tma(int c) { return c == N_FUSED; }
 const char* batch_tile_config_name(int c) {
-  return (c >= 0 && c < batch_tile_config_count()) ? k_bcfg[c].name : "";
+  if (c == N_FUSED) return "tma32x4x1/2";
+  return (c >= 0 && c < N_FUSED) ? k_bcfg[c].name : "";
 }
 void batch_tile_shape(int c, int& tx, int& ty, int& tz) {
-  if (c < 0 || c >= batch_tile_config_count()) c = 0;
+  if (c == N_FUSED) {
+    batch_tma_tile_shape(tx, ty, tz);
+    return;
+  }
+  if (c < 0 || c >= N_FUSED) c = 0;
   tx = k_bcfg[c].tx;
   ty = k_bcfg[c].ty;
   tz = k_bcfg[c].tz;
 }
 
 cudaError_t launch_batch_stage(int cfg, bool mixed, const MemberDev* mem, const BatchWork* wk,
-                               int stage, cudaStream_t s) {
-  if (cfg < 0 || cfg >= batch_tile_config_count()) cfg = 0;
+                               int stage, int* err, cudaStream_t s) {
+  if (cfg == N_FUSED && mixed) return launch_batch_stage_tma(mem, wk, stage, err, s);
+  if (cfg < 0 || cfg >= N_FUSED) cfg = 0;
   const BatchCfg& c = k_bcfg[cfg];
   const void* fn = mixed ? c.kmx : c.k64;
   const int threads = c.tx * c.ty * c.tz;

@@ -1,0 +1,96 @@
+// Shared-memory tile of the TMA-staged mixed stage kernels (single grid:
+// k_stage_tma.cu; batched: k_batch_tma.cu): tile shape, the staged fields,
+// the accessor that reads them from shared memory, and the bounded mbarrier
+// wait.
+//
+// A block owns TTX x TTY x TTZ interior points.  One cp.async.bulk.tensor load
+// per staged field brings the field's box over the tile plus three ghost
+// layers on every side (BXP x BYP x BZP floats; BXP rounded up so that a box
+// row is a multiple of 16 bytes).  The staged fields are the eight with second
+// derivatives and the widest stencils: W, the six gt_ij and alpha.
+#pragma once
+#include <cuda.h>
+
+#include "stage_point.cuh"
+
+namespace bssn {
+
+constexpr int TTX = 32, TTY = 4, TTZ = 1;
+constexpr int BXP = 40;            // box extent in x: TTX + 6 rounded up to a multiple of 4 floats
+constexpr int BYP = TTY + 2 * GH;  // 10
+constexpr int BZP = TTZ + 2 * GH;  // 7
+constexpr int BOXF = BXP * BYP * BZP;             // floats of one field's box (2800)
+constexpr int SLOTF = (BOXF + 31) / 32 * 32;      // slot stride: 128-byte aligned boxes
+constexpr int NSTAGED = 8;
+constexpr unsigned STAGED_BYTES = NSTAGED * BOXF * sizeof(float);  // bytes the copies deliver
+constexpr int SMEM_BYTES = NSTAGED * SLOTF * (int)sizeof(float) + 128;  // + alignment slack
+constexpr long long WAIT_LIMIT = 1LL << 24;
+
+__host__ __device__ __forceinline__ int staged_field(int s) {
+  return s == 0 ? F_CHI : (s <= 6 ? F_GT + (s - 1) : F_ALP);
+}
+__device__ __forceinline__ int staged_slot(int f) {
+  return f == F_CHI ? 0 : ((f >= F_GT && f < F_GT + 6) ? 1 + (f - F_GT) : (f == F_ALP ? 7 : -1));
+}
+
+// Accessor: staged fields from the shared box, the others from global.
+struct TileAcc {
+  const float* __restrict__ st;
+  long long id, fs, sd[3];
+  const float* sm;  // shared address of this point in slot 0
+  __device__ __forceinline__ const float* ptr(int f) const {
+    const int sl = staged_slot(f);
+    return sl >= 0 ? sm + sl * SLOTF : st + (long long)f * fs + id;
+  }
+  __device__ __forceinline__ long long s(int f, int d) const {
+    return staged_slot(f) >= 0 ? (d == 0 ? 1 : (d == 1 ? BXP : BXP * BYP)) : sd[d];
+  }
+  template <typename T>
+  __device__ __forceinline__ T ld(int f, const float* p) const {
+    return staged_slot(f) >= 0 ? T(*p) : T(__ldg(p));
+  }
+};
+
+__device__ __forceinline__ unsigned smem_addr(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity, long long limit) {
+  for (long long it = 0; it < limit; it++) {
+    unsigned done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void mbar_init(unsigned bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// Thread 0: arm the barrier for the staged bytes and issue one tensor load per
+// staged field, box origin (x0, y0, z0) in stored coordinates (the interior
+// start of the tile minus the ghost width; x0 a multiple of 32, so the
+// innermost offset is a multiple of 16 bytes).
+__device__ __forceinline__ void issue_staged_loads(const void* tmap, unsigned bar, float* smem, int x0, int y0,
+                                                   int z0) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(STAGED_BYTES)
+               : "memory");
+#pragma unroll
+  for (int s = 0; s < NSTAGED; s++) {
+    const int f = staged_field(s);
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_addr(smem + s * SLOTF)),
+        "l"(reinterpret_cast<unsigned long long>(tmap)), "r"(x0), "r"(y0), "r"(z0), "r"(f), "r"(bar)
+        : "memory");
+  }
+}
+
+}  // namespace bssn

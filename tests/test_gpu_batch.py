@@ -250,3 +250,49 @@ def test_batch_full_rows_fp64(torch_cuda):
     want = O.rk4(cfg, O.initial_data(cfg, "bl", bl_params(ragged)), 2)
     assert normwise_errors(mix.get_state(ids[1])[0], want).max() <= 1e-11
     mix.close()
+
+
+def test_batch_tma_tile_matches_single_grid_tma(torch_cuda):
+    """The TMA-staged batched kernel (mixed): each member's state is the same
+    bit for bit alone and in the mix, and matches the single-grid evolution on
+    the TMA-staged kernel to the mixed parity bar (the same per-point source,
+    compiled into two kernels whose floating-point contractions may differ);
+    the float64 batch refuses the tile."""
+    from paper_1111_3344_gb300 import bssn as B
+    n_cfg = B.load().bssn_batch_tile_count()
+    names = [B.load().bssn_batch_tile_name(c).decode() for c in range(n_cfg)]
+    tma = names.index("tma32x4x1/2")
+    cases = _members("mixed")
+    steps = 3
+    mix = B.Batch("mixed", pool_bytes=1 << 30)
+    ids = [mix.add(gpu_params(c)) for c in cases]
+    for mid, c in zip(ids, cases):
+        _load(mix, mid, c)
+    mix.set_tile(tma)
+    mix.step(steps)
+    single_tma = [B.bssn_tile_name(c) for c in range(B.bssn_tile_count())].index("tma32x4x1/2")
+    for mid, c in zip(ids, cases):
+        got, _ = mix.get_state(mid)
+        evo = B.Evolution(gpu_params(c))
+        kind, p = _initial(c)
+        if kind == "state":
+            evo.set_state(p, 0.0)
+        else:
+            evo.set_initial_data(kind, p)
+        B.bssn_set_tile(evo.ctx, single_tma)
+        evo.rk4_step(steps)
+        e = normwise_errors(got, evo.get_state()[0])
+        assert e.max() <= 1e-4, (c["n"], e.max())
+        evo.close()
+        alone = B.Batch("mixed", pool_bytes=1 << 29)
+        aid = alone.add(gpu_params(c))
+        _load(alone, aid, c)
+        alone.set_tile(tma)
+        alone.step(steps)
+        assert np.array_equal(alone.get_state(aid)[0], got)
+        alone.close()
+    mix.close()
+    f64 = B.Batch("fp64", pool_bytes=1 << 28)
+    with pytest.raises(Exception):
+        f64.set_tile(tma)
+    f64.close()
