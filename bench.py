@@ -297,7 +297,8 @@ def run_ours(args):
     # the library's copy stream while step n+1's state is uploaded
     host_out = [torch.empty(evo.shape, dtype=torch.float64, pin_memory=True).numpy() for _ in range(2)]
     host_in[...], _ = evo.get_state()
-    e2e_steps = max(2, min(args.steps, 10))
+    evo.enable_copy_staging()  # the copies overlap the steps as well as each other
+    e2e_steps = max(2, args.steps)
     barrier(world)
     t0 = time.perf_counter()
     for s in range(e2e_steps):
@@ -355,7 +356,8 @@ def run_ours(args):
         "rhs_evaluations_per_s": 4.0 * value * 1e6,  # four right-hand sides per point-update
         "e2e": {"value": e2e_value, "unit": "Mpoint-updates/s", "h2d_bytes_per_step": nbytes,
                 "d2h_bytes_per_step": nbytes, "steps": e2e_steps,
-                "copies": "pinned; the read-back of step n overlaps the upload of step n+1"},
+                "copies": "pinned; device staging areas: the upload of step n+1 and the read-back "
+                          "of step n overlap each other and the steps"},
         # the split mixed stage is two kernels per stage (stencils, algebra)
         "gpu_launches": stage_n * (2 if B.bssn_tile_name(tile).startswith("split") else 1) + bc_n,
         "clocks": clk,

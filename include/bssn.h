@@ -278,6 +278,22 @@ bssn_status bssn_set_state_async(bssn_ctx* ctx, const double* host_state, double
 bssn_status bssn_get_state_async(bssn_ctx* ctx, double* host_state, double* t);
 bssn_status bssn_wait_state(bssn_ctx* ctx);
 
+/* Optional staging areas for the asynchronous copies (no counterpart in the
+ * paper).
+ *  - d_mem: caller-owned device memory, 256-byte aligned, at least
+ *    bssn_staging_bytes(p) bytes: an upload area and a read-back area, each the
+ *    state in the host layout.  No kernel of a step touches them.
+ *  - With them bound, bssn_set_state_async copies on an upload stream of the
+ *    library while the context's stream may still be stepping, and repacks into
+ *    y_n in stream order.  bssn_get_state_async repacks into the read-back area
+ *    and copies from there on the copy stream.  The copies of a host loop
+ *    (upload, step, read back) then overlap the steps as well as each other.
+ *  - d_mem = NULL unbinds.  The call synchronises every stream of the context.
+ *  - bssn_staging_bytes is host only; it returns 0 on bad p.
+ *  - EINVAL on misalignment; ENOMEM if bytes is too small. */
+size_t bssn_staging_bytes(const bssn_params* p);
+bssn_status bssn_set_staging(bssn_ctx* ctx, void* d_mem, size_t bytes);
+
 /* Stage-kernel tile configurations: block shape (points along x, y, z) and the
  * minimum resident blocks per SM given to the compiler.  The last ones are for
  * the mixed path only: "tma32x4x1/2" stages the second-differenced fields in

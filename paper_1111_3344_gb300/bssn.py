@@ -130,6 +130,8 @@ _SIGS = [
     ("bssn_get_state_async", [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     ("bssn_set_state_async", [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double], ctypes.c_int),
     ("bssn_wait_state", [ctypes.c_void_p], ctypes.c_int),
+    ("bssn_staging_bytes", [ctypes.c_void_p], ctypes.c_size_t),
+    ("bssn_set_staging", [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t], ctypes.c_int),
     ("bssn_profile", [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     ("bssn_set_adm", [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double], ctypes.c_int),
     ("bssn_set_punctures", [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int32], ctypes.c_int),
@@ -411,6 +413,20 @@ class Evolution:
             self.close()
         except Exception:
             pass
+
+    def enable_copy_staging(self):
+        """Bind device staging areas (torch-owned) so that the asynchronous
+        host copies overlap the steps (bssn_set_staging)."""
+        p = self.params.c()
+        n = int(load().bssn_staging_bytes(ctypes.byref(p)))
+        if n == 0:
+            raise BssnError(1, load().bssn_last_error().decode())
+        self.staging = self.torch.empty(n, dtype=self.torch.uint8, device=self.device)
+        _check(load().bssn_set_staging(ctypes.c_void_p(self.ctx), ctypes.c_void_p(self.staging.data_ptr()), n))
+
+    def disable_copy_staging(self):
+        _check(load().bssn_set_staging(ctypes.c_void_p(self.ctx), None, 0))
+        self.staging = None
 
     # register helpers (marshalling between host arrays and the padded layout)
     @property

@@ -173,6 +173,16 @@ struct bssn_ctx {
   cudaStream_t cstream;
   cudaEvent_t ev_out_ready, ev_out_done;
   bool out_pending;
+  // caller-owned staging areas for the host copies (bssn_set_staging): the
+  // upload and read-back areas in the unpadded host layout, used by no
+  // kernel of a step, so that both copies overlap the steps; an upload
+  // stream; events: upload landed, upload area free again, read-back area
+  // free again (each recorded at least once when the flag is set)
+  double* stg_in;
+  double* stg_out;
+  cudaStream_t istream;
+  cudaEvent_t ev_in_ready, ev_in_free, ev_out_free;
+  bool in_used, out_used;
 };
 
 namespace {
@@ -275,16 +285,23 @@ bssn_status bssn_alloc(const bssn_params* p, void* d_mem, size_t bytes, void* cu
     for (int q = 0; q < 3 && ok; q++) ok = make_stage_tensor_map(g, ctx->m32[q], &ctx->tmap[q]) == cudaSuccess;
     ctx->tmap_ok = ok;
   }
-  ctx->cstream = nullptr;
-  ctx->ev_out_ready = ctx->ev_out_done = nullptr;
+  ctx->cstream = ctx->istream = nullptr;
+  ctx->ev_out_ready = ctx->ev_out_done = ctx->ev_in_ready = ctx->ev_in_free = ctx->ev_out_free = nullptr;
   ctx->out_pending = false;
+  ctx->stg_in = ctx->stg_out = nullptr;
+  ctx->in_used = ctx->out_used = false;
   if (cudaStreamCreateWithFlags(&ctx->cstream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&ctx->istream, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&ctx->ev_out_ready, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&ctx->ev_out_done, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->ev_in_ready, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->ev_in_free, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->ev_out_free, cudaEventDisableTiming) != cudaSuccess ||
       cudaMemsetAsync(ctx->err, 0, sizeof(int), ctx->stream) != cudaSuccess) {
-    if (ctx->ev_out_done) cudaEventDestroy(ctx->ev_out_done);
-    if (ctx->ev_out_ready) cudaEventDestroy(ctx->ev_out_ready);
+    for (cudaEvent_t ev : {ctx->ev_out_ready, ctx->ev_out_done, ctx->ev_in_ready, ctx->ev_in_free, ctx->ev_out_free})
+      if (ev) cudaEventDestroy(ev);
     if (ctx->cstream) cudaStreamDestroy(ctx->cstream);
+    if (ctx->istream) cudaStreamDestroy(ctx->istream);
     delete ctx;
     return fail(BSSN_ECUDA, "stream, events or error word init");
   }
@@ -304,11 +321,14 @@ bssn_status bssn_free(bssn_ctx* ctx) {
   if (!ctx) return fail(BSSN_EINVAL, "ctx is NULL");
   cudaError_t e = cudaStreamSynchronize(ctx->stream);
   cudaError_t e2 = cudaStreamSynchronize(ctx->cstream);
+  cudaError_t e3 = cudaStreamSynchronize(ctx->istream);
   if (e == cudaSuccess) e = e2;
+  if (e == cudaSuccess) e = e3;
   prof_clear(ctx);
-  cudaEventDestroy(ctx->ev_out_done);
-  cudaEventDestroy(ctx->ev_out_ready);
+  for (cudaEvent_t ev : {ctx->ev_out_ready, ctx->ev_out_done, ctx->ev_in_ready, ctx->ev_in_free, ctx->ev_out_free})
+    cudaEventDestroy(ev);
   cudaStreamDestroy(ctx->cstream);
+  cudaStreamDestroy(ctx->istream);
   delete ctx;
   if (e != cudaSuccess) return cuda_fail(e, "bssn_free");
   return BSSN_OK;
@@ -718,17 +738,78 @@ bssn_status bssn_set_state(bssn_ctx* ctx, const double* host, double t) {
   return BSSN_OK;
 }
 
+// Bytes of one staging area: the state in the unpadded host layout.
+static size_t stage_copy_bytes(const Grid& g) { return (size_t)NF * g.sx * g.sy * g.sz * sizeof(double); }
+
 bssn_status bssn_set_state_async(bssn_ctx* ctx, const double* host, double t) {
   if (!ctx || !host) return fail(BSSN_EINVAL, "NULL argument");
-  cudaError_t e = copy_state(ctx, const_cast<double*>(host), true);
+  cudaError_t e = cudaSuccess;
+  if (ctx->stg_in) {
+    // upload on the upload stream, into the staging area, while the library
+    // stream may still be stepping; then repacked into y_n in stream order
+    if (ctx->in_used) e = cudaStreamWaitEvent(ctx->istream, ctx->ev_in_free, 0);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(ctx->stg_in, host, stage_copy_bytes(ctx->g), cudaMemcpyHostToDevice, ctx->istream);
+    if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_in_ready, ctx->istream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->stream, ctx->ev_in_ready, 0);
+    if (e == cudaSuccess) e = launch_repack(ctx->g, ctx->stg_in, ctx->yn, 0, NF, true, ctx->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_in_free, ctx->stream);
+    if (e == cudaSuccess) ctx->in_used = true;
+  } else {
+    e = copy_state(ctx, const_cast<double*>(host), true);
+  }
   if (e != cudaSuccess) return cuda_fail(e, "set_state copy");
   ctx->t = t;
   ctx->shadow_valid = false;
   return BSSN_OK;
 }
 
+size_t bssn_staging_bytes(const bssn_params* p) {
+  std::string why;
+  if (!validate(p, why)) {
+    fail(BSSN_EINVAL, why);
+    return 0;
+  }
+  return 2 * align_up(stage_copy_bytes(make_grid(p)));
+}
+
+bssn_status bssn_set_staging(bssn_ctx* ctx, void* d_mem, size_t bytes) {
+  if (!ctx) return fail(BSSN_EINVAL, "ctx is NULL");
+  cudaError_t e = cudaStreamSynchronize(ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->cstream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->istream);
+  if (e != cudaSuccess) return cuda_fail(e, "set_staging sync");
+  ctx->in_used = ctx->out_used = false;
+  if (!d_mem) {
+    ctx->stg_in = ctx->stg_out = nullptr;
+    return BSSN_OK;
+  }
+  const size_t area = align_up(stage_copy_bytes(ctx->g));
+  if (((uintptr_t)d_mem) % ALIGN) return fail(BSSN_EINVAL, "d_mem must be 256-byte aligned");
+  if (bytes < 2 * area)
+    return fail(BSSN_ENOMEM, "staging block too small: need " + std::to_string(2 * area) + " bytes");
+  ctx->stg_in = (double*)d_mem;
+  ctx->stg_out = (double*)((char*)d_mem + area);
+  return BSSN_OK;
+}
+
 bssn_status bssn_get_state_async(bssn_ctx* ctx, double* host, double* t) {
   if (!ctx || !host) return fail(BSSN_EINVAL, "NULL argument");
+  if (ctx->stg_out) {
+    // repack into the caller's read-back area (free once the previous copy
+    // out of it is done), copied to the host on the copy stream
+    cudaError_t e = ctx->out_used ? cudaStreamWaitEvent(ctx->stream, ctx->ev_out_free, 0) : cudaSuccess;
+    if (e == cudaSuccess) e = launch_repack(ctx->g, ctx->stg_out, ctx->yn, 0, NF, false, ctx->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_out_ready, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->cstream, ctx->ev_out_ready, 0);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(host, ctx->stg_out, stage_copy_bytes(ctx->g), cudaMemcpyDeviceToHost, ctx->cstream);
+    if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_out_free, ctx->cstream);
+    if (e != cudaSuccess) return cuda_fail(e, "get_state_async");
+    ctx->out_used = true;
+    if (t) *t = ctx->t;
+    return BSSN_OK;
+  }
   const Grid& g = ctx->g;
   const size_t per = (size_t)g.sx * g.sy * g.sz;
   double* area[2];
@@ -754,7 +835,9 @@ bssn_status bssn_wait_state(bssn_ctx* ctx) {
   if (!ctx) return fail(BSSN_EINVAL, "ctx is NULL");
   cudaError_t e = cudaStreamSynchronize(ctx->stream);
   cudaError_t e2 = cudaStreamSynchronize(ctx->cstream);
+  cudaError_t e3 = cudaStreamSynchronize(ctx->istream);
   if (e == cudaSuccess) e = e2;
+  if (e == cudaSuccess) e = e3;
   if (e != cudaSuccess) return cuda_fail(e, "wait_state");
   return check_err(ctx);
 }

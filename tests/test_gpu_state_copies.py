@@ -1,7 +1,7 @@
 """Asynchronous host copies of the state (bssn_set_state_async,
 bssn_get_state_async, bssn_wait_state) against the synchronous ones.
 
-The bar is bit equality.
+The bar is bit equality, with and without device staging areas bound.
 * A loop that uploads a state, steps and reads the state back every step
   gives the same host arrays through the asynchronous calls (read-back of
   step n overlapping the upload of step n+1) as through the synchronous ones.
@@ -35,8 +35,11 @@ def _pinned(torch, shape):
     return torch.empty(shape, dtype=torch.float64, pin_memory=True).numpy()
 
 
+@pytest.mark.parametrize("staging", [False, True])
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_pipelined_copies_match_synchronous(torch_cuda, precision):
+def test_pipelined_copies_match_synchronous(torch_cuda, precision, staging):
+    """With device staging areas bound (bssn_set_staging), the uploads run on
+    their own stream while the previous step may still be running."""
     from paper_1111_3344_gb300 import bssn as B
     c = _case(precision)
     evo = B.Evolution(gpu_params(c))
@@ -49,6 +52,8 @@ def test_pipelined_copies_match_synchronous(torch_cuda, precision):
         evo.set_state(st0 * (1.0 + 1e-3 * s), 0.5 * s)
         evo.rk4_step(1)
         want.append(evo.get_state())
+    if staging:
+        evo.enable_copy_staging()
     host_in = [_pinned(torch_cuda, evo.shape) for _ in range(steps)]
     host_out = [_pinned(torch_cuda, evo.shape) for _ in range(steps)]
     times = []
@@ -64,12 +69,15 @@ def test_pipelined_copies_match_synchronous(torch_cuda, precision):
     evo.close()
 
 
+@pytest.mark.parametrize("staging", [False, True])
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_read_back_mid_evolution_leaves_it_unchanged(torch_cuda, precision):
+def test_read_back_mid_evolution_leaves_it_unchanged(torch_cuda, precision, staging):
     from paper_1111_3344_gb300 import bssn as B
     c = _case(precision)
     a = B.Evolution(gpu_params(c))
     b = B.Evolution(gpu_params(c))
+    if staging:
+        a.enable_copy_staging()
     for e in (a, b):
         e.set_initial_data("bl", bl_params(c))
     a.rk4_step(2)
@@ -84,3 +92,19 @@ def test_read_back_mid_evolution_leaves_it_unchanged(torch_cuda, precision):
     assert np.array_equal(a.get_state()[0], b.get_state()[0])
     a.close()
     b.close()
+
+
+def test_staging_rejects_small_or_misaligned_blocks(torch_cuda):
+    from paper_1111_3344_gb300 import bssn as B
+    c = _case("fp64")
+    evo = B.Evolution(gpu_params(c))
+    p = evo.params.c()
+    n = int(B.load().bssn_staging_bytes(B.ctypes.byref(p)))
+    assert n >= 2 * 24 * int(np.prod(evo.shape[1:])) * 8
+    buf = torch_cuda.empty(n + 256, dtype=torch_cuda.uint8, device="cuda")
+    base = buf.data_ptr()
+    assert B.load().bssn_set_staging(B.ctypes.c_void_p(evo.ctx), B.ctypes.c_void_p(base), n - 8) == 2  # ENOMEM
+    assert B.load().bssn_set_staging(B.ctypes.c_void_p(evo.ctx), B.ctypes.c_void_p(base + 8), n) == 1  # EINVAL
+    assert B.load().bssn_set_staging(B.ctypes.c_void_p(evo.ctx), B.ctypes.c_void_p(base), n) == 0
+    assert B.load().bssn_set_staging(B.ctypes.c_void_p(evo.ctx), None, 0) == 0
+    evo.close()
