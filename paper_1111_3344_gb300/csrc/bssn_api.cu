@@ -681,18 +681,21 @@ static double* stage_area(bssn_ctx* ctx, int* fields) {
   return (double*)ctx->m32[1];
 }
 
-static cudaError_t copy_state(bssn_ctx* ctx, double* host, bool to_device) {
+// shadow: uploads also write the mixed path's float shadow of y_n
+static cudaError_t copy_state(bssn_ctx* ctx, double* host, bool to_device, bool shadow = false) {
   const Grid& g = ctx->g;
   const size_t per = (size_t)g.sx * g.sy * g.sz;
   int chunk = 0;
   double* area = stage_area(ctx, &chunk);
   cudaError_t e = cudaSuccess;
+  float* s32 = shadow ? ctx->m32[0] : nullptr;
+  double* w = shadow ? ctx->mw[0] : nullptr;
   for (int f0 = 0; f0 < NF && e == cudaSuccess; f0 += chunk) {
     const int nf = f0 + chunk <= NF ? chunk : NF - f0;
     const size_t bytes = per * nf * sizeof(double);
     if (to_device) {
       e = cudaMemcpyAsync(area, host + per * f0, bytes, cudaMemcpyHostToDevice, ctx->stream);
-      if (e == cudaSuccess) e = launch_repack(g, area, ctx->yn, f0, nf, true, ctx->stream);
+      if (e == cudaSuccess) e = launch_repack(g, area, ctx->yn, f0, nf, true, ctx->stream, s32, w);
     } else {
       e = launch_repack(g, area, ctx->yn, f0, nf, false, ctx->stream);
       if (e == cudaSuccess) e = cudaMemcpyAsync(host + per * f0, area, bytes, cudaMemcpyDeviceToHost, ctx->stream);
@@ -744,6 +747,13 @@ static size_t stage_copy_bytes(const Grid& g) { return (size_t)NF * g.sx * g.sy 
 bssn_status bssn_set_state_async(bssn_ctx* ctx, const double* host, double t) {
   if (!ctx || !host) return fail(BSSN_EINVAL, "NULL argument");
   cudaError_t e = cudaSuccess;
+  // the repack also forms the mixed path's float shadow of y_n, unless a copy
+  // out of the shadow buffer (the read-back area without staging) may still
+  // run, or the grid is periodic (the next step refreshes the ghosts of y_n
+  // first and forms the shadow from them)
+  const bool shadow = ctx->p.precision == BSSN_MIXED && !ctx->out_pending && !ctx->g.periodic;
+  float* s32 = shadow ? ctx->m32[0] : nullptr;
+  double* w = shadow ? ctx->mw[0] : nullptr;
   if (ctx->stg_in) {
     // upload on the upload stream, into the staging area, while the library
     // stream may still be stepping; then repacked into y_n in stream order
@@ -752,15 +762,15 @@ bssn_status bssn_set_state_async(bssn_ctx* ctx, const double* host, double t) {
       e = cudaMemcpyAsync(ctx->stg_in, host, stage_copy_bytes(ctx->g), cudaMemcpyHostToDevice, ctx->istream);
     if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_in_ready, ctx->istream);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->stream, ctx->ev_in_ready, 0);
-    if (e == cudaSuccess) e = launch_repack(ctx->g, ctx->stg_in, ctx->yn, 0, NF, true, ctx->stream);
+    if (e == cudaSuccess) e = launch_repack(ctx->g, ctx->stg_in, ctx->yn, 0, NF, true, ctx->stream, s32, w);
     if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_in_free, ctx->stream);
     if (e == cudaSuccess) ctx->in_used = true;
   } else {
-    e = copy_state(ctx, const_cast<double*>(host), true);
+    e = copy_state(ctx, const_cast<double*>(host), true, shadow);
   }
   if (e != cudaSuccess) return cuda_fail(e, "set_state copy");
   ctx->t = t;
-  ctx->shadow_valid = false;
+  ctx->shadow_valid = shadow;
   return BSSN_OK;
 }
 

@@ -236,7 +236,10 @@ cudaError_t launch_periodic_fill_mixed(const Grid& g, float* y, double* w, cudaS
 cudaError_t launch_shadow(const Grid& g, const double* y, float* s32, double* w, cudaStream_t s);
 // Copy fields f0 .. f0+nf-1 between a contiguous unpadded block flat and the
 // pitched register reg (to_reg: flat -> reg) (k_boundary.cu).
-cudaError_t launch_repack(const Grid& g, double* flat, double* reg, int f0, int nf, bool to_reg, cudaStream_t s);
+// to_reg: host layout -> register, and (s32, w non-null) the float shadow
+// X - X0 and float64 W of the mixed path as well
+cudaError_t launch_repack(const Grid& g, double* flat, double* reg, int f0, int nf, bool to_reg, cudaStream_t s,
+                          float* s32 = nullptr, double* w = nullptr);
 cudaError_t launch_initial_data(const Grid& g, int kind, const double* dparams, int np,
                                 double* y, cudaStream_t s);
 // adm_scratch (may be null): 12 * fstride doubles; when given, the ADM fields

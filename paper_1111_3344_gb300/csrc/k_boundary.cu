@@ -68,32 +68,53 @@ cudaError_t launch_periodic_fill_mixed(const Grid& g, float* y, double* w, cudaS
 // Repacking between the unpadded host layout (nf fields of sz x sy x sx
 // doubles, contiguous) and the pitched register layout, fields f0 .. f0+nf-1:
 // the host copies then move one contiguous block at full link speed.
-__global__ void unpack_fields_kernel(Grid g, const double* __restrict__ flat, double* __restrict__ reg, int f0,
-                                     int nf) {
-  const long long per = (long long)g.sx * g.sy * g.sz;
-  const long long n = per * nf;
-  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n;
-       q += (long long)gridDim.x * blockDim.x) {
-    const long long f = q / per, r = q - f * per;
-    const long long row = r / g.sx, i = r - row * g.sx;  // row = k sy + j
-    reg[(f0 + f) * g.fstride + row * g.pitch + i] = flat[q];
-  }
-}
-__global__ void pack_fields_kernel(Grid g, const double* __restrict__ reg, double* __restrict__ flat, int f0,
-                                   int nf) {
-  const long long per = (long long)g.sx * g.sy * g.sz;
-  const long long n = per * nf;
-  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n;
-       q += (long long)gridDim.x * blockDim.x) {
-    const long long f = q / per, r = q - f * per;
-    const long long row = r / g.sx, i = r - row * g.sx;
-    flat[q] = reg[(f0 + f) * g.fstride + row * g.pitch + i];
+// Host-layout <-> register repacking: fields f0 .. f0+nf-1, every stored
+// point; the host layout has no x padding.  One warp-row of a block per stored
+// row of one field (consecutive x, coalesced on both sides), rows grid-strided:
+// no per-element index division.  Unpacking can also write the float shadow
+// of y_n (X - X0, the mixed path's stage input) and its float64 W.
+constexpr int RP_X = 32, RP_Y = 8;
+
+__global__ void __launch_bounds__(RP_X * RP_Y)
+    unpack_fields_kernel(Grid g, const double* __restrict__ flat, double* __restrict__ reg, int f0, int nf,
+                         float* __restrict__ s32, double* __restrict__ w) {
+  const long long rows = (long long)g.sy * g.sz;
+  const long long total = rows * nf;
+  for (long long r = (long long)blockIdx.x * RP_Y + threadIdx.y; r < total; r += (long long)gridDim.x * RP_Y) {
+    const int f = (int)(r / rows);
+    const long long rr = r - f * rows;  // k sy + j
+    const double* src = flat + r * g.sx;
+    const long long o = (long long)(f0 + f) * g.fstride + rr * g.pitch;
+    const double bg = background(g, f0 + f);
+    for (int i = threadIdx.x; i < g.sx; i += RP_X) {
+      const double v = src[i];
+      reg[o + i] = v;
+      if (s32) {
+        s32[o + i] = (float)(v - bg);
+        if (f0 + f == F_CHI) w[rr * g.pitch + i] = v;
+      }
+    }
   }
 }
 
-cudaError_t launch_repack(const Grid& g, double* flat, double* reg, int f0, int nf, bool to_reg, cudaStream_t s) {
-  if (to_reg) unpack_fields_kernel<<<152 * 8, 256, 0, s>>>(g, flat, reg, f0, nf);
-  else pack_fields_kernel<<<152 * 8, 256, 0, s>>>(g, reg, flat, f0, nf);
+__global__ void __launch_bounds__(RP_X * RP_Y)
+    pack_fields_kernel(Grid g, const double* __restrict__ reg, double* __restrict__ flat, int f0, int nf) {
+  const long long rows = (long long)g.sy * g.sz;
+  const long long total = rows * nf;
+  for (long long r = (long long)blockIdx.x * RP_Y + threadIdx.y; r < total; r += (long long)gridDim.x * RP_Y) {
+    const int f = (int)(r / rows);
+    const long long rr = r - f * rows;
+    double* dst = flat + r * g.sx;
+    const long long o = (long long)(f0 + f) * g.fstride + rr * g.pitch;
+    for (int i = threadIdx.x; i < g.sx; i += RP_X) dst[i] = reg[o + i];
+  }
+}
+
+cudaError_t launch_repack(const Grid& g, double* flat, double* reg, int f0, int nf, bool to_reg, cudaStream_t s,
+                          float* s32, double* w) {
+  const dim3 block(RP_X, RP_Y), grid(152 * 16);
+  if (to_reg) unpack_fields_kernel<<<grid, block, 0, s>>>(g, flat, reg, f0, nf, s32, w);
+  else pack_fields_kernel<<<grid, block, 0, s>>>(g, reg, flat, f0, nf);
   return cudaGetLastError();
 }
 

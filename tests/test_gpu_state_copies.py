@@ -108,3 +108,21 @@ def test_staging_rejects_small_or_misaligned_blocks(torch_cuda):
     assert B.load().bssn_set_staging(B.ctypes.c_void_p(evo.ctx), B.ctypes.c_void_p(base), n) == 0
     assert B.load().bssn_set_staging(B.ctypes.c_void_p(evo.ctx), None, 0) == 0
     evo.close()
+
+
+def test_upload_shadow_matches_shadow_kernel(torch_cuda):
+    """Mixed path: an upload forms the float shadow of y_n inside its repack;
+    the step after it equals, bit for bit, the step of an evolution whose
+    shadow comes from the separate shadow kernel (after initial data)."""
+    from paper_1111_3344_gb300 import bssn as B
+    c = _case("mixed")
+    a = B.Evolution(gpu_params(c))
+    b = B.Evolution(gpu_params(c))
+    a.set_initial_data("bl", bl_params(c))
+    st, _ = a.get_state()
+    b.set_state(st, 0.0)
+    a.rk4_step(2)
+    b.rk4_step(2)
+    assert np.array_equal(a.get_state()[0], b.get_state()[0])
+    a.close()
+    b.close()
