@@ -327,7 +327,8 @@ def run_ours(args):
                     "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)",
                     "algorithmic_bytes_per_launch": bytes_launch,
                     "traffic": MIXED_TRAFFIC_PER_POINT * pts if MIXED_TRAFFIC_PER_POINT else None,
-                    "launch_ms": stage_launch_ms, "launches": stage_n}
+                    "launch_ms": stage_launch_ms, "launches": stage_n,
+                    "boundary_launch_ms": bc_ms / max(bc_n, 1)}
     else:
         roofline = {"bound": "alu", "kernel": "stage_fp64_blocks_kernel" if rows else "stage_fp64_kernel",
                     "achieved": achieved * 1e3,
@@ -339,6 +340,7 @@ def run_ours(args):
                                        / (FP64_MEASURED_GFLOPS * 1e9 / 2),
                     "traffic": traffic_pt * pts,
                     "launch_ms": stage_launch_ms, "launches": stage_n,
+                    "boundary_launch_ms": bc_ms / max(bc_n, 1),
                     "hbm_frac": (HBM_BYTES_PER_POINT_STEP * pts * args.steps / (ms * 1e-3)) / HBM_MEASURED_GBS / 1e9}
     line = {
         "metric": ("BSSN RK4 point-updates/s (mixed FP32 RHS / FP64 state, Brill-Lindquist puncture 128^3)"

@@ -180,12 +180,16 @@ __device__ __forceinline__ void sommerfeld_point_mixed(const Grid& g, const Stag
   }
 }
 
-// mixed path, ghost point q, every field: the same per-field arithmetic as
-// sommerfeld_point_mixed with the geometry (index decode, anchor,
-// coordinates, normals) formed once for the 23 float fields.
-__device__ __forceinline__ void sommerfeld_point_mixed_all(const Grid& g, const StageArgsMixed& a,
-                                                           const float* __restrict__ kanchor, unsigned q) {
-  sommerfeld_point_mixed(g, a, kanchor, q, F_CHI);  // W: float64 geometry and arithmetic
+// mixed path, ghost point q, fields [F0, F1): the same per-field arithmetic
+// as sommerfeld_point_mixed with the geometry (index decode, anchor,
+// coordinates, normals) formed once for the group's float fields; W (field 0,
+// when in the group) in float64.  UNROLL: the field loop unrolled, so that the
+// group's loads are in flight together.
+template <int F0, int F1, bool UNROLL>
+__device__ __forceinline__ void sommerfeld_point_mixed_fields(const Grid& g, const StageArgsMixed& a,
+                                                              const float* __restrict__ kanchor, unsigned q) {
+  if constexpr (F0 == 0) sommerfeld_point_mixed(g, a, kanchor, q, F_CHI);  // W: float64 geometry and arithmetic
+  constexpr int FB = F0 == 0 ? 1 : F0;
   const long long fs = g.fstride;
   const int nf = g.shift == BSSN_SHIFT_FROZEN ? F_BETA : NF;
   int I[3], A[3];
@@ -206,7 +210,8 @@ __device__ __forceinline__ void sommerfeld_point_mixed_all(const Grid& g, const 
   const float nb[3] = {xb[0] * irb, xb[1] * irb, xb[2] * irb};
   const float na[3] = {xa[0] * ira, xa[1] * ira, xa[2] * ira};
   const float fac = (irb / ira) * (irb / ira);
-  for (int f = 1; f < NF; f++) {
+#pragma unroll (UNROLL ? F1 - FB : 1)
+  for (int f = FB; f < F1; f++) {
     const long long o = f * fs + ib;
     float rhs = 0.0f;
     if (f < nf) {
@@ -226,6 +231,12 @@ __device__ __forceinline__ void sommerfeld_point_mixed_all(const Grid& g, const 
       a.ksum[o] = a.mode == MODE_FIRST ? rhs : fmaf(2.0f, rhs, a.ksum[o]);
     }
   }
+}
+
+// every field in one thread (the batched boundary kernel)
+__device__ __forceinline__ void sommerfeld_point_mixed_all(const Grid& g, const StageArgsMixed& a,
+                                                           const float* __restrict__ kanchor, unsigned q) {
+  sommerfeld_point_mixed_fields<0, NF, false>(g, a, kanchor, q);
 }
 
 // Periodic ghosts: copy from the wrapped interior point, all fields (and the

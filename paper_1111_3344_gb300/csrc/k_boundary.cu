@@ -25,10 +25,19 @@ __global__ void sommerfeld_fp64_kernel(Grid g, StageArgs a, const double* __rest
 }
 
 // one thread per ghost point, every field (geometry formed once)
+// mixed: blockIdx.y picks one of four field groups (W and gt_ij; K and
+// At_ij but its last; the rest of At_ij, Gt^i, alpha; beta^i and B^i), each
+// a few unrolled fields per thread (their loads in flight together; the
+// kernel is bound by load latency)
 __global__ void sommerfeld_mixed_kernel(Grid g, StageArgsMixed a, const float* __restrict__ kanchor) {
   const unsigned q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= ghost_count(g)) return;
-  sommerfeld_point_mixed_all(g, a, kanchor, q);
+  switch (blockIdx.y) {
+    case 0: sommerfeld_point_mixed_fields<0, 7, true>(g, a, kanchor, q); break;
+    case 1: sommerfeld_point_mixed_fields<7, 13, true>(g, a, kanchor, q); break;
+    case 2: sommerfeld_point_mixed_fields<13, 18, true>(g, a, kanchor, q); break;
+    default: sommerfeld_point_mixed_fields<18, NF, true>(g, a, kanchor, q); break;
+  }
 }
 
 template <typename S>
@@ -49,7 +58,7 @@ cudaError_t launch_sommerfeld_mixed(const Grid& g, const StageArgsMixed& a, cons
                                     cudaStream_t s) {
   const unsigned total = ghost_count(g);
   const int bs = 128;
-  sommerfeld_mixed_kernel<<<(total + bs - 1) / bs, bs, 0, s>>>(g, a, kanchor);
+  sommerfeld_mixed_kernel<<<dim3((total + bs - 1) / bs, 4), bs, 0, s>>>(g, a, kanchor);
   return cudaGetLastError();
 }
 
