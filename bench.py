@@ -533,8 +533,9 @@ def run_analysis(args):
     """The analysis steps after the evolution on the benchmark puncture:
     Weyl scalar Psi4, ADM mass / angular momentum volume integrals, constraint
     norms (all float64), each timed over K launches with CUDA events on the
-    library's stream after W warm-up launches; and the puncture tracker's cost
-    per RK4 step (steps with and without tracking)."""
+    library's stream after W warm-up launches; the puncture tracker's cost
+    per RK4 step (steps with and without tracking); and RK4 steps of the
+    matter-coupled right-hand side (a smooth seeded T_{mu nu}) against vacuum."""
     import torch
 
     from paper_1111_3344_gb300 import bssn as B
@@ -577,6 +578,24 @@ def run_analysis(args):
         e1.record(stream)
         e1.synchronize()
         times[track] = e0.elapsed_time(e1) / args.steps
+    # matter-coupled right-hand side: RK4 steps with a smooth seeded T_{mu nu}
+    # (10 more float64 fields read per point) against vacuum, same state
+    from paper_1111_3344_gb300 import inputs
+    evo.track_punctures(False)
+    prm = workload_params("fp64")
+    tmunu = inputs.random_tmunu(7, prm.n, prm.xmin, prm.h)
+    mtimes = {}
+    for matter in (False, True):
+        evo.set_matter(tmunu if matter else None)
+        evo.rk4_step(1)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        evo.rk4_step(args.steps)
+        e1.record(stream)
+        e1.synchronize()
+        mtimes[matter] = e0.elapsed_time(e1) / args.steps
+    evo.set_matter(None)
     clk = clocks.stop()
     evo.close()
     top = res["psi4"]
@@ -593,7 +612,9 @@ def run_analysis(args):
         "kernels": res,
         "tracker": {"ms_per_step_without": times[False], "ms_per_step_with": times[True],
                     "overhead_ms": times[True] - times[False]},
-        "gpu_launches": 3 * args.steps + 2 * args.steps * (1 + 8),
+        "matter": {"ms_per_step_vacuum": mtimes[False], "ms_per_step_with_tmunu": mtimes[True],
+                   "Mpoint_updates_per_s_with_tmunu": pts / mtimes[True] / 1e3},
+        "gpu_launches": 3 * args.steps + 2 * args.steps * (1 + 8) + 2 * args.steps * 8,
         "clocks": clk,
     }
     print(json.dumps(line))
