@@ -53,9 +53,20 @@ HBM_BYTES_PER_POINT_STEP = 3264.0  # 17 register passes x 24 fields x 8 B
 # each); stage 4 reads src and the k-sum, reads and writes y_n (2 x 192 B) and
 # writes the new shadow m0 (696 B)
 HBM_BYTES_PER_POINT_STEP_MIXED = 312.0 + 2 * 520.0 + 696.0   # 2048
-HBM_MEASURED_GBS = 6764.0          # STREAM-style copy on this pool
+def _measured_hbm_gbs(default=6764.0):
+    """The STREAM-style copy bandwidth measured on these GB300s
+    (MEASURED_PEAKS.json beside this file, key hbm_gbs); the value it held
+    when the file is absent."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        return default
+
+
+HBM_MEASURED_GBS = _measured_hbm_gbs()
 FP64_PEAK_GFLOPS = 1250.0          # nominal GB300 FP64 rate
-FP64_MEASURED_GFLOPS = 1196.0      # dependent-chain DFMA microbenchmark on this pool
+FP64_MEASURED_GFLOPS = 1196.0      # dependent-chain DFMA microbenchmark on GB300 (2070 MHz)
 # DRAM bytes (read + write) per interior point of one stage launch, from the
 # ncu capture of the current kernels on the 64^3 case (traffic grows with the
 # points; profiles/stage_traffic_bl64.md); None until captured.

@@ -361,7 +361,7 @@ bssn_status bssn_batch_set_tile(bssn_batch* b, int32_t cfg);
 bssn_status bssn_batch_autotune(bssn_batch* b, int32_t reps, int32_t* best, double* ms_per_cfg);
 
 /* ------------------------------------------------------------- server
- * Continuous batching of evolution requests (BASELINE serving pattern): a
+ * Continuous batching of evolution requests (no counterpart in the paper): a
  * scheduler thread admits queued requests at RK4 step boundaries while their
  * register bytes fit in hbm_budget_bytes, keeps their state on the device,
  * advances all resident evolutions together (bssn_batch_step) and retires
