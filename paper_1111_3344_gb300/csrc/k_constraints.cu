@@ -16,6 +16,7 @@
 // per-block partials (8 sums of squares, 8 maxima, 2 counts); then one block
 // folds the partials the same way: the result does not depend on scheduling.
 #include "bssn_internal.cuh"
+#include "ricci3.cuh"
 
 namespace bssn {
 
@@ -112,41 +113,13 @@ __device__ void constraints_point(const Grid& g, const double* __restrict__ y,
     gu[4] = (g0[1] * g0[2] - g0[0] * g0[4]) * idet;
     gu[5] = (g0[0] * g0[3] - g0[1] * g0[1]) * idet;
   }
-  double G1[3][6], G2[3][6];
-#pragma unroll
-  for (int k = 0; k < 3; k++)
-#pragma unroll
-    for (int a = 0; a < 3; a++)
-#pragma unroll
-      for (int b = a; b < 3; b++)
-        G1[k][sym(a, b)] = 0.5 * (dg[a][sym(k, b)] + dg[b][sym(k, a)] - dg[k][sym(a, b)]);
-#pragma unroll
-  for (int k = 0; k < 3; k++)
-#pragma unroll
-    for (int m = 0; m < 6; m++)
-      G2[k][m] = gu[sym(k, 0)] * G1[0][m] + gu[sym(k, 1)] * G1[1][m] + gu[sym(k, 2)] * G1[2][m];
-
+  // Christoffel symbols and Ricci tensor (ricci3.cuh); R = g^ij R_ij
+  double G1[3][6], G2[3][6], Ric[6];
+  christoffel3(gu, dg, G1, G2);
+  ricci3(gu, ddg, G1, G2, Ric);
   double R = 0.0;
 #pragma unroll
-  for (int i = 0; i < 3; i++)
-#pragma unroll
-    for (int j = i; j < 3; j++) {
-      double s = 0.0;
-#pragma unroll
-      for (int k = 0; k < 3; k++)
-#pragma unroll
-        for (int l = 0; l < 3; l++) {
-          const double gkl = gu[sym(k, l)];
-          const double dd = ddg[sym(k, j)][sym(i, l)] + ddg[sym(i, l)][sym(k, j)] -
-                            ddg[sym(k, l)][sym(i, j)] - ddg[sym(i, j)][sym(k, l)];
-          double q = 0.5 * dd;
-#pragma unroll
-          for (int m = 0; m < 3; m++)
-            q += G2[m][sym(i, l)] * G1[m][sym(k, j)] - G2[m][sym(i, j)] * G1[m][sym(k, l)];
-          s = fma(gkl, q, s);
-        }
-      R = fma(i == j ? gu[sym(i, j)] : 2.0 * gu[sym(i, j)], s, R);
-    }
+  for (int m = 0; m < 6; m++) R = fma((m == 0 || m == 3 || m == 5) ? gu[m] : 2.0 * gu[m], Ric[m], R);
   double Kud[3][3];
 #pragma unroll
   for (int a = 0; a < 3; a++)

@@ -23,6 +23,7 @@
 // every stencil point and differenced with the 4th-order stencils.  Float64
 // in every precision mode; one thread per interior point.
 #include "bssn_internal.cuh"
+#include "ricci3.cuh"
 
 namespace bssn {
 
@@ -123,41 +124,11 @@ __device__ void psi4_point(const Grid& g, const double* __restrict__ y, const do
     gu[4] = (g0[1] * g0[2] - g0[0] * g0[4]) * idet;
     gu[5] = (g0[0] * g0[3] - g0[1] * g0[1]) * idet;
   }
-  // Christoffel symbols: first kind G1[k][ij] = Gamma_kij, second G2[k][ij] = Gamma^k_ij
-  double G1[3][6], G2[3][6];
-#pragma unroll
-  for (int k = 0; k < 3; k++)
-#pragma unroll
-    for (int a = 0; a < 3; a++)
-#pragma unroll
-      for (int b = a; b < 3; b++)
-        G1[k][sym(a, b)] = 0.5 * (dg[a][sym(k, b)] + dg[b][sym(k, a)] - dg[k][sym(a, b)]);
-#pragma unroll
-  for (int k = 0; k < 3; k++)
-#pragma unroll
-    for (int m = 0; m < 6; m++)
-      G2[k][m] = gu[sym(k, 0)] * G1[0][m] + gu[sym(k, 1)] * G1[1][m] + gu[sym(k, 2)] * G1[2][m];
-  // Ricci tensor R_ij = g^kl R_kilj
-  double Ric[6];
-#pragma unroll
-  for (int i = 0; i < 3; i++)
-#pragma unroll
-    for (int j = i; j < 3; j++) {
-      double s = 0.0;
-#pragma unroll
-      for (int k = 0; k < 3; k++)
-#pragma unroll
-        for (int l = 0; l < 3; l++) {
-          const double dd = ddg[sym(k, j)][sym(i, l)] + ddg[sym(i, l)][sym(k, j)] -
-                            ddg[sym(k, l)][sym(i, j)] - ddg[sym(i, j)][sym(k, l)];
-          double q = 0.5 * dd;
-#pragma unroll
-          for (int m = 0; m < 3; m++)
-            q += G2[m][sym(i, l)] * G1[m][sym(k, j)] - G2[m][sym(i, j)] * G1[m][sym(k, l)];
-          s = fma(gu[sym(k, l)], q, s);
-        }
-      Ric[sym(i, j)] = s;
-    }
+  // Christoffel symbols: first kind G1[k][ij] = Gamma_kij, second G2[k][ij] =
+  // Gamma^k_ij; Ricci tensor (ricci3.cuh)
+  double G1[3][6], G2[3][6], Ric[6];
+  christoffel3(gu, dg, G1, G2);
+  ricci3(gu, ddg, G1, G2, Ric);
   // fiducial triad, orthonormal in g
   double rv[3] = {x[0], x[1], x[2]};
   double pv[3] = {-x[1], x[0], 0.0};
