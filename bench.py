@@ -77,7 +77,7 @@ MIXED_TRAFFIC_PER_POINT = 488.0    # mean over the 4 stages of stage_mixed_tma_k
 # from ncu instruction counts; profiles/analysis_kernels_bl96.md).
 # psi4 and constraints include the ADM-field pass that precedes them
 # (36 flop per stored point, 44 per interior point at 96^3).
-ANALYSIS_FLOP_PER_POINT = {"psi4": 3409.0 + 44.0, "adm_integrals": 1858.0, "constraints": 1999.0 + 44.0}
+ANALYSIS_FLOP_PER_POINT = {"psi4": 3409.0 + 44.0, "adm_integrals": 1771.9, "constraints": 1999.0 + 44.0}
 
 
 def workload_params(precision="fp64"):

@@ -17,6 +17,7 @@
 // folds the partials the same way, so the result does not depend on
 // scheduling.
 #include "rhs_point.cuh"
+#include "ricci3.cuh"
 
 namespace bssn {
 
@@ -79,19 +80,9 @@ __device__ void adm_density(const Grid& g, const double* __restrict__ y, long lo
     }
 #undef PF
 #undef SD
+  // Christoffel symbols of gt (ricci3.cuh: the terms that cancel left out)
   double G1[3][6], G2[3][6];
-#pragma unroll
-  for (int kk = 0; kk < 3; kk++)
-#pragma unroll
-    for (int a = 0; a < 3; a++)
-#pragma unroll
-      for (int b = a; b < 3; b++)
-        G1[kk][sym(a, b)] = 0.5 * (dgt[a][sym(kk, b)] + dgt[b][sym(kk, a)] - dgt[kk][sym(a, b)]);
-#pragma unroll
-  for (int kk = 0; kk < 3; kk++)
-#pragma unroll
-    for (int m = 0; m < 6; m++)
-      G2[kk][m] = gu[sym(kk, 0)] * G1[0][m] + gu[sym(kk, 1)] * G1[1][m] + gu[sym(kk, 2)] * G1[2][m];
+  christoffel3(gu, dgt, G1, G2);
   double dgu[3];
   {
     double Tb[3];
@@ -130,17 +121,29 @@ __device__ void adm_density(const Grid& g, const double* __restrict__ y, long lo
         for (int kk = 0; kk < 3; kk++) {
           t = fma(gt[sym(kk, a)], dG[b][kk], t);
           t = fma(gt[sym(kk, b)], dG[a][kk], t);
-          t = fma(-(G1[a][sym(b, kk)] + G1[b][sym(a, kk)]), dgu[kk], t);
+          t = fma(-dgt[kk][ab], dgu[kk], t);  // Gt_akb + Gt_bka = d_k gt_ab
         }
         s = fma(0.5, t, s);
+        if (a == b) {  // the first two quadratic terms coincide
+          double q = 0.0;
 #pragma unroll
-        for (int kk = 0; kk < 3; kk++)
+          for (int kk = 0; kk < 3; kk++)
 #pragma unroll
-          for (int l = 0; l < 3; l++) {
-            s = fma(G2[kk][sym(l, a)], G1u[b][kk][l], s);
-            s = fma(G2[kk][sym(l, b)], G1u[a][kk][l], s);
-            s = fma(G2[kk][sym(a, l)], G1u[kk][b][l], s);
-          }
+            for (int l = 0; l < 3; l++) {
+              q = fma(G2[kk][sym(l, a)], G1u[a][kk][l], q);
+              s = fma(G2[kk][sym(a, l)], G1u[kk][a][l], s);
+            }
+          s = fma(2.0, q, s);
+        } else {
+#pragma unroll
+          for (int kk = 0; kk < 3; kk++)
+#pragma unroll
+            for (int l = 0; l < 3; l++) {
+              s = fma(G2[kk][sym(l, a)], G1u[b][kk][l], s);
+              s = fma(G2[kk][sym(l, b)], G1u[a][kk][l], s);
+              s = fma(G2[kk][sym(a, l)], G1u[kk][b][l], s);
+            }
+        }
         Rtr = fma(a == b ? gu[ab] : 2.0 * gu[ab], s, Rtr);
       }
   }

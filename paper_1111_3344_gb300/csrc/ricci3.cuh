@@ -1,6 +1,8 @@
 // Christoffel symbols and Ricci tensor of a 3-metric g_ij from its first and
-// second differences, float64, for the analysis kernels (constraints, Psi4;
-// arXiv:1111.3344, Sec. "Other analysis modules", Sec. "Gravitational Waves").
+// second differences, float64, for the analysis kernels (constraints and Psi4:
+// Ricci tensor of gamma_ij; ADM integrals: Christoffel symbols of gt_ij;
+// arXiv:1111.3344, Sec. "Other analysis modules", Sec. "Masses and Momenta",
+// Sec. "Gravitational Waves").
 //
 //   Gamma_kij   = (d_i g_kj + d_j g_ki - d_k g_ij) / 2,   Gamma^k_ij = g^ks Gamma_sij
 //   R_ij = 1/2 g^kl (d_k d_j g_il + d_i d_l g_kj - d_k d_l g_ij - d_i d_j g_kl)
