@@ -21,17 +21,17 @@ __device__ __forceinline__ double coordv(const Grid& g, int d, int i) {
 }
 
 // Radiative right-hand side of field f at stored point I in arithmetic C;
-// p points at the field's value there; nx = x / r, ir = 1 / r.
+// p points at the field's value there; ns = (x / r) / (2h), the normal scaled
+// by the difference weight (formed once per point for all fields), ir = 1 / r.
 template <typename C, typename S, bool DEV = false>
-__device__ C rad_at(const Grid& g, const S* __restrict__ p, int f, const int I[3], const C nx[3],
-                    C ir) {
+__device__ __forceinline__ C rad_at(const Grid& g, const S* __restrict__ p, int f, const int I[3],
+                                    const C ns[3], C ir) {
   const long long sd[3] = {1, g.pitch, g.plane};
   const int dims[3] = {g.sx, g.sy, g.sz};
   const bool one = (f == F_ALP || (f == F_CHI && g.use_w) || f == F_GT + 0 || f == F_GT + 3 ||
                    f == F_GT + 5);
   const C X0 = (DEV || !one) ? C(0) : C(1);  // DEV: p holds X - X0 already
   const C v0 = (f == F_ALP || f == F_TRK) ? C(1.4142135623730951) : C(1);
-  const C i2h = gc<C>(g.i2h, g.i2hf);
   C s = ((C)p[0] - X0) * ir;
 #pragma unroll
   for (int d = 0; d < 3; d++) {
@@ -43,7 +43,7 @@ __device__ C rad_at(const Grid& g, const S* __restrict__ p, int f, const int I[3
       der = C(3) * (C)p[0] - C(4) * (C)p[-q] + (C)p[-2 * q];
     else
       der = -(C(3) * (C)p[0] - C(4) * (C)p[q] + (C)p[2 * q]);
-    s = fmaT<C>(nx[d] * i2h, der, s);
+    s = fmaT<C>(ns[d], der, s);
   }
   return -v0 * s;
 }
@@ -53,6 +53,7 @@ struct GhostGeo {
   int I[3], A[3];
   long long ib, ia;
   double nb[3], na[3], irb, ira, fac;
+  double nbs[3], nas[3];  // nb, na times 1/(2h) (rad_at)
 };
 
 __device__ __forceinline__ void ghost_geo(const Grid& g, unsigned q, GhostGeo& G) {
@@ -81,6 +82,8 @@ __device__ __forceinline__ void ghost_geo(const Grid& g, unsigned q, GhostGeo& G
   for (int d = 0; d < 3; d++) {
     G.nb[d] = xb[d] * G.irb;
     G.na[d] = xa[d] * G.ira;
+    G.nbs[d] = G.nb[d] * g.i2h;
+    G.nas[d] = G.na[d] * g.i2h;
   }
   G.ib = lin(g, G.I[0], G.I[1], G.I[2]);
   G.ia = lin(g, G.A[0], G.A[1], G.A[2]);
@@ -96,8 +99,8 @@ __device__ __forceinline__ void sommerfeld_point_fp64(const Grid& g, const Stage
   for (int f = 0; f < NF; f++) {
     double rhs = 0.0;
     if (f < nf) {
-      const double radb = rad_at<double, double>(g, a.src + f * fs + G.ib, f, G.I, G.nb, G.irb);
-      const double rada = rad_at<double, double>(g, a.src + f * fs + G.ia, f, G.A, G.na, G.ira);
+      const double radb = rad_at<double, double>(g, a.src + f * fs + G.ib, f, G.I, G.nbs, G.irb);
+      const double rada = rad_at<double, double>(g, a.src + f * fs + G.ia, f, G.A, G.nas, G.ira);
       const double ka = (a.mode == MODE_RHS) ? a.rhs[f * fs + G.ia] : kanchor[f * fs + G.ia];
       rhs = fma(G.fac, ka - rada, radb);
     }
@@ -131,8 +134,8 @@ __device__ __forceinline__ void sommerfeld_point_mixed(const Grid& g, const Stag
   if (f == F_CHI) {
     GhostGeo G;
     ghost_geo(g, q, G);
-    const double radb = rad_at<double, double>(g, a.srcw + ib, f, I, G.nb, G.irb);
-    const double rada = rad_at<double, double>(g, a.srcw + ia, f, A, G.na, G.ira);
+    const double radb = rad_at<double, double>(g, a.srcw + ib, f, I, G.nbs, G.irb);
+    const double rada = rad_at<double, double>(g, a.srcw + ia, f, A, G.nas, G.ira);
     const double ka = (a.mode == MODE_RHS) ? a.rhs[ia] : (double)kanchor[ia];
     const double rhs = fma(G.fac, ka - rada, radb);
     if (a.mode == MODE_RHS) {
@@ -160,11 +163,11 @@ __device__ __forceinline__ void sommerfeld_point_mixed(const Grid& g, const Stag
     }
     const float irb = rsqrtf(xb[0] * xb[0] + xb[1] * xb[1] + xb[2] * xb[2]);
     const float ira = rsqrtf(xa[0] * xa[0] + xa[1] * xa[1] + xa[2] * xa[2]);
-    const float nb[3] = {xb[0] * irb, xb[1] * irb, xb[2] * irb};
-    const float na[3] = {xa[0] * ira, xa[1] * ira, xa[2] * ira};
+    const float nbs[3] = {xb[0] * irb * g.i2hf, xb[1] * irb * g.i2hf, xb[2] * irb * g.i2hf};
+    const float nas[3] = {xa[0] * ira * g.i2hf, xa[1] * ira * g.i2hf, xa[2] * ira * g.i2hf};
     const float fac = (irb / ira) * (irb / ira);
-    const float radb = rad_at<float, float, true>(g, a.src + o, f, I, nb, irb);
-    const float rada = rad_at<float, float, true>(g, a.src + f * fs + ia, f, A, na, ira);
+    const float radb = rad_at<float, float, true>(g, a.src + o, f, I, nbs, irb);
+    const float rada = rad_at<float, float, true>(g, a.src + f * fs + ia, f, A, nas, ira);
     const float ka = (a.mode == MODE_RHS) ? (float)a.rhs[f * fs + ia] : kanchor[f * fs + ia];
     rhs = fmaf(fac, ka - rada, radb);
   }
@@ -207,16 +210,17 @@ __device__ __forceinline__ void sommerfeld_point_mixed_fields(const Grid& g, con
   }
   const float irb = rsqrtf(xb[0] * xb[0] + xb[1] * xb[1] + xb[2] * xb[2]);
   const float ira = rsqrtf(xa[0] * xa[0] + xa[1] * xa[1] + xa[2] * xa[2]);
-  const float nb[3] = {xb[0] * irb, xb[1] * irb, xb[2] * irb};
-  const float na[3] = {xa[0] * ira, xa[1] * ira, xa[2] * ira};
+  // normals times 1/(2h) (rad_at)
+  const float nbs[3] = {xb[0] * irb * g.i2hf, xb[1] * irb * g.i2hf, xb[2] * irb * g.i2hf};
+  const float nas[3] = {xa[0] * ira * g.i2hf, xa[1] * ira * g.i2hf, xa[2] * ira * g.i2hf};
   const float fac = (irb / ira) * (irb / ira);
 #pragma unroll (UNROLL ? F1 - FB : 1)
   for (int f = FB; f < F1; f++) {
     const long long o = f * fs + ib;
     float rhs = 0.0f;
     if (f < nf) {
-      const float radb = rad_at<float, float, true>(g, a.src + o, f, I, nb, irb);
-      const float rada = rad_at<float, float, true>(g, a.src + f * fs + ia, f, A, na, ira);
+      const float radb = rad_at<float, float, true>(g, a.src + o, f, I, nbs, irb);
+      const float rada = rad_at<float, float, true>(g, a.src + f * fs + ia, f, A, nas, ira);
       const float ka = (a.mode == MODE_RHS) ? (float)a.rhs[f * fs + ia] : kanchor[f * fs + ia];
       rhs = fmaf(fac, ka - rada, radb);
     }
