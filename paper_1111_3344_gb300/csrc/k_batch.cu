@@ -108,6 +108,7 @@ __global__ void batch_boundary_kernel(const MemberDev* __restrict__ mem, const B
     if (M.g.periodic) {
       const unsigned q = (unsigned)local;
       if constexpr (MIXED) {
+        if (blockIdx.y != 0) continue;  // the first field group copies every field
         const StageArgsMixed& a = M.amx[stage];
         periodic_point<float>(M.g, a.out0, a.out0w, q);
         if (a.mode == MODE_LAST) periodic_point<double>(M.g, a.yn, nullptr, q);
@@ -116,8 +117,15 @@ __global__ void batch_boundary_kernel(const MemberDev* __restrict__ mem, const B
         periodic_point<double>(M.g, a.mode == MODE_LAST ? a.yn : a.out0, nullptr, q);
       }
     } else if constexpr (MIXED) {
+      // blockIdx.y: one of four field groups (as sommerfeld_mixed_kernel)
       const StageArgsMixed& a = M.amx[stage];
-      sommerfeld_point_mixed_all(M.g, a, a.kshell, (unsigned)local);
+      const unsigned q = (unsigned)local;
+      switch (blockIdx.y) {
+        case 0: sommerfeld_point_mixed_fields<0, 7, true>(M.g, a, a.kshell, q); break;
+        case 1: sommerfeld_point_mixed_fields<7, 13, true>(M.g, a, a.kshell, q); break;
+        case 2: sommerfeld_point_mixed_fields<13, 18, true>(M.g, a, a.kshell, q); break;
+        default: sommerfeld_point_mixed_fields<18, NF, true>(M.g, a, a.kshell, q); break;
+      }
     } else {
       const StageArgs& a = M.a64[stage];
       sommerfeld_point_fp64(M.g, a, a.kshell, (unsigned)local);
@@ -194,7 +202,9 @@ cudaError_t launch_batch_boundary(bool mixed, const MemberDev* mem, const BatchW
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return e;
   const dim3 grid((unsigned)(sms * 8)), block(256);
-  if (mixed) batch_boundary_kernel<true><<<grid, block, 0, s>>>(mem, wk, stage);
+  // mixed Sommerfeld: four field groups per ghost point (gridDim.y); periodic
+  // members copy every field in the first group and nothing in the others
+  if (mixed) batch_boundary_kernel<true><<<dim3(grid.x, 4), block, 0, s>>>(mem, wk, stage);
   else batch_boundary_kernel<false><<<grid, block, 0, s>>>(mem, wk, stage);
   return cudaGetLastError();
 }
