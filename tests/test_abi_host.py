@@ -62,3 +62,29 @@ def test_alloc_rejects_null_and_small_memory():
     with pytest.raises(B.BssnError) as e:
         B.bssn_alloc(p, 256, 16, 0)  # never dereferenced: size check fails first
     assert e.value.status == 2
+
+
+def test_staging_bytes():
+    """bssn_staging_bytes: two areas (upload, read-back), each the state in the
+    unpadded host layout rounded up to 256 bytes; 0 on bad parameters."""
+    import ctypes
+    lib = B.load()
+    p = B.Params(n=(37, 21, 19), xmin=(0.0,) * 3, h=0.1, boundary="sommerfeld")
+    c = p.c()
+    n = int(lib.bssn_staging_bytes(ctypes.byref(c)))
+    area = 24 * (37 + 6) * (21 + 6) * (19 + 6) * 8
+    assert n == 2 * ((area + 255) // 256 * 256)
+    bad = B.Params(n=(3, 8, 8), xmin=(0.0,) * 3, h=0.1).c()
+    assert int(lib.bssn_staging_bytes(ctypes.byref(bad))) == 0
+
+
+def test_batch_table_bytes_grow_with_members():
+    """The batch tables (member table with one tensor map per stage, work list,
+    error word) grow linearly with max_members; 0 outside 1..256
+    (BSSN_BATCH_MAX_MEMBERS)."""
+    lib = B.load()
+    t1, t2, t64 = (int(lib.bssn_batch_table_bytes(m)) for m in (1, 2, 64))
+    assert 0 < t1 < t2 < t64
+    assert (t64 - t2) >= 62 * 4 * 128  # at least the four 128-byte tensor maps per member
+    assert int(lib.bssn_batch_table_bytes(256)) > t64
+    assert int(lib.bssn_batch_table_bytes(0)) == 0 and int(lib.bssn_batch_table_bytes(257)) == 0
