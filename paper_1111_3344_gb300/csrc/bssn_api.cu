@@ -153,7 +153,7 @@ struct bssn_ctx {
   float* dr;  // mixed: derivative register of the split stage
   bool shadow_valid;
   int tile;  // stage-kernel tile configuration (see bssn_autotune)
-  CUtensorMap tmap[3];  // mixed: tensor maps of the float stage buffers (TMA kernel)
+  CUtensorMap tmap[2][3];  // mixed: tensor maps of the float stage buffers, per TMA variant
   bool tmap_ok;
   int* err;             // device error word (bounded waits that gave up)
   double* part;
@@ -184,6 +184,19 @@ struct bssn_ctx {
   cudaEvent_t ev_in_ready, ev_in_free, ev_out_free;
   bool in_used, out_used;
 };
+
+// Tile configuration indices: [0, tile_config_count()) fused kernels, then
+// N_TMA TMA-staged mixed kernels (variant 0: 32x4x1, two blocks per SM;
+// 1: 32x8x1, one block per SM), then the split-stage variants.
+constexpr int N_TMA = 2;
+static int tma_variant(int cfg) {
+  const int v = cfg - tile_config_count();
+  return (v >= 0 && v < N_TMA) ? v : -1;
+}
+static int split_variant(int cfg) {
+  const int v = cfg - tile_config_count() - N_TMA;
+  return (v >= 0 && v < split_config_count()) ? v : -1;
+}
 
 namespace {
 cudaError_t prof_mark(bssn_ctx* ctx, std::vector<cudaEvent_t>& v) {
@@ -282,7 +295,8 @@ bssn_status bssn_alloc(const bssn_params* p, void* d_mem, size_t bytes, void* cu
   ctx->tmap_ok = false;
   if (p->precision == BSSN_MIXED) {
     bool ok = true;
-    for (int q = 0; q < 3 && ok; q++) ok = make_stage_tensor_map(g, ctx->m32[q], &ctx->tmap[q]) == cudaSuccess;
+    for (int v = 0; v < 2 && ok; v++)
+      for (int q = 0; q < 3 && ok; q++) ok = make_stage_tensor_map(g, ctx->m32[q], &ctx->tmap[v][q], v) == cudaSuccess;
     ctx->tmap_ok = ok;
   }
   ctx->cstream = ctx->istream = nullptr;
@@ -476,10 +490,11 @@ bssn_status bssn_rhs(bssn_ctx* ctx, const void* d_state, void* d_rhs) {
   a.w_thr = ctx->p.w_fp64_threshold;
   a.mode = MODE_RHS;
   // the selected stage kernel, TMA-staged included (tmap[2] describes m32[2])
-  if (ctx->tile > tile_config_count())
-    e = launch_stage_mixed_split(ctx->g, a, ctx->dr, ctx->stream, ctx->tile - tile_config_count() - 1);
-  else if (ctx->tile == tile_config_count())
-    e = launch_stage_mixed_tma(ctx->g, a, ctx->tmap[2], ctx->err, ctx->stream);
+  if (split_variant(ctx->tile) >= 0)
+    e = launch_stage_mixed_split(ctx->g, a, ctx->dr, ctx->stream, split_variant(ctx->tile));
+  else if (tma_variant(ctx->tile) >= 0)
+    e = launch_stage_mixed_tma(ctx->g, a, ctx->tmap[tma_variant(ctx->tile)][2], ctx->err, ctx->stream,
+                               tma_variant(ctx->tile));
   else
     e = launch_stage_mixed(ctx->g, a, ctx->stream, ctx->tile);
   if (e != cudaSuccess) return cuda_fail(e, "bssn_rhs interior");
@@ -540,10 +555,11 @@ static bssn_status run_stage_mixed(bssn_ctx* ctx, int src, int mode, int out, do
   a.mode = mode;
   cudaError_t e;
   if (ctx->prof && (e = prof_mark(ctx, ctx->ev_stage)) != cudaSuccess) return cuda_fail(e, "profile");
-  if (ctx->tile == tile_config_count())
-    e = launch_stage_mixed_tma(ctx->g, a, ctx->tmap[src], ctx->err, ctx->stream);
-  else if (ctx->tile > tile_config_count())
-    e = launch_stage_mixed_split(ctx->g, a, ctx->dr, ctx->stream, ctx->tile - tile_config_count() - 1);
+  if (tma_variant(ctx->tile) >= 0)
+    e = launch_stage_mixed_tma(ctx->g, a, ctx->tmap[tma_variant(ctx->tile)][src], ctx->err, ctx->stream,
+                               tma_variant(ctx->tile));
+  else if (split_variant(ctx->tile) >= 0)
+    e = launch_stage_mixed_split(ctx->g, a, ctx->dr, ctx->stream, split_variant(ctx->tile));
   else
     e = launch_stage_mixed(ctx->g, a, ctx->stream, ctx->tile);
   if (e != cudaSuccess) return cuda_fail(e, "stage");
@@ -852,21 +868,22 @@ bssn_status bssn_wait_state(bssn_ctx* ctx) {
   return check_err(ctx);
 }
 
-// Configurations: [0, tile_config_count()) the fused kernels;
-// tile_config_count() the TMA-staged mixed kernel; then the split-stage
+// Configurations: [0, tile_config_count()) the fused kernels; the next
+// N_TMA the TMA-staged mixed kernels; then the split-stage
 // variants.
-int32_t bssn_tile_count(void) { return tile_config_count() + 1 + split_config_count(); }
+int32_t bssn_tile_count(void) { return tile_config_count() + N_TMA + split_config_count(); }
 
 const char* bssn_tile_name(int32_t cfg) {
-  if (cfg == tile_config_count()) return "tma32x4x1/2";
-  if (cfg > tile_config_count()) return split_config_name(cfg - tile_config_count() - 1);
+  if (tma_variant(cfg) == 0) return "tma32x4x1/2";
+  if (tma_variant(cfg) == 1) return "tma32x8x1/1";
+  if (split_variant(cfg) >= 0) return split_config_name(split_variant(cfg));
   return tile_config_name(cfg);
 }
 
 static bool tile_usable(const bssn_ctx* ctx, int cfg) {
   if (cfg < 0 || cfg >= bssn_tile_count()) return false;
-  if (cfg == tile_config_count()) return ctx->p.precision == BSSN_MIXED && ctx->tmap_ok;
-  if (cfg > tile_config_count()) return ctx->p.precision == BSSN_MIXED;
+  if (tma_variant(cfg) >= 0) return ctx->p.precision == BSSN_MIXED && ctx->tmap_ok;
+  if (split_variant(cfg) >= 0) return ctx->p.precision == BSSN_MIXED;
   return true;
 }
 
@@ -920,9 +937,11 @@ bssn_status bssn_autotune(bssn_ctx* ctx, int32_t reps, int32_t* best, double* ms
       a.yn = ctx->yn; a.out0 = ctx->m32[o]; a.out0w = ctx->mw[o];
       a.ksum = ctx->ks32; a.ksumw = ctx->ksw; a.a_dt = 0.5 * ctx->p.dt; a.a_dtf = (float)a.a_dt;
       a.w_thr = ctx->p.w_fp64_threshold; a.mode = second ? MODE_MID : MODE_FIRST;
-      if (c == tile_config_count()) return launch_stage_mixed_tma(ctx->g, a, ctx->tmap[q], ctx->err, ctx->stream);
-      if (c > tile_config_count())
-        return launch_stage_mixed_split(ctx->g, a, ctx->dr, ctx->stream, c - tile_config_count() - 1);
+      if (tma_variant(c) >= 0)
+        return launch_stage_mixed_tma(ctx->g, a, ctx->tmap[tma_variant(c)][q], ctx->err, ctx->stream,
+                                      tma_variant(c));
+      if (split_variant(c) >= 0)
+        return launch_stage_mixed_split(ctx->g, a, ctx->dr, ctx->stream, split_variant(c));
       return launch_stage_mixed(ctx->g, a, ctx->stream, c);
     };
     auto launch = [&]() -> cudaError_t {

@@ -216,9 +216,11 @@ int tile_config_count();
 const char* tile_config_name(int c);
 // TMA-staged mixed stage kernel (k_stage_tma.cu); map describes the float
 // stage buffer that is the stencil source.
-cudaError_t make_stage_tensor_map(const Grid& g, const float* base, CUtensorMap* out);
+// Tensor map of a float stage buffer for TMA-staged variant v (0: 32 x 4 x 1
+// tiles, 1: 32 x 8 x 1; the box is the tile plus three ghost layers).
+cudaError_t make_stage_tensor_map(const Grid& g, const float* base, CUtensorMap* out, int variant = 0);
 cudaError_t launch_stage_mixed_tma(const Grid& g, const StageArgsMixed& a, const CUtensorMap& map,
-                                   int* err, cudaStream_t s);
+                                   int* err, cudaStream_t s, int variant = 0);
 // Split mixed stage (k_stage_split.cu): a stencil pass into the derivative
 // register dr (split_slot_count() float fields of the register layout) and an
 // algebra pass.

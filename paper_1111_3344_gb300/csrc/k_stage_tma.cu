@@ -20,19 +20,21 @@
 
 namespace bssn {
 
-__global__ void __launch_bounds__(TTX * TTY * TTZ, 2)
+// Sh: tile shape (tma_tile.cuh); MINB: blocks per SM the registers are capped for.
+template <typename Sh, int MINB>
+__global__ void __launch_bounds__(Sh::TX * Sh::TY * Sh::TZ, MINB)
     stage_mixed_tma_kernel(const __grid_constant__ CUtensorMap tmap, Grid g, StageArgsMixed a,
                            int* __restrict__ err) {
   extern __shared__ __align__(128) float smem_raw[];
   __shared__ __align__(8) unsigned long long mbar;
   // 128-byte aligned start for the TMA destinations
   float* smem = smem_raw + ((128 - (smem_addr(smem_raw) & 127)) & 127) / sizeof(float);
-  const int tid = threadIdx.x + TTX * (threadIdx.y + TTY * threadIdx.z);
-  const int ii0 = blockIdx.x * TTX, jj0 = blockIdx.y * TTY, kk0 = blockIdx.z * TTZ;
+  const int tid = threadIdx.x + Sh::TX * (threadIdx.y + Sh::TY * threadIdx.z);
+  const int ii0 = blockIdx.x * Sh::TX, jj0 = blockIdx.y * Sh::TY, kk0 = blockIdx.z * Sh::TZ;
   const unsigned bar = smem_addr(&mbar);
   if (tid == 0) mbar_init(bar);
   __syncthreads();
-  if (tid == 0) issue_staged_loads(&tmap, bar, smem, ii0, jj0, kk0);
+  if (tid == 0) issue_staged_loads<Sh>(&tmap, bar, smem, ii0, jj0, kk0);
   if (!mbar_wait(bar, 0, WAIT_LIMIT)) {
     if (tid == 0) atomicExch(err, 1);
     mbar_wait(bar, 0, WAIT_LIMIT);  // let this block's own copies land before it exits
@@ -42,14 +44,14 @@ __global__ void __launch_bounds__(TTX * TTY * TTZ, 2)
   const int ii = ii0 + ti, jj = jj0 + tj, kk = kk0 + tk;
   if (ii >= g.n0 || jj >= g.n1 || kk >= g.n2) return;
   const int i = ii + GH, j = jj + GH, k = kk + GH;
-  TileAcc acc;
+  TileAccT<Sh> acc;
   acc.st = a.src;
   acc.id = lin(g, i, j, k);
   acc.fs = g.fstride;
   acc.sd[0] = 1;
   acc.sd[1] = g.pitch;
   acc.sd[2] = g.plane;
-  acc.sm = smem + ((tk + GH) * BYP + (tj + GH)) * BXP + (ti + GH);
+  acc.sm = smem + ((tk + GH) * Sh::BY + (tj + GH)) * Sh::BX + (ti + GH);
   stage_point_mixed_acc(g, a, acc, ii, jj, kk);
 }
 
@@ -58,7 +60,7 @@ namespace {
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 }
 
-cudaError_t make_stage_tensor_map(const Grid& g, const float* base, CUtensorMap* out) {
+cudaError_t make_stage_tensor_map(const Grid& g, const float* base, CUtensorMap* out, int variant) {
   if (!g_encode) {
     cudaDriverEntryPointQueryResult q;
     cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", (void**)&g_encode, 12000,
@@ -66,9 +68,10 @@ cudaError_t make_stage_tensor_map(const Grid& g, const float* base, CUtensorMap*
     if (e != cudaSuccess) return e;
     if (q != cudaDriverEntryPointSuccess || !g_encode) return cudaErrorNotSupported;
   }
+  const int by = variant == 1 ? TmaShape<8>::BY : TmaShape<4>::BY;
   cuuint64_t dims[4] = {(cuuint64_t)g.pitch, (cuuint64_t)g.sy, (cuuint64_t)g.sz, (cuuint64_t)NF};
   cuuint64_t strides[3] = {(cuuint64_t)g.pitch * 4, (cuuint64_t)g.plane * 4, (cuuint64_t)g.fstride * 4};
-  cuuint32_t box[4] = {BXP, BYP, BZP, 1};
+  cuuint32_t box[4] = {(cuuint32_t)TmaDefault::BX, (cuuint32_t)by, (cuuint32_t)TmaDefault::BZ, 1};
   cuuint32_t estr[4] = {1, 1, 1, 1};
   CUresult r = g_encode(out, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, (void*)base, dims, strides, box, estr,
                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -76,19 +79,28 @@ cudaError_t make_stage_tensor_map(const Grid& g, const float* base, CUtensorMap*
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-cudaError_t launch_stage_mixed_tma(const Grid& g, const StageArgsMixed& a, const CUtensorMap& map,
-                                   int* err, cudaStream_t s) {
+template <typename Sh, int MINB>
+static cudaError_t launch_tma(const Grid& g, const StageArgsMixed& a, const CUtensorMap& map, int* err,
+                              cudaStream_t s) {
   static bool attr = false;
-  const int bytes = SMEM_BYTES;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(stage_mixed_tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaError_t e = cudaFuncSetAttribute(stage_mixed_tma_kernel<Sh, MINB>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, Sh::SMEM);
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  dim3 block(TTX, TTY, TTZ);
-  dim3 grid((g.n0 + TTX - 1) / TTX, (g.n1 + TTY - 1) / TTY, (g.n2 + TTZ - 1) / TTZ);
-  stage_mixed_tma_kernel<<<grid, block, bytes, s>>>(map, g, a, err);
+  dim3 block(Sh::TX, Sh::TY, Sh::TZ);
+  dim3 grid((g.n0 + Sh::TX - 1) / Sh::TX, (g.n1 + Sh::TY - 1) / Sh::TY, (g.n2 + Sh::TZ - 1) / Sh::TZ);
+  stage_mixed_tma_kernel<Sh, MINB><<<grid, block, Sh::SMEM, s>>>(map, g, a, err);
   return cudaGetLastError();
+}
+
+// variant 0: 32 x 4 x 1 tiles, two blocks per SM; 1: 32 x 8 x 1 tiles, one
+// block per SM (half the shared memory per SM, so more L1 for the fields read
+// through it); map: a tensor map made for the same variant
+cudaError_t launch_stage_mixed_tma(const Grid& g, const StageArgsMixed& a, const CUtensorMap& map,
+                                   int* err, cudaStream_t s, int variant) {
+  return variant == 1 ? launch_tma<TmaShape<8>, 1>(g, a, map, err, s) : launch_tma<TmaShape<4>, 2>(g, a, map, err, s);
 }
 
 }  // namespace bssn

@@ -15,16 +15,29 @@
 
 namespace bssn {
 
-constexpr int TTX = 32, TTY = 4, TTZ = 1;
-constexpr int BXP = 40;            // box extent in x: TTX + 6 rounded up to a multiple of 4 floats
-constexpr int BYP = TTY + 2 * GH;  // 10
-constexpr int BZP = TTZ + 2 * GH;  // 7
-constexpr int BOXF = BXP * BYP * BZP;             // floats of one field's box (2800)
-constexpr int SLOTF = (BOXF + 31) / 32 * 32;      // slot stride: 128-byte aligned boxes
 constexpr int NSTAGED = 8;
-constexpr unsigned STAGED_BYTES = NSTAGED * BOXF * sizeof(float);  // bytes the copies deliver
-constexpr int SMEM_BYTES = NSTAGED * SLOTF * (int)sizeof(float) + 128;  // + alignment slack
 constexpr long long WAIT_LIMIT = 1LL << 24;
+
+// Tile of 32 x TY x 1 interior points and its boxes: BX = 32 + 6 rounded up
+// to a multiple of 4 floats, BY = TY + 6, BZ = 7 (three ghost layers on every
+// side); slots of the staged fields 128-byte aligned.
+template <int TY_>
+struct TmaShape {
+  static constexpr int TX = 32, TY = TY_, TZ = 1;
+  static constexpr int BX = 40, BY = TY + 2 * GH, BZ = TZ + 2 * GH;
+  static constexpr int BOX = BX * BY * BZ;                              // floats of one field's box
+  static constexpr int SLOT = (BOX + 31) / 32 * 32;                     // slot stride
+  static constexpr unsigned BYTES = NSTAGED * BOX * sizeof(float);     // bytes the copies deliver
+  static constexpr int SMEM = NSTAGED * SLOT * (int)sizeof(float) + 128;  // + alignment slack
+};
+
+// the 32 x 4 x 1 tile (two blocks per SM): the batched kernel and the names below
+using TmaDefault = TmaShape<4>;
+constexpr int TTX = TmaDefault::TX, TTY = TmaDefault::TY, TTZ = TmaDefault::TZ;
+constexpr int BXP = TmaDefault::BX, BYP = TmaDefault::BY, BZP = TmaDefault::BZ;
+constexpr int BOXF = TmaDefault::BOX, SLOTF = TmaDefault::SLOT;
+constexpr unsigned STAGED_BYTES = TmaDefault::BYTES;
+constexpr int SMEM_BYTES = TmaDefault::SMEM;
 
 __host__ __device__ __forceinline__ int staged_field(int s) {
   return s == 0 ? F_CHI : (s <= 6 ? F_GT + (s - 1) : F_ALP);
@@ -34,22 +47,24 @@ __device__ __forceinline__ int staged_slot(int f) {
 }
 
 // Accessor: staged fields from the shared box, the others from global.
-struct TileAcc {
+template <typename Sh>
+struct TileAccT {
   const float* __restrict__ st;
   long long id, fs, sd[3];
   const float* sm;  // shared address of this point in slot 0
   __device__ __forceinline__ const float* ptr(int f) const {
     const int sl = staged_slot(f);
-    return sl >= 0 ? sm + sl * SLOTF : st + (long long)f * fs + id;
+    return sl >= 0 ? sm + sl * Sh::SLOT : st + (long long)f * fs + id;
   }
   __device__ __forceinline__ long long s(int f, int d) const {
-    return staged_slot(f) >= 0 ? (d == 0 ? 1 : (d == 1 ? BXP : BXP * BYP)) : sd[d];
+    return staged_slot(f) >= 0 ? (d == 0 ? 1 : (d == 1 ? Sh::BX : Sh::BX * Sh::BY)) : sd[d];
   }
   template <typename T>
   __device__ __forceinline__ T ld(int f, const float* p) const {
     return staged_slot(f) >= 0 ? T(*p) : T(__ldg(p));
   }
 };
+using TileAcc = TileAccT<TmaDefault>;
 
 __device__ __forceinline__ unsigned smem_addr(const void* p) {
   return (unsigned)__cvta_generic_to_shared(p);
@@ -77,17 +92,19 @@ __device__ __forceinline__ void mbar_init(unsigned bar) {
 // Thread 0: arm the barrier for the staged bytes and issue one tensor load per
 // staged field, box origin (x0, y0, z0) in stored coordinates (the interior
 // start of the tile minus the ghost width; x0 a multiple of 32, so the
-// innermost offset is a multiple of 16 bytes).
+// innermost offset is a multiple of 16 bytes).  The tensor map's box is
+// Sh::BX x Sh::BY x Sh::BZ.
+template <typename Sh = TmaDefault>
 __device__ __forceinline__ void issue_staged_loads(const void* tmap, unsigned bar, float* smem, int x0, int y0,
                                                    int z0) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(STAGED_BYTES)
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(Sh::BYTES)
                : "memory");
 #pragma unroll
   for (int s = 0; s < NSTAGED; s++) {
     const int f = staged_field(s);
     asm volatile(
         "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-        " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_addr(smem + s * SLOTF)),
+        " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_addr(smem + s * Sh::SLOT)),
         "l"(reinterpret_cast<unsigned long long>(tmap)), "r"(x0), "r"(y0), "r"(z0), "r"(f), "r"(bar)
         : "memory");
   }
