@@ -5,6 +5,10 @@
 namespace bssn {
 
 constexpr int BATCH_MAX = BSSN_BATCH_MAX_MEMBERS;
+// work lists of a batch: every active member (boundary, persistent and TMA
+// stage kernels); float64 members with full tiles and the others (the
+// one-block-per-tile stage kernels, one point function each)
+constexpr int WORK_ALL = 0, WORK_FULL = 1, WORK_REST = 2, NWORK = 3;
 
 // One member as the batched kernels see it: its grid and the arguments of its
 // four RK4 stages (pointer roles fixed, y_n advanced in place).
@@ -29,17 +33,25 @@ struct BatchWork {
   unsigned long long bc_base[BATCH_MAX + 1];
 };
 
-// Tile configurations of the batched stage: [0, count - 1) fused kernels
-// (both precisions); count - 1 the TMA-staged kernel (mixed only).
+// Tile configurations of the batched stage: persistent fused kernels (both
+// precisions), one-block-per-tile fused kernels (both precisions), and last
+// the TMA-staged kernel (mixed only).
 int batch_tile_config_count();
 const char* batch_tile_config_name(int c);
 void batch_tile_shape(int c, int& tx, int& ty, int& tz);
 bool batch_tile_is_tma(int c);
+bool batch_tile_is_per_tile(int c);
 int batch_default_tile(bool mixed);
-// Persistent stage kernel over every active member's tiles (grid = blocks).
-// err: device error word (a bounded wait of the TMA kernel gave up).
-cudaError_t launch_batch_stage(int cfg, bool mixed, const MemberDev* mem, const BatchWork* wk,
-                               int stage, int* err, cudaStream_t s);
+// Whether a float64 member has full tiles under configuration cfg (n0 a
+// multiple of 32 = the tile's x extent, n1 and n2 of its y and z extents).
+bool batch_tile_full(int cfg, const Grid& g);
+// Stage kernel over the tiles of one work list.  Persistent and TMA-staged
+// configurations: grid = resident blocks, every member (WORK_ALL).
+// One-block-per-tile configurations: grid = ntiles, the list's tile count;
+// full selects the full-block float64 point function (WORK_FULL).  err: device
+// error word (a bounded wait of the TMA kernel gave up).
+cudaError_t launch_batch_stage(int cfg, bool mixed, bool full, const MemberDev* mem, const BatchWork* wk,
+                               unsigned ntiles, int stage, int* err, cudaStream_t s);
 // TMA-staged form (k_batch_tma.cu)
 void batch_tma_tile_shape(int& tx, int& ty, int& tz);
 cudaError_t prepare_batch_stage_tma();

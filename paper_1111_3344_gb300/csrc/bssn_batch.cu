@@ -138,11 +138,11 @@ struct bssn_batch {
   Pool alloc;
   std::vector<Member> m;
   MemberDev* d_mem;
-  BatchWork* d_work;
+  BatchWork* d_work;  // NWORK lists (batch_internal.cuh)
   int* d_err;          // error word of the TMA-staged kernel's bounded waits
   bool tma_ok = true;  // every member's tensor maps could be encoded
   std::vector<MemberDev> h_mem;
-  BatchWork h_work;
+  BatchWork h_work[NWORK];
   bool work_dirty = true;
   int cfg = 0;
   cudaGraph_t graph = nullptr;
@@ -217,30 +217,69 @@ cudaError_t upload_member(bssn_batch* b, int id) {
 }
 
 cudaError_t rebuild_work(bssn_batch* b) {
-  BatchWork& W = b->h_work;
-  W.count = 0;
-  W.total_tiles = 0;
-  W.total_bc = 0;
-  unsigned tb = 0;
+  for (int w = 0; w < NWORK; w++) {
+    BatchWork& W = b->h_work[w];
+    W.count = 0;
+    W.total_tiles = 0;
+    W.total_bc = 0;
+  }
+  unsigned tb[NWORK] = {0, 0, 0};
   unsigned long long bb = 0;
   for (int id = 0; id < b->maxm; id++) {
     const Member& M = b->m[id];
     if (!M.used || !M.active) continue;
     const MemberDev& D = b->h_mem[id];
-    W.member[W.count] = id;
-    W.tile_base[W.count] = tb;
-    W.bc_base[W.count] = bb;
-    tb += (unsigned)D.tiles[0] * D.tiles[1] * D.tiles[2];
-    const unsigned long long ng = ghost_count(M.g);
-    bb += ng;  // one thread per ghost point (every field)
-    W.count++;
+    const unsigned tiles = (unsigned)D.tiles[0] * D.tiles[1] * D.tiles[2];
+    const int v = batch_tile_full(b->cfg, M.g) ? WORK_FULL : WORK_REST;
+    for (int w : {WORK_ALL, v}) {
+      BatchWork& W = b->h_work[w];
+      W.member[W.count] = id;
+      W.tile_base[W.count] = tb[w];
+      if (w == WORK_ALL) W.bc_base[W.count] = bb;
+      tb[w] += tiles;
+      W.count++;
+    }
+    bb += ghost_count(M.g);  // one thread per ghost point (every field)
   }
-  W.tile_base[W.count] = tb;
-  W.bc_base[W.count] = bb;
-  W.total_tiles = tb;
-  W.total_bc = bb;
+  for (int w = 0; w < NWORK; w++) {
+    BatchWork& W = b->h_work[w];
+    W.tile_base[W.count] = tb[w];
+    W.total_tiles = tb[w];
+  }
+  BatchWork& A = b->h_work[WORK_ALL];
+  A.bc_base[A.count] = bb;
+  A.total_bc = bb;
   b->work_dirty = false;
-  return cudaMemcpyAsync(b->d_work, &W, sizeof(BatchWork), cudaMemcpyHostToDevice, b->stream);
+  // the one-block-per-tile kernels are captured with the lists' tile counts as
+  // their grids: the graph is made again for the new composition
+  if (batch_tile_is_per_tile(b->cfg)) {
+    if (b->exec) {
+      cudaGraphExecDestroy(b->exec);
+      b->exec = nullptr;
+    }
+    if (b->graph) {
+      cudaGraphDestroy(b->graph);
+      b->graph = nullptr;
+    }
+  }
+  return cudaMemcpyAsync(b->d_work, b->h_work, sizeof(b->h_work), cudaMemcpyHostToDevice, b->stream);
+}
+
+// The stage launches of one RK4 stage under configuration cfg: persistent and
+// TMA-staged kernels, one launch over every member; one-block-per-tile
+// kernels, one launch per float64 list (members with full tiles, the others),
+// or one over every member (mixed).
+cudaError_t launch_stage_lists(bssn_batch* b, int cfg, int stage) {
+  const bool mixed = b->precision == BSSN_MIXED;
+  if (!batch_tile_is_per_tile(cfg) || mixed)
+    return launch_batch_stage(cfg, mixed, false, b->d_mem, b->d_work + WORK_ALL, b->h_work[WORK_ALL].total_tiles,
+                              stage, b->d_err, b->stream);
+  cudaError_t e = launch_batch_stage(cfg, false, true, b->d_mem, b->d_work + WORK_FULL,
+                                     b->h_work[WORK_FULL].total_tiles, stage, b->d_err, b->stream);
+  if (e == cudaSuccess)
+    e = launch_batch_stage(cfg, false, false, b->d_mem, b->d_work + WORK_REST, b->h_work[WORK_REST].total_tiles,
+                           stage, b->d_err, b->stream);
+  return e;
 }
 
 cudaError_t capture(bssn_batch* b) {
@@ -256,8 +295,8 @@ cudaError_t capture(bssn_batch* b) {
   if (e != cudaSuccess) return e;
   const bool mixed = b->precision == BSSN_MIXED;
   for (int s = 0; s < 4 && e == cudaSuccess; s++) {
-    e = launch_batch_stage(b->cfg, mixed, b->d_mem, b->d_work, s, b->d_err, b->stream);
-    if (e == cudaSuccess) e = launch_batch_boundary(mixed, b->d_mem, b->d_work, s, b->stream);
+    e = launch_stage_lists(b, b->cfg, s);
+    if (e == cudaSuccess) e = launch_batch_boundary(mixed, b->d_mem, b->d_work + WORK_ALL, s, b->stream);
   }
   cudaGraph_t g = nullptr;
   cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
@@ -340,7 +379,7 @@ size_t bssn_batch_member_bytes(const bssn_params* p) {
 
 size_t bssn_batch_table_bytes(int32_t max_members) {
   if (max_members < 1 || max_members > BATCH_MAX) return 0;
-  return aup(sizeof(MemberDev) * (size_t)max_members) + aup(sizeof(BatchWork)) + aup(sizeof(int));
+  return aup(sizeof(MemberDev) * (size_t)max_members) + aup(NWORK * sizeof(BatchWork)) + aup(sizeof(int));
 }
 
 bssn_status bssn_batch_create(int32_t precision, int32_t max_members, void* d_pool, size_t pool_bytes,
@@ -364,10 +403,10 @@ bssn_status bssn_batch_create(int32_t precision, int32_t max_members, void* d_po
   b->alloc.init(tb, pool_bytes);
   b->m.resize(max_members);
   b->h_mem.resize(max_members);
-  memset(&b->h_work, 0, sizeof(BatchWork));
+  memset(b->h_work, 0, sizeof(b->h_work));
   b->d_mem = (MemberDev*)b->pool;
   b->d_work = (BatchWork*)(b->pool + aup(sizeof(MemberDev) * (size_t)max_members));
-  b->d_err = (int*)((char*)b->d_work + aup(sizeof(BatchWork)));
+  b->d_err = (int*)((char*)b->d_work + aup(NWORK * sizeof(BatchWork)));
   b->cfg = batch_default_tile(precision == BSSN_MIXED);
   cudaError_t e = batch_tile_is_tma(b->cfg) ? prepare_batch_stage_tma() : cudaSuccess;
   if (e == cudaSuccess) e = cudaMemsetAsync(b->d_err, 0, sizeof(int), b->stream);
@@ -512,7 +551,7 @@ bssn_status bssn_batch_step(bssn_batch* b, int32_t nsteps) {
   if (b->work_dirty) e = rebuild_work(b);
   if (e == cudaSuccess && !b->exec) e = capture(b);
   if (e != cudaSuccess) return bcuda(e, "batch step setup");
-  if (b->h_work.count == 0) return BSSN_OK;
+  if (b->h_work[WORK_ALL].count == 0) return BSSN_OK;
   for (int s = 0; s < nsteps; s++) {
     e = cudaGraphLaunch(b->exec, b->stream);
     if (e != cudaSuccess) return bcuda(e, "batch graph launch");
@@ -580,10 +619,9 @@ bssn_status bssn_batch_autotune(bssn_batch* b, int32_t reps, int32_t* best, doub
     // stages 0 and 1 write only stage buffers and the k-sum (y_n is left
     // unchanged, the next step overwrites them); the second stage carries the
     // combine's extra loads, which the first alone would not weigh
-    const bool mixed = b->precision == BSSN_MIXED;
     auto pair = [&]() -> cudaError_t {
-      cudaError_t r = launch_batch_stage(c, mixed, b->d_mem, b->d_work, 0, b->d_err, b->stream);
-      return r == cudaSuccess ? launch_batch_stage(c, mixed, b->d_mem, b->d_work, 1, b->d_err, b->stream) : r;
+      cudaError_t r = launch_stage_lists(b, c, 0);
+      return r == cudaSuccess ? launch_stage_lists(b, c, 1) : r;
     };
     e = pair();
     cudaEventRecord(e0, b->stream);

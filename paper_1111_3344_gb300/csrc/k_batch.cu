@@ -95,6 +95,44 @@ __global__ void __launch_bounds__(TX * TY * TZ, MINB)
   }
 }
 
+// One block per tile of one work list (grid = the list's tile count): the
+// block looks up its member once and runs one point function.  Against the
+// persistent kernel above this trades the resident-block loop for a launch
+// over all tiles; the compiler then allocates registers as for a single-grid
+// stage (about 200 B of spills per thread for float64, against 1.2-1.8 KB in
+// the loop).  FULL (float64): every member of the list has full tiles, so every
+// warp is a full x-row and every thread of a block is inside the grid.
+template <int TX, int TY, int TZ, int MINB, bool MIXED, bool FULL>
+__global__ void __launch_bounds__(TX * TY * TZ, MINB)
+    batch_tile_kernel(const MemberDev* __restrict__ mem, const BatchWork* __restrict__ wk, int stage) {
+  __shared__ int sid;
+  __shared__ unsigned slocal;
+  const int tid = threadIdx.x + TX * (threadIdx.y + TY * threadIdx.z);
+  const unsigned t = blockIdx.x;
+  if (t >= wk->total_tiles) return;  // whole block
+  if (tid == 0) {
+    const int slot = find_member(wk->tile_base, wk->count, t);
+    sid = wk->member[slot];
+    slocal = t - wk->tile_base[slot];
+  }
+  __syncthreads();
+  const MemberDev& M = mem[sid];
+  unsigned lt = slocal;
+  const int bx = (int)(lt % (unsigned)M.tiles[0]);
+  lt /= (unsigned)M.tiles[0];
+  const int by = (int)(lt % (unsigned)M.tiles[1]);
+  const int bz = (int)(lt / (unsigned)M.tiles[1]);
+  const int ii = bx * TX + threadIdx.x, jj = by * TY + threadIdx.y, kk = bz * TZ + threadIdx.z;
+  if (ii < M.g.n0 && jj < M.g.n1 && kk < M.g.n2) {
+    if constexpr (MIXED)
+      stage_point_mixed(M.g, M.amx[stage], ii, jj, kk);
+    else if constexpr (FULL && TX == 32)
+      stage_point_fp64<32, TY, TZ>(M.g, M.a64[stage], ii, jj, kk);
+    else
+      stage_point_fp64<0>(M.g, M.a64[stage], ii, jj, kk);
+  }
+}
+
 template <bool MIXED>
 __global__ void batch_boundary_kernel(const MemberDev* __restrict__ mem, const BatchWork* __restrict__ wk,
                                       int stage) {
@@ -150,21 +188,48 @@ static const BatchCfg k_bcfg[] = {
 };
 #undef BCFG
 
-constexpr int N_FUSED = (int)(sizeof(k_bcfg) / sizeof(k_bcfg[0]));
+// one-block-per-tile configurations
+struct TileCfgB {
+  const char* name;
+  int tx, ty, tz;
+  const void* k64full;
+  const void* k64;
+  const void* kmx;
+};
+#define TCFG(TX, TY, TZ, MINB)                                                      \
+  { "tiles" #TX "x" #TY "x" #TZ "/" #MINB, TX, TY, TZ,                            \
+    (const void*)batch_tile_kernel<TX, TY, TZ, MINB, false, true>,                \
+    (const void*)batch_tile_kernel<TX, TY, TZ, MINB, false, false>,               \
+    (const void*)batch_tile_kernel<TX, TY, TZ, MINB, true, false> }
+static const TileCfgB k_tcfg[] = {TCFG(32, 4, 1, 2), TCFG(32, 8, 1, 1)};
+#undef TCFG
 
-int batch_tile_config_count() { return N_FUSED + 1; }
+constexpr int N_FUSED = (int)(sizeof(k_bcfg) / sizeof(k_bcfg[0]));
+constexpr int N_TILE = (int)(sizeof(k_tcfg) / sizeof(k_tcfg[0]));
+constexpr int C_TMA = N_FUSED + N_TILE;
+
+int batch_tile_config_count() { return C_TMA + 1; }
 // Default tile of a new batch (the serving loop keeps it): the fastest
-// configuration of the 64-binary batched workload on GB300 -- the TMA-staged
-// kernel for mixed batches, 32x4x1/3 for float64 ones.
-int batch_default_tile(bool mixed) { return mixed ? N_FUSED : 2; }
-bool batch_tile_is_tma(int c) { return c == N_FUSED; }
+// persistent configuration of the 64-binary batched workload on GB300 -- the
+// TMA-staged kernel for mixed batches, 32x4x1/3 for float64 ones.
+int batch_default_tile(bool mixed) { return mixed ? C_TMA : 2; }
+bool batch_tile_is_tma(int c) { return c == C_TMA; }
+bool batch_tile_is_per_tile(int c) { return c >= N_FUSED && c < C_TMA; }
 const char* batch_tile_config_name(int c) {
-  if (c == N_FUSED) return "tma32x4x1/2";
+  if (c == C_TMA) return "tma32x4x1/2";
+  if (batch_tile_is_per_tile(c)) return k_tcfg[c - N_FUSED].name;
   return (c >= 0 && c < N_FUSED) ? k_bcfg[c].name : "";
 }
 void batch_tile_shape(int c, int& tx, int& ty, int& tz) {
-  if (c == N_FUSED) {
+  if (c == C_TMA) {
     batch_tma_tile_shape(tx, ty, tz);
+    return;
+  }
+  if (batch_tile_is_per_tile(c)) {
+    const TileCfgB& t = k_tcfg[c - N_FUSED];
+    tx = t.tx;
+    ty = t.ty;
+    tz = t.tz;
     return;
   }
   if (c < 0 || c >= N_FUSED) c = 0;
@@ -173,9 +238,25 @@ void batch_tile_shape(int c, int& tx, int& ty, int& tz) {
   tz = k_bcfg[c].tz;
 }
 
-cudaError_t launch_batch_stage(int cfg, bool mixed, const MemberDev* mem, const BatchWork* wk,
-                               int stage, int* err, cudaStream_t s) {
-  if (cfg == N_FUSED && mixed) return launch_batch_stage_tma(mem, wk, stage, err, s);
+bool batch_tile_full(int cfg, const Grid& g) {
+  int tx, ty, tz;
+  batch_tile_shape(cfg, tx, ty, tz);
+  return tx == 32 && g.n0 % 32 == 0 && g.n1 % ty == 0 && g.n2 % tz == 0;
+}
+
+cudaError_t launch_batch_stage(int cfg, bool mixed, bool full, const MemberDev* mem, const BatchWork* wk,
+                               unsigned ntiles, int stage, int* err, cudaStream_t s) {
+  if (cfg == C_TMA && mixed) return launch_batch_stage_tma(mem, wk, stage, err, s);
+  if (batch_tile_is_per_tile(cfg)) {
+    const TileCfgB& c = k_tcfg[cfg - N_FUSED];
+    if (ntiles == 0) return cudaSuccess;
+    full = full && !mixed;
+    const void* fn = mixed ? c.kmx : (full ? c.k64full : c.k64);
+    const size_t smem = full ? (size_t)11 * (c.ty + 4) * c.tz * 32 * sizeof(double) : 0;
+    dim3 block(c.tx, c.ty, c.tz);
+    void* args[] = {(void*)&mem, (void*)&wk, (void*)&stage};
+    return cudaLaunchKernel(fn, dim3(ntiles), block, args, smem, s);
+  }
   if (cfg < 0 || cfg >= N_FUSED) cfg = 0;
   const BatchCfg& c = k_bcfg[cfg];
   const void* fn = mixed ? c.kmx : c.k64;
