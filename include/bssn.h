@@ -347,9 +347,15 @@ bssn_status bssn_batch_get_state(bssn_batch* b, int32_t member, double* host, do
 /* Advance every active member nsteps RK4 steps (asynchronous). */
 bssn_status bssn_batch_step(bssn_batch* b, int32_t nsteps);
 bssn_status bssn_batch_constraints(bssn_batch* b, int32_t member, double out[16]); /* synchronises */
-/* Tile configurations of the persistent stage kernel.  The last one,
- * "tma32x4x1/2", stages W, gt_ij and alpha of each 32x4x1 tile in shared
- * memory by tensor loads (mixed batches only; BSSN_EINVAL for float64).  A
+/* Tile configurations of the batched stage, each one launch per RK4 stage over
+ * every active member's tiles:
+ *   "TXxTYxTZ/B"     persistent kernels (resident blocks loop over the tiles);
+ *   "tilesTXxTYxTZ/B" one block per tile (no loop, fewer register spills; the
+ *                    graph is captured again when the membership changes);
+ *   "tma32x4x1/2"    (last) persistent, staging W, gt_ij and alpha of each
+ *                    32x4x1 tile in shared memory by tensor loads (mixed
+ *                    batches only; BSSN_EINVAL for float64).
+ * A new batch starts on "tma32x4x1/2" (mixed) or "32x4x1/3" (float64).  A
  * tensor-load wait that gives up (bounded) makes the next
  * bssn_batch_get_state or bssn_batch_constraints return BSSN_ETIMEOUT. */
 int32_t bssn_batch_tile_count(void);
