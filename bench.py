@@ -427,6 +427,15 @@ def run_batched(args):
     ms = start.elapsed_time(stop)
     pts = sum(p.n[0] * p.n[1] * p.n[2] for p in params)
     value = pts * args.steps / (ms * 1e-3) / 1e6
+    # launches per step: a stage and a boundary launch per RK4 stage; the
+    # one-block-per-tile float64 configurations launch the members with full
+    # tiles and the others separately
+    tname = list(tile_ms)[best]
+    stage_launches = 1
+    if tname.startswith("tiles") and args.precision == "fp64":
+        tx, ty, tz = (int(v) for v in tname[len("tiles"):].split("/")[0].split("x"))
+        full = [tx == 32 and p.n[0] % 32 == 0 and p.n[1] % ty == 0 and p.n[2] % tz == 0 for p in params]
+        stage_launches = int(any(full)) + int(not all(full))
     line = {"metric": f"batched BSSN RK4 point-updates/s ({args.precision})", "value": value,
             "unit": "Mpoint-updates/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -434,7 +443,7 @@ def run_batched(args):
             "config": {"workload": f"{len(params)} Brill-Lindquist binaries, grids {{48,64,96,128}}^3, seed 1111",
                        "interior_points": pts, "tile": list(tile_ms)[best],
                        "autotune_ms_stage1": {k: round(v, 3) for k, v in tile_ms.items() if v >= 0},
-                       "launches_per_step": 8, "graph": True}}
+                       "launches_per_step": 4 * (stage_launches + 1), "graph": True}}
     print(json.dumps(line))
     batch.close()
 
