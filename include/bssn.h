@@ -417,7 +417,8 @@ bssn_status bssn_profile(bssn_ctx* ctx, int32_t enable, double out[4]);
  * Synchronises cuda_stream.  The reduction scratch is a fixed static device
  * array (2.25 MiB) that every GPU which loads the library holds until exit;
  * its device address is looked up on the first call made on each device, so
- * make that first call before any stream capture.  All calls on a device share
+ * make that first call before any stream capture (a lookup that fails returns
+ * ECUDA and is tried again on the next call).  All calls on a device share
  * that array: calls whose work overlaps on the GPU (other streams, other host
  * threads) race and must be serialised by the caller.  No cudaMalloc,
  * cudaFree or allocating library routine is called. */

@@ -40,30 +40,31 @@ static __device__ __align__(256) double g_noalloc_out[16];
 struct SymbolAddrs {
   double* partials = nullptr;
   double* out = nullptr;
-  cudaError_t err = cudaSuccess;
   bool done = false;
 };
 SymbolAddrs g_addrs[MAX_DEVICES];
 std::mutex g_addrs_mu;
 
 // Resolve the device addresses of the static arrays on the current device.
+// Only a successful lookup is remembered: after a failure (for instance a
+// first call made while the stream was being captured) the next call looks
+// the addresses up again.
 cudaError_t resolve(int dev, double** partials, double** out) {
   std::lock_guard<std::mutex> lk(g_addrs_mu);
   SymbolAddrs& s = g_addrs[dev];
   if (!s.done) {
     void* p = nullptr;
     void* o = nullptr;
-    s.err = cudaGetSymbolAddress(&p, g_noalloc_partials);
-    if (s.err == cudaSuccess) s.err = cudaGetSymbolAddress(&o, g_noalloc_out);
-    if (s.err == cudaSuccess) {
-      s.partials = (double*)p;
-      s.out = (double*)o;
-    }
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_partials);
+    if (e == cudaSuccess) e = cudaGetSymbolAddress(&o, g_noalloc_out);
+    if (e != cudaSuccess) return e;
+    s.partials = (double*)p;
+    s.out = (double*)o;
     s.done = true;
   }
   *partials = s.partials;
   *out = s.out;
-  return s.err;
+  return cudaSuccess;
 }
 
 bssn_status nfail(bssn_status st, const std::string& m) {

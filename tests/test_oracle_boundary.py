@@ -109,3 +109,62 @@ def test_periodic_fill_copies_interior():
         a = out[f]
         inner = a[g:-g, g:-g, g:-g]
         np.testing.assert_array_equal(a, np.pad(inner, g, mode="wrap"))
+
+
+def _all_classes_of_points(cfg):
+    """Every class of stored point of the grid: interior points (next to the
+    boundary and deep inside), and ghost points of each of the three layers on
+    faces, edges and corners of every side, (i, j, k) in stored indices."""
+    g = O.GHOST
+    ext = [cfg.n[d] + 2 * g for d in range(3)]
+    picks = []
+    for d in range(3):
+        lo = [0, 1, 2]                            # the three ghost layers below
+        hi = [ext[d] - 1, ext[d] - 2, ext[d] - 3]  # and above
+        inner = [g, g + 1, ext[d] // 2, ext[d] - g - 1]
+        picks.append(lo + hi + inner)
+    pts = [(i, j, k) for i in picks[0] for j in picks[1] for k in picks[2]]
+    return np.array(pts, dtype=np.int32)
+
+
+@pytest.mark.parametrize("use_w", [True, False])
+@pytest.mark.parametrize("shift", ["gamma-driver", "frozen"])
+def test_rhs_points_equals_whole_grid_rhs(use_w, shift):
+    """The point-wise oracle (rhs_points: each ghost point recurses through its
+    inner neighbours, the Sommerfeld layers innermost first) and the whole-grid
+    oracle (rhs: interior, then the three ghost layers in order) state the same
+    right-hand side, so they agree bit for bit at every class of point: the
+    interior, and every ghost layer on faces, edges and corners.  The whole-grid
+    form is the one the boundary pins above check; this carries those pins over
+    to the point-wise form that the full-size GPU tests compare against."""
+    from paper_1111_3344_gb300 import inputs
+    n = (13, 11, 12)
+    xmin = (-2.1, -1.7, -1.9)
+    h = 0.33
+    cfg = O.Config(n=n, xmin=xmin, h=h, periodic=False, use_w=use_w, shift=shift,
+                   punctures=[(0.7, 0.11, -0.05, 0.08)])
+    bg = O.initial_data(cfg, "bl", [1, 0.7, 0.11, -0.05, 0.08])
+    st = inputs.random_state(5, n, xmin, h, amp=0.05, background=bg)
+    whole = O.rhs(cfg, st)
+    ijk = _all_classes_of_points(cfg)
+    got = O.rhs_points(cfg, st, ijk)
+    want = np.stack([whole[:, k, j, i] for (i, j, k) in ijk])
+    assert np.array_equal(got, want)
+    # the sample holds ghost points of all three layers on faces, edges, corners
+    g = O.GHOST
+    depth = [sum(1 for d, v in enumerate(p) if v < g or v >= n[d] + g) for p in ijk]
+    assert {0, 1, 2, 3} <= set(depth)
+
+
+def test_rhs_points_periodic_ghosts_are_zero():
+    """On a periodic grid the right-hand side lives on interior points only; the
+    point-wise oracle gives 0 on ghosts, as the whole-grid one does."""
+    from paper_1111_3344_gb300 import inputs
+    n = (9, 8, 10)
+    cfg = O.Config(n=n, xmin=(-0.5,) * 3, h=1.0 / 9, periodic=True)
+    st = O.fill_periodic(cfg, inputs.random_state(3, n, (-0.5,) * 3, 1.0 / 9, amp=0.05))
+    whole = O.rhs(cfg, st)
+    ijk = _all_classes_of_points(cfg)
+    got = O.rhs_points(cfg, st, ijk)
+    want = np.stack([whole[:, k, j, i] for (i, j, k) in ijk])
+    assert np.array_equal(got, want)
