@@ -50,8 +50,11 @@ ID_KIND = {"flat": 0, "gauge_wave": 1, "bl": 2, "kasner": 3}
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "bssn_oracle.c")
+_HDR = os.path.join(_HERE, "bssn_rhs.h")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
+_INSTR_SRC = os.path.join(_HERE, "bssn_oracle_instrumented.cpp")
+_INSTR_PATH = os.path.join(_BUILD, "liboracle_instr.so")
 _lock = threading.Lock()
 _lib = None
 
@@ -137,18 +140,27 @@ class Config:
         return self.xmin[axis] + (i - GHOST + 0.5) * self.h
 
 
+def _compile(out: str, cmd_tail, deps, force: bool) -> str:
+    if (not force and os.path.exists(out)
+            and os.path.getmtime(out) >= max(os.path.getmtime(q) for q in deps)):
+        return out
+    tmp = out + f".{os.getpid()}.tmp"
+    subprocess.run([*cmd_tail[:1], *cmd_tail[1:], "-o", tmp], check=True)
+    os.replace(tmp, out)
+    return out
+
+
 def build(force: bool = False) -> str:
-    """Compile bssn_oracle.c with gcc into oracle/_build/liboracle.so."""
+    """Compile bssn_oracle.c with gcc into oracle/_build/liboracle.so, and the
+    instrumented right-hand side (bssn_oracle_instrumented.cpp: magnitudes and
+    operation counts of the same expressions) with g++ into
+    oracle/_build/liboracle_instr.so."""
     with _lock:
         os.makedirs(_BUILD, exist_ok=True)
-        if (not force and os.path.exists(_LIB_PATH)
-                and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
-            return _LIB_PATH
-        tmp = _LIB_PATH + f".{os.getpid()}.tmp"
-        cmd = ["gcc", "-O2", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared",
-               "-std=gnu11", "-o", tmp, _SRC, "-lm"]
-        subprocess.run(cmd, check=True)
-        os.replace(tmp, _LIB_PATH)
+        _compile(_LIB_PATH, ["gcc", "-O2", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared",
+                             "-std=gnu11", _SRC, "-lm"], (_SRC, _HDR), force)
+        _compile(_INSTR_PATH, ["g++", "-O2", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared",
+                               "-std=c++17", _INSTR_SRC], (_INSTR_SRC, _HDR), force)
         return _LIB_PATH
 
 
@@ -249,6 +261,77 @@ def rhs_points(cfg: Config, st: np.ndarray, ijk: np.ndarray) -> np.ndarray:
     lib.oracle_rhs_points(ctypes.byref(c), _dp(st), ijk.shape[0],
                           ijk.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _dp(out))
     return out
+
+
+_instr = None
+
+
+def _load_instr():
+    global _instr
+    if _instr is None:
+        _load()  # builds both libraries
+        lib = ctypes.CDLL(_INSTR_PATH)
+        P = ctypes.POINTER
+        dp = P(ctypes.c_double)
+        lib.oracle_rhs_points_mag.argtypes = [P(_OCfg), dp, ctypes.c_int, P(ctypes.c_int), dp, dp]
+        lib.oracle_rhs_points_ext.argtypes = [P(_OCfg), dp, ctypes.c_int, P(ctypes.c_int), dp]
+        lib.oracle_rhs_opcount.argtypes = [P(_OCfg), dp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                           P(ctypes.c_longlong)]
+        _instr = lib
+    return _instr
+
+
+def rhs_points_mag(cfg: Config, st: np.ndarray, ijk: np.ndarray):
+    """Right-hand side at stored points ijk (as rhs_points) by the instrumented
+    build: (values, magnitudes), each (P, 24).  The values equal rhs_points
+    bit for bit; a magnitude is the same expression evaluated on absolute
+    values (every difference a sum), the scale that bounds the rounding error
+    of any evaluation order of that expression (bssn_oracle_instrumented.cpp)."""
+    lib = _load_instr()
+    st = _state(cfg, st)
+    ijk = np.ascontiguousarray(ijk, dtype=np.int32).reshape(-1, 3)
+    val = np.zeros((ijk.shape[0], NF))
+    mag = np.zeros((ijk.shape[0], NF))
+    c = cfg._c()
+    lib.oracle_rhs_points_mag(ctypes.byref(c), _dp(st), ijk.shape[0],
+                              ijk.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _dp(val), _dp(mag))
+    return val, mag
+
+
+def rhs_mag(cfg: Config, st: np.ndarray):
+    """rhs_points_mag at every stored point, as two arrays of the state's shape
+    (24, Z, Y, X): the right-hand side (equal to rhs) and its magnitudes."""
+    Z, Y, X = cfg.shape[1:]
+    k, j, i = np.meshgrid(np.arange(Z), np.arange(Y), np.arange(X), indexing="ij")
+    ijk = np.stack([i.ravel(), j.ravel(), k.ravel()], axis=1)
+    val, mag = rhs_points_mag(cfg, st, ijk)
+    return (np.ascontiguousarray(val.T).reshape(cfg.shape), np.ascontiguousarray(mag.T).reshape(cfg.shape))
+
+
+def rhs_points_ext(cfg: Config, st: np.ndarray, ijk: np.ndarray) -> np.ndarray:
+    """The same right-hand side evaluated in long double (the instrumented
+    build's second copy of the header), rounded to float64 at the end."""
+    lib = _load_instr()
+    st = _state(cfg, st)
+    ijk = np.ascontiguousarray(ijk, dtype=np.int32).reshape(-1, 3)
+    out = np.zeros((ijk.shape[0], NF))
+    c = cfg._c()
+    lib.oracle_rhs_points_ext(ctypes.byref(c), _dp(st), ijk.shape[0],
+                              ijk.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _dp(out))
+    return out
+
+
+def rhs_opcount(cfg: Config, st: np.ndarray, point) -> dict:
+    """Operations of one right-hand-side evaluation (all 24 fields) at the
+    stored point (i, j, k) in the oracle's printed arrangement: additions and
+    subtractions, multiplications, divisions, square roots and exponentials."""
+    lib = _load_instr()
+    st = _state(cfg, st)
+    out = (ctypes.c_longlong * 4)()
+    c = cfg._c()
+    i, j, k = (int(v) for v in point)
+    lib.oracle_rhs_opcount(ctypes.byref(c), _dp(st), i, j, k, out)
+    return {"add": out[0], "mul": out[1], "div": out[2], "fun": out[3]}
 
 
 def fill_periodic(cfg: Config, st: np.ndarray) -> np.ndarray:

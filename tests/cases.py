@@ -2,7 +2,9 @@
 the oracle's Config and the CUDA library's Params from it, and measure the
 normwise per-field error used as the parity metric:
     e_f = max|gpu - cpu| / max(max|cpu_f|, 1e-3 max_g max|cpu_g|)
-(the floor keeps fields whose exact value is ~0 from dividing by rounding)."""
+(the floor keeps fields whose exact value is ~0 from dividing by rounding),
+and the rounding-aware form of the float64 right-hand-side bar (see
+rounding_aware_errors)."""
 import math
 
 import numpy as np
@@ -42,3 +44,25 @@ def normwise_errors(gpu, cpu):
     fmax = np.abs(cpu).max(axis=1)
     floor = 1e-3 * fmax.max()
     return np.abs(gpu - cpu).max(axis=1) / np.maximum(np.maximum(fmax, floor), 1e-300)
+
+
+def rounding_aware_errors(gpu, cpu, mag, rtol=1e-12):
+    """Per field f, the largest ratio over points p of
+        |gpu_pf - cpu_pf| / (rtol max(S_f, M_pf)),
+    with S_f the normwise scale of normwise_errors and M_pf the oracle's
+    magnitude of the same expression evaluated on absolute values (the
+    instrumented oracle build).  A ratio <= 1 passes.
+
+    Where a right-hand side is a small difference of much larger terms (K and
+    At half a cell from a puncture: W^2 times the lapse Laplacian against
+    2 W^2 grad(phi).grad(alpha)), two float64 evaluations in different orders
+    differ by a few u M_pf, u = 2^-53, which can exceed 1e-12 of the field's
+    largest value; elsewhere M_pf is small and the bar is the normwise
+    1e-12 S_f.  Arrays are (24, ...) with the field axis first."""
+    gpu = np.asarray(gpu).reshape(gpu.shape[0], -1)
+    cpu = np.asarray(cpu).reshape(cpu.shape[0], -1)
+    mag = np.asarray(mag).reshape(mag.shape[0], -1)
+    fmax = np.abs(cpu).max(axis=1)
+    scale = np.maximum(np.maximum(fmax, 1e-3 * fmax.max()), 1e-300)
+    bar = rtol * np.maximum(scale[:, None], mag)
+    return (np.abs(gpu - cpu) / bar).max(axis=1)

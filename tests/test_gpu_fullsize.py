@@ -13,7 +13,7 @@ import numpy as np
 import pytest
 
 import oracle as O
-from cases import normwise_errors
+from cases import normwise_errors, rounding_aware_errors
 from paper_1111_3344_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
@@ -81,21 +81,23 @@ def test_fullsize_rhs_sampled(torch_cuda, oracle_id):
     evo = _evo()
     got = evo.register_to_numpy(evo.rhs(evo.numpy_to_register(st)))
     ijk = _sample_points(np.random.default_rng(1), count=4000)
-    want = O.rhs_points(_cfg(), st, ijk)                       # (P, 24), oracle
+    want, mag = O.rhs_points_mag(_cfg(), st, ijk)              # (P, 24), oracle
     g = np.stack([got[:, k, j, i] for (i, j, k) in ijk])       # (P, 24), CUDA path
     # normwise per field over the sample (which includes the points next to
     # the puncture, where every field takes its largest values)
-    scale = np.abs(want).max(axis=0)
-    floor = 1e-3 * scale.max()
-    err = np.abs(g - want).max(axis=0) / np.maximum(np.maximum(scale, floor), 1e-300)
+    err = normwise_errors(g.T, want.T)
     print("full-size rhs normwise errors", dict(zip(O.FIELD_NAMES, err)))
     # Half a cell from the puncture the K and At right-hand sides are small
     # differences of terms ~1e3 times larger (W^2 times the lapse Laplacian
     # against 2 W^2 grad(phi).grad(alpha), with grad(phi) ~ 1/r), so two float64
-    # evaluations that round in a different order differ there by ~1e3 ulp of
-    # the result: measured 2.7e-12 normwise in trK; every other field and every
-    # small-grid case stays within 1e-12.
-    assert err.max() <= 5e-12, dict(zip(O.FIELD_NAMES, err))
+    # evaluations that round in a different order differ there by a few ulp
+    # of those terms (normwise 2.7e-12 in trK).  The bar is therefore 1e-12 of
+    # the larger of the field's scale and the oracle's magnitude of the terms
+    # at the point (cases.rounding_aware_errors).
+    r = rounding_aware_errors(g.T, want.T, mag.T)
+    print("full-size rhs rounding-aware ratios", dict(zip(O.FIELD_NAMES, r)))
+    assert r.max() <= 1.0, dict(zip(O.FIELD_NAMES, r))
+    # away from the cancellation the plain normwise bar holds as well
     away = [O.F_CHI] + list(range(O.F_GT, O.F_GT + 6)) + [O.F_ALP] + list(range(O.F_BETA, 24))
     assert err[away].max() <= 1e-12, dict(zip(O.FIELD_NAMES, err))
     evo.close()
