@@ -9,6 +9,14 @@ ghost layers, RK4 with dt = 0.25 h, float64.  One "step" is one full RK4 step
 Throughput is reported as interior point-updates per second (one point
 advanced one RK4 step).
 
+At N = 1 the same line also carries the rest of the benchmark's metric, each
+part timed with its own CUDA events and clock sample: ``mixed`` (the same
+puncture with float32 stencils and right-hand side, float64 RK4 state),
+``batched`` (64 Brill-Lindquist binaries on grids 48^3..128^3, float64 and
+mixed, a few of their 100 steps) and ``served_sample`` (the first requests of
+the served workload's Poisson stream at 0.8x a capacity measured in the same
+run, with p50/p99 completion latency).
+
 Launch: ``python bench.py [--gpus N] [--steps K] [--warmup W]`` for N = 1, or
 under torchrun for N > 1 (one independent replica per GPU: the path does not
 shard, so ranks exchange nothing but the timing barrier).
@@ -33,26 +41,44 @@ sys.path.insert(0, ROOT)
 
 N_SIDE = 128
 DOMAIN = 8.0
-# Float64 work per interior point per fused stage launch (right-hand side plus
-# RK4 combine), from the ncu instruction counts of the stage kernel
-# (profiles/stage_fp64_bl64.md): 535 DADD + 239 DMUL + 1485 DFMA.
-FLOP_PER_POINT_RHS = 3744.0        # DADD + DMUL + 2 DFMA
-DPINST_PER_POINT_RHS = 2259.0      # float64 instructions issued
-# The 32-wide tiles on grids whose n0 is a multiple of 32 and whose n1, n2
-# fill the blocks (the benchmark grid) run the full-block kernel: x-mixed
-# second differences shared across lanes, D_y D_z across rows through shared
-# memory; 302.5 DADD + 251.8 DMUL + 1366.8 DFMA per point
-# (profiles/stage_fp64_rows_bl64.md).
+# Algorithmic HBM bytes per interior point-update (one RK4 step; every
+# register read or written once per pass, 24 fields): float64 3072 B -- stage
+# 1 reads y_n and writes the stage value and k-sum (576), stages 2 and 3 read
+# the stage value, y_n and the k-sum and write the next stage value and the
+# k-sum (960 each), stage 4 reads the stage value and the k-sum and writes
+# y_n (576); mixed 2496 B, the stage values in float (480 + 768 + 768 + 480).
+# The dominant kernel's roofline uses the mean per stage launch (a quarter).
+ALG_BYTES_PER_POINT_STEP = {"fp64": 3072.0, "mixed": 2496.0}
+# Float64 work the stage kernels execute per interior point per launch
+# (right-hand side plus RK4 combine), from ncu instruction counts at 64^3
+# (DADD + DMUL + 2 DFMA): the every-stencil kernel 535 DADD + 239 DMUL + 1485
+# DFMA; the full-block kernel (32-wide rows, D_y D_z through shared memory)
+# 302.5 DADD + 251.8 DMUL + 1366.8 DFMA.
+FLOP_PER_POINT_RHS = 3744.0
+DPINST_PER_POINT_RHS = 2259.0
 ROWS_TILES = ("32x8x1/1", "32x4x1/1", "32x4x2/1", "32x2x2/2")
 FLOP_PER_POINT_RHS_ROWS = 3287.9
 DPINST_PER_POINT_RHS_ROWS = 1921.1
-HBM_BYTES_PER_POINT_STEP = 3264.0  # 17 register passes x 24 fields x 8 B
-# mixed: float stage buffers (24 x 4 B) each with a float64 W (8 B), 104 B a
-# buffer pass; per RK4 step: stage 1 reads m0, writes m1 and the k-sum (312 B);
-# stages 2-3 read src, m0 and the k-sum and write out and the k-sum (520 B
-# each); stage 4 reads src and the k-sum, reads and writes y_n (2 x 192 B) and
-# writes the new shadow m0 (696 B)
-HBM_BYTES_PER_POINT_STEP_MIXED = 312.0 + 2 * 520.0 + 696.0   # 2048
+# Operations of one right-hand side at an interior point in the oracle's
+# printed arrangement (its instrumented build, W variant, Gamma-driver shift:
+# 5395 additions, 7874 multiplications, 299 divisions).  The arrangement
+# evaluates all 81 second derivatives of gt_ij, symmetric duplicates
+# included, as 25-point products, so it is 4.1x the kernels' count: it is
+# reported beside the roofline, not used as its numerator.
+ORACLE_FLOP_PER_POINT_RHS = 5395 + 7874 + 299
+# DRAM bytes (read + write) per interior point of one stage launch, from ncu
+# captures of single launches; None where no capture of the current kernel
+# at the benchmark size exists.
+FP64_TRAFFIC_PER_POINT = 1587.9     # stage_fp64_kernel 64x4x1/1 (capture at 64^3)
+FP64_ROWS_TRAFFIC_PER_POINT = None  # stage_fp64_blocks_kernel 32x4x1/1 at 128^3
+MIXED_TRAFFIC_PER_POINT = None      # stage_mixed_tma_kernel at 128^3
+# Float64 work per interior point of the analysis kernels (DADD + DMUL + 2 DFMA
+# from ncu instruction counts at 96^3).  psi4 and constraints include the
+# ADM-field pass that precedes them (36 flop per stored point, 44 per
+# interior point at 96^3).
+ANALYSIS_FLOP_PER_POINT = {"psi4": 3409.0 + 44.0, "adm_integrals": 1771.9, "constraints": 1999.0 + 44.0}
+
+
 def _measured_hbm_gbs(default=6764.0):
     """The STREAM-style copy bandwidth measured on these GB300s
     (MEASURED_PEAKS.json beside this file, key hbm_gbs); the value it held
@@ -65,19 +91,7 @@ def _measured_hbm_gbs(default=6764.0):
 
 
 HBM_MEASURED_GBS = _measured_hbm_gbs()
-FP64_PEAK_GFLOPS = 1250.0          # nominal GB300 FP64 rate
-FP64_MEASURED_GFLOPS = 1196.0      # dependent-chain DFMA microbenchmark on GB300 (2070 MHz)
-# DRAM bytes (read + write) per interior point of one stage launch, from the
-# ncu capture of the current kernels on the 64^3 case (traffic grows with the
-# points; profiles/stage_traffic_bl64.md); None until captured.
-FP64_TRAFFIC_PER_POINT = 1587.9    # (100.8 + 315.4) MB / 262,144 points, stage_fp64_kernel 64x4x1/1
-FP64_ROWS_TRAFFIC_PER_POINT = 620.3  # (83.2 + 79.4) MB / 262,144 points, stage_fp64_blocks_kernel 32x4x1/1
-MIXED_TRAFFIC_PER_POINT = 488.0    # mean over the 4 stages of stage_mixed_tma_kernel: 282, 501, 492, 677 B
-# Float64 work per interior point of the analysis kernels (DADD + DMUL + 2 DFMA
-# from ncu instruction counts; profiles/analysis_kernels_bl96.md).
-# psi4 and constraints include the ADM-field pass that precedes them
-# (36 flop per stored point, 44 per interior point at 96^3).
-ANALYSIS_FLOP_PER_POINT = {"psi4": 3409.0 + 44.0, "adm_integrals": 1771.9, "constraints": 1999.0 + 44.0}
+FP64_NOMINAL_GFLOPS = 1250.0        # nominal GB300 float64 rate (context only)
 
 
 def workload_params(precision="fp64"):
@@ -266,12 +280,33 @@ def run_reference(args):
     print(json.dumps(line))
 
 
-def run_ours(args):
+def _sink(torch):
+    return torch.zeros(1, dtype=torch.float64, device="cuda")
+
+
+def measured_peaks(B, torch, stream):
+    """float64 and float32 multiply-add rates of this GPU, GFLOP/s, measured in
+    this process by the library's probe (bssn_peak_probe)."""
+    sink = _sink(torch)
+    with torch.cuda.stream(stream):
+        fp64 = B.bssn_peak_probe("fp64", sink.data_ptr(), stream.cuda_stream, reps=5)
+        fp32 = B.bssn_peak_probe("fp32", sink.data_ptr(), stream.cuda_stream, reps=5)
+    return {"fp64_gflops": fp64, "fp32_gflops": fp32,
+            "how": "bssn_peak_probe: 152x4 blocks x 256 threads x 8 independent FMA chains, CUDA events, "
+                   "2 flops per FMA, measured in this run"}
+
+
+def puncture_run(args, precision, world, local, steps, e2e=True):
+    """The single-puncture workload at N_SIDE^3 in one precision: autotuned
+    tiles, W untimed warm-up steps, then `steps` RK4 steps timed with CUDA
+    events on the library's stream (clocks sampled meanwhile), with the stage
+    and boundary launch durations; then `steps` end-to-end steps through the
+    C ABI with the state uploaded from and read back to pinned host memory
+    every step."""
     import torch
 
     from paper_1111_3344_gb300 import bssn as B
-    rank, world, local = dist_setup(args.gpus)
-    params = workload_params(args.precision)
+    params = workload_params(precision)
     evo = B.Evolution(params)
     evo.set_initial_data("bl", BL_P)
     stream = evo.stream
@@ -279,7 +314,7 @@ def run_ours(args):
         tile = [B.bssn_tile_name(c) for c in range(B.bssn_tile_count())].index(args.tile)
         B.bssn_set_tile(evo.ctx, tile)
     else:
-        tile, tile_ms = B.bssn_autotune(evo.ctx, reps=5)  # untimed: picks the stage-kernel tiles
+        tile, _ = B.bssn_autotune(evo.ctx, reps=5)  # untimed: picks the stage-kernel tiles
     for _ in range(args.warmup):
         evo.rk4_step(1)
     barrier(world)
@@ -290,7 +325,7 @@ def run_ours(args):
     stop = torch.cuda.Event(enable_timing=True)
     barrier(world)
     start.record(stream)
-    for _ in range(args.steps):
+    for _ in range(steps):
         evo.rk4_step(1)
     stop.record(stream)
     stop.synchronize()
@@ -299,90 +334,137 @@ def run_ours(args):
     stage_ms, stage_n, bc_ms, bc_n = B.bssn_profile(evo.ctx, False)
     clk = clocks.stop()
     pts = N_SIDE ** 3
-    value, ms = whole_job_rate(pts, args.steps, ms_local, world)
+    value, ms = whole_job_rate(pts, steps, ms_local, world)
+    out = {"value": value, "ms": ms, "steps": steps, "tile": B.bssn_tile_name(tile),
+           "stage_launch_ms": stage_ms / max(stage_n, 1), "stage_launches": stage_n,
+           "boundary_launch_ms": bc_ms / max(bc_n, 1), "boundary_launches": bc_n, "clocks": clk}
+    if e2e:
+        # two read-back buffers: the copy of step n's state to the host runs
+        # on the library's copy stream while step n+1's state is uploaded
+        host_in = torch.empty(evo.shape, dtype=torch.float64, pin_memory=True).numpy()
+        host_out = [torch.empty(evo.shape, dtype=torch.float64, pin_memory=True).numpy() for _ in range(2)]
+        host_in[...], _ = evo.get_state()
+        evo.enable_copy_staging()  # the copies overlap the steps as well as each other
+        e2e_steps = max(2, steps)
+        barrier(world)
+        t0 = time.perf_counter()
+        for s_ in range(e2e_steps):
+            B.bssn_set_state_async(evo.ctx, host_in, 0.0)
+            evo.rk4_step(1)
+            B.bssn_get_state_async(evo.ctx, host_out[s_ % 2])
+        B.bssn_wait_state(evo.ctx)
+        e2e_s = max_over_ranks(time.perf_counter() - t0, world)
+        out["e2e"] = {"value": pts * e2e_steps * world / e2e_s / 1e6, "unit": "Mpoint-updates/s",
+                      "h2d_bytes_per_step": host_in.nbytes, "d2h_bytes_per_step": host_in.nbytes,
+                      "steps": e2e_steps,
+                      "copies": "pinned; device staging areas: the upload of step n+1 and the read-back "
+                                "of step n overlap each other and the steps"}
+    evo.close()
+    del evo
+    torch.cuda.empty_cache()
+    return out
 
-    # end to end through the C ABI with pinned host buffers: upload state,
-    # one RK4 step, read the state back, every step
-    host_in = torch.empty(evo.shape, dtype=torch.float64, pin_memory=True).numpy()
-    # two read-back buffers: the copy of step n's state to the host runs on
-    # the library's copy stream while step n+1's state is uploaded
-    host_out = [torch.empty(evo.shape, dtype=torch.float64, pin_memory=True).numpy() for _ in range(2)]
-    host_in[...], _ = evo.get_state()
-    evo.enable_copy_staging()  # the copies overlap the steps as well as each other
-    e2e_steps = max(2, args.steps)
-    barrier(world)
-    t0 = time.perf_counter()
-    for s in range(e2e_steps):
-        B.bssn_set_state_async(evo.ctx, host_in, 0.0)
-        evo.rk4_step(1)
-        B.bssn_get_state_async(evo.ctx, host_out[s % 2])
-    B.bssn_wait_state(evo.ctx)
-    e2e_s = max_over_ranks(time.perf_counter() - t0, world)
-    e2e_value = pts * e2e_steps * world / e2e_s / 1e6
-    nbytes = host_in.nbytes
 
-    rows = B.bssn_tile_name(tile) in ROWS_TILES and N_SIDE % 32 == 0
-    flop_pt = FLOP_PER_POINT_RHS_ROWS if rows else FLOP_PER_POINT_RHS
-    dpinst_pt = DPINST_PER_POINT_RHS_ROWS if rows else DPINST_PER_POINT_RHS
-    traffic_pt = FP64_ROWS_TRAFFIC_PER_POINT if rows else FP64_TRAFFIC_PER_POINT
-    flop_launch = flop_pt * pts
-    stage_launch_ms = stage_ms / max(stage_n, 1)
-    achieved = flop_launch / (stage_launch_ms * 1e-3) / 1e12
+def hbm_roofline(run, precision, kernel, traffic_per_point):
+    """The dominant (stage) kernel against HBM: algorithmic bytes of one stage
+    launch (a quarter of the per-step bytes, per interior point) over its
+    mean launch duration."""
+    pts = N_SIDE ** 3
+    bytes_launch = ALG_BYTES_PER_POINT_STEP[precision] / 4.0 * pts
+    gbs = bytes_launch / (run["stage_launch_ms"] * 1e-3) / 1e9
+    return {"bound": "hbm", "kernel": kernel, "achieved": gbs, "peak": HBM_MEASURED_GBS, "unit": "GB/s",
+            "frac": gbs / HBM_MEASURED_GBS,
+            "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs, burst copy)",
+            "algorithmic_bytes_per_launch": bytes_launch,
+            "traffic": traffic_per_point * pts if traffic_per_point else None,
+            "launch_ms": run["stage_launch_ms"], "launches": run["stage_launches"],
+            "boundary_launch_ms": run["boundary_launch_ms"]}
+
+
+def run_ours(args):
+    import torch
+
+    from paper_1111_3344_gb300 import bssn as B
+    rank, world, local = dist_setup(args.gpus)
+    run = puncture_run(args, args.precision, world, local, args.steps)
+    pts = N_SIDE ** 3
     mixed = args.precision == "mixed"
+    rows = run["tile"] in ROWS_TILES and N_SIDE % 32 == 0
     if mixed:
-        # HBM-bound form: algorithmic bytes per stage launch over its duration
-        bytes_launch = HBM_BYTES_PER_POINT_STEP_MIXED / 4.0 * pts
-        gbs = bytes_launch / (stage_launch_ms * 1e-3) / 1e9
-        roofline = {"bound": "hbm", "kernel": B.bssn_tile_name(tile), "achieved": gbs,
-                    "peak": HBM_MEASURED_GBS, "unit": "GB/s", "frac": gbs / HBM_MEASURED_GBS,
-                    "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)",
-                    "algorithmic_bytes_per_launch": bytes_launch,
-                    "traffic": MIXED_TRAFFIC_PER_POINT * pts if MIXED_TRAFFIC_PER_POINT else None,
-                    "launch_ms": stage_launch_ms, "launches": stage_n,
-                    "boundary_launch_ms": bc_ms / max(bc_n, 1)}
+        kernel = "stage_mixed_tma_kernel" if run["tile"].startswith("tma") else "stage_mixed_kernel"
+        roofline = hbm_roofline(run, "mixed", kernel, MIXED_TRAFFIC_PER_POINT)
     else:
-        roofline = {"bound": "alu", "kernel": "stage_fp64_blocks_kernel" if rows else "stage_fp64_kernel",
-                    "achieved": achieved * 1e3,
-                    "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s (FP64)",
-                    "peak_source": "nominal GB300 FP64 rate (no tensor-core path: stencil)",
-                    "frac": achieved * 1e3 / FP64_PEAK_GFLOPS,
-                    "frac_of_measured_dfma": achieved * 1e3 / FP64_MEASURED_GFLOPS,
-                    "fp64_issue_frac": dpinst_pt * pts / (stage_launch_ms * 1e-3)
-                                       / (FP64_MEASURED_GFLOPS * 1e9 / 2),
-                    "traffic": traffic_pt * pts,
-                    "launch_ms": stage_launch_ms, "launches": stage_n,
-                    "boundary_launch_ms": bc_ms / max(bc_n, 1),
-                    "hbm_frac": (HBM_BYTES_PER_POINT_STEP * pts * args.steps / (ms * 1e-3)) / HBM_MEASURED_GBS / 1e9}
+        kernel = "stage_fp64_blocks_kernel" if rows else "stage_fp64_kernel"
+        roofline = hbm_roofline(run, "fp64", kernel,
+                                FP64_ROWS_TRAFFIC_PER_POINT if rows else FP64_TRAFFIC_PER_POINT)
+        peaks = measured_peaks(B, torch, torch.cuda.Stream())
+        flop_pt = FLOP_PER_POINT_RHS_ROWS if rows else FLOP_PER_POINT_RHS
+        dpinst_pt = DPINST_PER_POINT_RHS_ROWS if rows else DPINST_PER_POINT_RHS
+        sec = run["stage_launch_ms"] * 1e-3
+        # the pipe that binds the float64 stage: executed float64 work of a
+        # launch over the float64 FMA rate measured in this run
+        roofline["binding"] = {
+            "bound": "alu", "pipe": "fp64", "unit": "GFLOP/s",
+            "achieved": flop_pt * pts / sec / 1e9, "peak": peaks["fp64_gflops"],
+            "frac": flop_pt * pts / sec / 1e9 / peaks["fp64_gflops"],
+            "peak_source": "measured in this run (bssn_peak_probe, float64 FMA chains)",
+            "executed_flop_per_point": flop_pt,
+            "fp64_issue_frac": dpinst_pt * pts / sec / (peaks["fp64_gflops"] * 1e9 / 2),
+            "oracle_flop_per_point_rhs": ORACLE_FLOP_PER_POINT_RHS,
+            "nominal_fp64_gflops": FP64_NOMINAL_GFLOPS}
+        roofline["measured_peaks"] = peaks
     line = {
         "metric": ("BSSN RK4 point-updates/s (mixed FP32 RHS / FP64 state, Brill-Lindquist puncture 128^3)"
                    if mixed else "BSSN RK4 point-updates/s (FP64, Brill-Lindquist puncture 128^3)"),
-        "value": value, "unit": "Mpoint-updates/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f64",
+        "value": run["value"], "unit": "Mpoint-updates/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": run["ms"] / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if mixed else "f64",
         "data": "synthetic",
         "config": {"workload": "single Brill-Lindquist puncture M=1, 128^3 on [-8,8]^3, W, 1+log, "
                                "Gamma-driver eta=2, Sommerfeld, RK4 dt=0.25h",
                    "global_batch": world, "grid": [N_SIDE] * 3, "parallelism": f"replicas{world}",
-                   "precision": args.precision, "tile": B.bssn_tile_name(tile),
+                   "precision": args.precision, "tile": run["tile"],
                    "l2": "inputs larger than L2 (4 float64 registers of 469 MB each)"},
         "roofline": roofline,
-        "rhs_evaluations_per_s": 4.0 * value * 1e6,  # four right-hand sides per point-update
-        "e2e": {"value": e2e_value, "unit": "Mpoint-updates/s", "h2d_bytes_per_step": nbytes,
-                "d2h_bytes_per_step": nbytes, "steps": e2e_steps,
-                "copies": "pinned; device staging areas: the upload of step n+1 and the read-back "
-                          "of step n overlap each other and the steps"},
+        "rhs_evaluations_per_s": 4.0 * run["value"] * 1e6,  # four right-hand sides per point-update
+        "e2e": run["e2e"],
         # the split mixed stage is two kernels per stage (stencils, algebra)
-        "gpu_launches": stage_n * (2 if B.bssn_tile_name(tile).startswith("split") else 1) + bc_n,
-        "clocks": clk,
+        "gpu_launches": run["stage_launches"] * (2 if run["tile"].startswith("split") else 1)
+                        + run["boundary_launches"],
+        "clocks": run["clocks"],
     }
+    if world == 1 and not args.no_extras and not mixed:
+        line.update(extras(args))
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = oracle_cpu_baseline()
     if rank == 0:
         print(json.dumps(line))
-    evo.close()
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def extras(args):
+    """The rest of the benchmark's metric, each part with its own CUDA-event
+    timing and clock sample: the mixed-precision puncture at 128^3, the
+    batched 64-binary workload in both precisions, and a labelled sample of
+    the served workload whose arrival rate is 0.8x a capacity measured on the
+    served request mix in this run."""
+    import torch
+    mixed = puncture_run(args, "mixed", 1, 0, args.steps)
+    kernel = "stage_mixed_tma_kernel" if mixed["tile"].startswith("tma") else "stage_mixed_kernel"
+    out = {"mixed": {
+        "metric": "BSSN RK4 point-updates/s (mixed FP32 RHS / FP64 state, Brill-Lindquist puncture 128^3)",
+        "value": mixed["value"], "unit": "Mpoint-updates/s", "ms_per_step": mixed["ms"] / mixed["steps"],
+        "steps": mixed["steps"], "dtype": "f32+f64", "tile": mixed["tile"],
+        "roofline": hbm_roofline(mixed, "mixed", kernel, MIXED_TRAFFIC_PER_POINT),
+        "e2e": mixed["e2e"], "gpu_launches": mixed["stage_launches"] + mixed["boundary_launches"],
+        "clocks": mixed["clocks"]}}
+    bsteps = max(2, args.steps // 4)
+    out["batched"] = {prec: batched_run(args, prec, steps=bsteps) for prec in ("fp64", "mixed")}
+    torch.cuda.empty_cache()
+    out["served_sample"] = served_run(args, "mixed", requests=args.served_sample)
+    return out
 
 
 def _bl_params(member, precision):
@@ -393,74 +475,77 @@ def _bl_params(member, precision):
                   precision=precision, w_fp64_threshold=0.2, r_excise=1.0)
 
 
-def run_batched(args):
+def _make_batch(B, params_list, precision):
+    need = sum(B.Batch.member_bytes(p) for p in params_list) + (64 << 20)
+    return B.Batch(precision, pool_bytes=need, max_members=max(len(params_list), 1))
+
+
+def batched_run(args, precision, steps=None, members=None):
     """64 time-symmetric Brill-Lindquist binaries (masses U[0.3,0.7], separations
     U[2,6], grids from {48,64,96,128}^3, seed 1111) advanced together, one
-    persistent launch per RK4 stage under a CUDA graph."""
+    launch per RK4 stage (plus one boundary launch) under a CUDA graph; steps
+    timed with CUDA events on the batch's stream."""
     import torch
 
     from paper_1111_3344_gb300 import bssn as B
     from paper_1111_3344_gb300 import inputs
     torch.cuda.set_device(0)
-    members = inputs.binary_bl_batch(seed=1111, count=args.members)
-    params = [_bl_params(m, args.precision) for m in members]
-    need = sum(B.Batch.member_bytes(p) for p in params) + (64 << 20)
-    batch = B.Batch(args.precision, pool_bytes=need, max_members=max(len(params), 1))
-    ids = []
-    for m, p in zip(members, params):
+    steps = args.steps if steps is None else steps
+    mems = inputs.binary_bl_batch(seed=1111, count=members or args.members)
+    params = [_bl_params(m, precision) for m in mems]
+    batch = _make_batch(B, params, precision)
+    for m, p in zip(mems, params):
         mid = batch.add(p)
         bl = [len(m["punctures"])] + [v for q in m["punctures"] for v in q]
         batch.set_initial_data(mid, "bl", bl)
-        ids.append(mid)
     best, tile_ms = batch.autotune(reps=2)
-    if args.tile:
+    if args.tile and args.tile in tile_ms:
         best = list(tile_ms).index(args.tile)
         batch.set_tile(best)
     batch.step(args.warmup)
     batch.synchronize()
+    clocks = ClockSampler(0)
+    clocks.start()
     start = torch.cuda.Event(enable_timing=True)
     stop = torch.cuda.Event(enable_timing=True)
     start.record(batch.stream)
-    batch.step(args.steps)
+    batch.step(steps)
     stop.record(batch.stream)
     stop.synchronize()
+    clk = clocks.stop()
     ms = start.elapsed_time(stop)
     pts = sum(p.n[0] * p.n[1] * p.n[2] for p in params)
-    value = pts * args.steps / (ms * 1e-3) / 1e6
     # launches per step: a stage and a boundary launch per RK4 stage; the
     # one-block-per-tile float64 configurations launch the members with full
     # tiles and the others separately
     tname = list(tile_ms)[best]
     stage_launches = 1
-    if tname.startswith("tiles") and args.precision == "fp64":
+    if tname.startswith("tiles") and precision == "fp64":
         tx, ty, tz = (int(v) for v in tname[len("tiles"):].split("/")[0].split("x"))
         full = [tx == 32 and p.n[0] % 32 == 0 and p.n[1] % ty == 0 and p.n[2] % tz == 0 for p in params]
         stage_launches = int(any(full)) + int(not all(full))
-    line = {"metric": f"batched BSSN RK4 point-updates/s ({args.precision})", "value": value,
-            "unit": "Mpoint-updates/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": ms / args.steps, "higher_is_better": True,
-            "dtype": "f64" if args.precision == "fp64" else "f32+f64", "data": "synthetic",
-            "config": {"workload": f"{len(params)} Brill-Lindquist binaries, grids {{48,64,96,128}}^3, seed 1111",
-                       "interior_points": pts, "tile": list(tile_ms)[best],
-                       "autotune_ms_stage1": {k: round(v, 3) for k, v in tile_ms.items() if v >= 0},
-                       "launches_per_step": 4 * (stage_launches + 1), "graph": True}}
-    print(json.dumps(line))
     batch.close()
+    del batch
+    torch.cuda.empty_cache()
+    return {"metric": f"batched BSSN RK4 point-updates/s ({precision})",
+            "value": pts * steps / (ms * 1e-3) / 1e6, "unit": "Mpoint-updates/s", "steps": steps,
+            "ms_per_step": ms / steps, "dtype": "f64" if precision == "fp64" else "f32+f64",
+            "workload": f"{len(params)} Brill-Lindquist binaries, grids {{48,64,96,128}}^3, seed 1111, "
+                        f"{steps} of the configuration's 100 steps",
+            "interior_points": pts, "tile": tname,
+            "autotune_ms_per_stage": {k: round(v, 3) for k, v in tile_ms.items() if v >= 0},
+            "launches_per_step": 4 * (stage_launches + 1), "gpu_launches": 4 * (stage_launches + 1) * steps,
+            "graph": True, "clocks": clk}
 
 
-def run_served(args):
-    """Poisson arrivals of puncture evolutions (grids 32^3..192^3, 50..400 steps,
-    Brill-Lindquist binaries as in the batched workload, seed 3344), admitted by
-    HBM budget into a continuous-batching server; reports p50/p99 time from
-    submission to completion and the aggregate point-update rate."""
-    import torch
-
-    from paper_1111_3344_gb300 import bssn as B
-    torch.cuda.set_device(0)
-    rng = np.random.default_rng(3344)
+def served_requests(count, precision, seed=3344):
+    """The served workload's request stream: grids from {32,...,192}^3, 50 to
+    400 steps, Brill-Lindquist binaries as in the batched workload (punctures
+    snapped half a cell off the grid)."""
+    rng = np.random.default_rng(seed)
     sizes = [32, 48, 64, 96, 128, 160, 192]
     reqs = []
-    for _ in range(args.requests):
+    for _ in range(count):
         n = int(rng.choice(sizes))
         steps = int(rng.integers(50, 401))
         m1, m2 = rng.uniform(0.3, 0.7, size=2)
@@ -471,37 +556,100 @@ def run_served(args):
         x1 = -L + round((x1 + L) / h) * h
         x2 = -L + round((x2 + L) / h) * h
         mem = dict(n=(n, n, n), xmin=(-L,) * 3, h=h)
-        reqs.append((_bl_params(mem, args.precision), [2, m1, x1, 0.0, 0.0, m2, x2, 0.0, 0.0], steps))
+        reqs.append((_bl_params(mem, precision), [2, m1, x1, 0.0, 0.0, m2, x2, 0.0, 0.0], steps))
+    return rng, reqs
+
+
+def served_capacity(reqs, precision, steps=3):
+    """Capacity of the serving path on its own request mix, M point-updates/s:
+    the first requests of the stream (up to 24) resident together in one batch
+    with the serving path's kernels (autotuned), `steps` RK4 steps timed with
+    CUDA events."""
+    import torch
+
+    from paper_1111_3344_gb300 import bssn as B
+    sample = reqs[:24]
+    params = [p for p, _, _ in sample]
+    batch = _make_batch(B, params, precision)
+    for p, idp, _ in sample:
+        batch.set_initial_data(batch.add(p), "bl", idp)
+    batch.autotune(reps=1)
+    batch.step(1)
+    batch.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(batch.stream)
+    batch.step(steps)
+    e1.record(batch.stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    batch.close()
+    del batch
+    torch.cuda.empty_cache()
+    pts = sum(p.n[0] * p.n[1] * p.n[2] for p in params)
+    return pts * steps / (ms * 1e-3) / 1e6, len(sample)
+
+
+def served_run(args, precision, requests):
+    """Poisson arrivals of puncture evolutions admitted by HBM budget into a
+    continuous-batching server: the arrival rate is 0.8x the capacity
+    measured on the same request mix just before; reports p50/p99 time from
+    submission to completion, the queueing part of them, and throughput both
+    over wall-clock time and over the time the server spent stepping."""
+    import torch
+
+    from paper_1111_3344_gb300 import bssn as B
+    torch.cuda.set_device(0)
+    rng, reqs = served_requests(requests, precision)
+    capacity, cap_n = served_capacity(reqs, precision)
     work = sum(p.n[0] ** 3 * st for p, _, st in reqs)
-    budget = int(args.budget_gb * (1 << 30))
-    srv = B.Server(args.precision, budget_bytes=budget)
-    # arrival rate: 0.8 x the capacity in requests/s implied by a throughput estimate
-    est_rate = args.capacity_mpts * 1e6  # point-updates/s
-    lam = 0.8 * est_rate / (work / len(reqs))
+    lam = 0.8 * capacity * 1e6 / (work / len(reqs))
     gaps = rng.exponential(1.0 / lam, size=len(reqs))
+    budget = int(args.budget_gb * (1 << 30))
+    srv = B.Server(precision, budget_bytes=budget)
+    clocks = ClockSampler(0)
+    clocks.start()
     t0 = time.perf_counter()
     tickets = []
     for (p, idp, st), gap in zip(reqs, gaps):
         time.sleep(gap)
         tickets.append(srv.submit(p, "bl", idp, st))
-    lats, fails = [], 0
+    lats, queued, fails = [], [], 0
     for t in tickets:
         st, norms, lat = srv.wait(t, timeout=3600)
         lats.append(lat)
+        queued.append(srv.detail(t)[1])
         fails += st != 0
     wall = time.perf_counter() - t0
+    clk = clocks.stop()
     stats = srv.stats()
     srv.close()
-    lats = np.array(lats)
-    line = {"metric": "served BSSN evolutions: p50/p99 completion latency, aggregate point-updates/s",
-            "value": stats["point_updates"] / wall / 1e6, "unit": "Mpoint-updates/s", "n_gpus": 1,
-            "higher_is_better": True, "dtype": "f32+f64" if args.precision == "mixed" else "f64",
-            "data": "synthetic",
-            "p50_s": float(np.percentile(lats, 50)), "p99_s": float(np.percentile(lats, 99)),
+    lats, queued = np.array(lats), np.array(queued)
+    p99 = float(np.percentile(lats, 99))
+    i99 = int(np.argmin(np.abs(lats - p99)))
+    return {"metric": "served BSSN evolutions: p50/p99 completion latency, aggregate point-updates/s",
+            "value": stats["point_updates"] / wall / 1e6, "unit": "Mpoint-updates/s",
+            "busy_value": stats["point_updates"] / stats["busy_s"] / 1e6,
+            "p50_s": float(np.percentile(lats, 50)), "p99_s": p99,
+            "p99_queued_s": float(queued[i99]), "mean_queued_s": float(queued.mean()),
             "failed": int(fails), "wall_s": wall, "busy_s": stats["busy_s"],
-            "config": {"workload": f"{len(reqs)} Poisson-arrival Brill-Lindquist binaries, grids 32^3..192^3, "
-                                   f"50..400 steps, seed 3344", "precision": args.precision, "lambda_per_s": lam,
-                       "budget_gb": args.budget_gb, "point_updates": work}}
+            "dtype": "f32+f64" if precision == "mixed" else "f64",
+            "workload": f"first {len(reqs)} requests of the served stream (seed 3344): Poisson arrivals of "
+                        f"Brill-Lindquist binaries, grids 32^3..192^3, 50..400 steps",
+            "lambda_per_s": lam, "capacity_mpts": capacity,
+            "capacity_source": f"{cap_n} requests of the same stream resident in one batch, 3 steps timed "
+                               "with CUDA events in this run; lambda = 0.8 x capacity / mean work per request",
+            "budget_gb": args.budget_gb, "point_updates": work, "clocks": clk}
+
+
+def run_batched(args):
+    line = batched_run(args, args.precision)
+    line.update({"n_gpus": 1, "warmup": args.warmup, "higher_is_better": True, "data": "synthetic"})
+    print(json.dumps(line))
+
+
+def run_served(args):
+    line = served_run(args, args.precision, args.requests)
+    line.update({"n_gpus": 1, "higher_is_better": True, "data": "synthetic"})
     print(json.dumps(line))
 
 
@@ -617,6 +765,7 @@ def run_analysis(args):
         mtimes[matter] = e0.elapsed_time(e1) / args.steps
     evo.set_matter(None)
     clk = clocks.stop()
+    peaks = measured_peaks(B, torch, stream)
     evo.close()
     top = res["psi4"]
     line = {
@@ -627,8 +776,9 @@ def run_analysis(args):
         "config": {"workload": "Psi4 / ADM integrals / constraint norms of the 128^3 puncture after 4 RK4 steps",
                    "grid": [N_SIDE] * 3},
         "roofline": {"bound": "alu", "kernel": "psi4_kernel", "achieved": top["fp64_gflops"],
-                     "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s (FP64)",
-                     "frac": top["fp64_gflops"] / FP64_PEAK_GFLOPS, "traffic": None},
+                     "peak": peaks["fp64_gflops"], "unit": "GFLOP/s (FP64)",
+                     "peak_source": "measured in this run (bssn_peak_probe, float64 FMA chains)",
+                     "frac": top["fp64_gflops"] / peaks["fp64_gflops"], "traffic": None},
         "kernels": res,
         "tracker": {"ms_per_step_without": times[False], "ms_per_step_with": times[True],
                     "overhead_ms": times[True] - times[False]},
@@ -657,17 +807,17 @@ def main():
     ap.add_argument("--members", type=int, default=64)
     ap.add_argument("--requests", type=int, default=256)
     ap.add_argument("--budget-gb", type=float, default=64.0)
-    ap.add_argument("--capacity-mpts", type=float, default=None,
-                    help="served: throughput estimate (M point-updates/s) that sets the arrival rate "
-                         "(default 250 mixed, 50 float64)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="puncture workload: print the float64 line only, without the mixed, batched and "
+                         "served parts of the metric")
+    ap.add_argument("--served-sample", type=int, default=32,
+                    help="requests of the served stream in the default line's served sample")
     ap.add_argument("--n", type=int, default=128,
                     help="grid points per side (128 is the benchmark workload; smaller sizes are "
                          "for profiling captures only)")
     args = ap.parse_args()
     if args.precision is None:
         args.precision = "mixed" if args.workload == "served" else "fp64"
-    if args.capacity_mpts is None:
-        args.capacity_mpts = 250.0 if args.precision == "mixed" else 50.0
     global N_SIDE
     N_SIDE = args.n
     if args.warmup < 3 and args.impl == "ours":

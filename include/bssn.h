@@ -367,6 +367,14 @@ bssn_status bssn_batch_set_tile(bssn_batch* b, int32_t cfg);
  * entries, may be NULL) gets the mean milliseconds per stage launch, -1 for
  * the configurations the batch cannot use. */
 bssn_status bssn_batch_autotune(bssn_batch* b, int32_t reps, int32_t* best, double* ms_per_cfg);
+/* Test hook of the bounded wait (no counterpart in the paper), as
+ * bssn_test_stall_tma for the batch's TMA-staged stage kernel: polls > 0 makes
+ * every block issue no tile copy and give up after that many polls; the next
+ * bssn_batch_get_state or bssn_batch_constraints returns BSSN_ETIMEOUT (and
+ * clears the error word).  The member tables are re-uploaded in stream order;
+ * the captured graph is kept.  polls in [0, 2^20]; 0 restores normal
+ * operation. */
+bssn_status bssn_batch_test_stall_tma(bssn_batch* b, int32_t polls);
 
 /* ------------------------------------------------------------- server
  * Continuous batching of evolution requests (no counterpart in the paper): a
@@ -386,6 +394,11 @@ bssn_status bssn_submit(bssn_server* s, const bssn_params* p, int32_t id_kind, c
  * *latency_s seconds from submit to completion) or BSSN_EFAILED when NaN/Inf
  * appeared in that request's state (other requests are unaffected). */
 bssn_status bssn_poll(bssn_server* s, uint64_t ticket, double norms_out[16], double* latency_s);
+/* Timing of a finished request: out[0] seconds from submission to completion
+ * (as bssn_poll), out[1] seconds it waited in the queue before admission,
+ * out[2] seconds resident on the device.  Returns as bssn_poll (EAGAIN while
+ * queued or running, ENOTFOUND for an unknown ticket). */
+bssn_status bssn_poll_detail(bssn_server* s, uint64_t ticket, double out[3]);
 /* out[0] completed, [1] failed, [2] queued, [3] resident, [4] interior
  * point-updates done, [5] seconds spent stepping, [6] seconds since create,
  * [7] bytes of the budget in use. */
@@ -398,6 +411,31 @@ bssn_status bssn_server_destroy(bssn_server* s); /* stops the scheduler; synchro
  * out[0] = total stage-kernel milliseconds, out[1] = stage launches,
  * out[2] = total boundary-kernel milliseconds, out[3] = boundary launches. */
 bssn_status bssn_profile(bssn_ctx* ctx, int32_t enable, double out[4]);
+
+/* Test hook of the bounded wait (no counterpart in the paper).  The
+ * TMA-staged stage kernels wait on an mbarrier for their tile copies, with a
+ * poll limit after which they set the context's error word and return without
+ * writing results.  With polls > 0 those kernels issue no copy at all and give
+ * up after `polls` polls, so that this path runs without any copy in flight:
+ * the next synchronising call (bssn_get_state, bssn_wait_state,
+ * bssn_constraints) returns BSSN_ETIMEOUT and clears the error word; the
+ * context stays usable.  polls in [0, 2^20]; 0 (the default) restores normal
+ * operation.  Affects only the TMA-staged configurations of mixed contexts. */
+bssn_status bssn_test_stall_tma(bssn_ctx* ctx, int32_t polls);
+
+/* Measured arithmetic peak of the current GPU (no counterpart in the paper:
+ * it is the denominator of the roofline on which the stage kernels are
+ * placed, since the stencil path uses no tensor cores and is bound by the
+ * float64 or float32 FMA pipe or by HBM).
+ *  kind     0: float64 fused multiply-add, 1: float32 fused multiply-add.
+ *  d_sink   caller-owned device memory of at least 8 bytes, 8-byte aligned;
+ *           the kernel never actually writes it (it only could).
+ *  reps     timed launches after one warm-up launch (each about 10 GFLOP).
+ *  gflops   out: GFLOP/s, two flops per multiply-add, from CUDA events
+ *           around the timed launches on cuda_stream.
+ * Synchronises cuda_stream.  EINVAL on a bad argument, ECUDA on a CUDA
+ * failure. */
+bssn_status bssn_peak_probe(int32_t kind, void* d_sink, void* cuda_stream, int32_t reps, double* gflops);
 
 /* Largest interior grid (n0 * n1 * n2) bssn_constraints_noalloc accepts. */
 #define BSSN_NOALLOC_MAX_POINTS 4194304

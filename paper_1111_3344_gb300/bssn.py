@@ -149,6 +149,9 @@ _SIGS = [
     ("bssn_constraints_noalloc", [ctypes.POINTER(bssn_params), ctypes.c_void_p,
                                   ctypes.POINTER(ctypes.c_double), ctypes.c_int32, ctypes.c_void_p,
                                   ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+    ("bssn_test_stall_tma", [ctypes.c_void_p, ctypes.c_int32], ctypes.c_int),
+    ("bssn_peak_probe", [ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                         ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
 ]
 
 
@@ -170,6 +173,7 @@ _SIGS += [
     ("bssn_batch_step", [ctypes.c_void_p, ctypes.c_int32], ctypes.c_int),
     ("bssn_batch_constraints", [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_double)],
      ctypes.c_int),
+    ("bssn_batch_test_stall_tma", [ctypes.c_void_p, ctypes.c_int32], ctypes.c_int),
     ("bssn_batch_tile_count", [], ctypes.c_int32),
     ("bssn_batch_tile_name", [ctypes.c_int32], ctypes.c_char_p),
     ("bssn_batch_set_tile", [ctypes.c_void_p, ctypes.c_int32], ctypes.c_int),
@@ -182,6 +186,7 @@ _SIGS += [
                      ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
     ("bssn_poll", [ctypes.c_void_p, ctypes.c_uint64, ctypes.POINTER(ctypes.c_double),
                    ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+    ("bssn_poll_detail", [ctypes.c_void_p, ctypes.c_uint64, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     ("bssn_server_stats", [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     ("bssn_server_destroy", [ctypes.c_void_p], ctypes.c_int),
 ]
@@ -355,6 +360,17 @@ def bssn_set_tile(ctx: int, cfg: int):
     _check(load().bssn_set_tile(ctypes.c_void_p(ctx), int(cfg)))
 
 
+def bssn_test_stall_tma(ctx: int, polls: int):
+    """Test hook: TMA-staged stage kernels issue no copy and give up waiting
+    after `polls` polls (0: normal operation); see include/bssn.h."""
+    _check(load().bssn_test_stall_tma(ctypes.c_void_p(ctx), int(polls)))
+
+
+def bssn_batch_test_stall_tma(batch: int, polls: int):
+    """Test hook of the batch's TMA-staged stage kernel; see include/bssn.h."""
+    _check(load().bssn_batch_test_stall_tma(ctypes.c_void_p(batch), int(polls)))
+
+
 def bssn_autotune(ctx: int, reps: int = 3):
     """Time every tile configuration on the live state; selects and returns
     (best_index, {name: ms_per_launch})."""
@@ -383,6 +399,16 @@ def bssn_constraints_noalloc(params: Params, d_state: int, punctures=(), stream:
     _check(load().bssn_constraints_noalloc(ctypes.byref(p), ctypes.c_void_p(d_state), arr,
                                            len(punctures), ctypes.c_void_p(stream), out))
     return np.array(out[:], dtype=np.float64)
+
+
+def bssn_peak_probe(kind: str, d_sink: int, stream: int = 0, reps: int = 5) -> float:
+    """Measured float64 ("fp64") or float32 ("fp32") fused multiply-add rate of
+    the current GPU in GFLOP/s (see include/bssn.h); d_sink: >= 8 bytes of
+    device memory."""
+    out = ctypes.c_double()
+    _check(load().bssn_peak_probe({"fp64": 0, "fp32": 1}[kind], ctypes.c_void_p(d_sink),
+                                  ctypes.c_void_p(stream), int(reps), ctypes.byref(out)))
+    return out.value
 
 
 # ------------------------------------------------------- convenience class
@@ -680,6 +706,14 @@ class Server:
             if time.time() - t0 > timeout:
                 raise TimeoutError(f"ticket {ticket} not done after {timeout} s")
             time.sleep(0.001)
+
+    def detail(self, ticket: int):
+        """For a finished request: (latency_s, queued_s, resident_s)."""
+        out = (ctypes.c_double * 3)()
+        st = load().bssn_poll_detail(ctypes.c_void_p(self.handle), ctypes.c_uint64(ticket), out)
+        if st not in (0, 7):
+            raise BssnError(st, load().bssn_last_error().decode())
+        return out[0], out[1], out[2]
 
     def stats(self):
         out = (ctypes.c_double * 8)()

@@ -156,6 +156,7 @@ struct bssn_ctx {
   CUtensorMap tmap[2][3];  // mixed: tensor maps of the float stage buffers, per TMA variant
   bool tmap_ok;
   int* err;             // device error word (bounded waits that gave up)
+  int stall_polls;      // test hook of the TMA-staged kernels (bssn_test_stall_tma)
   double* part;
   double* out16;
   double t;
@@ -289,6 +290,7 @@ bssn_status bssn_alloc(const bssn_params* p, void* d_mem, size_t bytes, void* cu
   ctx->npunct = 0;
   ctx->prof = false;
   ctx->err = (int*)(ctx->mem + c.err);
+  ctx->stall_polls = 0;
   ctx->trk = (double*)(ctx->mem + c.trk);
   ctx->tracking = false;
   ctx->trk_stale = false;
@@ -489,6 +491,7 @@ bssn_status bssn_rhs(bssn_ctx* ctx, const void* d_state, void* d_rhs) {
   a.rhs = out;
   a.w_thr = ctx->p.w_fp64_threshold;
   a.mode = MODE_RHS;
+  a.stall_polls = ctx->stall_polls;
   // the selected stage kernel, TMA-staged included (tmap[2] describes m32[2])
   if (split_variant(ctx->tile) >= 0)
     e = launch_stage_mixed_split(ctx->g, a, ctx->dr, ctx->stream, split_variant(ctx->tile));
@@ -553,6 +556,7 @@ static bssn_status run_stage_mixed(bssn_ctx* ctx, int src, int mode, int out, do
   a.b_dt = b_dt;
   a.w_thr = ctx->p.w_fp64_threshold;
   a.mode = mode;
+  a.stall_polls = ctx->stall_polls;
   cudaError_t e;
   if (ctx->prof && (e = prof_mark(ctx, ctx->ev_stage)) != cudaSuccess) return cuda_fail(e, "profile");
   if (tma_variant(ctx->tile) >= 0)
@@ -965,6 +969,13 @@ bssn_status bssn_autotune(bssn_ctx* ctx, int32_t reps, int32_t* best, double* ms
   if (st != BSSN_OK) return st;
   ctx->tile = best_c;
   if (best) *best = best_c;
+  return BSSN_OK;
+}
+
+bssn_status bssn_test_stall_tma(bssn_ctx* ctx, int32_t polls) {
+  if (!ctx) return fail(BSSN_EINVAL, "ctx is NULL");
+  if (polls < 0 || polls > (1 << 20)) return fail(BSSN_EINVAL, "polls must be in [0, 2^20]");
+  ctx->stall_polls = polls;
   return BSSN_OK;
 }
 

@@ -141,6 +141,7 @@ struct bssn_batch {
   BatchWork* d_work;  // NWORK lists (batch_internal.cuh)
   int* d_err;          // error word of the TMA-staged kernel's bounded waits
   bool tma_ok = true;  // every member's tensor maps could be encoded
+  int stall_polls = 0;  // test hook of the TMA-staged kernel (bssn_batch_test_stall_tma)
   std::vector<MemberDev> h_mem;
   BatchWork h_work[NWORK];
   bool work_dirty = true;
@@ -206,6 +207,7 @@ void fill_member_dev(bssn_batch* b, int id) {
       a.b_dt = b_dt[s];
       a.w_thr = M.p.w_fp64_threshold;
       a.mode = mode[s];
+      a.stall_polls = b->stall_polls;
       if (make_stage_tensor_map(M.g, a.src, &D.tmap[s]) != cudaSuccess) b->tma_ok = false;
     }
   }
@@ -581,6 +583,23 @@ bssn_status bssn_batch_constraints(bssn_batch* b, int32_t id, double out[16]) {
   return check_batch_err(b);
 }
 
+bssn_status bssn_batch_test_stall_tma(bssn_batch* b, int32_t polls) {
+  if (!b) return bfail(BSSN_EINVAL, "batch is NULL");
+  if (polls < 0 || polls > (1 << 20)) return bfail(BSSN_EINVAL, "polls must be in [0, 2^20]");
+  std::lock_guard<std::mutex> lk(b->mu);
+  b->stall_polls = polls;
+  // the captured graph reads the member tables from device memory: refill
+  // and upload them in stream order, no re-capture
+  cudaError_t e = cudaSuccess;
+  for (int id = 0; id < b->maxm && e == cudaSuccess; id++)
+    if (b->m[id].used) {
+      fill_member_dev(b, id);
+      e = upload_member(b, id);
+    }
+  if (e != cudaSuccess) return bcuda(e, "batch member tables");
+  return BSSN_OK;
+}
+
 int32_t bssn_batch_tile_count(void) { return batch_tile_config_count(); }
 const char* bssn_batch_tile_name(int32_t c) { return batch_tile_config_name(c); }
 
@@ -676,6 +695,7 @@ struct Res {
   bssn_status status = BSSN_EAGAIN;
   double norms[16] = {};
   double latency = 0.0;
+  double queued = 0.0;  // seconds from submission to admission
 };
 
 struct Act {
@@ -684,6 +704,7 @@ struct Act {
   size_t bytes;
   double t_submit;
   long long points;  // interior points
+  double t_admit;
 };
 
 }  // namespace
@@ -719,6 +740,7 @@ void retire(bssn_server* S, int id, const Act& a) {
   r.status = st != BSSN_OK ? st : (bad ? BSSN_EFAILED : BSSN_OK);
   if (st == BSSN_OK) memcpy(r.norms, norms, sizeof(norms));
   r.latency = now_s() - a.t_submit;
+  r.queued = a.t_admit - a.t_submit;
   bssn_batch_remove(S->batch, id);
   std::lock_guard<std::mutex> lk(S->mu);
   S->used -= a.bytes;
@@ -774,7 +796,7 @@ void scheduler(bssn_server* S) {
         continue;
       }
       Act a{r.ticket, r.nsteps, r.bytes, r.t_submit,
-            (long long)r.p.n[0] * r.p.n[1] * r.p.n[2]};
+            (long long)r.p.n[0] * r.p.n[1] * r.p.n[2], now_s()};
       if (a.remaining <= 0) {
         retire(S, id, a);
         continue;
@@ -879,6 +901,21 @@ bssn_status bssn_poll(bssn_server* S, uint64_t ticket, double norms_out[16], dou
   }
   if (norms_out) memcpy(norms_out, it->second.norms, sizeof(it->second.norms));
   if (latency_s) *latency_s = it->second.latency;
+  return it->second.status;
+}
+
+bssn_status bssn_poll_detail(bssn_server* S, uint64_t ticket, double out[3]) {
+  if (!S || !out) return bfail(BSSN_EINVAL, "NULL argument");
+  std::lock_guard<std::mutex> lk(S->mu);
+  auto it = S->results.find(ticket);
+  if (it == S->results.end()) return bfail(BSSN_ENOTFOUND, "unknown ticket");
+  if (!it->second.done) {
+    if (S->stop.load()) return bfail(BSSN_EFAILED, "server stopped: " + S->error);
+    return BSSN_EAGAIN;
+  }
+  out[0] = it->second.latency;
+  out[1] = it->second.queued;
+  out[2] = it->second.latency - it->second.queued;
   return it->second.status;
 }
 

@@ -197,6 +197,10 @@ struct StageArgsT {
   float a_dtf;           // a_dt as float (mixed stage values)
   double w_thr;          // mixed: W below this -> W right-hand side in float64
   int mode;
+  // test hook of the TMA-staged kernels: > 0 issues no tile copy and gives up
+  // waiting after this many polls, so that the bounded-wait path runs with
+  // nothing in flight; 0 in normal operation
+  int stall_polls;
 };
 using StageArgs = StageArgsT<double>;
 using StageArgsMixed = StageArgsT<float>;

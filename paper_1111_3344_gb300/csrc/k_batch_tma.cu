@@ -13,7 +13,9 @@
 // The wait on the mbarrier is bounded.  Whether the block gives up is decided
 // for the whole block at once (a barrier vote), so that no thread leaves while
 // others wait at a barrier: on a timeout the block sets the error word, waits
-// once more, boundedly, for its own copies, and returns.
+// once more, boundedly, for its own copies, and returns.  With the test hook
+// StageArgsT::stall_polls set in the member's arguments the block issues no
+// copy and gives up after that many polls.
 #include "batch_internal.cuh"
 #include "tma_tile.cuh"
 
@@ -76,18 +78,19 @@ __global__ void __launch_bounds__(TTX * TTY * TTZ, 2)
     const int by = (int)(lt % (unsigned)stile[1]);
     const int bz = (int)(lt / (unsigned)stile[1]);
     const int ii0 = bx * TTX, jj0 = by * TTY, kk0 = bz * TTZ;
+    const bool stall = sa.stall_polls > 0;  // test hook: no copy, short wait
     if (tid == 0) {
       // the map was written through the generic proxy (a copy from the host)
       asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(smap) : "memory");
       // the boxes were last read through the generic proxy; the loads write them
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      issue_staged_loads(smap, bar, smem, ii0, jj0, kk0);
+      if (!stall) issue_staged_loads(smap, bar, smem, ii0, jj0, kk0);
     }
-    const bool ok = mbar_wait(bar, phase, WAIT_LIMIT);
+    const bool ok = mbar_wait(bar, phase, stall ? (long long)sa.stall_polls : WAIT_LIMIT);
     if (__syncthreads_or(!ok)) {
       if (tid == 0) {
         atomicExch(err, 1);
-        mbar_wait(bar, phase, WAIT_LIMIT);  // let this block's own copies land before it exits
+        if (!stall) mbar_wait(bar, phase, WAIT_LIMIT);  // let this block's own copies land before it exits
       }
       return;
     }

@@ -12,7 +12,10 @@
 //
 // The wait on the mbarrier is bounded: after WAIT_LIMIT polls the block sets
 // the error word (read back by the host as BSSN_ETIMEOUT), waits once more,
-// boundedly, for its own copies, and returns without writing results.
+// boundedly, for its own copies, and returns without writing results.  A
+// test hook (StageArgsT::stall_polls) makes the wait run out on purpose: the
+// block then issues no copy at all, polls that many times, sets the error
+// word and returns.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -34,10 +37,11 @@ __global__ void __launch_bounds__(Sh::TX * Sh::TY * Sh::TZ, MINB)
   const unsigned bar = smem_addr(&mbar);
   if (tid == 0) mbar_init(bar);
   __syncthreads();
-  if (tid == 0) issue_staged_loads<Sh>(&tmap, bar, smem, ii0, jj0, kk0);
-  if (!mbar_wait(bar, 0, WAIT_LIMIT)) {
+  const bool stall = a.stall_polls > 0;  // test hook: no copy, short wait
+  if (tid == 0 && !stall) issue_staged_loads<Sh>(&tmap, bar, smem, ii0, jj0, kk0);
+  if (!mbar_wait(bar, 0, stall ? (long long)a.stall_polls : WAIT_LIMIT)) {
     if (tid == 0) atomicExch(err, 1);
-    mbar_wait(bar, 0, WAIT_LIMIT);  // let this block's own copies land before it exits
+    if (!stall) mbar_wait(bar, 0, WAIT_LIMIT);  // let this block's own copies land before it exits
     return;
   }
   const int ti = threadIdx.x, tj = threadIdx.y, tk = threadIdx.z;

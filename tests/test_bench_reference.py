@@ -27,3 +27,18 @@ def test_reference_arm_prints_one_contract_line():
     assert e["value"] == d["value"] and e["unit"] == d["unit"]
     assert e["h2d_bytes_per_step"] == 0 and e["d2h_bytes_per_step"] == 0
     assert "workload" in d["config"]
+
+
+def test_bench_oracle_flop_count_is_the_oracles():
+    """The operation count bench.py reports beside the roofline is the one the
+    instrumented oracle counts for the benchmark configuration (W variant,
+    1+log slicing, Gamma-driver shift, Sommerfeld grid) at an interior point."""
+    sys.path.insert(0, ROOT)
+    import bench
+    import oracle as O
+    n = 12
+    cfg = O.Config(n=(n,) * 3, xmin=(-1.5,) * 3, h=0.25, periodic=False, use_w=True, slicing="1+log",
+                   shift="gamma-driver", eta=2.0, punctures=[(1.0, 0.0, 0.0, 0.0)])
+    st = O.initial_data(cfg, "bl", [1, 1.0, 0.0, 0.0, 0.0])
+    c = O.rhs_opcount(cfg, st, (9, 8, 7))
+    assert c["add"] + c["mul"] + c["div"] == bench.ORACLE_FLOP_PER_POINT_RHS
