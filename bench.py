@@ -48,7 +48,9 @@ DOMAIN = 8.0
 # k-sum (960 each), stage 4 reads the stage value and the k-sum and writes
 # y_n (576); mixed 2496 B, the stage values in float (480 + 768 + 768 + 480).
 # The dominant kernel's roofline uses the mean per stage launch (a quarter).
-ALG_BYTES_PER_POINT_STEP = {"fp64": 3072.0, "mixed": 2496.0}
+# The double-word path moves 8-byte values like float64 but also reads y_n and
+# writes its double-word shadow in stage 4 (576 + 960 + 960 + 960 = 3456 B).
+ALG_BYTES_PER_POINT_STEP = {"fp64": 3072.0, "mixed": 2496.0, "ff": 3456.0}
 # Float64 work the stage kernels execute per interior point per launch
 # (right-hand side plus RK4 combine), from ncu instruction counts at 64^3
 # (DADD + DMUL + 2 DFMA): the every-stencil kernel 535 DADD + 239 DMUL + 1485
@@ -393,6 +395,8 @@ def run_ours(args):
     if mixed:
         kernel = "stage_mixed_tma_kernel" if run["tile"].startswith("tma") else "stage_mixed_kernel"
         roofline = hbm_roofline(run, "mixed", kernel, MIXED_TRAFFIC_PER_POINT)
+    elif args.precision == "ff":
+        roofline = hbm_roofline(run, "ff", "stage_ff_kernel", None)
     else:
         kernel = "stage_fp64_blocks_kernel" if rows else "stage_fp64_kernel"
         roofline = hbm_roofline(run, "fp64", kernel,
@@ -414,11 +418,14 @@ def run_ours(args):
             "nominal_fp64_gflops": FP64_NOMINAL_GFLOPS}
         roofline["measured_peaks"] = peaks
     line = {
-        "metric": ("BSSN RK4 point-updates/s (mixed FP32 RHS / FP64 state, Brill-Lindquist puncture 128^3)"
-                   if mixed else "BSSN RK4 point-updates/s (FP64, Brill-Lindquist puncture 128^3)"),
+        "metric": {"mixed": "BSSN RK4 point-updates/s (mixed FP32 RHS / FP64 state, Brill-Lindquist puncture 128^3)",
+                   "ff": "BSSN RK4 point-updates/s (double-word FP32 RHS / FP64 state, Brill-Lindquist puncture "
+                         "128^3)"}.get(args.precision,
+                                       "BSSN RK4 point-updates/s (FP64, Brill-Lindquist puncture 128^3)"),
         "value": run["value"], "unit": "Mpoint-updates/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": run["ms"] / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if mixed else "f64",
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": {"mixed": "f32+f64", "ff": "f32x2+f64"}.get(args.precision, "f64"),
         "data": "synthetic",
         "config": {"workload": "single Brill-Lindquist puncture M=1, 128^3 on [-8,8]^3, W, 1+log, "
                                "Gamma-driver eta=2, Sommerfeld, RK4 dt=0.25h",
@@ -433,7 +440,7 @@ def run_ours(args):
                         + run["boundary_launches"],
         "clocks": run["clocks"],
     }
-    if world == 1 and not args.no_extras and not mixed:
+    if world == 1 and not args.no_extras and args.precision == "fp64":
         line.update(extras(args))
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = oracle_cpu_baseline()
@@ -654,46 +661,62 @@ def run_served(args):
 
 
 def run_precision(args):
-    """Mixed precision against float64 on the same GPU: the puncture at
-    args.n^3 (256^3 by default for this mode) evolved args.steps RK4 steps
-    both ways; per-field L2/Linf of the state difference, relative difference
-    of every constraint norm, and the speedup."""
+    """Reduced-precision forms against float64 on the same GPU: the puncture at
+    args.n^3 (the configuration is 256^3, 100 steps) evolved args.steps RK4
+    steps in float64 and in each of args.variants; for each variant the
+    per-field L2 and Linf of the state difference from the float64 run
+    (interior points; absolute and relative to the field's largest float64
+    value), the relative difference of every constraint norm (full domain and
+    excised), the time of the steps (CUDA events) and the speedup."""
     import torch
 
     from paper_1111_3344_gb300 import bssn as B
     torch.cuda.set_device(0)
+    variants = [v for v in args.variants.split(",") if v and v != "fp64"]
     out = {}
-    for prec in ("fp64", "mixed"):
+    for prec in ["fp64"] + variants:
         evo = B.Evolution(workload_params(prec))
         evo.set_initial_data("bl", BL_P)
-        B.bssn_autotune(evo.ctx, reps=2)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
+        tile, _ = B.bssn_autotune(evo.ctx, reps=2)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(evo.stream)
         evo.rk4_step(args.steps)
-        torch.cuda.synchronize()
-        dt = time.perf_counter() - t0
+        e1.record(evo.stream)
+        e1.synchronize()
         st, _ = evo.get_state()
-        out[prec] = (st, evo.constraints(), dt)
+        out[prec] = (st, evo.constraints(), e0.elapsed_time(e1) * 1e-3, B.bssn_tile_name(tile))
         evo.close()
         del evo
         torch.cuda.empty_cache()
-    s64, c64, t64 = out["fp64"]
-    smx, cmx, tmx = out["mixed"]
+    s64, c64, t64, tile64 = out["fp64"]
     g = 3
-    d = (smx - s64)[:, g:-g, g:-g, g:-g].reshape(24, -1)
-    ref = np.abs(s64[:, g:-g, g:-g, g:-g]).reshape(24, -1).max(axis=1)
     names = ["chi", "gt_xx", "gt_xy", "gt_xz", "gt_yy", "gt_yz", "gt_zz", "trK", "At_xx", "At_xy",
              "At_xz", "At_yy", "At_yz", "At_zz", "Gt_x", "Gt_y", "Gt_z", "alpha", "beta_x", "beta_y",
              "beta_z", "B_x", "B_y", "B_z"]
-    fields = {nm: {"L2": float(np.sqrt((d[f] ** 2).mean())), "Linf": float(np.abs(d[f]).max()),
-                   "max_abs_fp64": float(ref[f])} for f, nm in enumerate(names)}
+    ref = np.abs(s64[:, g:-g, g:-g, g:-g]).reshape(24, -1).max(axis=1)
     cn = ["H", "Mx", "My", "Mz"]
     keys = [f"{k}_{n}_{s}" for s in ("full", "excised") for k in ("L2", "Linf") for n in cn]
-    rel = {k: float(abs(a - b) / abs(b)) if b != 0 else None for k, a, b in zip(keys, cmx, c64)}
-    line = {"metric": "mixed vs float64: per-field state error and constraint-norm relative difference",
-            "grid": args.n, "steps": args.steps, "speedup_mixed_over_fp64": t64 / tmx,
-            "seconds": {"fp64": t64, "mixed": tmx}, "constraint_norms_fp64": dict(zip(keys, c64.tolist())),
-            "constraint_norm_rel_diff": rel, "fields": fields}
+    res = {}
+    for prec in variants:
+        sv, cv, tv, tilev = out[prec]
+        d = (sv - s64)[:, g:-g, g:-g, g:-g].reshape(24, -1)
+        l2 = np.sqrt((d ** 2).mean(axis=1))
+        linf = np.abs(d).max(axis=1)
+        fields = {nm: {"L2": float(l2[f]), "Linf": float(linf[f]), "L2_rel": float(l2[f] / max(ref[f], 1e-300)),
+                       "Linf_rel": float(linf[f] / max(ref[f], 1e-300)), "max_abs_fp64": float(ref[f])}
+                  for f, nm in enumerate(names)}
+        rel = {k: float(abs(a - b) / abs(b)) if b != 0 else None for k, a, b in zip(keys, cv, c64)}
+        res[prec] = {"seconds": tv, "speedup_over_fp64": t64 / tv, "tile": tilev,
+                     "max_constraint_norm_rel_diff": max(v for v in rel.values() if v is not None),
+                     "constraint_norm_rel_diff": rel, "constraint_norms": dict(zip(keys, cv.tolist())),
+                     "max_field_Linf_rel": float(max(f["Linf_rel"] for f in fields.values())),
+                     "fields": fields}
+    line = {"metric": "reduced-precision forms vs float64: per-field state error and constraint-norm relative "
+                      "difference, speedup",
+            "workload": f"single Brill-Lindquist puncture M=1, {args.n}^3 on [-8,8]^3, {args.steps} RK4 steps",
+            "grid": args.n, "steps": args.steps, "bar": "constraint norms within 1e-6 relative of the float64 run",
+            "fp64": {"seconds": t64, "tile": tile64, "constraint_norms": dict(zip(keys, c64.tolist()))},
+            "variants": res}
     print(json.dumps(line))
 
 
@@ -796,7 +819,7 @@ def main():
     ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--precision", choices=["fp64", "mixed"], default=None,
+    ap.add_argument("--precision", choices=["fp64", "mixed", "ff"], default=None,
                     help="default: mixed for the served workload (its configuration), float64 otherwise")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", choices=["puncture", "batched", "served", "precision", "analysis"],
@@ -812,6 +835,8 @@ def main():
                          "served parts of the metric")
     ap.add_argument("--served-sample", type=int, default=32,
                     help="requests of the served stream in the default line's served sample")
+    ap.add_argument("--variants", default="mixed,ff",
+                    help="precision workload: the forms compared with float64 (mixed, ff)")
     ap.add_argument("--n", type=int, default=128,
                     help="grid points per side (128 is the benchmark workload; smaller sizes are "
                          "for profiling captures only)")

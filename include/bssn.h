@@ -53,7 +53,7 @@ enum { BSSN_BC_PERIODIC = 0, BSSN_BC_SOMMERFELD = 1 };
 enum { BSSN_PHI = 0, BSSN_W = 1 };
 enum { BSSN_1PLUSLOG = 0, BSSN_HARMONIC = 1, BSSN_GEODESIC = 2 };
 enum { BSSN_GAMMA_DRIVER = 0, BSSN_SHIFT_FROZEN = 1 };
-enum { BSSN_FP64 = 0, BSSN_MIXED = 1 };
+enum { BSSN_FP64 = 0, BSSN_MIXED = 1, BSSN_FF = 2 };
 enum { BSSN_ID_FLAT = 0, BSSN_ID_GAUGE_WAVE = 1, BSSN_ID_BL = 2, BSSN_ID_KASNER = 3 };
 
 /* Grid and method parameters.
@@ -74,7 +74,12 @@ enum { BSSN_ID_FLAT = 0, BSSN_ID_GAUGE_WAVE = 1, BSSN_ID_BL = 2, BSSN_ID_KASNER 
  *  dt                  RK4 time step.
  *  precision           BSSN_FP64: everything in float64.  BSSN_MIXED:
  *                      stencils and right-hand side in float32, RK4 state
- *                      and constraint reductions in float64.
+ *                      and constraint reductions in float64.  BSSN_FF:
+ *                      stencils and right-hand side in double-word
+ *                      ("float-float", 48-bit) arithmetic on the float32
+ *                      pipe, RK4 state, k-sum and reductions in float64
+ *                      (single-grid contexts only; batches and the server
+ *                      take BSSN_FP64 or BSSN_MIXED).
  *  w_fp64_threshold    mixed precision: points with W below this take the
  *                      W/phi right-hand side in float64.
  *  r_excise            constraint norms: excised set is r > r_excise from

@@ -23,7 +23,7 @@ BC = {"periodic": 0, "sommerfeld": 1}
 CONFORMAL = {"phi": 0, "W": 1}
 SLICING = {"1+log": 0, "harmonic": 1, "geodesic": 2}
 SHIFT = {"gamma-driver": 0, "frozen": 1}
-PRECISION = {"fp64": 0, "mixed": 1}
+PRECISION = {"fp64": 0, "mixed": 1, "ff": 2}
 ID_KIND = {"flat": 0, "gauge_wave": 1, "bl": 2, "kasner": 3}
 STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "EAGAIN", 5: "ETIMEOUT",
           6: "ENOTFOUND", 7: "EFAILED"}

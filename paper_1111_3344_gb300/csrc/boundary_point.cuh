@@ -20,6 +20,20 @@ __device__ __forceinline__ double coordv(const Grid& g, int d, int i) {
   return xm + (i - GH + 0.5) * g.h;
 }
 
+// A stored value in arithmetic C (a double-word value {hi, lo} to float64).
+template <typename C, typename S>
+__device__ __forceinline__ C cvt(S v) {
+  return (C)v;
+}
+template <>
+__device__ __forceinline__ double cvt<double, float2>(float2 v) {
+  return (double)v.x + (double)v.y;
+}
+template <>
+__device__ __forceinline__ ff cvt<ff, float2>(float2 v) {
+  return ff(v);
+}
+
 // Radiative right-hand side of field f at stored point I in arithmetic C;
 // p points at the field's value there; ns = (x / r) / (2h), the normal scaled
 // by the difference weight (formed once per point for all fields), ir = 1 / r.
@@ -32,17 +46,17 @@ __device__ __forceinline__ C rad_at(const Grid& g, const S* __restrict__ p, int 
                    f == F_GT + 5);
   const C X0 = (DEV || !one) ? C(0) : C(1);  // DEV: p holds X - X0 already
   const C v0 = (f == F_ALP || f == F_TRK) ? C(1.4142135623730951) : C(1);
-  C s = ((C)p[0] - X0) * ir;
+  C s = (cvt<C>(p[0]) - X0) * ir;
 #pragma unroll
   for (int d = 0; d < 3; d++) {
     const long long q = sd[d];
     C der;
     if (I[d] >= 1 && I[d] + 1 < dims[d])
-      der = (C)p[q] - (C)p[-q];
+      der = cvt<C>(p[q]) - cvt<C>(p[-q]);
     else if (I[d] + 1 >= dims[d])
-      der = C(3) * (C)p[0] - C(4) * (C)p[-q] + (C)p[-2 * q];
+      der = C(3) * cvt<C>(p[0]) - C(4) * cvt<C>(p[-q]) + cvt<C>(p[-2 * q]);
     else
-      der = -(C(3) * (C)p[0] - C(4) * (C)p[q] + (C)p[2 * q]);
+      der = -(C(3) * cvt<C>(p[0]) - C(4) * cvt<C>(p[q]) + cvt<C>(p[2 * q]));
     s = fmaT<C>(ns[d], der, s);
   }
   return -v0 * s;

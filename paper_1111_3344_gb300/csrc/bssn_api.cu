@@ -43,7 +43,10 @@ bool validate(const bssn_params* p, std::string& why) {
   if (p->conformal != BSSN_PHI && p->conformal != BSSN_W) { why = "bad conformal"; return false; }
   if (p->slicing < BSSN_1PLUSLOG || p->slicing > BSSN_GEODESIC) { why = "bad slicing"; return false; }
   if (p->shift != BSSN_GAMMA_DRIVER && p->shift != BSSN_SHIFT_FROZEN) { why = "bad shift"; return false; }
-  if (p->precision != BSSN_FP64 && p->precision != BSSN_MIXED) { why = "bad precision"; return false; }
+  if (p->precision != BSSN_FP64 && p->precision != BSSN_MIXED && p->precision != BSSN_FF) {
+    why = "bad precision";
+    return false;
+  }
   if (!(p->w_fp64_threshold >= 0.0) || !std::isfinite(p->w_fp64_threshold)) {
     why = "w_fp64_threshold must be finite and >= 0";
     return false;
@@ -91,6 +94,7 @@ Grid make_grid(const bssn_params* p) {
 struct Carve {
   size_t reg, yn, ks, s1, s2, ksh, part, out16, err, trk, total;
   size_t m32[3], mw[3], ks32, ksw, dr;
+  size_t f2[3];  // double-word path: stage buffers of float2 {hi, lo}
   int nblocks;
 };
 
@@ -106,6 +110,15 @@ Carve carve(const bssn_params* p, const Grid& g) {
     c.ks = o; o += regb;
     c.s1 = o; o += regb;
     c.s2 = o; o += regb;
+    c.ksh = o;
+    if (p->boundary == BSSN_BC_SOMMERFELD) o += regb;
+  } else if (p->precision == BSSN_FF) {
+    // y_n and the k-sum in float64; three double-word stage buffers (s0 the
+    // shadow of y_n), each the size of a float64 register; double-word anchors
+    c.ks = o; o += regb;
+    for (int q = 0; q < 3; q++) {
+      c.f2[q] = o; o += regb;
+    }
     c.ksh = o;
     if (p->boundary == BSSN_BC_SOMMERFELD) o += regb;
   } else {
@@ -151,6 +164,8 @@ struct bssn_ctx {
   double* ksw;
   float* ksh32;
   float* dr;  // mixed: derivative register of the split stage
+  float2* f2[3];  // double-word path: stage buffers (f2[0]: shadow of y_n)
+  float2* kshf;   // double-word path: boundary anchors
   bool shadow_valid;
   int tile;  // stage-kernel tile configuration (see bssn_autotune)
   CUtensorMap tmap[2][3];  // mixed: tensor maps of the float stage buffers, per TMA variant
@@ -197,6 +212,12 @@ static int tma_variant(int cfg) {
 static int split_variant(int cfg) {
   const int v = cfg - tile_config_count() - N_TMA;
   return (v >= 0 && v < split_config_count()) ? v : -1;
+}
+// then the double-word configurations
+static int ff_cfg_index(int v) { return tile_config_count() + N_TMA + split_config_count() + v; }
+static int ff_variant(int cfg) {
+  const int v = cfg - ff_cfg_index(0);
+  return (v >= 0 && v < ff_config_count()) ? v : -1;
 }
 
 namespace {
@@ -266,12 +287,15 @@ bssn_status bssn_alloc(const bssn_params* p, void* d_mem, size_t bytes, void* cu
   ctx->stream = (cudaStream_t)cuda_stream;
   ctx->mem = (char*)d_mem;
   ctx->yn = (double*)(ctx->mem + c.yn);
-  ctx->ks = p->precision == BSSN_FP64 ? (double*)(ctx->mem + c.ks) : nullptr;
+  ctx->ks = p->precision != BSSN_MIXED ? (double*)(ctx->mem + c.ks) : nullptr;
   ctx->s1 = p->precision == BSSN_FP64 ? (double*)(ctx->mem + c.s1) : nullptr;
   ctx->s2 = p->precision == BSSN_FP64 ? (double*)(ctx->mem + c.s2) : nullptr;
   const bool som = p->boundary == BSSN_BC_SOMMERFELD;
   if (p->precision == BSSN_FP64) {
     ctx->ksh = som ? (double*)(ctx->mem + c.ksh) : nullptr;
+  } else if (p->precision == BSSN_FF) {
+    for (int q = 0; q < 3; q++) ctx->f2[q] = (float2*)(ctx->mem + c.f2[q]);
+    ctx->kshf = som ? (float2*)(ctx->mem + c.ksh) : nullptr;
   } else {
     for (int q = 0; q < 3; q++) {
       ctx->m32[q] = (float*)(ctx->mem + c.m32[q]);
@@ -283,7 +307,7 @@ bssn_status bssn_alloc(const bssn_params* p, void* d_mem, size_t bytes, void* cu
     ctx->dr = (float*)(ctx->mem + c.dr);
   }
   ctx->shadow_valid = false;
-  ctx->tile = 0;
+  ctx->tile = p->precision == BSSN_FF ? ff_cfg_index(0) : 0;
   ctx->part = (double*)(ctx->mem + c.part);
   ctx->out16 = (double*)(ctx->mem + c.out16);
   ctx->t = 0.0;
@@ -482,6 +506,22 @@ bssn_status bssn_rhs(bssn_ctx* ctx, const void* d_state, void* d_rhs) {
     }
     return BSSN_OK;
   }
+  if (ctx->p.precision == BSSN_FF) {
+    // double-word copy of the state in stage buffer 2
+    e = launch_shadow_ff(ctx->g, src, ctx->f2[2], ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "bssn_rhs shadow");
+    StageArgsFF a{};
+    a.src = ctx->f2[2];
+    a.rhs = out;
+    a.mode = MODE_RHS;
+    e = launch_stage_ff(ctx->g, a, ctx->stream, ff_variant(ctx->tile));
+    if (e != cudaSuccess) return cuda_fail(e, "bssn_rhs interior");
+    if (!ctx->g.periodic) {
+      e = launch_sommerfeld_ff(ctx->g, a, nullptr, ctx->stream);
+      if (e != cudaSuccess) return cuda_fail(e, "bssn_rhs boundary");
+    }
+    return BSSN_OK;
+  }
   // mixed: float copy of the state (with float64 W) in stage buffer 2
   e = launch_shadow(ctx->g, src, ctx->m32[2], ctx->mw[2], ctx->stream);
   if (e != cudaSuccess) return cuda_fail(e, "bssn_rhs shadow");
@@ -580,12 +620,45 @@ static bssn_status run_stage_mixed(bssn_ctx* ctx, int src, int mode, int out, do
   return BSSN_OK;
 }
 
+// double-word stage: src/out are stage-buffer indices into f2 (f2[0] = shadow of y_n)
+static bssn_status run_stage_ff(bssn_ctx* ctx, int src, int mode, int out, double a_dt, double b_dt) {
+  StageArgsFF a{};
+  a.src = ctx->f2[src];
+  a.src0 = ctx->f2[0];
+  a.yn = ctx->yn;
+  a.out0 = ctx->f2[out];
+  a.ksum = ctx->ks;
+  a.kshell = ctx->kshf;
+  a.a_dt = a_dt;
+  a.b_dt = b_dt;
+  a.a_hi = (float)a_dt;
+  a.a_lo = (float)(a_dt - (double)a.a_hi);
+  a.mode = mode;
+  cudaError_t e;
+  if (ctx->prof && (e = prof_mark(ctx, ctx->ev_stage)) != cudaSuccess) return cuda_fail(e, "profile");
+  e = launch_stage_ff(ctx->g, a, ctx->stream, ff_variant(ctx->tile));
+  if (e != cudaSuccess) return cuda_fail(e, "stage");
+  if (ctx->prof && (e = prof_mark(ctx, ctx->ev_stage)) != cudaSuccess) return cuda_fail(e, "profile");
+  if (ctx->prof && (e = prof_mark(ctx, ctx->ev_bc)) != cudaSuccess) return cuda_fail(e, "profile");
+  if (ctx->g.periodic) {
+    // the periodic copy moves 8-byte values whatever they hold
+    e = launch_periodic_fill(ctx->g, (double*)ctx->f2[out], ctx->stream);
+    if (e == cudaSuccess && mode == MODE_LAST) e = launch_periodic_fill(ctx->g, ctx->yn, ctx->stream);
+  } else {
+    e = launch_sommerfeld_ff(ctx->g, a, ctx->kshf, ctx->stream);
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "boundary");
+  if (ctx->prof && (e = prof_mark(ctx, ctx->ev_bc)) != cudaSuccess) return cuda_fail(e, "profile");
+  return BSSN_OK;
+}
+
 bssn_status bssn_rk4_step(bssn_ctx* ctx, int32_t nsteps) {
   if (!ctx) return fail(BSSN_EINVAL, "ctx is NULL");
   if (nsteps < 0) return fail(BSSN_EINVAL, "nsteps < 0");
   if (cudaError_t ed = drain_out(ctx)) return cuda_fail(ed, "wait for the state read-back");
   const double dt = ctx->p.dt;
   const bool mixed = ctx->p.precision == BSSN_MIXED;
+  const bool dword = ctx->p.precision == BSSN_FF;
   for (int s = 0; s < nsteps; s++) {
     bssn_status st;
     cudaError_t e;
@@ -595,11 +668,21 @@ bssn_status bssn_rk4_step(bssn_ctx* ctx, int32_t nsteps) {
       if (e != cudaSuccess) return cuda_fail(e, "track");
       ctx->trk_stale = true;
     }
-    if (ctx->g.periodic && !(mixed && ctx->shadow_valid)) {
+    if (ctx->g.periodic && !((mixed || dword) && ctx->shadow_valid)) {
       e = launch_periodic_fill(ctx->g, ctx->yn, ctx->stream);
       if (e != cudaSuccess) return cuda_fail(e, "periodic fill");
     }
-    if (!mixed) {
+    if (dword) {
+      if (!ctx->shadow_valid) {
+        e = launch_shadow_ff(ctx->g, ctx->yn, ctx->f2[0], ctx->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "shadow");
+        ctx->shadow_valid = true;
+      }
+      if ((st = run_stage_ff(ctx, 0, MODE_FIRST, 1, 0.5 * dt, 0.0)) != BSSN_OK) return st;
+      if ((st = run_stage_ff(ctx, 1, MODE_MID, 2, 0.5 * dt, 0.0)) != BSSN_OK) return st;
+      if ((st = run_stage_ff(ctx, 2, MODE_MID, 1, dt, 0.0)) != BSSN_OK) return st;
+      if ((st = run_stage_ff(ctx, 1, MODE_LAST, 0, 0.0, dt / 6.0)) != BSSN_OK) return st;
+    } else if (!mixed) {
       if ((st = run_stage(ctx, ctx->yn, MODE_FIRST, ctx->s1, 0.5 * dt, 0.0)) != BSSN_OK) return st;
       if ((st = run_stage(ctx, ctx->s1, MODE_MID, ctx->s2, 0.5 * dt, 0.0)) != BSSN_OK) return st;
       if ((st = run_stage(ctx, ctx->s2, MODE_MID, ctx->s1, dt, 0.0)) != BSSN_OK) return st;
@@ -627,6 +710,7 @@ static bssn_status check_err(bssn_ctx* ctx);
 // m[1], 24 floats = 12 doubles per point).  Stream order keeps a following
 // step from overwriting it early.
 static double* adm_scratch(bssn_ctx* ctx) {
+  if (ctx->p.precision == BSSN_FF) return (double*)ctx->f2[1];
   return ctx->p.precision == BSSN_FP64 ? ctx->s1 : (double*)ctx->m32[1];
 }
 
@@ -697,6 +781,10 @@ static double* stage_area(bssn_ctx* ctx, int* fields) {
     *fields = NF;
     return ctx->s1;
   }
+  if (ctx->p.precision == BSSN_FF) {  // a double-word register holds 24 fields of doubles
+    *fields = NF;
+    return (double*)ctx->f2[1];
+  }
   *fields = NF / 2;
   return (double*)ctx->m32[1];
 }
@@ -732,6 +820,11 @@ static cudaError_t copy_state(bssn_ctx* ctx, double* host, bool to_device, bool 
 static int out_areas(bssn_ctx* ctx, double* area[2], int nf[2]) {
   if (ctx->p.precision == BSSN_FP64) {
     area[0] = ctx->s2;
+    nf[0] = NF;
+    return 1;
+  }
+  if (ctx->p.precision == BSSN_FF) {
+    area[0] = (double*)ctx->f2[2];
     nf[0] = NF;
     return 1;
   }
@@ -875,9 +968,10 @@ bssn_status bssn_wait_state(bssn_ctx* ctx) {
 // Configurations: [0, tile_config_count()) the fused kernels; the next
 // N_TMA the TMA-staged mixed kernels; then the split-stage
 // variants.
-int32_t bssn_tile_count(void) { return tile_config_count() + N_TMA + split_config_count(); }
+int32_t bssn_tile_count(void) { return tile_config_count() + N_TMA + split_config_count() + ff_config_count(); }
 
 const char* bssn_tile_name(int32_t cfg) {
+  if (ff_variant(cfg) >= 0) return ff_config_name(ff_variant(cfg));
   if (tma_variant(cfg) == 0) return "tma32x4x1/2";
   if (tma_variant(cfg) == 1) return "tma32x8x1/1";
   if (split_variant(cfg) >= 0) return split_config_name(split_variant(cfg));
@@ -886,6 +980,7 @@ const char* bssn_tile_name(int32_t cfg) {
 
 static bool tile_usable(const bssn_ctx* ctx, int cfg) {
   if (cfg < 0 || cfg >= bssn_tile_count()) return false;
+  if ((ff_variant(cfg) >= 0) != (ctx->p.precision == BSSN_FF)) return false;
   if (tma_variant(cfg) >= 0) return ctx->p.precision == BSSN_MIXED && ctx->tmap_ok;
   if (split_variant(cfg) >= 0) return ctx->p.precision == BSSN_MIXED;
   return true;
@@ -894,7 +989,9 @@ static bool tile_usable(const bssn_ctx* ctx, int cfg) {
 bssn_status bssn_set_tile(bssn_ctx* ctx, int32_t cfg) {
   if (!ctx) return fail(BSSN_EINVAL, "ctx is NULL");
   if (!tile_usable(ctx, cfg))
-    return fail(BSSN_EINVAL, "tile config out of range (the TMA and split kernels are for the mixed path)");
+    return fail(BSSN_EINVAL,
+                "tile config out of range or not for this precision (the TMA and split kernels are for the "
+                "mixed path, the ff kernels for the double-word path)");
   ctx->tile = cfg;
   return BSSN_OK;
 }
@@ -903,8 +1000,10 @@ bssn_status bssn_autotune(bssn_ctx* ctx, int32_t reps, int32_t* best, double* ms
   if (!ctx || reps < 1) return fail(BSSN_EINVAL, "bad argument");
   if (cudaError_t ed = drain_out(ctx)) return cuda_fail(ed, "wait for the state read-back");
   const bool mixed = ctx->p.precision == BSSN_MIXED;
-  if (mixed && !ctx->shadow_valid) {
-    cudaError_t e = launch_shadow(ctx->g, ctx->yn, ctx->m32[0], ctx->mw[0], ctx->stream);
+  const bool dword = ctx->p.precision == BSSN_FF;
+  if ((mixed || dword) && !ctx->shadow_valid) {
+    cudaError_t e = mixed ? launch_shadow(ctx->g, ctx->yn, ctx->m32[0], ctx->mw[0], ctx->stream)
+                          : launch_shadow_ff(ctx->g, ctx->yn, ctx->f2[0], ctx->stream);
     if (e != cudaSuccess) return cuda_fail(e, "shadow");
     ctx->shadow_valid = true;
   }
@@ -928,6 +1027,14 @@ bssn_status bssn_autotune(bssn_ctx* ctx, int32_t reps, int32_t* best, double* ms
     }
     auto launch1 = [&](int stage) -> cudaError_t {
       const bool second = stage == 1;
+      if (dword) {
+        StageArgsFF a{};
+        a.src = ctx->f2[second ? 1 : 0]; a.src0 = ctx->f2[0]; a.yn = ctx->yn;
+        a.out0 = ctx->f2[second ? 2 : 1]; a.ksum = ctx->ks; a.a_dt = 0.5 * ctx->p.dt;
+        a.a_hi = (float)a.a_dt; a.a_lo = (float)(a.a_dt - (double)a.a_hi);
+        a.mode = second ? MODE_MID : MODE_FIRST;
+        return launch_stage_ff(ctx->g, a, ctx->stream, ff_variant(c));
+      }
       if (!mixed) {
         StageArgs a{};
         a.src = second ? ctx->s1 : ctx->yn; a.src0 = ctx->yn; a.yn = ctx->yn;

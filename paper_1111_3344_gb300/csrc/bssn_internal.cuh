@@ -3,10 +3,12 @@
 #pragma once
 #include <cstdint>
 #include <string>
+#include <type_traits>
 #include <cuda.h>
 #include <cuda_runtime.h>
 
 #include "bssn.h"
+#include "ff.cuh"
 
 namespace bssn {
 
@@ -44,6 +46,9 @@ struct Grid {
   // float64 pipe on every thread that would otherwise compute it)
   double i12h, i12h2, i144h2, kos, i2h;  // 1/(12h), 1/(12h^2), 1/(144h^2), eps/(64h), 1/(2h)
   float i12hf, i12h2f, i144h2f, kosf, i2hf, w_floorf, etaf, hf;
+  // the float remainders d - (double)f of the same constants (the low words
+  // of their double-word forms)
+  float i12hl, i12h2l, i144h2l, kosl, w_floorl, etal;
   float xminf[3];
   // stress-energy tensor T_{mu nu} (10 fields in the register layout: T_00,
   // T_0x, T_0y, T_0z, T_xx, T_xy, T_xz, T_yy, T_yz, T_zz), or null (vacuum)
@@ -68,15 +73,29 @@ inline void grid_constants(Grid& g) {
   g.xminf[0] = (float)g.xmin0;
   g.xminf[1] = (float)g.xmin1;
   g.xminf[2] = (float)g.xmin2;
+  g.i12hl = (float)(g.i12h - (double)g.i12hf);
+  g.i12h2l = (float)(g.i12h2 - (double)g.i12h2f);
+  g.i144h2l = (float)(g.i144h2 - (double)g.i144h2f);
+  g.kosl = (float)(g.kos - (double)g.kosf);
+  g.w_floorl = (float)(g.w_floor - (double)g.w_floorf);
+  g.etal = (float)(g.eta - (double)g.etaf);
 }
 
-// Pick the float64 or float copy of a constant.
+// Pick the float64, float or double-word (float f + remainder l) copy of a
+// constant.
 template <typename T>
-__host__ __device__ __forceinline__ T gc(double d, float f);
+__host__ __device__ __forceinline__ T gc(double d, float f, float l);
 template <>
-__host__ __device__ __forceinline__ double gc<double>(double d, float) { return d; }
+__host__ __device__ __forceinline__ double gc<double>(double d, float, float) { return d; }
 template <>
-__host__ __device__ __forceinline__ float gc<float>(double, float f) { return f; }
+__host__ __device__ __forceinline__ float gc<float>(double, float f, float) { return f; }
+template <>
+__host__ __device__ __forceinline__ ff gc<ff>(double, float f, float l) { return ff(f, l); }
+
+template <typename T>
+constexpr bool is_f32 = std::is_same<T, float>::value;
+template <typename T>
+constexpr bool is_f64 = std::is_same<T, double>::value;
 
 // Matter projections of T_{mu nu} at linear index id (Sec. "Spacetime Curvature
 // Evolution"): E = (T_00 - 2 beta^i T_0i + beta^i beta^j T_ij)/alpha^2,
@@ -205,6 +224,22 @@ struct StageArgsT {
 using StageArgs = StageArgsT<double>;
 using StageArgsMixed = StageArgsT<float>;
 
+// Arguments of a fused stage of the double-word path: the stage buffers hold
+// double-word values (float2 {hi, lo}) of X itself; y_n and the weighted sum
+// of the k are float64; the right-hand side runs in double-word arithmetic.
+struct StageArgsFF {
+  const float2* src;   // stage input (stencil source)
+  const float2* src0;  // double-word shadow of y_n (base of the stage values)
+  double* yn;          // y_n, advanced in place by LAST
+  float2* out0;        // next stage state (FIRST/MID); LAST: the shadow of y_{n+1}
+  double* ksum;        // k1 + 2 k2 + 2 k3, float64
+  double* rhs;         // MODE_RHS output (float64 register)
+  float2* kshell;      // if non-null: k at interior points next to the outer boundary
+  double a_dt, b_dt;   // stage coefficients times dt
+  float a_hi, a_lo;    // a_dt as a double-word constant
+  int mode;
+};
+
 // Punctures {m, x, y, z} (at most 8) and the excision radius of the excised
 // norms and integrals, passed to kernels by value.
 struct Punct {
@@ -238,6 +273,14 @@ cudaError_t launch_sommerfeld(const Grid& g, const StageArgs& a, const double* k
 cudaError_t launch_sommerfeld_mixed(const Grid& g, const StageArgsMixed& a, const float* kanchor,
                                     cudaStream_t s);
 cudaError_t launch_periodic_fill(const Grid& g, double* y, cudaStream_t s);
+// Double-word path (k_stage_ff.cu): fused stage in configuration cfg
+// (ff_config_count() of them), Sommerfeld boundary (float64 arithmetic on the
+// double-word stage values), double-word shadow of a float64 register.
+int ff_config_count();
+const char* ff_config_name(int c);
+cudaError_t launch_stage_ff(const Grid& g, const StageArgsFF& a, cudaStream_t s, int cfg);
+cudaError_t launch_sommerfeld_ff(const Grid& g, const StageArgsFF& a, const float2* kanchor, cudaStream_t s);
+cudaError_t launch_shadow_ff(const Grid& g, const double* y, float2* s2, cudaStream_t s);
 cudaError_t launch_periodic_fill_mixed(const Grid& g, float* y, double* w, cudaStream_t s);
 cudaError_t launch_shadow(const Grid& g, const double* y, float* s32, double* w, cudaStream_t s);
 // Copy fields f0 .. f0+nf-1 between a contiguous unpadded block flat and the

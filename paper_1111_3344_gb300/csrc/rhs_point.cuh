@@ -28,6 +28,18 @@ template <>
 __device__ __forceinline__ double fmaT<double>(double a, double b, double c) { return fma(a, b, c); }
 template <>
 __device__ __forceinline__ float fmaT<float>(float a, float b, float c) { return fmaf(a, b, c); }
+template <>
+__device__ __forceinline__ ff fmaT<ff>(ff a, ff b, ff c) { return ff_fma(a, b, c); }
+
+// |x| and e^x in the arithmetic type
+template <typename T>
+__device__ __forceinline__ T absT(T x) { return fabs(x); }
+template <>
+__device__ __forceinline__ ff absT<ff>(ff x) { return ff_fabs(x); }
+template <typename T>
+__device__ __forceinline__ T expT(T x) { return exp(x); }
+template <>
+__device__ __forceinline__ ff expT<ff>(ff x) { return ff_exp(x); }
 
 template <typename T, typename S>
 __device__ __forceinline__ T ldg(const S* p) {
@@ -74,7 +86,7 @@ __device__ __forceinline__ T d1u(const A& acc, int f, const P* p, long long s) {
 // cheaper plain form.
 template <typename T, typename A, typename P>
 __device__ __forceinline__ T d2u(const A& acc, int f, const P* p, long long s, T f0) {
-  if constexpr (sizeof(T) == 4) {
+  if constexpr (is_f32<T>) {
     T a = (acc.template ld<T>(f, p + s) - f0) + (acc.template ld<T>(f, p - s) - f0);
     T b = (acc.template ld<T>(f, p + 2 * s) - f0) + (acc.template ld<T>(f, p - 2 * s) - f0);
     return fmaT<T>(T(16), a, -b);
@@ -98,25 +110,27 @@ __device__ __forceinline__ T dmu(const A& acc, int f, const P* p, long long sa, 
 // (at x -+ 2), and the mixed difference costs 3 float64 operations instead
 // of 15.  Same stencil as dmu (D1 along x applied to D1 along b); the result
 // is 12 h times the mixed derivative (v already carries 1/(12h)).
-template <int W, typename A, typename P>
-__device__ __forceinline__ double dmx_shfl(const A& acc, int f, const P* p, long long sb, double v,
-                                           double i12h) {
+__device__ __forceinline__ double shflT(double v, int src, int W) { return __shfl_sync(0xffffffffu, v, src, W); }
+__device__ __forceinline__ ff shflT(ff v, int src, int W) {
+  return ff(__shfl_sync(0xffffffffu, v.hi, src, W), __shfl_sync(0xffffffffu, v.lo, src, W));
+}
+template <int W, typename T, typename A, typename P>
+__device__ __forceinline__ T dmx_shfl(const A& acc, int f, const P* p, long long sb, T v, T i12h) {
   const int lane = threadIdx.x & (W - 1);
   const bool lo = lane < 2, hi = lane >= W - 2;
-  double ve = 0.0;
-  if (lo || hi) ve = d1u<double>(acc, f, p + (lo ? -2 : 2), sb) * i12h;  // x - 2 or x + 2
-  const unsigned full = 0xffffffffu;
-  const double sm2 = __shfl_sync(full, v, lane - 2, W);
-  const double sm1 = __shfl_sync(full, v, lane - 1, W);
-  const double sp1 = __shfl_sync(full, v, lane + 1, W);
-  const double sp2 = __shfl_sync(full, v, lane + 2, W);
-  const double e1 = __shfl_sync(full, ve, 1, W);       // lane 1 holds x_0 - 1
-  const double ew = __shfl_sync(full, ve, W - 2, W);   // lane W-2 holds x_{W-1} + 1
-  const double vm2 = lane >= 2 ? sm2 : ve;
-  const double vm1 = lane >= 1 ? sm1 : e1;
-  const double vp1 = lane <= W - 2 ? sp1 : ew;
-  const double vp2 = lane <= W - 3 ? sp2 : ve;
-  return fma(8.0, vp1 - vm1, -(vp2 - vm2));
+  T ve = T(0);
+  if (lo || hi) ve = d1u<T>(acc, f, p + (lo ? -2 : 2), sb) * i12h;  // x - 2 or x + 2
+  const T sm2 = shflT(v, lane - 2, W);
+  const T sm1 = shflT(v, lane - 1, W);
+  const T sp1 = shflT(v, lane + 1, W);
+  const T sp2 = shflT(v, lane + 2, W);
+  const T e1 = shflT(ve, 1, W);       // lane 1 holds x_0 - 1
+  const T ew = shflT(ve, W - 2, W);   // lane W-2 holds x_{W-1} + 1
+  const T vm2 = lane >= 2 ? sm2 : ve;
+  const T vm1 = lane >= 1 ? sm1 : e1;
+  const T vp1 = lane <= W - 2 ? sp1 : ew;
+  const T vp2 = lane <= W - 3 ? sp2 : ve;
+  return fmaT<T>(T(8), vp1 - vm1, -(vp2 - vm2));
 }
 
 // the same helpers over the plain read-only global path (one field)
@@ -145,6 +159,18 @@ __device__ __forceinline__ double up_coef(bool pos, int m) {
   const double cn[7] = {1.0, -6.0, 18.0, -10.0, -3.0, 0.0, 0.0};
   return pos ? cp[m + 3] : cn[m + 3];
 }
+// the same weight in the arithmetic type T (float and double-word: from the
+// float constants, which hold these small integers exactly)
+template <typename T>
+__device__ __forceinline__ T up_coefT(bool pos, int m) {
+  if constexpr (is_f64<T>) {
+    return up_coef(pos, m);
+  } else {
+    const float cp[7] = {0.0f, 0.0f, -3.0f, -10.0f, 18.0f, -6.0f, 1.0f};
+    const float cn[7] = {1.0f, -6.0f, 18.0f, -10.0f, -3.0f, 0.0f, 0.0f};
+    return T(pos ? cp[m + 3] : cn[m + 3]);
+  }
+}
 
 // Background value X0 of field f (1 for W, the diagonal of gt and alpha; 0
 // otherwise).  The float stage buffers of the mixed path hold X - X0, so that
@@ -168,9 +194,18 @@ __host__ __device__ __forceinline__ double background(const Grid& g, int f) {
 template <typename T, typename S, bool DEV, typename A, int XSEG = 0, int YROWS = 0, int ZS = 1>
 __device__ __forceinline__ void rhs_point_acc(const Grid& g, const A& acc, int i, int j, int k,
                                               T out[NF]) {
-  const T i12h = gc<T>(g.i12h, g.i12hf);
-  const T i12h2 = gc<T>(g.i12h2, g.i12h2f);
-  const T i144h2 = gc<T>(g.i144h2, g.i144h2f);
+  // ROLL (double-word arithmetic): a double-word operation is 7 to 15 float
+  // instructions, so the fully unrolled right-hand side would be some 30,000
+  // instructions of straight-line code per point, far beyond the instruction
+  // cache (ncu: warps stalled mostly on instruction fetch).  The second
+  // derivatives (six pairs) and the advection / dissipation stencils (24
+  // fields) then run as loops over the pairs and the fields, in the same order
+  // and with the same arithmetic, with their per-iteration values kept in
+  // arrays indexed at run time.
+  constexpr bool ROLL = std::is_same<T, ff>::value;
+  const T i12h = gc<T>(g.i12h, g.i12hf, g.i12hl);
+  const T i12h2 = gc<T>(g.i12h2, g.i12h2f, g.i12h2l);
+  const T i144h2 = gc<T>(g.i144h2, g.i144h2f, g.i144h2l);
 #define PF(f) acc.ptr(f)
 #define SD(f, d) acc.s((f), (d))
 #define LD(f, p) acc.template ld<T>((f), (p))
@@ -206,7 +241,7 @@ __device__ __forceinline__ void rhs_point_acc(const Grid& g, const A& acc, int i
     T det = gt[0] * c00 + gt[1] * c01 + gt[2] * c02;
     T idet;
     if (g.use_w) {
-      const T wf = gc<T>(g.w_floor, g.w_floorf);
+      const T wf = gc<T>(g.w_floor, g.w_floorf, g.w_floorl);
       const T Wd = chi > wf ? chi : wf;
       const T r = T(1) / (det * Wd);
       idet = Wd * r;
@@ -240,11 +275,12 @@ __device__ __forceinline__ void rhs_point_acc(const Grid& g, const A& acc, int i
 
   // ---- D_y D_z through shared memory (full blocks of full rows)
   [[maybe_unused]] T dyz[11];  // gt_ij (6), phi|W, alpha, beta^i (3)
-  if constexpr (YROWS > 0 && XSEG == 32 && sizeof(T) == 8) {
-    extern __shared__ double yz_smem[];
+  if constexpr (YROWS > 0 && XSEG == 32 && !is_f32<T>) {
+    extern __shared__ double yz_smem[];  // 8-byte slots: float64 or double-word values
+    T* yz = reinterpret_cast<T*>(yz_smem);
     constexpr int ROWS = YROWS + 4;
     const int ty = threadIdx.y, tz = threadIdx.z, lane = threadIdx.x;
-    auto at = [&](int q, int row) -> double& { return yz_smem[((q * ROWS + row) * ZS + tz) * 32 + lane]; };
+    auto at = [&](int q, int row) -> T& { return yz[((q * ROWS + row) * ZS + tz) * 32 + lane]; };
     auto dz_of = [&](int q) -> T {
       return q < 6 ? dgt[2][q] : (q == 6 ? dchi[2] : (q == 7 ? dalp[2] : db[2][q - 8]));
     };
@@ -282,7 +318,79 @@ __device__ __forceinline__ void rhs_point_acc(const Grid& g, const A& acc, int i
   for (int m = 0; m < 6; m++) Rdd[m] = T(0);
 #pragma unroll
   for (int a = 0; a < 3; a++) lapb[a] = gdiv[a] = T(0);
-  {
+  if constexpr (ROLL) {
+    // The six pairs (a, b) as a loop that is not unrolled: the same stencils
+    // and the same contractions in the same order, with the pair's strides,
+    // scale and first differences picked at run time -- one copy of the code
+    // instead of six (see ROLL).
+    const long long s3[3] = {SD(F_GT, 0), SD(F_GT, 1), SD(F_GT, 2)};
+#pragma unroll 1
+    for (int pq = 0; pq < 6; pq++) {
+      const int pa = pq < 3 ? 0 : (pq < 5 ? 1 : 2);
+      const int pb = pq < 3 ? pq : (pq < 5 ? pq - 2 : 2);
+      const long long sa = pa == 0 ? s3[0] : (pa == 1 ? s3[1] : s3[2]);
+      const long long sb = pb == 0 ? s3[0] : (pb == 1 ? s3[1] : s3[2]);
+      T dd[6], vb[3], vchi, valp, sc;
+      if (pa == pb) {
+        sc = i12h2;
+#pragma unroll
+        for (int m = 0; m < 6; m++) dd[m] = d2u<T>(acc, F_GT + m, PF(F_GT + m), sa, gt_r[m]);
+        vchi = d2u<T>(acc, F_CHI, PF(F_CHI), sa, chi_r) * i12h2;
+        valp = d2u<T>(acc, F_ALP, PF(F_ALP), sa, alp_r);
+#pragma unroll
+        for (int a = 0; a < 3; a++) vb[a] = d2u<T>(acc, F_BETA + a, PF(F_BETA + a), sa, beta[a]);
+      } else if (XSEG > 0 && pa == 0) {
+        if constexpr (XSEG > 0) {
+          sc = i12h;
+          const bool y = pb == 1;
+#pragma unroll
+          for (int m = 0; m < 6; m++)
+            dd[m] = dmx_shfl<XSEG>(acc, F_GT + m, PF(F_GT + m), sb, y ? dgt[1][m] : dgt[2][m], i12h);
+          vchi = dmx_shfl<XSEG>(acc, F_CHI, PF(F_CHI), sb, y ? dchi[1] : dchi[2], i12h) * i12h;
+          valp = dmx_shfl<XSEG>(acc, F_ALP, PF(F_ALP), sb, y ? dalp[1] : dalp[2], i12h);
+#pragma unroll
+          for (int a = 0; a < 3; a++)
+            vb[a] = dmx_shfl<XSEG>(acc, F_BETA + a, PF(F_BETA + a), sb, y ? db[1][a] : db[2][a], i12h);
+        }
+      } else if (YROWS > 0 && pa == 1) {  // (1, 2) from the rows' differences along z
+        sc = i12h;
+#pragma unroll
+        for (int m = 0; m < 6; m++) dd[m] = dyz[m];
+        vchi = dyz[6] * i12h;
+        valp = dyz[7];
+#pragma unroll
+        for (int a = 0; a < 3; a++) vb[a] = dyz[8 + a];
+      } else {
+        sc = i144h2;
+#pragma unroll
+        for (int m = 0; m < 6; m++) dd[m] = dmu<T>(acc, F_GT + m, PF(F_GT + m), sa, sb);
+        vchi = dmu<T>(acc, F_CHI, PF(F_CHI), sa, sb) * i144h2;
+        valp = dmu<T>(acc, F_ALP, PF(F_ALP), sa, sb);
+#pragma unroll
+        for (int a = 0; a < 3; a++) vb[a] = dmu<T>(acc, F_BETA + a, PF(F_BETA + a), sa, sb);
+      }
+      ddchi[pq] = vchi;
+      ddalp[pq] = valp;
+      sc2[pq] = sc;
+      T g2 = g2u[0];
+#pragma unroll
+      for (int m = 1; m < 6; m++) g2 = pq == m ? g2u[m] : g2;
+      const T wb = sc * g2;
+      const T w = T(-0.5) * wb;
+#pragma unroll
+      for (int m = 0; m < 6; m++) Rdd[m] = fmaT<T>(w, dd[m], Rdd[m]);
+#pragma unroll
+      for (int a = 0; a < 3; a++) {
+        lapb[a] = fmaT<T>(wb, vb[a], lapb[a]);
+        // d_pa d_pb beta^a: into gdiv[pa] when a == pb, into gdiv[pb] when a == pa != pb
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+          if (a == pb && k == pa) gdiv[k] = fmaT<T>(sc, vb[a], gdiv[k]);
+          if (pa != pb && a == pa && k == pb) gdiv[k] = fmaT<T>(sc, vb[a], gdiv[k]);
+        }
+      }
+    }
+  } else {
 #pragma unroll
     for (int pa = 0; pa < 3; pa++) {
 #pragma unroll
@@ -296,7 +404,7 @@ __device__ __forceinline__ void rhs_point_acc(const Grid& g, const A& acc, int i
           for (int m = 0; m < 6; m++) dd[m] = d2u<T>(acc, F_GT + m, PF(F_GT + m), SD(F_GT + m, pa), gt_r[m]);
           ddchi[pq] = d2u<T>(acc, F_CHI, PF(F_CHI), SD(F_CHI, pa), chi_r) * i12h2;
           ddalp[pq] = d2u<T>(acc, F_ALP, PF(F_ALP), SD(F_ALP, pa), alp_r);
-        } else if constexpr (XSEG > 0 && sizeof(T) == 8) {
+        } else if constexpr (XSEG > 0 && !is_f32<T>) {
           if (pa == 0) {
             sc = i12h;
 #pragma unroll
@@ -336,7 +444,7 @@ __device__ __forceinline__ void rhs_point_acc(const Grid& g, const A& acc, int i
           T v;
           if (pa == pb) {
             v = d2u<T>(acc, F_BETA + a, PF(F_BETA + a), SD(F_BETA + a, pa), beta[a]);
-          } else if constexpr (XSEG > 0 && sizeof(T) == 8) {
+          } else if constexpr (XSEG > 0 && !is_f32<T>) {
             if (pa == 0)
               v = dmx_shfl<XSEG>(acc, F_BETA + a, PF(F_BETA + a), SD(F_BETA + a, pb), db[pb][a], i12h);
             else if constexpr (YROWS > 0)
@@ -368,7 +476,7 @@ __device__ __forceinline__ void rhs_point_acc(const Grid& g, const A& acc, int i
       for (int b = a; b < 3; b++)
         ddphi[sym(a, b)] = fmaT<T>(T(2) * dphi[a], dphi[b], -ddchi[sym(a, b)] * ih);
   } else {
-    em4 = exp(T(-4) * chi);
+    em4 = expT<T>(T(-4) * chi);
 #pragma unroll
     for (int a = 0; a < 3; a++) dphi[a] = dchi[a];
 #pragma unroll
@@ -640,7 +748,7 @@ __device__ __forceinline__ void rhs_point_acc(const Grid& g, const A& acc, int i
 #pragma unroll
     for (int a = 0; a < 3; a++) {
       out[F_BETA + a] = T(0.75) * Bv[a];
-      out[F_B + a] = gam_rhs[a] - gc<T>(g.eta, g.etaf) * q * Bv[a];
+      out[F_B + a] = gam_rhs[a] - gc<T>(g.eta, g.etaf, g.etal) * q * Bv[a];
     }
   }
 
@@ -653,12 +761,46 @@ __device__ __forceinline__ void rhs_point_acc(const Grid& g, const A& acc, int i
 #pragma unroll
     for (int f = 0; f < NF; f++)
       if (f < nf) out[f] += acc.template advko<T>(f);
+  } else if constexpr (ROLL) {
+    // one loop over the fields: the same weights and the same order of
+    // accumulation as below (centre term, then axes x, y, z, offsets -3..3)
+    const T kap = gc<T>(g.kos, g.kosf, g.kosl);
+    T bh[3];
+#pragma unroll
+    for (int d = 0; d < 3; d++) bh[d] = absT<T>(beta[d]) * i12h;
+    const T w0 = fmaT<T>(T(-10), bh[0] + bh[1] + bh[2], T(-60) * kap);
+    const T cko[7] = {T(1), T(-6), T(15), T(-20), T(15), T(-6), T(1)};
+    T w[3][7];
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+      const bool pos = beta[d] >= T(0);
+#pragma unroll
+      for (int m = -3; m <= 3; m++)
+        if (m != 0) w[d][m + 3] = fmaT<T>(bh[d], up_coefT<T>(pos, m), kap * cko[m + 3]);
+    }
+    T r[NF];  // indexed at run time
+#pragma unroll
+    for (int f = 0; f < NF; f++) r[f] = out[f];
+    const long long s3[3] = {SD(F_GT, 0), SD(F_GT, 1), SD(F_GT, 2)};
+#pragma unroll 1
+    for (int f = 0; f < nf; f++) {
+      const auto* p = PF(f);
+      T accv = fmaT<T>(w0, LD(f, p), r[f]);
+#pragma unroll
+      for (int d = 0; d < 3; d++)
+#pragma unroll
+        for (int m = -3; m <= 3; m++)
+          if (m != 0) accv = fmaT<T>(w[d][m + 3], LD(f, p + m * s3[d]), accv);
+      r[f] = accv;
+    }
+#pragma unroll
+    for (int f = 0; f < NF; f++) out[f] = r[f];
   } else {
-    const T kap = gc<T>(g.kos, g.kosf);
+    const T kap = gc<T>(g.kos, g.kosf, g.kosl);
     T f0s[NF];  // centre values as stored (float: the stencil is applied to f_m - f0)
     T bh[3];
 #pragma unroll
-    for (int d = 0; d < 3; d++) bh[d] = fabs(beta[d]) * i12h;
+    for (int d = 0; d < 3; d++) bh[d] = absT<T>(beta[d]) * i12h;
     const T w0 = fmaT<T>(T(-10), bh[0] + bh[1] + bh[2], T(-60) * kap);
 #pragma unroll
     for (int f = 0; f < NF; f++) {
@@ -672,7 +814,7 @@ __device__ __forceinline__ void rhs_point_acc(const Grid& g, const A& acc, int i
       else if (f >= F_BETA && f < F_BETA + 3) f0 = beta[f - F_BETA];
       else if (f >= F_B) f0 = Bv[f - F_B];
       else f0 = LD(f, PF(f));
-      if constexpr (sizeof(T) == 8) out[f] = fmaT<T>(w0, f0, out[f]);
+      if constexpr (!is_f32<T>) out[f] = fmaT<T>(w0, f0, out[f]);
       f0s[f] = f0;
     }
     const T cko[7] = {T(1), T(-6), T(15), T(-20), T(15), T(-6), T(1)};
@@ -682,13 +824,13 @@ __device__ __forceinline__ void rhs_point_acc(const Grid& g, const A& acc, int i
       T w[7];
 #pragma unroll
       for (int m = -3; m <= 3; m++)
-        if (m != 0) w[m + 3] = fmaT<T>(bh[d], T(up_coef(pos, m)), kap * cko[m + 3]);
+        if (m != 0) w[m + 3] = fmaT<T>(bh[d], up_coefT<T>(pos, m), kap * cko[m + 3]);
 #pragma unroll
       for (int f = 0; f < NF; f++) {
         if (f >= nf) break;
         const auto* p = PF(f);
         T accv = out[f];
-        if constexpr (sizeof(T) == 4) {
+        if constexpr (is_f32<T>) {
           // the weights sum to zero: apply them to differences to the centre
 #pragma unroll
           for (int m = -3; m <= 3; m++)

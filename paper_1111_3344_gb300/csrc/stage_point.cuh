@@ -167,4 +167,46 @@ __device__ __forceinline__ void stage_point_mixed(const Grid& g, const StageArgs
   stage_point_mixed_acc(g, a, acc, ii, jj, kk);
 }
 
+// ------------------------------------------------------------ double-word
+
+// Fused stage at interior point (ii, jj, kk), double-word arithmetic.  XSEG,
+// YROWS, ZS as for the float64 stage (stage_point_fp64): full 32-point rows
+// share first differences across lanes for D_x D_y and D_x D_z, full blocks
+// share them across rows through shared memory for D_y D_z.
+template <int XSEG = 0, int YROWS = 0, int ZS = 1>
+__device__ __forceinline__ void stage_point_ff(const Grid& g, const StageArgsFF& a, int ii, int jj, int kk) {
+  const int i = ii + GH, j = jj + GH, k = kk + GH;
+  const long long id = lin(g, i, j, k);
+  ff r[NF];
+  rhs_point<ff, float2, false, XSEG, YROWS, ZS>(g, a.src, id, i, j, k, r);
+  const long long fs = g.fstride;
+  if (a.mode == MODE_RHS) {
+#pragma unroll
+    for (int f = 0; f < NF; f++) a.rhs[f * fs + id] = ff_to_double(r[f]);
+    return;
+  }
+  if (a.kshell && on_shell(g, ii, jj, kk)) {
+#pragma unroll
+    for (int f = 0; f < NF; f++) a.kshell[f * fs + id] = r[f].f2();
+  }
+  if (a.mode == MODE_LAST) {
+#pragma unroll
+    for (int f = 0; f < NF; f++) {
+      const long long o = f * fs + id;
+      const double v = fma(a.b_dt, a.ksum[o] + ff_to_double(r[f]), a.yn[o]);
+      a.yn[o] = v;
+      a.out0[o] = ff_from_double(v).f2();
+    }
+    return;
+  }
+  const ff adt(a.a_hi, a.a_lo);
+#pragma unroll
+  for (int f = 0; f < NF; f++) {
+    const long long o = f * fs + id;
+    a.out0[o] = ff_fma(adt, r[f], ff(__ldg(a.src0 + o))).f2();
+    const double kd = ff_to_double(r[f]);
+    a.ksum[o] = a.mode == MODE_FIRST ? kd : fma(2.0, kd, a.ksum[o]);
+  }
+}
+
 }  // namespace bssn
