@@ -97,12 +97,17 @@ FP64_NOMINAL_GFLOPS = 1250.0        # nominal GB300 float64 rate (context only)
 
 
 def workload_params(precision="fp64"):
+    """The benchmark puncture's parameters in one precision form: fp64, mixed,
+    mixed_ks64 (mixed with the k-sum of every field in float64) or ff
+    (double-word right-hand side)."""
     from paper_1111_3344_gb300.bssn import Params
     h = 2 * DOMAIN / N_SIDE
+    ks64 = precision == "mixed_ks64"
     # mixed: W right-hand side in float64 below W = 0.2 (r < ~0.6 M from the puncture)
     return Params(n=(N_SIDE,) * 3, xmin=(-DOMAIN,) * 3, h=h, boundary="sommerfeld", conformal="W",
                   slicing="1+log", shift="gamma-driver", eta=2.0, ko_eps=0.1, dt=0.25 * h,
-                  precision=precision, w_fp64_threshold=0.2, r_excise=1.0)
+                  precision="mixed" if ks64 else precision, ksum_fp64=ks64, w_fp64_threshold=0.2,
+                  r_excise=1.0)
 
 
 BL_P = [1, 1.0, 0.0, 0.0, 0.0]
@@ -835,8 +840,8 @@ def main():
                          "served parts of the metric")
     ap.add_argument("--served-sample", type=int, default=32,
                     help="requests of the served stream in the default line's served sample")
-    ap.add_argument("--variants", default="mixed,ff",
-                    help="precision workload: the forms compared with float64 (mixed, ff)")
+    ap.add_argument("--variants", default="mixed,mixed_ks64,ff",
+                    help="precision workload: the forms compared with float64 (mixed, mixed_ks64, ff)")
     ap.add_argument("--n", type=int, default=128,
                     help="grid points per side (128 is the benchmark workload; smaller sizes are "
                          "for profiling captures only)")

@@ -80,6 +80,10 @@ enum { BSSN_ID_FLAT = 0, BSSN_ID_GAUGE_WAVE = 1, BSSN_ID_BL = 2, BSSN_ID_KASNER 
  *                      pipe, RK4 state, k-sum and reductions in float64
  *                      (single-grid contexts only; batches and the server
  *                      take BSSN_FP64 or BSSN_MIXED).
+ *  ksum_fp64           mixed precision, single-grid contexts only: 1 keeps
+ *                      the weighted sum of the RK4 k of every field in
+ *                      float64 (one more float64 register; W's is float64
+ *                      in any case), 0 in float (the default).
  *  w_fp64_threshold    mixed precision: points with W below this take the
  *                      W/phi right-hand side in float64.
  *  r_excise            constraint norms: excised set is r > r_excise from
@@ -100,7 +104,7 @@ typedef struct bssn_params {
   double ko_eps;
   double dt;
   int32_t precision;
-  int32_t reserved0;
+  int32_t ksum_fp64;
   double w_fp64_threshold;
   double r_excise;
   double w_floor;

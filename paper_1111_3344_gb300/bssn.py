@@ -50,7 +50,7 @@ class bssn_params(ctypes.Structure):
         ("ko_eps", ctypes.c_double),
         ("dt", ctypes.c_double),
         ("precision", ctypes.c_int32),
-        ("reserved0", ctypes.c_int32),
+        ("ksum_fp64", ctypes.c_int32),
         ("w_fp64_threshold", ctypes.c_double),
         ("r_excise", ctypes.c_double),
         ("w_floor", ctypes.c_double),
@@ -83,6 +83,7 @@ class Params:
     ko_eps: float = 0.1
     dt: float = 0.25 / 24.0
     precision: str = "fp64"
+    ksum_fp64: bool = False
     w_fp64_threshold: float = 0.0
     r_excise: float = 1.0
     w_floor: float = 1e-10
@@ -103,6 +104,7 @@ class Params:
         p.ko_eps = float(self.ko_eps)
         p.dt = float(self.dt)
         p.precision = PRECISION[self.precision]
+        p.ksum_fp64 = 1 if self.ksum_fp64 else 0
         p.w_fp64_threshold = float(self.w_fp64_threshold)
         p.r_excise = float(self.r_excise)
         p.w_floor = float(self.w_floor)

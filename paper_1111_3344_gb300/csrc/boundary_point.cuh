@@ -188,12 +188,16 @@ __device__ __forceinline__ void sommerfeld_point_mixed(const Grid& g, const Stag
   if (a.mode == MODE_RHS) {
     a.rhs[o] = (double)rhs;
   } else if (a.mode == MODE_LAST) {
-    const double v = fma(a.b_dt, (double)(a.ksum[o] + rhs), a.yn[o]);
+    const double ks = a.ksum64 ? a.ksum64[o] + (double)rhs : (double)(a.ksum[o] + rhs);
+    const double v = fma(a.b_dt, ks, a.yn[o]);
     a.yn[o] = v;
     a.out0[o] = (float)(v - background(g, f));
   } else {
     a.out0[o] = fmaf(a.a_dtf, rhs, a.src0[o]);
-    a.ksum[o] = a.mode == MODE_FIRST ? rhs : fmaf(2.0f, rhs, a.ksum[o]);
+    if (a.ksum64)
+      a.ksum64[o] = a.mode == MODE_FIRST ? (double)rhs : fma(2.0, (double)rhs, a.ksum64[o]);
+    else
+      a.ksum[o] = a.mode == MODE_FIRST ? rhs : fmaf(2.0f, rhs, a.ksum[o]);
   }
 }
 
@@ -241,12 +245,16 @@ __device__ __forceinline__ void sommerfeld_point_mixed_fields(const Grid& g, con
     if (a.mode == MODE_RHS) {
       a.rhs[o] = (double)rhs;
     } else if (a.mode == MODE_LAST) {
-      const double v = fma(a.b_dt, (double)(a.ksum[o] + rhs), a.yn[o]);
+      const double ks = a.ksum64 ? a.ksum64[o] + (double)rhs : (double)(a.ksum[o] + rhs);
+      const double v = fma(a.b_dt, ks, a.yn[o]);
       a.yn[o] = v;
       a.out0[o] = (float)(v - background(g, f));
     } else {
       a.out0[o] = fmaf(a.a_dtf, rhs, a.src0[o]);
-      a.ksum[o] = a.mode == MODE_FIRST ? rhs : fmaf(2.0f, rhs, a.ksum[o]);
+      if (a.ksum64)
+        a.ksum64[o] = a.mode == MODE_FIRST ? (double)rhs : fma(2.0, (double)rhs, a.ksum64[o]);
+      else
+        a.ksum[o] = a.mode == MODE_FIRST ? rhs : fmaf(2.0f, rhs, a.ksum[o]);
     }
   }
 }

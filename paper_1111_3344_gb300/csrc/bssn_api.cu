@@ -47,6 +47,10 @@ bool validate(const bssn_params* p, std::string& why) {
     why = "bad precision";
     return false;
   }
+  if (p->ksum_fp64 != 0 && (p->ksum_fp64 != 1 || p->precision != BSSN_MIXED)) {
+    why = "ksum_fp64 must be 0, or 1 with mixed precision";
+    return false;
+  }
   if (!(p->w_fp64_threshold >= 0.0) || !std::isfinite(p->w_fp64_threshold)) {
     why = "w_fp64_threshold must be finite and >= 0";
     return false;
@@ -93,7 +97,7 @@ Grid make_grid(const bssn_params* p) {
 // register of the split stage (135 float fields).
 struct Carve {
   size_t reg, yn, ks, s1, s2, ksh, part, out16, err, trk, total;
-  size_t m32[3], mw[3], ks32, ksw, dr;
+  size_t m32[3], mw[3], ks32, ksw, dr, ks64;
   size_t f2[3];  // double-word path: stage buffers of float2 {hi, lo}
   int nblocks;
 };
@@ -128,6 +132,9 @@ Carve carve(const bssn_params* p, const Grid& g) {
     }
     c.ks32 = o; o += reg32;
     c.ksw = o; o += wb;
+    if (p->ksum_fp64) {  // the k-sum of every field in float64
+      c.ks64 = o; o += regb;
+    }
     c.ksh = o;
     if (p->boundary == BSSN_BC_SOMMERFELD) o += reg32;
     c.dr = o; o += align_up((size_t)split_slot_count() * (size_t)g.fstride * sizeof(float));
@@ -164,6 +171,7 @@ struct bssn_ctx {
   double* ksw;
   float* ksh32;
   float* dr;  // mixed: derivative register of the split stage
+  double* ks64;  // mixed with ksum_fp64: float64 k-sum of every field (else null)
   float2* f2[3];  // double-word path: stage buffers (f2[0]: shadow of y_n)
   float2* kshf;   // double-word path: boundary anchors
   bool shadow_valid;
@@ -305,6 +313,7 @@ bssn_status bssn_alloc(const bssn_params* p, void* d_mem, size_t bytes, void* cu
     ctx->ksw = (double*)(ctx->mem + c.ksw);
     ctx->ksh32 = som ? (float*)(ctx->mem + c.ksh) : nullptr;
     ctx->dr = (float*)(ctx->mem + c.dr);
+    ctx->ks64 = p->ksum_fp64 ? (double*)(ctx->mem + c.ks64) : nullptr;
   }
   ctx->shadow_valid = false;
   ctx->tile = p->precision == BSSN_FF ? ff_cfg_index(0) : 0;
@@ -590,6 +599,7 @@ static bssn_status run_stage_mixed(bssn_ctx* ctx, int src, int mode, int out, do
   a.out0w = ctx->mw[out];
   a.ksum = ctx->ks32;
   a.ksumw = ctx->ksw;
+  a.ksum64 = ctx->ks64;
   a.kshell = ctx->ksh32;
   a.a_dt = a_dt;
   a.a_dtf = (float)a_dt;
@@ -1046,7 +1056,8 @@ bssn_status bssn_autotune(bssn_ctx* ctx, int32_t reps, int32_t* best, double* ms
       StageArgsMixed a{};
       a.src = ctx->m32[q]; a.srcw = ctx->mw[q]; a.src0 = ctx->m32[0]; a.src0w = ctx->mw[0];
       a.yn = ctx->yn; a.out0 = ctx->m32[o]; a.out0w = ctx->mw[o];
-      a.ksum = ctx->ks32; a.ksumw = ctx->ksw; a.a_dt = 0.5 * ctx->p.dt; a.a_dtf = (float)a.a_dt;
+      a.ksum = ctx->ks32; a.ksumw = ctx->ksw; a.ksum64 = ctx->ks64; a.a_dt = 0.5 * ctx->p.dt;
+      a.a_dtf = (float)a.a_dt;
       a.w_thr = ctx->p.w_fp64_threshold; a.mode = second ? MODE_MID : MODE_FIRST;
       if (tma_variant(c) >= 0)
         return launch_stage_mixed_tma(ctx->g, a, ctx->tmap[tma_variant(c)][q], ctx->err, ctx->stream,

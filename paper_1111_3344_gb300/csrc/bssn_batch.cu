@@ -438,6 +438,7 @@ bssn_status bssn_batch_add(bssn_batch* b, const bssn_params* p, int32_t* member)
   std::string why;
   if (!validate_params(p, why)) return bfail(BSSN_EINVAL, why);
   if (p->precision != b->precision) return bfail(BSSN_EINVAL, "member precision differs from the batch's");
+  if (p->ksum_fp64) return bfail(BSSN_EINVAL, "ksum_fp64 is for single-grid contexts");
   int id = -1;
   for (int q = 0; q < b->maxm; q++)
     if (!b->m[q].used) { id = q; break; }

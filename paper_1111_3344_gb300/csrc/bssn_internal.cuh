@@ -210,6 +210,7 @@ struct StageArgsT {
   double* out0w;         // mixed: float64 W of out0 (else null)
   S* ksum;               // k1 + 2 k2 + 2 k3
   double* ksumw;         // mixed: the same for W in float64
+  double* ksum64;        // mixed: if non-null, the k-sum of every field in float64 (ksum unused)
   double* rhs;           // MODE_RHS output (float64 register)
   S* kshell;             // if non-null: k at interior points next to the outer boundary
   double a_dt, b_dt;     // stage coefficients times dt

@@ -100,16 +100,17 @@ __device__ __forceinline__ void stage_point_mixed_acc(const Grid& g, const Stage
   // memory, which comes back from L1.
   float pk[NF], ps[NF];
   double py[NF];
+  const bool ks64 = a.ksum64 != nullptr;  // float64 k-sum of every field (ksum_fp64)
   if (a.mode == MODE_MID) {
 #pragma unroll
     for (int f = 1; f < NF; f++) {
       ps[f] = a.src0[f * fs + id];
-      pk[f] = a.ksum[f * fs + id];
+      if (!ks64) pk[f] = a.ksum[f * fs + id];
     }
   } else if (a.mode == MODE_LAST) {
 #pragma unroll
     for (int f = 1; f < NF; f++) {
-      pk[f] = a.ksum[f * fs + id];
+      if (!ks64) pk[f] = a.ksum[f * fs + id];
       py[f] = a.yn[f * fs + id];
     }
   }
@@ -140,7 +141,7 @@ __device__ __forceinline__ void stage_point_mixed_acc(const Grid& g, const Stage
 #pragma unroll
     for (int f = 1; f < NF; f++) {
       const long long o = f * fs + id;
-      const double v = fma(a.b_dt, (double)(pk[f] + r[f]), py[f]);
+      const double v = fma(a.b_dt, ks64 ? a.ksum64[o] + (double)r[f] : (double)(pk[f] + r[f]), py[f]);
       a.yn[o] = v;
       a.out0[o] = (float)(v - background(g, f));
     }
@@ -157,7 +158,10 @@ __device__ __forceinline__ void stage_point_mixed_acc(const Grid& g, const Stage
   for (int f = 1; f < NF; f++) {
     const long long o = f * fs + id;
     a.out0[o] = fmaf(af, r[f], a.mode == MODE_FIRST ? a.src0[o] : ps[f]);
-    a.ksum[o] = a.mode == MODE_FIRST ? r[f] : fmaf(2.0f, r[f], pk[f]);
+    if (ks64)
+      a.ksum64[o] = a.mode == MODE_FIRST ? (double)r[f] : fma(2.0, (double)r[f], a.ksum64[o]);
+    else
+      a.ksum[o] = a.mode == MODE_FIRST ? r[f] : fmaf(2.0f, r[f], pk[f]);
   }
 }
 

@@ -153,3 +153,38 @@ def test_split_stage_matches_oracle_and_fused(torch_cuda):
         # two RK4 steps: float rounding of different operation orders, the
         # bar of the tile-configuration test
         assert normwise_errors(step, fused_step).max() <= 1e-4, name
+
+
+def test_mixed_float64_ksum_option(torch_cuda):
+    """ksum_fp64 keeps the weighted sum of the k of every field in float64
+    (the other mixed arithmetic unchanged).  Three steps against the float64
+    oracle within the mixed step bar; the k-sum form changes the state by no
+    more than the float rounding of the k that it avoids (dt times float32
+    unit roundoff times |k| per step, below the mixed step bar); and a
+    batch refuses the option."""
+    from paper_1111_3344_gb300 import bssn as B
+    case = dict(BL, precision="mixed", w_fp64_threshold=0.3)
+    cfg = oracle_cfg(case)
+    bg = O.initial_data(cfg, "bl", bl_params(case))
+    st = inputs.random_state(9, case["n"], case["xmin"], case["h"], amp=0.03, background=bg)
+    want = O.rk4(cfg, st, 3)
+    out = {}
+    for ks in (False, True):
+        p = gpu_params(case)
+        p.ksum_fp64 = ks
+        evo = B.Evolution(p)
+        evo.set_state(st, 0.0)
+        evo.rk4_step(3)
+        out[ks] = evo.get_state()[0]
+        evo.close()
+    e = normwise_errors(out[True], want)
+    print("mixed ksum_fp64 3 steps normwise", e.max())
+    assert e.max() <= 5e-4, dict(zip(O.FIELD_NAMES, e))
+    d = normwise_errors(out[True], out[False])
+    assert 0 < d.max() <= 5e-4, d.max()
+    p = gpu_params(case)
+    p.ksum_fp64 = True
+    b = B.Batch("mixed", pool_bytes=B.Batch.member_bytes(gpu_params(case)) + (16 << 20), max_members=2)
+    with pytest.raises(B.BssnError):
+        b.add(p)
+    b.close()

@@ -152,9 +152,11 @@ def test_tile_configs_agree_and_are_deterministic(torch_cuda, precision):
     st = _state_for("bl", case)
     runs = {}
     for cfg in range(B.bssn_tile_count()):
-        if precision == "fp64" and B.bssn_tile_name(cfg).startswith(("tma", "split")):
+        name = B.bssn_tile_name(cfg)
+        if (precision == "fp64" and name.startswith(("tma", "split"))) or name.startswith("ff"):
             evo = _evo(case)
-            with pytest.raises(B.BssnError):  # the TMA-staged and split kernels are mixed-only
+            # the TMA-staged and split kernels are mixed-only, the ff kernels double-word only
+            with pytest.raises(B.BssnError):
                 B.bssn_set_tile(evo.ctx, cfg)
             evo.close()
             continue
