@@ -68,12 +68,13 @@ DPINST_PER_POINT_RHS_ROWS = 1921.1
 # included, as 25-point products, so it is 4.1x the kernels' count: it is
 # reported beside the roofline, not used as its numerator.
 ORACLE_FLOP_PER_POINT_RHS = 5395 + 7874 + 299
-# DRAM bytes (read + write) per interior point of one stage launch, from ncu
-# captures of single launches; None where no capture of the current kernel
-# at the benchmark size exists.
-FP64_TRAFFIC_PER_POINT = 1587.9     # stage_fp64_kernel 64x4x1/1 (capture at 64^3)
-FP64_ROWS_TRAFFIC_PER_POINT = None  # stage_fp64_blocks_kernel 32x4x1/1 at 128^3
-MIXED_TRAFFIC_PER_POINT = None      # stage_mixed_tma_kernel at 128^3
+# DRAM bytes (read + write) per interior point of one stage launch, the mean
+# over the four stages of one RK4 step, from ncu captures of single launches
+# at the benchmark size (128^3; dram__bytes_read.sum + dram__bytes_write.sum);
+# None where no capture of the kernel at that size exists.
+FP64_TRAFFIC_PER_POINT = None       # stage_fp64_kernel (grids with n0 % 32 != 0)
+FP64_ROWS_TRAFFIC_PER_POINT = 954.5  # stage_fp64_blocks_kernel 32x4x1/1: 8006.6 MB per step
+MIXED_TRAFFIC_PER_POINT = 565.3     # stage_mixed_tma_kernel tma32x4x1/2: 4741.9 MB per step
 # Float64 work per interior point of the analysis kernels (DADD + DMUL + 2 DFMA
 # from ncu instruction counts at 96^3).  psi4 and constraints include the
 # ADM-field pass that precedes them (36 flop per stored point, 44 per
