@@ -474,7 +474,7 @@ def extras(args):
         "e2e": mixed["e2e"], "gpu_launches": mixed["stage_launches"] + mixed["boundary_launches"],
         "clocks": mixed["clocks"]}}
     bsteps = max(2, args.steps // 4)
-    out["batched"] = {prec: batched_run(args, prec, steps=bsteps) for prec in ("fp64", "mixed")}
+    out["batched"] = {prec: batched_run(args, prec, steps=bsteps) for prec in ("fp64", "mixed", "ff")}
     torch.cuda.empty_cache()
     out["served_sample"] = served_run(args, "mixed", requests=args.served_sample)
     return out
@@ -533,8 +533,8 @@ def batched_run(args, precision, steps=None, members=None):
     # tiles and the others separately
     tname = list(tile_ms)[best]
     stage_launches = 1
-    if tname.startswith("tiles") and precision == "fp64":
-        tx, ty, tz = (int(v) for v in tname[len("tiles"):].split("/")[0].split("x"))
+    if tname.startswith(("tiles", "fftiles")) and precision in ("fp64", "ff"):
+        tx, ty, tz = (int(v) for v in tname.split("tiles")[1].split("/")[0].split("x"))
         full = [tx == 32 and p.n[0] % 32 == 0 and p.n[1] % ty == 0 and p.n[2] % tz == 0 for p in params]
         stage_launches = int(any(full)) + int(not all(full))
     batch.close()
@@ -542,7 +542,7 @@ def batched_run(args, precision, steps=None, members=None):
     torch.cuda.empty_cache()
     return {"metric": f"batched BSSN RK4 point-updates/s ({precision})",
             "value": pts * steps / (ms * 1e-3) / 1e6, "unit": "Mpoint-updates/s", "steps": steps,
-            "ms_per_step": ms / steps, "dtype": "f64" if precision == "fp64" else "f32+f64",
+            "ms_per_step": ms / steps, "dtype": {"fp64": "f64", "mixed": "f32+f64", "ff": "f32x2+f64"}[precision],
             "workload": f"{len(params)} Brill-Lindquist binaries, grids {{48,64,96,128}}^3, seed 1111, "
                         f"{steps} of the configuration's 100 steps",
             "interior_points": pts, "tile": tname,
@@ -726,6 +726,67 @@ def run_precision(args):
     print(json.dumps(line))
 
 
+def run_precision_batched(args):
+    """The batched workload (64 Brill-Lindquist binaries, seed 1111) advanced
+    args.steps RK4 steps (the configuration's 100) in float64 and in each of
+    args.variants (mixed, ff); for each variant, every member's 16 constraint
+    norms against the same member's float64 norms, the largest relative
+    difference over members (and over the full-domain and the excised norms
+    separately), and the time of the steps (CUDA events) against float64."""
+    import torch
+
+    from paper_1111_3344_gb300 import bssn as B
+    from paper_1111_3344_gb300 import inputs
+    torch.cuda.set_device(0)
+    mems = inputs.binary_bl_batch(seed=1111, count=args.members)
+    variants = [v for v in args.variants.split(",") if v in ("mixed", "ff")]
+    norms, secs, tiles = {}, {}, {}
+    for prec in ["fp64"] + variants:
+        params = [_bl_params(m, prec) for m in mems]
+        batch = _make_batch(B, params, prec)
+        ids = []
+        for m, p in zip(mems, params):
+            mid = batch.add(p)
+            batch.set_initial_data(mid, "bl", [len(m["punctures"])] + [v for q in m["punctures"] for v in q])
+            ids.append(mid)
+        best, tile_ms = batch.autotune(reps=1)
+        # autotuning ran stages 1-2 only (y_n unchanged); start the timed run from t = 0
+        for mid, m in zip(ids, mems):
+            batch.set_initial_data(mid, "bl", [len(m["punctures"])] + [v for q in m["punctures"] for v in q])
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(batch.stream)
+        batch.step(args.steps)
+        e1.record(batch.stream)
+        e1.synchronize()
+        secs[prec] = e0.elapsed_time(e1) * 1e-3
+        tiles[prec] = list(tile_ms)[best]
+        norms[prec] = np.array([batch.constraints(mid) for mid in ids])
+        batch.close()
+        del batch
+        torch.cuda.empty_cache()
+    ref = norms["fp64"]
+    res = {}
+    for prec in variants:
+        rel = np.abs(norms[prec] - ref) / np.where(ref != 0, np.abs(ref), np.inf)
+        res[prec] = {"seconds": secs[prec], "speedup_over_fp64": secs["fp64"] / secs[prec], "tile": tiles[prec],
+                     "max_constraint_norm_rel_diff": float(rel.max()),
+                     "max_rel_diff_full_domain": float(rel[:, :8].max()),
+                     "max_rel_diff_excised": float(rel[:, 8:].max()),
+                     "median_over_members_of_max": float(np.median(rel.max(axis=1))),
+                     "members_within_1e-6": int((rel.max(axis=1) <= 1e-6).sum())}
+    pts = sum(m["n"][0] * m["n"][1] * m["n"][2] for m in mems)
+    line = {"metric": "batched reduced-precision forms vs float64: per-member constraint-norm relative difference, "
+                      "speedup",
+            "workload": f"{len(mems)} Brill-Lindquist binaries, grids {{48,64,96,128}}^3, seed 1111, "
+                        f"{args.steps} RK4 steps each",
+            "members": len(mems), "steps": args.steps, "interior_points": pts,
+            "bar": "constraint norms within 1e-6 relative of the float64 run",
+            "fp64": {"seconds": secs["fp64"], "tile": tiles["fp64"],
+                     "Mpoint_updates_per_s": pts * args.steps / secs["fp64"] / 1e6},
+            "variants": res}
+    print(json.dumps(line))
+
+
 def run_analysis(args):
     """The analysis steps after the evolution on the benchmark puncture:
     Weyl scalar Psi4, ADM mass / angular momentum volume integrals, constraint
@@ -828,7 +889,8 @@ def main():
     ap.add_argument("--precision", choices=["fp64", "mixed", "ff"], default=None,
                     help="default: mixed for the served workload (its configuration), float64 otherwise")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["puncture", "batched", "served", "precision", "analysis"],
+    ap.add_argument("--workload", choices=["puncture", "batched", "served", "precision", "precision_batched",
+                                           "analysis"],
                     default="puncture",
                     help="puncture: the benchmark line (single 128^3 puncture); batched / served: "
                          "the multi-evolution workloads, reported on their own lines")
@@ -861,6 +923,8 @@ def main():
         run_served(args)
     elif args.workload == "precision":
         run_precision(args)
+    elif args.workload == "precision_batched":
+        run_precision_batched(args)
     elif args.workload == "analysis":
         run_analysis(args)
     else:

@@ -78,8 +78,7 @@ enum { BSSN_ID_FLAT = 0, BSSN_ID_GAUGE_WAVE = 1, BSSN_ID_BL = 2, BSSN_ID_KASNER 
  *                      stencils and right-hand side in double-word
  *                      ("float-float", 48-bit) arithmetic on the float32
  *                      pipe, RK4 state, k-sum and reductions in float64
- *                      (single-grid contexts only; batches and the server
- *                      take BSSN_FP64 or BSSN_MIXED).
+ *                      (contexts, batches and the server).
  *  ksum_fp64           mixed precision, single-grid contexts only: 1 keeps
  *                      the weighted sum of the RK4 k of every field in
  *                      float64 (one more float64 register; W's is float64

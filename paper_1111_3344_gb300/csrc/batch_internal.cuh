@@ -16,6 +16,7 @@ struct MemberDev {
   Grid g;
   StageArgs a64[4];
   StageArgsMixed amx[4];
+  StageArgsFF aff[4];  // double-word batches
   int tiles[3];  // stage tiles per axis for the batch's current tile shape
   // mixed: tensor map of each stage's input float buffer (TMA-staged batch
   // kernel); 64-byte aligned, as the tensor loads require
@@ -42,6 +43,7 @@ void batch_tile_shape(int c, int& tx, int& ty, int& tz);
 bool batch_tile_is_tma(int c);
 bool batch_tile_is_per_tile(int c);
 int batch_default_tile(bool mixed);
+int batch_default_tile_ff();
 // Whether a float64 member has full tiles under configuration cfg (n0 a
 // multiple of 32 = the tile's x extent, n1 and n2 of its y and z extents).
 bool batch_tile_full(int cfg, const Grid& g);
@@ -60,5 +62,18 @@ cudaError_t launch_batch_stage_tma(const MemberDev* mem, const BatchWork* wk, in
 // Boundary of every active member after a stage (Sommerfeld or periodic).
 cudaError_t launch_batch_boundary(bool mixed, const MemberDev* mem, const BatchWork* wk, int stage,
                                   cudaStream_t s);
+// Double-word batches (k_batch_ff.cu): one-block-per-tile configurations v in
+// [0, batch_ff_config_count()), their tile shapes, the stage launch over one
+// work list (full: the members with full tiles) and the boundary launch.
+int batch_ff_config_count();
+const char* batch_ff_config_name(int v);
+void batch_ff_tile_shape(int v, int& tx, int& ty, int& tz);
+cudaError_t launch_batch_stage_ff(int v, bool full, const MemberDev* mem, const BatchWork* wk, unsigned ntiles,
+                                  int stage, cudaStream_t s);
+cudaError_t launch_batch_boundary_ff(const MemberDev* mem, const BatchWork* wk, int stage, cudaStream_t s);
+// index of double-word configuration v in the batch's configuration list, and
+// the inverse (-1 for other configurations)
+int batch_ff_cfg_index(int v);
+int batch_ff_variant(int cfg);
 
 }  // namespace bssn

@@ -280,4 +280,46 @@ __device__ __forceinline__ void periodic_point(const Grid& g, S* __restrict__ y,
   if (w) w[d] = w[s];
 }
 
+// Sommerfeld boundary of the double-word path: ghost point q, all fields (the
+// closed form of the layered recursion, as on the float64 path).  The
+// geometry is formed once per point in float64 and rounded to double-word
+// values; the radiative terms run in double-word arithmetic on the stage
+// values; the k-sum and y_n as in the stage kernel.
+__device__ __forceinline__ void sommerfeld_point_ff(const Grid& g, const StageArgsFF& a,
+                                                    const float2* __restrict__ kanchor, unsigned q) {
+  GhostGeo G;
+  ghost_geo(g, q, G);
+  ff nbs[3], nas[3];
+#pragma unroll
+  for (int d = 0; d < 3; d++) {
+    nbs[d] = ff_from_double(G.nbs[d]);
+    nas[d] = ff_from_double(G.nas[d]);
+  }
+  const ff irb = ff_from_double(G.irb), ira = ff_from_double(G.ira), fac = ff_from_double(G.fac);
+  const ff adt(a.a_hi, a.a_lo);
+  const long long fs = g.fstride;
+  const int nf = g.shift == BSSN_SHIFT_FROZEN ? F_BETA : NF;
+  for (int f = 0; f < NF; f++) {
+    ff rhs(0.0f, 0.0f);
+    if (f < nf) {
+      const ff radb = rad_at<ff, float2>(g, a.src + f * fs + G.ib, f, G.I, nbs, irb);
+      const ff rada = rad_at<ff, float2>(g, a.src + f * fs + G.ia, f, G.A, nas, ira);
+      const ff ka = (a.mode == MODE_RHS) ? ff_from_double(a.rhs[f * fs + G.ia]) : ff(kanchor[f * fs + G.ia]);
+      rhs = ff_fma(fac, ka - rada, radb);
+    }
+    const long long o = f * fs + G.ib;
+    if (a.mode == MODE_RHS) {
+      a.rhs[o] = ff_to_double(rhs);
+    } else if (a.mode == MODE_LAST) {
+      const double v = fma(a.b_dt, a.ksum[o] + ff_to_double(rhs), a.yn[o]);
+      a.yn[o] = v;
+      a.out0[o] = ff_from_double(v).f2();
+    } else {
+      a.out0[o] = ff_fma(adt, rhs, ff(a.src0[o])).f2();
+      const double kd = ff_to_double(rhs);
+      a.ksum[o] = a.mode == MODE_FIRST ? kd : fma(2.0, kd, a.ksum[o]);
+    }
+  }
+}
+
 }  // namespace bssn

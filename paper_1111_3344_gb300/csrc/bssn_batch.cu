@@ -80,8 +80,9 @@ struct Pool {
 
 // Register layout of one member inside its pool block.
 struct MemberLayout {
-  size_t yn, ks, s1, s2, ksh;      // float64 path
+  size_t yn, ks, s1, s2, ksh;      // float64 path (ks, ksh also double-word)
   size_t m32[3], mw[3], ks32, ksw; // mixed path
+  size_t f2[3];                    // double-word path: stage buffers (f2[0] the shadow of y_n)
   size_t part, out16, total;
   int nblocks;
 };
@@ -98,6 +99,12 @@ MemberLayout member_layout(const bssn_params* p, const Grid& g) {
     L.ks = o; o += regb;
     L.s1 = o; o += regb;
     L.s2 = o; o += regb;
+    L.ksh = o; if (som) o += regb;
+  } else if (p->precision == BSSN_FF) {
+    L.ks = o; o += regb;
+    for (int q = 0; q < 3; q++) {
+      L.f2[q] = o; o += regb;
+    }
     L.ksh = o; if (som) o += regb;
   } else {
     for (int q = 0; q < 3; q++) {
@@ -188,6 +195,22 @@ void fill_member_dev(bssn_batch* b, int id) {
       a.b_dt = b_dt[s];
       a.mode = mode[s];
     }
+  } else if (b->precision == BSSN_FF) {
+    const int src[4] = {0, 1, 2, 1}, out[4] = {1, 2, 1, 0};
+    for (int s = 0; s < 4; s++) {
+      StageArgsFF& a = D.aff[s];
+      a.src = (const float2*)mptr(b, M, M.L.f2[src[s]]);
+      a.src0 = (const float2*)mptr(b, M, M.L.f2[0]);
+      a.yn = (double*)mptr(b, M, M.L.yn);
+      a.out0 = (float2*)mptr(b, M, M.L.f2[out[s]]);
+      a.ksum = (double*)mptr(b, M, M.L.ks);
+      a.kshell = som ? (float2*)mptr(b, M, M.L.ksh) : nullptr;
+      a.a_dt = a_dt[s];
+      a.b_dt = b_dt[s];
+      a.a_hi = (float)a_dt[s];
+      a.a_lo = (float)(a_dt[s] - (double)a.a_hi);
+      a.mode = mode[s];
+    }
   } else {
     const int src[4] = {0, 1, 2, 1}, out[4] = {1, 2, 1, 0};
     for (int s = 0; s < 4; s++) {
@@ -273,6 +296,15 @@ cudaError_t rebuild_work(bssn_batch* b) {
 // or one over every member (mixed).
 cudaError_t launch_stage_lists(bssn_batch* b, int cfg, int stage) {
   const bool mixed = b->precision == BSSN_MIXED;
+  if (b->precision == BSSN_FF) {
+    const int v = batch_ff_variant(cfg);
+    cudaError_t e = launch_batch_stage_ff(v, true, b->d_mem, b->d_work + WORK_FULL, b->h_work[WORK_FULL].total_tiles,
+                                          stage, b->stream);
+    if (e == cudaSuccess)
+      e = launch_batch_stage_ff(v, false, b->d_mem, b->d_work + WORK_REST, b->h_work[WORK_REST].total_tiles, stage,
+                                b->stream);
+    return e;
+  }
   if (!batch_tile_is_per_tile(cfg) || mixed)
     return launch_batch_stage(cfg, mixed, false, b->d_mem, b->d_work + WORK_ALL, b->h_work[WORK_ALL].total_tiles,
                               stage, b->d_err, b->stream);
@@ -298,7 +330,9 @@ cudaError_t capture(bssn_batch* b) {
   const bool mixed = b->precision == BSSN_MIXED;
   for (int s = 0; s < 4 && e == cudaSuccess; s++) {
     e = launch_stage_lists(b, b->cfg, s);
-    if (e == cudaSuccess) e = launch_batch_boundary(mixed, b->d_mem, b->d_work + WORK_ALL, s, b->stream);
+    if (e == cudaSuccess)
+      e = b->precision == BSSN_FF ? launch_batch_boundary_ff(b->d_mem, b->d_work + WORK_ALL, s, b->stream)
+                                  : launch_batch_boundary(mixed, b->d_mem, b->d_work + WORK_ALL, s, b->stream);
   }
   cudaGraph_t g = nullptr;
   cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
@@ -319,12 +353,15 @@ cudaError_t after_state(bssn_batch* b, Member& M) {
   if (M.g.periodic) e = launch_periodic_fill(M.g, yn, b->stream);
   if (e == cudaSuccess && b->precision == BSSN_MIXED)
     e = launch_shadow(M.g, yn, (float*)mptr(b, M, M.L.m32[0]), (double*)mptr(b, M, M.L.mw[0]), b->stream);
+  if (e == cudaSuccess && b->precision == BSSN_FF)
+    e = launch_shadow_ff(M.g, yn, (float2*)mptr(b, M, M.L.f2[0]), b->stream);
   return e;
 }
 
 bool member_ok(bssn_batch* b, int id) { return b && id >= 0 && id < b->maxm && b->m[id].used; }
 
 bool tile_usable(const bssn_batch* b, int c) {
+  if ((batch_ff_variant(c) >= 0) != (b->precision == BSSN_FF)) return false;
   return !batch_tile_is_tma(c) || (b->precision == BSSN_MIXED && b->tma_ok);
 }
 
@@ -388,7 +425,8 @@ bssn_status bssn_batch_create(int32_t precision, int32_t max_members, void* d_po
                               void* cuda_stream, bssn_batch** out) {
   if (!out) return bfail(BSSN_EINVAL, "out is NULL");
   *out = nullptr;
-  if (precision != BSSN_FP64 && precision != BSSN_MIXED) return bfail(BSSN_EINVAL, "bad precision");
+  if (precision != BSSN_FP64 && precision != BSSN_MIXED && precision != BSSN_FF)
+    return bfail(BSSN_EINVAL, "bad precision");
   if (max_members < 1 || max_members > BATCH_MAX)
     return bfail(BSSN_EINVAL, "max_members must be 1.." + std::to_string(BATCH_MAX));
   if (!d_pool || ((uintptr_t)d_pool) % ALIGN) return bfail(BSSN_EINVAL, "d_pool must be non-NULL, 256-byte aligned");
@@ -409,7 +447,7 @@ bssn_status bssn_batch_create(int32_t precision, int32_t max_members, void* d_po
   b->d_mem = (MemberDev*)b->pool;
   b->d_work = (BatchWork*)(b->pool + aup(sizeof(MemberDev) * (size_t)max_members));
   b->d_err = (int*)((char*)b->d_work + aup(NWORK * sizeof(BatchWork)));
-  b->cfg = batch_default_tile(precision == BSSN_MIXED);
+  b->cfg = precision == BSSN_FF ? batch_default_tile_ff() : batch_default_tile(precision == BSSN_MIXED);
   cudaError_t e = batch_tile_is_tma(b->cfg) ? prepare_batch_stage_tma() : cudaSuccess;
   if (e == cudaSuccess) e = cudaMemsetAsync(b->d_err, 0, sizeof(int), b->stream);
   if (e == cudaSuccess) e = rebuild_work(b);
@@ -608,7 +646,9 @@ bssn_status bssn_batch_set_tile(bssn_batch* b, int32_t cfg) {
   if (!b) return bfail(BSSN_EINVAL, "batch is NULL");
   std::lock_guard<std::mutex> lk(b->mu);
   if (cfg < 0 || cfg >= batch_tile_config_count()) return bfail(BSSN_EINVAL, "tile config out of range");
-  if (!tile_usable(b, cfg)) return bfail(BSSN_EINVAL, "the TMA-staged tile is for mixed batches");
+  if (!tile_usable(b, cfg))
+    return bfail(BSSN_EINVAL, "tile not for this batch's precision (the TMA-staged tile is for mixed batches, "
+                              "the fftiles ones for double-word batches)");
   cudaError_t e = cudaStreamSynchronize(b->stream);
   if (e == cudaSuccess) e = apply_cfg(b, cfg);
   if (e != cudaSuccess) return bcuda(e, "set tile");

@@ -208,19 +208,31 @@ constexpr int N_FUSED = (int)(sizeof(k_bcfg) / sizeof(k_bcfg[0]));
 constexpr int N_TILE = (int)(sizeof(k_tcfg) / sizeof(k_tcfg[0]));
 constexpr int C_TMA = N_FUSED + N_TILE;
 
-int batch_tile_config_count() { return C_TMA + 1; }
+int batch_tile_config_count() { return C_TMA + 1 + batch_ff_config_count(); }
+int batch_ff_cfg_index(int v) { return C_TMA + 1 + v; }
+int batch_ff_variant(int cfg) {
+  const int v = cfg - (C_TMA + 1);
+  return (v >= 0 && v < batch_ff_config_count()) ? v : -1;
+}
 // Default tile of a new batch (the serving loop keeps it): the fastest
 // persistent configuration of the 64-binary batched workload on GB300 -- the
 // TMA-staged kernel for mixed batches, 32x4x1/3 for float64 ones.
 int batch_default_tile(bool mixed) { return mixed ? C_TMA : 2; }
+// double-word batches: the 64-register one-block-per-tile configuration
+int batch_default_tile_ff() { return batch_ff_cfg_index(0); }
 bool batch_tile_is_tma(int c) { return c == C_TMA; }
-bool batch_tile_is_per_tile(int c) { return c >= N_FUSED && c < C_TMA; }
+bool batch_tile_is_per_tile(int c) { return (c >= N_FUSED && c < C_TMA) || batch_ff_variant(c) >= 0; }
 const char* batch_tile_config_name(int c) {
+  if (batch_ff_variant(c) >= 0) return batch_ff_config_name(batch_ff_variant(c));
   if (c == C_TMA) return "tma32x4x1/2";
   if (batch_tile_is_per_tile(c)) return k_tcfg[c - N_FUSED].name;
   return (c >= 0 && c < N_FUSED) ? k_bcfg[c].name : "";
 }
 void batch_tile_shape(int c, int& tx, int& ty, int& tz) {
+  if (batch_ff_variant(c) >= 0) {
+    batch_ff_tile_shape(batch_ff_variant(c), tx, ty, tz);
+    return;
+  }
   if (c == C_TMA) {
     batch_tma_tile_shape(tx, ty, tz);
     return;
@@ -247,7 +259,7 @@ bool batch_tile_full(int cfg, const Grid& g) {
 cudaError_t launch_batch_stage(int cfg, bool mixed, bool full, const MemberDev* mem, const BatchWork* wk,
                                unsigned ntiles, int stage, int* err, cudaStream_t s) {
   if (cfg == C_TMA && mixed) return launch_batch_stage_tma(mem, wk, stage, err, s);
-  if (batch_tile_is_per_tile(cfg)) {
+  if (batch_tile_is_per_tile(cfg) && batch_ff_variant(cfg) < 0) {
     const TileCfgB& c = k_tcfg[cfg - N_FUSED];
     if (ntiles == 0) return cudaSuccess;
     full = full && !mixed;

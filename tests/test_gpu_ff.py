@@ -147,3 +147,99 @@ def test_ff_async_copies_match_synchronous(torch_cuda):
     for s in range(2):
         assert np.array_equal(host[s], outs[s])
     evo.close()
+
+
+def _ff_member(n, xmin, punct, boundary="sommerfeld"):
+    return dict(n=n, xmin=xmin, h=0.2, boundary=boundary, conformal="W", slicing="1+log",
+                shift="gamma-driver", eta=2.0, punctures=punct, precision="ff")
+
+
+def test_ff_batch_matches_single_grid_bit_for_bit(torch_cuda):
+    """A double-word batch runs the single-grid double-word point functions, so
+    each member's state after its steps is the same, bit for bit, alone in a
+    batch, in the mix with others, and through a bssn_ctx: the full-tile member
+    (n0 a multiple of 32, n1 of 4) against the full-row configuration of the
+    same register cap, the ragged one against the every-stencil configuration.
+    The full-tile member is also checked against the oracle (three steps)."""
+    from paper_1111_3344_gb300 import bssn as B
+    full = _ff_member((32, 16, 20), (-3.2, -1.6, -2.0), [(0.8, 0.1, 0.0, 0.0)])
+    ragged = _ff_member((33, 17, 21), (-3.3, -1.7, -2.1), [(0.6, 0.2, 0.1, 0.0)])
+    per = _ff_member((16, 12, 20), (0.0, 0.0, 0.0), [], boundary="periodic")
+    cases = [full, ragged, per]
+    states = []
+    for c in cases:
+        if c["punctures"]:
+            cfg = oracle_cfg(c)
+            bg = O.initial_data(cfg, "bl", bl_params(c))
+            states.append(inputs.random_state(17, c["n"], c["xmin"], c["h"], amp=0.03, background=bg))
+        else:
+            states.append(O.fill_periodic(oracle_cfg(c), inputs.random_state(5, c["n"], c["xmin"], c["h"],
+                                                                            amp=0.05)))
+    params = [gpu_params(c) for c in cases]
+    lib = B.load()
+    bnames = [lib.bssn_batch_tile_name(i).decode() for i in range(lib.bssn_batch_tile_count())]
+
+    def run(idx):
+        b = B.Batch("ff", pool_bytes=sum(B.Batch.member_bytes(params[i]) for i in idx) + (16 << 20),
+                    max_members=4)
+        b.set_tile(bnames.index("fftiles32x4x1/8"))
+        ids = [b.add(params[i]) for i in idx]
+        for m, i in zip(ids, idx):
+            b.set_state(m, states[i], 0.0)
+        b.step(3)
+        out = {i: b.get_state(m)[0] for m, i in zip(ids, idx)}
+        b.close()
+        return out
+
+    mix = run([0, 1, 2])
+    for i in range(3):
+        assert np.array_equal(run([i])[i], mix[i]), i
+    names = [B.bssn_tile_name(c) for c in range(B.bssn_tile_count())]
+    for i, tile in ((0, "ffrows32x4x1/8"), (1, "ff32x4x1/1")):
+        evo = _evo(cases[i])
+        B.bssn_set_tile(evo.ctx, names.index(tile))
+        evo.set_state(states[i], 0.0)
+        evo.rk4_step(3)
+        assert np.array_equal(evo.get_state()[0], mix[i]), i
+        evo.close()
+    e = normwise_errors(mix[0], O.rk4(oracle_cfg(full), states[0], 3))
+    assert e.max() <= TOL_STEP, dict(zip(O.FIELD_NAMES, e))
+    # float64 and mixed configurations are refused on a double-word batch
+    b = B.Batch("ff", pool_bytes=B.Batch.member_bytes(params[0]) + (16 << 20), max_members=2)
+    with pytest.raises(B.BssnError):
+        b.set_tile(bnames.index("tma32x4x1/2"))
+    b.close()
+
+
+def test_ff_server_same_alone_and_in_the_mix(torch_cuda):
+    """The continuous-batching server in double-word precision: requests give the
+    same constraint norms, bit for bit, alone and admitted while others run."""
+    import time
+    from paper_1111_3344_gb300.bssn import Params, Server
+
+    def req(n):
+        L = 4.0
+        h = 2 * L / n
+        return Params(n=(n, n, n), xmin=(-L,) * 3, h=h, boundary="sommerfeld", conformal="W",
+                      dt=0.25 * h, precision="ff", r_excise=0.5)
+
+    reqs = [(24, [1, 0.5, 0.3, 0.0, 0.0], 6), (32, [2, 0.6, 1.0, 0.0, 0.0, 0.4, -1.5, 0.0, 0.0], 4),
+            (20, [1, 1.0, 0.0, 0.0, 0.0], 8)]
+    alone = {}
+    for i, (n, p, steps) in enumerate(reqs):
+        s = Server("ff", budget_bytes=1 << 28)
+        st, norms, _ = s.wait(s.submit(req(n), "bl", p, steps))
+        assert st == 0
+        alone[i] = norms
+        s.close()
+    s = Server("ff", budget_bytes=1 << 29)
+    long_t = s.submit(req(24), "bl", reqs[0][1], 200)
+    t0 = time.time()
+    while s.stats()["resident"] < 1 and time.time() - t0 < 30:
+        time.sleep(0.001)
+    tickets = [s.submit(req(n), "bl", p, steps) for (n, p, steps) in reqs]
+    for i, t in enumerate(tickets):
+        st, norms, _ = s.wait(t)
+        assert st == 0 and np.array_equal(norms, alone[i]), i
+    assert s.wait(long_t)[0] == 0
+    s.close()
