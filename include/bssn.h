@@ -304,7 +304,7 @@ bssn_status bssn_set_staging(bssn_ctx* ctx, void* d_mem, size_t bytes);
 
 /* Stage-kernel tile configurations: block shape (points along x, y, z) and the
  * minimum resident blocks per SM given to the compiler.  The last ones are for
- * the mixed path only: "tma32x4x1/2" and "tma32x8x1/1" stage the
+ * the mixed path only: "tma32x4x1/2", "tma32x8x1/1" and "tma32x4x2/1" stage the
  * second-differenced fields of each tile in shared memory by TMA (two blocks
  * of 32x4 points per SM, or one block of 32x8 points per SM, which leaves more
  * L1 for the other fields); "split32x4x1/B" (B = 2, 3, 4) run the stencils as one

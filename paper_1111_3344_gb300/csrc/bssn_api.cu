@@ -176,7 +176,7 @@ struct bssn_ctx {
   float2* kshf;   // double-word path: boundary anchors
   bool shadow_valid;
   int tile;  // stage-kernel tile configuration (see bssn_autotune)
-  CUtensorMap tmap[2][3];  // mixed: tensor maps of the float stage buffers, per TMA variant
+  CUtensorMap tmap[3][3];  // mixed: tensor maps of the float stage buffers, per TMA variant
   bool tmap_ok;
   int* err;             // device error word (bounded waits that gave up)
   int stall_polls;      // test hook of the TMA-staged kernels (bssn_test_stall_tma)
@@ -211,8 +211,9 @@ struct bssn_ctx {
 
 // Tile configuration indices: [0, tile_config_count()) fused kernels, then
 // N_TMA TMA-staged mixed kernels (variant 0: 32x4x1, two blocks per SM;
-// 1: 32x8x1, one block per SM), then the split-stage variants.
-constexpr int N_TMA = 2;
+// 1: 32x8x1, one block per SM; 2: 32x4x2, one block per SM), then the
+// split-stage variants.
+constexpr int N_TMA = 3;
 static int tma_variant(int cfg) {
   const int v = cfg - tile_config_count();
   return (v >= 0 && v < N_TMA) ? v : -1;
@@ -330,7 +331,7 @@ bssn_status bssn_alloc(const bssn_params* p, void* d_mem, size_t bytes, void* cu
   ctx->tmap_ok = false;
   if (p->precision == BSSN_MIXED) {
     bool ok = true;
-    for (int v = 0; v < 2 && ok; v++)
+    for (int v = 0; v < N_TMA && ok; v++)
       for (int q = 0; q < 3 && ok; q++) ok = make_stage_tensor_map(g, ctx->m32[q], &ctx->tmap[v][q], v) == cudaSuccess;
     ctx->tmap_ok = ok;
   }
@@ -984,6 +985,7 @@ const char* bssn_tile_name(int32_t cfg) {
   if (ff_variant(cfg) >= 0) return ff_config_name(ff_variant(cfg));
   if (tma_variant(cfg) == 0) return "tma32x4x1/2";
   if (tma_variant(cfg) == 1) return "tma32x8x1/1";
+  if (tma_variant(cfg) == 2) return "tma32x4x2/1";
   if (split_variant(cfg) >= 0) return split_config_name(split_variant(cfg));
   return tile_config_name(cfg);
 }
@@ -991,6 +993,7 @@ const char* bssn_tile_name(int32_t cfg) {
 static bool tile_usable(const bssn_ctx* ctx, int cfg) {
   if (cfg < 0 || cfg >= bssn_tile_count()) return false;
   if ((ff_variant(cfg) >= 0) != (ctx->p.precision == BSSN_FF)) return false;
+  if (cfg < tile_config_count() && ctx->p.precision == BSSN_FP64 && !tile_config_has_fp64(cfg)) return false;
   if (tma_variant(cfg) >= 0) return ctx->p.precision == BSSN_MIXED && ctx->tmap_ok;
   if (split_variant(cfg) >= 0) return ctx->p.precision == BSSN_MIXED;
   return true;

@@ -253,6 +253,7 @@ struct Punct {
 cudaError_t launch_stage_fp64(const Grid& g, const StageArgs& a, cudaStream_t s, int cfg = 0);
 cudaError_t launch_stage_mixed(const Grid& g, const StageArgsMixed& a, cudaStream_t s, int cfg = 0);
 int tile_config_count();
+bool tile_config_has_fp64(int c);  // false for the mixed-only configurations
 const char* tile_config_name(int c);
 // TMA-staged mixed stage kernel (k_stage_tma.cu); map describes the float
 // stage buffer that is the stencil source.

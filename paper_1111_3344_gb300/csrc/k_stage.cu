@@ -87,20 +87,27 @@ struct TileCfg {
 #define TILE_ROWS(TY, TZ, MINB)                                                 \
   { "32x" #TY "x" #TZ "/" #MINB, launch_fp64_t<32, TY, TZ, MINB>,              \
     launch_mixed_t<32, TY, TZ, MINB>, launch_fp64_rows<TY, TZ, MINB> }
+// mixed only: registers capped for four or six resident blocks per SM (more
+// warps to cover the load latency, more spills)
+#define TILE_MX(TX, TY, TZ, MINB) \
+  { #TX "x" #TY "x" #TZ "/" #MINB, nullptr, launch_mixed_t<TX, TY, TZ, MINB>, nullptr }
 static const TileCfg k_tiles[] = {
     TILE_ROWS(8, 1, 1), TILE_ROWS(4, 1, 1), TILE_ROWS(4, 2, 1), TILE(64, 4, 1, 1),
     TILE(16, 8, 2, 1), TILE_ROWS(2, 2, 2), TILE(32, 8, 1, 2), TILE(32, 4, 1, 3),
+    TILE_MX(32, 4, 1, 4), TILE_MX(32, 4, 1, 6),
 };
+#undef TILE_MX
 #undef TILE
 #undef TILE_ROWS
 
 int tile_config_count() { return (int)(sizeof(k_tiles) / sizeof(k_tiles[0])); }
+bool tile_config_has_fp64(int c) { return c >= 0 && c < tile_config_count() && k_tiles[c].fp64 != nullptr; }
 const char* tile_config_name(int c) {
   return (c >= 0 && c < tile_config_count()) ? k_tiles[c].name : "";
 }
 
 cudaError_t launch_stage_fp64(const Grid& g, const StageArgs& a, cudaStream_t s, int cfg) {
-  if (cfg < 0 || cfg >= tile_config_count()) cfg = 0;
+  if (!tile_config_has_fp64(cfg)) cfg = 0;
   if (k_tiles[cfg].fp64_rows && g.n0 % 32 == 0) return k_tiles[cfg].fp64_rows(g, a, s);
   return k_tiles[cfg].fp64(g, a, s);
 }

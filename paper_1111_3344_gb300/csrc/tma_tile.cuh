@@ -18,12 +18,13 @@ namespace bssn {
 constexpr int NSTAGED = 8;
 constexpr long long WAIT_LIMIT = 1LL << 24;
 
-// Tile of 32 x TY x 1 interior points and its boxes: BX = 32 + 6 rounded up
-// to a multiple of 4 floats, BY = TY + 6, BZ = 7 (three ghost layers on every
-// side); slots of the staged fields 128-byte aligned.
-template <int TY_>
+// Tile of 32 x TY x TZ interior points and its boxes: BX = 32 + 6 rounded up
+// to a multiple of 4 floats, BY = TY + 6, BZ = TZ + 6 (three ghost layers on
+// every side); slots of the staged fields 128-byte aligned.  A thicker tile
+// (TZ = 2) stages 8 planes for 2 planes of points instead of 7 for 1.
+template <int TY_, int TZ_ = 1>
 struct TmaShape {
-  static constexpr int TX = 32, TY = TY_, TZ = 1;
+  static constexpr int TX = 32, TY = TY_, TZ = TZ_;
   static constexpr int BX = 40, BY = TY + 2 * GH, BZ = TZ + 2 * GH;
   static constexpr int BOX = BX * BY * BZ;                              // floats of one field's box
   static constexpr int SLOT = (BOX + 31) / 32 * 32;                     // slot stride
