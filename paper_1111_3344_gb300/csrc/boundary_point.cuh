@@ -103,7 +103,95 @@ __device__ __forceinline__ void ghost_geo(const Grid& g, unsigned q, GhostGeo& G
   G.ia = lin(g, G.A[0], G.A[1], G.A[2]);
 }
 
-// float64 path: ghost point q, all fields.
+// Geometry table of the float64 Sommerfeld boundary, one entry per ghost
+// point q (formed once per context by ghost_geo, so the same values): the
+// stored indices packed in 21 bits each, and nbs[3], irb, fac.
+constexpr int GEO_DOUBLES = 5;
+__host__ __device__ inline size_t ghost_table_bytes(const Grid& g) {
+  return (size_t)ghost_count(g) * (GEO_DOUBLES * sizeof(double) + sizeof(long long));
+}
+__device__ __forceinline__ void ghost_table_fill(const Grid& g, unsigned q, double* __restrict__ tab,
+                                                 long long* __restrict__ itab) {
+  GhostGeo G;
+  ghost_geo(g, q, G);
+  const size_t n = ghost_count(g);
+  tab[0 * n + q] = G.nbs[0];
+  tab[1 * n + q] = G.nbs[1];
+  tab[2 * n + q] = G.nbs[2];
+  tab[3 * n + q] = G.irb;
+  tab[4 * n + q] = G.fac;
+  itab[q] = (long long)G.I[0] | ((long long)G.I[1] << 21) | ((long long)G.I[2] << 42);
+}
+
+// float64 path from the table, after the anchor pass: ghost point q, fields
+// [F0, F1) (a group of the 24 per thread, their loads in flight together).
+template <int F0, int F1>
+__device__ __forceinline__ void sommerfeld_point_fp64_tab(const Grid& g, const StageArgs& a,
+                                                          const double* __restrict__ kanchor,
+                                                          const double* __restrict__ tab,
+                                                          const long long* __restrict__ itab, unsigned q) {
+  const size_t n = ghost_count(g);
+  const long long pk = itab[q];
+  const int I[3] = {(int)(pk & 0x1fffff), (int)((pk >> 21) & 0x1fffff), (int)((pk >> 42) & 0x1fffff)};
+  const int nn[3] = {g.n0, g.n1, g.n2};
+  int A[3];
+#pragma unroll
+  for (int d = 0; d < 3; d++) A[d] = I[d] < GH ? GH : (I[d] >= GH + nn[d] ? GH + nn[d] - 1 : I[d]);
+  const double nbs[3] = {tab[q], tab[n + q], tab[2 * n + q]};
+  const double irb = tab[3 * n + q], fac = tab[4 * n + q];
+  const long long ib = lin(g, I[0], I[1], I[2]), ia = lin(g, A[0], A[1], A[2]);
+  const long long fs = g.fstride;
+  const int nf = g.shift == BSSN_SHIFT_FROZEN ? F_BETA : NF;
+#pragma unroll
+  for (int f = F0; f < F1; f++) {
+    double rhs = 0.0;
+    if (f < nf) {
+      const double radb = rad_at<double, double>(g, a.src + f * fs + ib, f, I, nbs, irb);
+      rhs = fma(fac, kanchor[f * fs + ia], radb);
+    }
+    const long long o = f * fs + ib;
+    if (a.mode == MODE_LAST) {
+      a.yn[o] = fma(a.b_dt, a.ksum[o] + rhs, a.yn[o]);
+    } else {
+      a.out0[o] = fma(a.a_dt, rhs, a.src0[o]);
+      a.ksum[o] = a.mode == MODE_FIRST ? rhs : fma(2.0, rhs, a.ksum[o]);
+    }
+  }
+}
+
+// float64 path, anchor pass: interior point q of the boundary shell, fields
+// [F0, F1): k - rad at the anchor, in place of the k the stage kernel left in
+// kanchor (the same operations the ghost points of that anchor would repeat,
+// one to three layers and up to eight neighbours over; see sommerfeld_point_fp64).
+template <int F0 = 0, int F1 = NF>
+__device__ __forceinline__ void sommerfeld_anchor_fp64(const Grid& g, const StageArgs& a,
+                                                       double* __restrict__ kanchor, unsigned q) {
+  int ii, jj, kk;
+  shell_decode(g, q, ii, jj, kk);
+  const int A[3] = {ii + GH, jj + GH, kk + GH};
+  double xa[3];
+#pragma unroll
+  for (int d = 0; d < 3; d++) xa[d] = coordv(g, d, A[d]);
+  // as ghost_geo forms the anchor's factors
+  const double ra = sqrt(xa[0] * xa[0] + xa[1] * xa[1] + xa[2] * xa[2]);
+  const double ira = 1.0 / ra;
+  double nas[3];
+#pragma unroll
+  for (int d = 0; d < 3; d++) nas[d] = (xa[d] * ira) * g.i2h;
+  const long long ia = lin(g, A[0], A[1], A[2]);
+  const long long fs = g.fstride;
+  const int nf = g.shift == BSSN_SHIFT_FROZEN ? F_BETA : NF;
+#pragma unroll
+  for (int f = F0; f < F1; f++) {
+    if (f >= nf) break;
+    const double rada = rad_at<double, double>(g, a.src + f * fs + ia, f, A, nas, ira);
+    kanchor[f * fs + ia] -= rada;
+  }
+}
+
+// float64 path: ghost point q, all fields.  PRE: kanchor already holds
+// k - rad at the anchor (the anchor pass ran), else k itself.
+template <bool PRE = false>
 __device__ __forceinline__ void sommerfeld_point_fp64(const Grid& g, const StageArgs& a,
                                                       const double* __restrict__ kanchor, unsigned q) {
   GhostGeo G;
@@ -114,9 +202,13 @@ __device__ __forceinline__ void sommerfeld_point_fp64(const Grid& g, const Stage
     double rhs = 0.0;
     if (f < nf) {
       const double radb = rad_at<double, double>(g, a.src + f * fs + G.ib, f, G.I, G.nbs, G.irb);
-      const double rada = rad_at<double, double>(g, a.src + f * fs + G.ia, f, G.A, G.nas, G.ira);
-      const double ka = (a.mode == MODE_RHS) ? a.rhs[f * fs + G.ia] : kanchor[f * fs + G.ia];
-      rhs = fma(G.fac, ka - rada, radb);
+      if (PRE && a.mode != MODE_RHS) {
+        rhs = fma(G.fac, kanchor[f * fs + G.ia], radb);
+      } else {
+        const double rada = rad_at<double, double>(g, a.src + f * fs + G.ia, f, G.A, G.nas, G.ira);
+        const double ka = (a.mode == MODE_RHS) ? a.rhs[f * fs + G.ia] : kanchor[f * fs + G.ia];
+        rhs = fma(G.fac, ka - rada, radb);
+      }
     }
     const long long o = f * fs + G.ib;
     if (a.mode == MODE_RHS) {

@@ -96,7 +96,7 @@ Grid make_grid(const bssn_params* p) {
 // array; the float k-sum with its float64 W; float anchors; the derivative
 // register of the split stage (135 float fields).
 struct Carve {
-  size_t reg, yn, ks, s1, s2, ksh, part, out16, err, trk, total;
+  size_t reg, yn, ks, s1, s2, ksh, part, out16, err, trk, total, gtab;
   size_t m32[3], mw[3], ks32, ksw, dr, ks64;
   size_t f2[3];  // double-word path: stage buffers of float2 {hi, lo}
   int nblocks;
@@ -115,7 +115,11 @@ Carve carve(const bssn_params* p, const Grid& g) {
     c.s1 = o; o += regb;
     c.s2 = o; o += regb;
     c.ksh = o;
-    if (p->boundary == BSSN_BC_SOMMERFELD) o += regb;
+    if (p->boundary == BSSN_BC_SOMMERFELD) {
+      o += regb;
+      c.gtab = o;  // ghost-point geometry of the Sommerfeld boundary
+      o += align_up(ghost_table_size(g));
+    }
   } else if (p->precision == BSSN_FF) {
     // y_n and the k-sum in float64; three double-word stage buffers (s0 the
     // shadow of y_n), each the size of a float64 register; double-word anchors
@@ -165,6 +169,7 @@ struct bssn_ctx {
   double* s1;
   double* s2;
   double* ksh;
+  void* gtab;  // float64 Sommerfeld: ghost-point geometry table (null otherwise)
   float* m32[3];
   double* mw[3];
   float* ks32;
@@ -300,8 +305,10 @@ bssn_status bssn_alloc(const bssn_params* p, void* d_mem, size_t bytes, void* cu
   ctx->s1 = p->precision == BSSN_FP64 ? (double*)(ctx->mem + c.s1) : nullptr;
   ctx->s2 = p->precision == BSSN_FP64 ? (double*)(ctx->mem + c.s2) : nullptr;
   const bool som = p->boundary == BSSN_BC_SOMMERFELD;
+  ctx->gtab = nullptr;
   if (p->precision == BSSN_FP64) {
     ctx->ksh = som ? (double*)(ctx->mem + c.ksh) : nullptr;
+    ctx->gtab = som ? (void*)(ctx->mem + c.gtab) : nullptr;
   } else if (p->precision == BSSN_FF) {
     for (int q = 0; q < 3; q++) ctx->f2[q] = (float2*)(ctx->mem + c.f2[q]);
     ctx->kshf = som ? (float2*)(ctx->mem + c.ksh) : nullptr;
@@ -347,7 +354,8 @@ bssn_status bssn_alloc(const bssn_params* p, void* d_mem, size_t bytes, void* cu
       cudaEventCreateWithFlags(&ctx->ev_in_ready, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&ctx->ev_in_free, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&ctx->ev_out_free, cudaEventDisableTiming) != cudaSuccess ||
-      cudaMemsetAsync(ctx->err, 0, sizeof(int), ctx->stream) != cudaSuccess) {
+      cudaMemsetAsync(ctx->err, 0, sizeof(int), ctx->stream) != cudaSuccess ||
+      (ctx->gtab && launch_ghost_table(g, ctx->gtab, ctx->stream) != cudaSuccess)) {
     for (cudaEvent_t ev : {ctx->ev_out_ready, ctx->ev_out_done, ctx->ev_in_ready, ctx->ev_in_free, ctx->ev_out_free})
       if (ev) cudaEventDestroy(ev);
     if (ctx->cstream) cudaStreamDestroy(ctx->cstream);
@@ -580,7 +588,7 @@ static bssn_status run_stage(bssn_ctx* ctx, const double* src, int mode, double*
   if (ctx->g.periodic) {
     e = launch_periodic_fill(ctx->g, mode == MODE_LAST ? ctx->yn : out0, ctx->stream);
   } else {
-    e = launch_sommerfeld(ctx->g, a, ctx->ksh, ctx->stream);
+    e = launch_sommerfeld(ctx->g, a, ctx->ksh, ctx->stream, ctx->gtab);
   }
   if (e != cudaSuccess) return cuda_fail(e, "boundary");
   if (ctx->prof && (e = prof_mark(ctx, ctx->ev_bc)) != cudaSuccess) return cuda_fail(e, "profile");

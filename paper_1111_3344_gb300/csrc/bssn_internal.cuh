@@ -179,6 +179,38 @@ __host__ __device__ inline void ghost_decode(const Grid& g, unsigned q, int& i, 
   }
 }
 
+// Interior points next to the outer boundary (the anchors of the Sommerfeld
+// closed form), enumerated: the bottom and top interior z-planes, then per
+// interior z-plane its first and last interior rows, then the first and last
+// point of every other row.  Interior indices (0 .. n-1).
+__host__ __device__ inline unsigned shell_count(const Grid& g) {
+  if (g.n2 < 2) return (unsigned)g.n0 * g.n1 * g.n2;
+  const unsigned per = (g.n1 < 2) ? (unsigned)g.n0 : 2u * g.n0 + 2u * (g.n1 - 2);
+  return 2u * g.n0 * g.n1 + (unsigned)(g.n2 - 2) * per;
+}
+__host__ __device__ inline void shell_decode(const Grid& g, unsigned q, int& ii, int& jj, int& kk) {
+  const unsigned pl = (unsigned)g.n0 * g.n1;
+  if (q < 2u * pl) {
+    kk = q < pl ? 0 : g.n2 - 1;
+    const unsigned r = q % pl;
+    jj = (int)(r / g.n0);
+    ii = (int)(r % g.n0);
+    return;
+  }
+  const unsigned per = 2u * g.n0 + 2u * (g.n1 - 2);
+  const unsigned q2 = q - 2u * pl;
+  kk = 1 + (int)(q2 / per);
+  unsigned r = q2 % per;
+  if (r < 2u * g.n0) {
+    jj = r < (unsigned)g.n0 ? 0 : g.n1 - 1;
+    ii = (int)(r % g.n0);
+  } else {
+    r -= 2u * g.n0;
+    jj = 1 + (int)(r / 2u);
+    ii = (r & 1u) ? g.n0 - 1 : 0;
+  }
+}
+
 // RK4 stage combination modes of the fused stage kernel.  Classical RK4 as
 //   y_{n+1} = y_n + dt/6 (k1 + 2 k2 + 2 k3 + k4),
 // with y_n advanced in place once per step and the weighted sum of the k kept
@@ -270,8 +302,11 @@ int split_config_count();
 const char* split_config_name(int v);
 cudaError_t launch_stage_mixed_split(const Grid& g, const StageArgsMixed& a, float* dr, cudaStream_t s,
                                      int variant);
+// table (may be null): the context's ghost-geometry table (launch_ghost_table)
 cudaError_t launch_sommerfeld(const Grid& g, const StageArgs& a, const double* kanchor,
-                              cudaStream_t s);
+                              cudaStream_t s, const void* table = nullptr);
+size_t ghost_table_size(const Grid& g);
+cudaError_t launch_ghost_table(const Grid& g, void* table, cudaStream_t s);
 cudaError_t launch_sommerfeld_mixed(const Grid& g, const StageArgsMixed& a, const float* kanchor,
                                     cudaStream_t s);
 cudaError_t launch_periodic_fill(const Grid& g, double* y, cudaStream_t s);

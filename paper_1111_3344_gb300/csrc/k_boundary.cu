@@ -18,11 +18,54 @@
 
 namespace bssn {
 
+template <bool PRE>
 __global__ void sommerfeld_fp64_kernel(Grid g, StageArgs a, const double* __restrict__ kanchor) {
   const unsigned q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= ghost_count(g)) return;
-  sommerfeld_point_fp64(g, a, kanchor, q);
+  sommerfeld_point_fp64<PRE>(g, a, kanchor, q);
 }
+
+// blockIdx.y: one of four field groups (W and gt_ij; K and At_ij but its last;
+// the rest of At_ij, Gt^i, alpha; beta^i and B^i)
+__global__ void sommerfeld_anchor_fp64_kernel(Grid g, StageArgs a, double* __restrict__ kanchor) {
+  const unsigned q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= shell_count(g)) return;
+  switch (blockIdx.y) {
+    case 0: sommerfeld_anchor_fp64<0, 7>(g, a, kanchor, q); break;
+    case 1: sommerfeld_anchor_fp64<7, 13>(g, a, kanchor, q); break;
+    case 2: sommerfeld_anchor_fp64<13, 18>(g, a, kanchor, q); break;
+    default: sommerfeld_anchor_fp64<18, NF>(g, a, kanchor, q); break;
+  }
+}
+
+__global__ void sommerfeld_fp64_tab_kernel(Grid g, StageArgs a, const double* __restrict__ kanchor,
+                                           const double* __restrict__ tab, const long long* __restrict__ itab) {
+  const unsigned q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= ghost_count(g)) return;
+  switch (blockIdx.y) {  // six groups of four fields
+    case 0: sommerfeld_point_fp64_tab<0, 4>(g, a, kanchor, tab, itab, q); break;
+    case 1: sommerfeld_point_fp64_tab<4, 8>(g, a, kanchor, tab, itab, q); break;
+    case 2: sommerfeld_point_fp64_tab<8, 12>(g, a, kanchor, tab, itab, q); break;
+    case 3: sommerfeld_point_fp64_tab<12, 16>(g, a, kanchor, tab, itab, q); break;
+    case 4: sommerfeld_point_fp64_tab<16, 20>(g, a, kanchor, tab, itab, q); break;
+    default: sommerfeld_point_fp64_tab<20, NF>(g, a, kanchor, tab, itab, q); break;
+  }
+}
+
+__global__ void ghost_table_kernel(Grid g, double* __restrict__ tab, long long* __restrict__ itab) {
+  const unsigned q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= ghost_count(g)) return;
+  ghost_table_fill(g, q, tab, itab);
+}
+
+cudaError_t launch_ghost_table(const Grid& g, void* table, cudaStream_t s) {
+  const unsigned total = ghost_count(g);
+  double* tab = (double*)table;
+  long long* itab = (long long*)(tab + (size_t)GEO_DOUBLES * total);
+  ghost_table_kernel<<<(total + 127) / 128, 128, 0, s>>>(g, tab, itab);
+  return cudaGetLastError();
+}
+size_t ghost_table_size(const Grid& g) { return ghost_table_bytes(g); }
 
 // one thread per ghost point, every field (geometry formed once)
 // mixed: blockIdx.y picks one of four field groups (W and gt_ij; K and
@@ -47,11 +90,26 @@ __global__ void periodic_fill_kernel(Grid g, S* __restrict__ y, double* __restri
   periodic_point<S>(g, y, w, q);
 }
 
+// Stage modes: the anchor pass (one thread per shell point) turns the k left at
+// the anchors into k - rad once, then the ghost points each form only their
+// own radiative term.  MODE_RHS (no anchors): every ghost point forms both.
 cudaError_t launch_sommerfeld(const Grid& g, const StageArgs& a, const double* kanchor,
-                              cudaStream_t s) {
+                              cudaStream_t s, const void* table) {
   const unsigned total = ghost_count(g);
   const int bs = 128;
-  sommerfeld_fp64_kernel<<<(total + bs - 1) / bs, bs, 0, s>>>(g, a, kanchor);
+  if (a.mode != MODE_RHS && kanchor) {
+    const unsigned ns = shell_count(g);
+    sommerfeld_anchor_fp64_kernel<<<dim3((ns + bs - 1) / bs, 4), bs, 0, s>>>(g, a, const_cast<double*>(kanchor));
+    if (table) {
+      const double* tab = (const double*)table;
+      const long long* itab = (const long long*)(tab + (size_t)GEO_DOUBLES * total);
+      sommerfeld_fp64_tab_kernel<<<dim3((total + bs - 1) / bs, 6), bs, 0, s>>>(g, a, kanchor, tab, itab);
+    } else {
+      sommerfeld_fp64_kernel<true><<<(total + bs - 1) / bs, bs, 0, s>>>(g, a, kanchor);
+    }
+  } else {
+    sommerfeld_fp64_kernel<false><<<(total + bs - 1) / bs, bs, 0, s>>>(g, a, kanchor);
+  }
   return cudaGetLastError();
 }
 cudaError_t launch_sommerfeld_mixed(const Grid& g, const StageArgsMixed& a, const float* kanchor,
