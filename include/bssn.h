@@ -82,7 +82,9 @@ enum { BSSN_ID_FLAT = 0, BSSN_ID_GAUGE_WAVE = 1, BSSN_ID_BL = 2, BSSN_ID_KASNER 
  *  ksum_fp64           mixed precision, single-grid contexts only: 1 keeps
  *                      the weighted sum of the RK4 k of every field in
  *                      float64 (one more float64 register; W's is float64
- *                      in any case), 0 in float (the default).
+ *                      in any case; the stage runs the fused 32x8x1 kernel
+ *                      whatever the tile configuration), 0 in float (the
+ *                      default).
  *  w_fp64_threshold    mixed precision: points with W below this take the
  *                      W/phi right-hand side in float64.
  *  r_excise            constraint norms: excised set is r > r_excise from
@@ -304,7 +306,7 @@ bssn_status bssn_set_staging(bssn_ctx* ctx, void* d_mem, size_t bytes);
 
 /* Stage-kernel tile configurations: block shape (points along x, y, z) and the
  * minimum resident blocks per SM given to the compiler.  The last ones are for
- * the mixed path only: "tma32x4x1/2", "tma32x8x1/1" and "tma32x4x2/1" stage the
+ * the mixed path only: "tma32x4x1/2" and "tma32x8x1/1" stage the
  * second-differenced fields of each tile in shared memory by TMA (two blocks
  * of 32x4 points per SM, or one block of 32x8 points per SM, which leaves more
  * L1 for the other fields); "split32x4x1/B" (B = 2, 3, 4) run the stencils as one

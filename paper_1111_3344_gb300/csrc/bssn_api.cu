@@ -181,7 +181,7 @@ struct bssn_ctx {
   float2* kshf;   // double-word path: boundary anchors
   bool shadow_valid;
   int tile;  // stage-kernel tile configuration (see bssn_autotune)
-  CUtensorMap tmap[3][3];  // mixed: tensor maps of the float stage buffers, per TMA variant
+  CUtensorMap tmap[2][3];  // mixed: tensor maps of the float stage buffers, per TMA variant
   bool tmap_ok;
   int* err;             // device error word (bounded waits that gave up)
   int stall_polls;      // test hook of the TMA-staged kernels (bssn_test_stall_tma)
@@ -216,9 +216,8 @@ struct bssn_ctx {
 
 // Tile configuration indices: [0, tile_config_count()) fused kernels, then
 // N_TMA TMA-staged mixed kernels (variant 0: 32x4x1, two blocks per SM;
-// 1: 32x8x1, one block per SM; 2: 32x4x2, one block per SM), then the
-// split-stage variants.
-constexpr int N_TMA = 3;
+// 1: 32x8x1, one block per SM), then the split-stage variants.
+constexpr int N_TMA = 2;
 static int tma_variant(int cfg) {
   const int v = cfg - tile_config_count();
   return (v >= 0 && v < N_TMA) ? v : -1;
@@ -618,7 +617,9 @@ static bssn_status run_stage_mixed(bssn_ctx* ctx, int src, int mode, int out, do
   a.stall_polls = ctx->stall_polls;
   cudaError_t e;
   if (ctx->prof && (e = prof_mark(ctx, ctx->ev_stage)) != cudaSuccess) return cuda_fail(e, "profile");
-  if (tma_variant(ctx->tile) >= 0)
+  if (ctx->ks64)
+    e = launch_stage_mixed_ks64(ctx->g, a, ctx->stream);
+  else if (tma_variant(ctx->tile) >= 0)
     e = launch_stage_mixed_tma(ctx->g, a, ctx->tmap[tma_variant(ctx->tile)][src], ctx->err, ctx->stream,
                                tma_variant(ctx->tile));
   else if (split_variant(ctx->tile) >= 0)
@@ -993,7 +994,6 @@ const char* bssn_tile_name(int32_t cfg) {
   if (ff_variant(cfg) >= 0) return ff_config_name(ff_variant(cfg));
   if (tma_variant(cfg) == 0) return "tma32x4x1/2";
   if (tma_variant(cfg) == 1) return "tma32x8x1/1";
-  if (tma_variant(cfg) == 2) return "tma32x4x2/1";
   if (split_variant(cfg) >= 0) return split_config_name(split_variant(cfg));
   return tile_config_name(cfg);
 }
@@ -1070,6 +1070,7 @@ bssn_status bssn_autotune(bssn_ctx* ctx, int32_t reps, int32_t* best, double* ms
       a.ksum = ctx->ks32; a.ksumw = ctx->ksw; a.ksum64 = ctx->ks64; a.a_dt = 0.5 * ctx->p.dt;
       a.a_dtf = (float)a.a_dt;
       a.w_thr = ctx->p.w_fp64_threshold; a.mode = second ? MODE_MID : MODE_FIRST;
+      if (ctx->ks64) return launch_stage_mixed_ks64(ctx->g, a, ctx->stream);
       if (tma_variant(c) >= 0)
         return launch_stage_mixed_tma(ctx->g, a, ctx->tmap[tma_variant(c)][q], ctx->err, ctx->stream,
                                       tma_variant(c));

@@ -284,6 +284,7 @@ struct Punct {
 // Launch wrappers (defined in the .cu files); all return cudaError_t of the launch.
 cudaError_t launch_stage_fp64(const Grid& g, const StageArgs& a, cudaStream_t s, int cfg = 0);
 cudaError_t launch_stage_mixed(const Grid& g, const StageArgsMixed& a, cudaStream_t s, int cfg = 0);
+cudaError_t launch_stage_mixed_ks64(const Grid& g, const StageArgsMixed& a, cudaStream_t s);
 int tile_config_count();
 bool tile_config_has_fp64(int c);  // false for the mixed-only configurations
 const char* tile_config_name(int c);

@@ -36,13 +36,13 @@ __global__ void __launch_bounds__(TX * TY * TZ, MINB) stage_fp64_kernel(Grid g, 
   stage_point_fp64<0>(g, a, ii, jj, kk);
 }
 
-template <int TX, int TY, int TZ, int MINB>
+template <int TX, int TY, int TZ, int MINB, bool KS64 = false>
 __global__ void __launch_bounds__(TX * TY * TZ, MINB) stage_mixed_kernel(Grid g, StageArgsMixed a) {
   const int ii = blockIdx.x * TX + threadIdx.x;
   const int jj = blockIdx.y * TY + threadIdx.y;
   const int kk = blockIdx.z * TZ + threadIdx.z;
   if (ii >= g.n0 || jj >= g.n1 || kk >= g.n2) return;
-  stage_point_mixed(g, a, ii, jj, kk);
+  stage_point_mixed<KS64>(g, a, ii, jj, kk);
 }
 
 // float64 full-row variants, defined in k_stage_shfl.cu
@@ -115,6 +115,15 @@ cudaError_t launch_stage_fp64(const Grid& g, const StageArgs& a, cudaStream_t s,
 cudaError_t launch_stage_mixed(const Grid& g, const StageArgsMixed& a, cudaStream_t s, int cfg) {
   if (cfg < 0 || cfg >= tile_config_count()) cfg = 0;
   return k_tiles[cfg].mixed(g, a, s);
+}
+
+// the mixed stage with the float64 k-sum of every field (ksum_fp64): the fused
+// 32 x 8 x 1 kernel, whatever the context's tile configuration
+cudaError_t launch_stage_mixed_ks64(const Grid& g, const StageArgsMixed& a, cudaStream_t s) {
+  dim3 block(32, 8, 1);
+  dim3 grid((g.n0 + 31) / 32, (g.n1 + 7) / 8, g.n2);
+  stage_mixed_kernel<32, 8, 1, 1, true><<<grid, block, 0, s>>>(g, a);
+  return cudaGetLastError();
 }
 
 // float shadow X - X0 (and float64 W) of a float64 register, every stored point

@@ -86,8 +86,10 @@ __device__ __forceinline__ double chi_rhs_fp64(const Grid& g, const float* __res
 }
 
 // Fused stage at interior point (ii, jj, kk), mixed precision; the accessor
-// says where each field of the stage input is read from.
-template <typename A>
+// says where each field of the stage input is read from.  KS64: the k-sum of
+// every field is float64 (a.ksum64; the ksum_fp64 option), a separate
+// instantiation so that the default kernels keep their register allocation.
+template <typename A, bool KS64 = false>
 __device__ __forceinline__ void stage_point_mixed_acc(const Grid& g, const StageArgsMixed& a,
                                                       const A& acc, int ii, int jj, int kk) {
   const int i = ii + GH, j = jj + GH, k = kk + GH;
@@ -100,7 +102,7 @@ __device__ __forceinline__ void stage_point_mixed_acc(const Grid& g, const Stage
   // memory, which comes back from L1.
   float pk[NF], ps[NF];
   double py[NF];
-  const bool ks64 = a.ksum64 != nullptr;  // float64 k-sum of every field (ksum_fp64)
+  constexpr bool ks64 = KS64;  // float64 k-sum of every field (ksum_fp64)
   if (a.mode == MODE_MID) {
 #pragma unroll
     for (int f = 1; f < NF; f++) {
@@ -165,10 +167,11 @@ __device__ __forceinline__ void stage_point_mixed_acc(const Grid& g, const Stage
   }
 }
 
+template <bool KS64 = false>
 __device__ __forceinline__ void stage_point_mixed(const Grid& g, const StageArgsMixed& a, int ii,
                                                   int jj, int kk) {
   const GlobalAcc<float> acc(g, a.src, lin(g, ii + GH, jj + GH, kk + GH));
-  stage_point_mixed_acc(g, a, acc, ii, jj, kk);
+  stage_point_mixed_acc<GlobalAcc<float>, KS64>(g, a, acc, ii, jj, kk);
 }
 
 // ------------------------------------------------------------ double-word

@@ -20,8 +20,7 @@ constexpr long long WAIT_LIMIT = 1LL << 24;
 
 // Tile of 32 x TY x TZ interior points and its boxes: BX = 32 + 6 rounded up
 // to a multiple of 4 floats, BY = TY + 6, BZ = TZ + 6 (three ghost layers on
-// every side); slots of the staged fields 128-byte aligned.  A thicker tile
-// (TZ = 2) stages 8 planes for 2 planes of points instead of 7 for 1.
+// every side); slots of the staged fields 128-byte aligned.
 template <int TY_, int TZ_ = 1>
 struct TmaShape {
   static constexpr int TX = 32, TY = TY_, TZ = TZ_;
