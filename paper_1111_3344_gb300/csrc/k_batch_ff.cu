@@ -29,28 +29,36 @@ __device__ __forceinline__ int find_member_ff(const unsigned* base, int count, u
 template <int TY, int TZ, int MINB, bool FULL>
 __global__ void __launch_bounds__(32 * TY * TZ, MINB)
     batch_tile_ff_kernel(const MemberDev* __restrict__ mem, const BatchWork* __restrict__ wk, int stage) {
-  __shared__ int sid;
+  // the member's grid and stage arguments are copied to shared memory once per
+  // block: under a tight register cap the point function reloads them often,
+  // and shared loads are cheaper than loads of the member table
+  __shared__ Grid sg;
+  __shared__ StageArgsFF sa;
+  __shared__ int stile[2];
   __shared__ unsigned slocal;
   const int tid = threadIdx.x + 32 * (threadIdx.y + TY * threadIdx.z);
   const unsigned t = blockIdx.x;
   if (t >= wk->total_tiles) return;  // whole block
   if (tid == 0) {
     const int slot = find_member_ff(wk->tile_base, wk->count, t);
-    sid = wk->member[slot];
+    const MemberDev& M = mem[wk->member[slot]];
+    sg = M.g;
+    sa = M.aff[stage];
+    stile[0] = M.tiles[0];
+    stile[1] = M.tiles[1];
     slocal = t - wk->tile_base[slot];
   }
   __syncthreads();
-  const MemberDev& M = mem[sid];
   unsigned lt = slocal;
-  const int bx = (int)(lt % (unsigned)M.tiles[0]);
-  lt /= (unsigned)M.tiles[0];
-  const int by = (int)(lt % (unsigned)M.tiles[1]);
-  const int bz = (int)(lt / (unsigned)M.tiles[1]);
+  const int bx = (int)(lt % (unsigned)stile[0]);
+  lt /= (unsigned)stile[0];
+  const int by = (int)(lt % (unsigned)stile[1]);
+  const int bz = (int)(lt / (unsigned)stile[1]);
   const int ii = bx * 32 + threadIdx.x, jj = by * TY + threadIdx.y, kk = bz * TZ + threadIdx.z;
   if constexpr (FULL) {
-    stage_point_ff<32, TY, TZ>(M.g, M.aff[stage], ii, jj, kk);  // every thread inside the grid
+    stage_point_ff<32, TY, TZ>(sg, sa, ii, jj, kk);  // every thread inside the grid
   } else {
-    if (ii < M.g.n0 && jj < M.g.n1 && kk < M.g.n2) stage_point_ff<0>(M.g, M.aff[stage], ii, jj, kk);
+    if (ii < sg.n0 && jj < sg.n1 && kk < sg.n2) stage_point_ff<0>(sg, sa, ii, jj, kk);
   }
 }
 
@@ -79,18 +87,20 @@ __global__ void batch_boundary_ff_kernel(const MemberDev* __restrict__ mem, cons
   }
 }
 
-// configurations: 32 x TY x TZ tiles, registers capped for MINB blocks per SM
+// configurations: 32 x TY x TZ tiles, registers capped for MF blocks per SM
+// in the full-tile kernel and MR in the every-stencil one (which spills more
+// at the same cap)
 struct FfBatchCfg {
   const char* name;
   int ty, tz;
   const void* kfull;
   const void* krest;
 };
-#define FCFG(TY, TZ, MINB)                                                  \
-  { "fftiles32x" #TY "x" #TZ "/" #MINB, TY, TZ,                            \
-    (const void*)batch_tile_ff_kernel<TY, TZ, MINB, true>,                 \
-    (const void*)batch_tile_ff_kernel<TY, TZ, MINB, false> }
-static const FfBatchCfg k_ffcfg[] = {FCFG(4, 1, 8), FCFG(4, 1, 4)};
+#define FCFG(TY, TZ, MF, MR)                                                \
+  { "fftiles32x" #TY "x" #TZ "/" #MF "+" #MR, TY, TZ,                      \
+    (const void*)batch_tile_ff_kernel<TY, TZ, MF, true>,                   \
+    (const void*)batch_tile_ff_kernel<TY, TZ, MR, false> }
+static const FfBatchCfg k_ffcfg[] = {FCFG(4, 1, 8, 4), FCFG(4, 1, 8, 8), FCFG(4, 1, 4, 4)};
 #undef FCFG
 
 int batch_ff_config_count() { return (int)(sizeof(k_ffcfg) / sizeof(k_ffcfg[0])); }

@@ -182,7 +182,7 @@ def test_ff_batch_matches_single_grid_bit_for_bit(torch_cuda):
     def run(idx):
         b = B.Batch("ff", pool_bytes=sum(B.Batch.member_bytes(params[i]) for i in idx) + (16 << 20),
                     max_members=4)
-        b.set_tile(bnames.index("fftiles32x4x1/8"))
+        b.set_tile(bnames.index("fftiles32x4x1/8+8"))
         ids = [b.add(params[i]) for i in idx]
         for m, i in zip(ids, idx):
             b.set_state(m, states[i], 0.0)
