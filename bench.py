@@ -645,7 +645,7 @@ def served_run(args, precision, requests):
             "p50_s": float(np.percentile(lats, 50)), "p99_s": p99,
             "p99_queued_s": float(queued[i99]), "mean_queued_s": float(queued.mean()),
             "failed": int(fails), "wall_s": wall, "busy_s": stats["busy_s"],
-            "dtype": "f32+f64" if precision == "mixed" else "f64",
+            "dtype": {"fp64": "f64", "mixed": "f32+f64", "ff": "f32x2+f64"}[precision],
             "workload": f"first {len(reqs)} requests of the served stream (seed 3344): Poisson arrivals of "
                         f"Brill-Lindquist binaries, grids 32^3..192^3, 50..400 steps",
             "lambda_per_s": lam, "capacity_mpts": capacity,
