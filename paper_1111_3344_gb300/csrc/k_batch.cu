@@ -35,12 +35,11 @@ __device__ __forceinline__ int find_member64(const unsigned long long* base, int
   return lo;
 }
 
-template <int TX, int TY, int TZ, int MINB, bool MIXED>
+template <int TX, int TY, int TZ, int MINB>
 __global__ void __launch_bounds__(TX * TY * TZ, MINB)
     batch_stage_kernel(const MemberDev* __restrict__ mem, const BatchWork* __restrict__ wk, int stage) {
-  using Args = StageArgsT<typename std::conditional<MIXED, float, double>::type>;
   __shared__ Grid sg;
-  __shared__ Args sa;
+  __shared__ StageArgsMixed sa;
   __shared__ int stile[3];
   __shared__ unsigned slocal;
   const int tid = threadIdx.x + TX * (threadIdx.y + TY * threadIdx.z);
@@ -57,8 +56,7 @@ __global__ void __launch_bounds__(TX * TY * TZ, MINB)
         const int slot = find_member(wk->tile_base, count, t);
         const MemberDev& M = mem[wk->member[slot]];
         sg = M.g;
-        if constexpr (MIXED) sa = M.amx[stage];
-        else sa = M.a64[stage];
+        sa = M.amx[stage];
         stile[0] = M.tiles[0];
         stile[1] = M.tiles[1];
         stile[2] = M.tiles[2];
@@ -74,24 +72,61 @@ __global__ void __launch_bounds__(TX * TY * TZ, MINB)
     const int by = (int)(lt % (unsigned)stile[1]);
     const int bz = (int)(lt / (unsigned)stile[1]);
     const int ii = bx * TX + threadIdx.x, jj = by * TY + threadIdx.y, kk = bz * TZ + threadIdx.z;
-    if (ii < sg.n0 && jj < sg.n1 && kk < sg.n2) {
-      if constexpr (MIXED) {
-        stage_point_mixed(sg, sa, ii, jj, kk);
-      } else if constexpr (TX == 32) {
-        // members whose tiles are all full (n0 a multiple of 32, n1 of TY, n2
-        // of TZ): every warp is a full x-row and every thread of the block is
-        // inside the grid, so the x-mixed second differences share first
-        // differences across lanes and D_y D_z across rows through shared
-        // memory (one barrier, reached by the whole block: the choice is
-        // uniform over the member)
-        if (sg.n0 % 32 == 0 && sg.n1 % TY == 0 && sg.n2 % TZ == 0)
-          stage_point_fp64<32, TY, TZ>(sg, sa, ii, jj, kk);
-        else
-          stage_point_fp64<0>(sg, sa, ii, jj, kk);
-      } else {
-        stage_point_fp64<0>(sg, sa, ii, jj, kk);
+    if (ii < sg.n0 && jj < sg.n1 && kk < sg.n2) stage_point_mixed(sg, sa, ii, jj, kk);
+  }
+}
+
+// Float64 persistent stage: the body of one tile is a call of its own
+// (__noinline__), so that it gets the register allocation of a one-tile
+// kernel.  Inlined into the loop over tiles, the float64 stage spills
+// 1.2-1.8 KB per thread whether its arguments sit in shared memory or in the
+// member table; behind the call, about 330 B (full tiles, 255 registers).  The callee reads the member's grid and
+// stage arguments from the read-only member table.  FULL: the member has full
+// tiles (every warp a full x-row, every thread of the block inside the grid),
+// which the caller decides uniformly over the block.
+template <int TY, int TZ, bool FULL>
+__device__ __noinline__ void batch_fp64_tile(const MemberDev* __restrict__ mem, int sid, unsigned lt, int stage) {
+  const MemberDev& M = mem[sid];
+  const int bx = (int)(lt % (unsigned)M.tiles[0]);
+  lt /= (unsigned)M.tiles[0];
+  const int by = (int)(lt % (unsigned)M.tiles[1]);
+  const int bz = (int)(lt / (unsigned)M.tiles[1]);
+  const int ii = bx * 32 + threadIdx.x, jj = by * TY + threadIdx.y, kk = bz * TZ + threadIdx.z;
+  if constexpr (FULL)
+    stage_point_fp64<32, TY, TZ>(M.g, M.a64[stage], ii, jj, kk);
+  else if (ii < M.g.n0 && jj < M.g.n1 && kk < M.g.n2)
+    stage_point_fp64<0>(M.g, M.a64[stage], ii, jj, kk);
+}
+
+template <int TY, int TZ, int MINB>
+__global__ void __launch_bounds__(32 * TY * TZ, MINB)
+    batch_stage_fp64_kernel(const MemberDev* __restrict__ mem, const BatchWork* __restrict__ wk, int stage) {
+  __shared__ int sid, sfull;
+  __shared__ unsigned slocal;
+  const int tid = threadIdx.x + 32 * (threadIdx.y + TY * threadIdx.z);
+  const unsigned total = wk->total_tiles;
+  const int count = wk->count;
+  // thread 0: the member of the block's current tile and its tile range
+  unsigned t_lo = 1u, t_hi = 0u;
+  int cur = 0, full = 0;
+  for (unsigned t = blockIdx.x; t < total; t += gridDim.x) {
+    __syncthreads();  // the previous tile is done with sid, sfull, slocal
+    if (tid == 0) {
+      if (t < t_lo || t >= t_hi) {
+        const int slot = find_member(wk->tile_base, count, t);
+        cur = wk->member[slot];
+        const Grid& g = mem[cur].g;
+        full = g.n0 % 32 == 0 && g.n1 % TY == 0 && g.n2 % TZ == 0;
+        t_lo = wk->tile_base[slot];
+        t_hi = wk->tile_base[slot + 1];
       }
+      sid = cur;
+      sfull = full;
+      slocal = t - t_lo;
     }
+    __syncthreads();
+    if (sfull) batch_fp64_tile<TY, TZ, true>(mem, sid, slocal, stage);
+    else batch_fp64_tile<TY, TZ, false>(mem, sid, slocal, stage);
   }
 }
 
@@ -181,8 +216,8 @@ struct BatchCfg {
 
 #define BCFG(TX, TY, TZ, MINB)                                                       \
   { #TX "x" #TY "x" #TZ "/" #MINB, TX, TY, TZ,                                      \
-    (const void*)batch_stage_kernel<TX, TY, TZ, MINB, false>,                       \
-    (const void*)batch_stage_kernel<TX, TY, TZ, MINB, true> }
+    (const void*)batch_stage_fp64_kernel<TY, TZ, MINB>,                             \
+    (const void*)batch_stage_kernel<TX, TY, TZ, MINB> }
 static const BatchCfg k_bcfg[] = {
     BCFG(32, 8, 1, 1), BCFG(32, 2, 2, 2), BCFG(32, 4, 1, 3), BCFG(32, 4, 2, 1),
 };

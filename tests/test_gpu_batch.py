@@ -252,6 +252,39 @@ def test_batch_full_rows_fp64(torch_cuda):
     mix.close()
 
 
+def test_batch_fp64_configurations_agree_bitwise(torch_cuda):
+    """Every float64 tile configuration of a batch -- the persistent kernels,
+    whose per-tile body is a call of its own, and the one-block-per-tile
+    kernels -- runs the same point functions on a member with full tiles and
+    on members with ragged ones: two steps give the same bits whichever
+    configuration runs them."""
+    from paper_1111_3344_gb300 import bssn as B
+    from paper_1111_3344_gb300.bssn import Batch
+    rows = dict(n=(64, 16, 8), xmin=(-8.0, -2.0, -1.0), h=0.25, boundary="sommerfeld", conformal="W",
+                slicing="1+log", shift="gamma-driver", eta=2.0, punctures=[(1.0, 0.05, 0.0, 0.0)],
+                precision="fp64", w_fp64_threshold=0.3)
+    cases = [rows] + _members("fp64")[:3]
+    lib = B.load()
+    names = [lib.bssn_batch_tile_name(c).decode() for c in range(lib.bssn_batch_tile_count())]
+    fp64_cfgs = [c for c, nm in enumerate(names) if not nm.startswith(("tma", "ff"))]
+    assert "32x4x1/3" in names and "tiles32x4x1/2" in names
+    ref = None
+    for c in fp64_cfgs:
+        b = Batch("fp64", pool_bytes=1 << 29)
+        ids = [b.add(gpu_params(cs)) for cs in cases]
+        for m, cs in zip(ids, cases):
+            _load(b, m, cs)
+        b.set_tile(c)
+        b.step(2)
+        got = [b.get_state(m)[0] for m in ids]
+        b.close()
+        if ref is None:
+            ref = got
+            continue
+        for x, y in zip(ref, got):
+            assert np.array_equal(x, y), names[c]
+
+
 def test_batch_tma_tile_matches_single_grid_tma(torch_cuda):
     """The TMA-staged batched kernel (mixed): each member's state is the same
     bit for bit alone and in the mix, and matches the single-grid evolution on
