@@ -304,6 +304,31 @@ def measured_peaks(B, torch, stream):
                    "2 flops per FMA, measured in this run"}
 
 
+def confirm_by_steps(tile_ms, set_cfg, step, stream, top=3, steps=1):
+    """The autotuners time the first two RK4 stages (the state stays unchanged);
+    a configuration's last stage, which advances y_n, can weigh differently.
+    Time `steps` whole RK4 steps under each of the `top` fastest candidates
+    (CUDA events on the stream the steps run on, after one untimed step under
+    that configuration) and keep the fastest.  Returns (index, {name: ms per
+    step}).  The state advances: call before the warm-up."""
+    import torch
+    names = list(tile_ms)
+    cands = sorted((c for c, nm in enumerate(names) if tile_ms[nm] >= 0), key=lambda c: tile_ms[names[c]])[:top]
+    ms_step = {}
+    for c in cands:
+        set_cfg(c)
+        step(1)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step(steps)
+        e1.record(stream)
+        e1.synchronize()
+        ms_step[names[c]] = e0.elapsed_time(e1) / steps
+    best = min(cands, key=lambda c: ms_step[names[c]])
+    set_cfg(best)
+    return best, ms_step
+
+
 def puncture_run(args, precision, world, local, steps, e2e=True):
     """The single-puncture workload at N_SIDE^3 in one precision: autotuned
     tiles, W untimed warm-up steps, then `steps` RK4 steps timed with CUDA
@@ -322,7 +347,11 @@ def puncture_run(args, precision, world, local, steps, e2e=True):
         tile = [B.bssn_tile_name(c) for c in range(B.bssn_tile_count())].index(args.tile)
         B.bssn_set_tile(evo.ctx, tile)
     else:
-        tile, _ = B.bssn_autotune(evo.ctx, reps=5)  # untimed: picks the stage-kernel tiles
+        # untimed: the autotuner's two-stage timing, then whole steps of its
+        # three fastest candidates
+        _, tile_ms = B.bssn_autotune(evo.ctx, reps=5)
+        tile, _ = confirm_by_steps(tile_ms, lambda c: B.bssn_set_tile(evo.ctx, c), evo.rk4_step, stream,
+                                   steps=2)
     for _ in range(args.warmup):
         evo.rk4_step(1)
     barrier(world)
@@ -512,9 +541,12 @@ def batched_run(args, precision, steps=None, members=None):
         bl = [len(m["punctures"])] + [v for q in m["punctures"] for v in q]
         batch.set_initial_data(mid, "bl", bl)
     best, tile_ms = batch.autotune(reps=2)
+    step_ms = {}
     if args.tile and args.tile in tile_ms:
         best = list(tile_ms).index(args.tile)
         batch.set_tile(best)
+    else:
+        best, step_ms = confirm_by_steps(tile_ms, batch.set_tile, batch.step, batch.stream)
     batch.step(args.warmup)
     batch.synchronize()
     clocks = ClockSampler(0)
@@ -547,6 +579,7 @@ def batched_run(args, precision, steps=None, members=None):
                         f"{steps} of the configuration's 100 steps",
             "interior_points": pts, "tile": tname,
             "autotune_ms_per_stage": {k: round(v, 3) for k, v in tile_ms.items() if v >= 0},
+            "confirm_ms_per_step": {k: round(v, 3) for k, v in step_ms.items()},
             "launches_per_step": 4 * (stage_launches + 1), "gpu_launches": 4 * (stage_launches + 1) * steps,
             "graph": True, "clocks": clk}
 
@@ -576,8 +609,8 @@ def served_requests(count, precision, seed=3344):
 def served_capacity(reqs, precision, steps=3):
     """Capacity of the serving path on its own request mix, M point-updates/s:
     the first requests of the stream (up to 24) resident together in one batch
-    with the serving path's kernels (autotuned), `steps` RK4 steps timed with
-    CUDA events."""
+    with the serving path's kernels (the default configuration of a new batch,
+    which the server runs), `steps` RK4 steps timed with CUDA events."""
     import torch
 
     from paper_1111_3344_gb300 import bssn as B
@@ -586,7 +619,6 @@ def served_capacity(reqs, precision, steps=3):
     batch = _make_batch(B, params, precision)
     for p, idp, _ in sample:
         batch.set_initial_data(batch.add(p), "bl", idp)
-    batch.autotune(reps=1)
     batch.step(1)
     batch.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -683,7 +715,9 @@ def run_precision(args):
     for prec in ["fp64"] + variants:
         evo = B.Evolution(workload_params(prec))
         evo.set_initial_data("bl", BL_P)
-        tile, _ = B.bssn_autotune(evo.ctx, reps=2)
+        _, tile_ms = B.bssn_autotune(evo.ctx, reps=2)
+        tile, _ = confirm_by_steps(tile_ms, lambda c: B.bssn_set_tile(evo.ctx, c), evo.rk4_step, evo.stream)
+        evo.set_initial_data("bl", BL_P)  # the timed run starts at t = 0
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(evo.stream)
         evo.rk4_step(args.steps)
@@ -750,7 +784,8 @@ def run_precision_batched(args):
             batch.set_initial_data(mid, "bl", [len(m["punctures"])] + [v for q in m["punctures"] for v in q])
             ids.append(mid)
         best, tile_ms = batch.autotune(reps=1)
-        # autotuning ran stages 1-2 only (y_n unchanged); start the timed run from t = 0
+        best, _ = confirm_by_steps(tile_ms, batch.set_tile, batch.step, batch.stream)
+        # start the timed run from t = 0
         for mid, m in zip(ids, mems):
             batch.set_initial_data(mid, "bl", [len(m["punctures"])] + [v for q in m["punctures"] for v in q])
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

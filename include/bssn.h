@@ -307,9 +307,11 @@ bssn_status bssn_set_staging(bssn_ctx* ctx, void* d_mem, size_t bytes);
 /* Stage-kernel tile configurations: block shape (points along x, y, z) and the
  * minimum resident blocks per SM given to the compiler.  The last ones are for
  * the mixed path only: "tma32x4x1/2" and "tma32x8x1/1" stage the
- * second-differenced fields of each tile in shared memory by TMA (two blocks
- * of 32x4 points per SM, or one block of 32x8 points per SM, which leaves more
- * L1 for the other fields); "split32x4x1/B" (B = 2, 3, 4) run the stencils as one
+ * second-differenced fields W, gt_ij and alpha of each tile in shared memory by
+ * TMA (two blocks of 32x4 points per SM, or one block of 32x8 points per SM,
+ * which leaves more L1 for the other fields); "tma11_32x8x1/1" stages beta^i
+ * as well (eleven fields, 173 KB of shared memory, one block of 32x8 points
+ * per SM); "split32x4x1/B" (B = 2, 3, 4) run the stencils as one
  * pass per field into a derivative register and the algebra as a second pass.
  * Every configuration evaluates the same per-point arithmetic, so results agree
  * to rounding and each configuration is reproducible bit for bit. */

@@ -181,7 +181,7 @@ struct bssn_ctx {
   float2* kshf;   // double-word path: boundary anchors
   bool shadow_valid;
   int tile;  // stage-kernel tile configuration (see bssn_autotune)
-  CUtensorMap tmap[2][3];  // mixed: tensor maps of the float stage buffers, per TMA variant
+  CUtensorMap tmap[2][3];  // mixed: tensor maps of the float stage buffers, per TMA box (tma_map)
   bool tmap_ok;
   int* err;             // device error word (bounded waits that gave up)
   int stall_polls;      // test hook of the TMA-staged kernels (bssn_test_stall_tma)
@@ -216,12 +216,15 @@ struct bssn_ctx {
 
 // Tile configuration indices: [0, tile_config_count()) fused kernels, then
 // N_TMA TMA-staged mixed kernels (variant 0: 32x4x1, two blocks per SM;
-// 1: 32x8x1, one block per SM), then the split-stage variants.
-constexpr int N_TMA = 2;
+// 1: 32x8x1, one block per SM; 2: 32x8x1 staging beta^i too), then the
+// split-stage variants.
+constexpr int N_TMA = 3;
 static int tma_variant(int cfg) {
   const int v = cfg - tile_config_count();
   return (v >= 0 && v < N_TMA) ? v : -1;
 }
+// tensor map of a TMA variant: variants 1 and 2 share the 32x8x1 box
+static int tma_map(int v) { return v >= 1 ? 1 : 0; }
 static int split_variant(int cfg) {
   const int v = cfg - tile_config_count() - N_TMA;
   return (v >= 0 && v < split_config_count()) ? v : -1;
@@ -337,7 +340,7 @@ bssn_status bssn_alloc(const bssn_params* p, void* d_mem, size_t bytes, void* cu
   ctx->tmap_ok = false;
   if (p->precision == BSSN_MIXED) {
     bool ok = true;
-    for (int v = 0; v < N_TMA && ok; v++)
+    for (int v = 0; v < 2 && ok; v++)
       for (int q = 0; q < 3 && ok; q++) ok = make_stage_tensor_map(g, ctx->m32[q], &ctx->tmap[v][q], v) == cudaSuccess;
     ctx->tmap_ok = ok;
   }
@@ -553,7 +556,7 @@ bssn_status bssn_rhs(bssn_ctx* ctx, const void* d_state, void* d_rhs) {
   if (split_variant(ctx->tile) >= 0)
     e = launch_stage_mixed_split(ctx->g, a, ctx->dr, ctx->stream, split_variant(ctx->tile));
   else if (tma_variant(ctx->tile) >= 0)
-    e = launch_stage_mixed_tma(ctx->g, a, ctx->tmap[tma_variant(ctx->tile)][2], ctx->err, ctx->stream,
+    e = launch_stage_mixed_tma(ctx->g, a, ctx->tmap[tma_map(tma_variant(ctx->tile))][2], ctx->err, ctx->stream,
                                tma_variant(ctx->tile));
   else
     e = launch_stage_mixed(ctx->g, a, ctx->stream, ctx->tile);
@@ -620,8 +623,8 @@ static bssn_status run_stage_mixed(bssn_ctx* ctx, int src, int mode, int out, do
   if (ctx->ks64)
     e = launch_stage_mixed_ks64(ctx->g, a, ctx->stream);
   else if (tma_variant(ctx->tile) >= 0)
-    e = launch_stage_mixed_tma(ctx->g, a, ctx->tmap[tma_variant(ctx->tile)][src], ctx->err, ctx->stream,
-                               tma_variant(ctx->tile));
+    e = launch_stage_mixed_tma(ctx->g, a, ctx->tmap[tma_map(tma_variant(ctx->tile))][src], ctx->err,
+                               ctx->stream, tma_variant(ctx->tile));
   else if (split_variant(ctx->tile) >= 0)
     e = launch_stage_mixed_split(ctx->g, a, ctx->dr, ctx->stream, split_variant(ctx->tile));
   else
@@ -994,6 +997,7 @@ const char* bssn_tile_name(int32_t cfg) {
   if (ff_variant(cfg) >= 0) return ff_config_name(ff_variant(cfg));
   if (tma_variant(cfg) == 0) return "tma32x4x1/2";
   if (tma_variant(cfg) == 1) return "tma32x8x1/1";
+  if (tma_variant(cfg) == 2) return "tma11_32x8x1/1";
   if (split_variant(cfg) >= 0) return split_config_name(split_variant(cfg));
   return tile_config_name(cfg);
 }
@@ -1072,7 +1076,7 @@ bssn_status bssn_autotune(bssn_ctx* ctx, int32_t reps, int32_t* best, double* ms
       a.w_thr = ctx->p.w_fp64_threshold; a.mode = second ? MODE_MID : MODE_FIRST;
       if (ctx->ks64) return launch_stage_mixed_ks64(ctx->g, a, ctx->stream);
       if (tma_variant(c) >= 0)
-        return launch_stage_mixed_tma(ctx->g, a, ctx->tmap[tma_variant(c)][q], ctx->err, ctx->stream,
+        return launch_stage_mixed_tma(ctx->g, a, ctx->tmap[tma_map(tma_variant(c))][q], ctx->err, ctx->stream,
                                       tma_variant(c));
       if (split_variant(c) >= 0)
         return launch_stage_mixed_split(ctx->g, a, ctx->dr, ctx->stream, split_variant(c));

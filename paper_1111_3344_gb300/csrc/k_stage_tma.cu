@@ -72,7 +72,7 @@ cudaError_t make_stage_tensor_map(const Grid& g, const float* base, CUtensorMap*
     if (e != cudaSuccess) return e;
     if (q != cudaDriverEntryPointSuccess || !g_encode) return cudaErrorNotSupported;
   }
-  const int by = variant == 1 ? TmaShape<8>::BY : TmaShape<4>::BY;
+  const int by = variant >= 1 ? TmaShape<8>::BY : TmaShape<4>::BY;
   const int bz = TmaShape<4>::BZ;
   cuuint64_t dims[4] = {(cuuint64_t)g.pitch, (cuuint64_t)g.sy, (cuuint64_t)g.sz, (cuuint64_t)NF};
   cuuint64_t strides[3] = {(cuuint64_t)g.pitch * 4, (cuuint64_t)g.plane * 4, (cuuint64_t)g.fstride * 4};
@@ -102,9 +102,12 @@ static cudaError_t launch_tma(const Grid& g, const StageArgsMixed& a, const CUte
 
 // variant 0: 32 x 4 x 1 tiles, two blocks per SM; 1: 32 x 8 x 1 tiles, one
 // block per SM (half the shared memory per SM, so more L1 for the fields read
-// through it); map: a tensor map made for the same variant
+// through it); 2: 32 x 8 x 1 tiles staging beta^i as well (eleven fields,
+// 173 KB, one block per SM; the tensor map of variant 1 serves, same box);
+// map: a tensor map made for the same variant
 cudaError_t launch_stage_mixed_tma(const Grid& g, const StageArgsMixed& a, const CUtensorMap& map,
                                    int* err, cudaStream_t s, int variant) {
+  if (variant == 2) return launch_tma<TmaShape<8, 1, 11>, 1>(g, a, map, err, s);
   return variant == 1 ? launch_tma<TmaShape<8>, 1>(g, a, map, err, s) : launch_tma<TmaShape<4>, 2>(g, a, map, err, s);
 }
 

@@ -7,7 +7,8 @@
 // per staged field brings the field's box over the tile plus three ghost
 // layers on every side (BXP x BYP x BZP floats; BXP rounded up so that a box
 // row is a multiple of 16 bytes).  The staged fields are the eight with second
-// derivatives and the widest stencils: W, the six gt_ij and alpha.
+// derivatives and the widest stencils, W, the six gt_ij and alpha, and in the
+// eleven-field form also the three beta^i (second-differenced as well).
 #pragma once
 #include <cuda.h>
 
@@ -20,15 +21,16 @@ constexpr long long WAIT_LIMIT = 1LL << 24;
 
 // Tile of 32 x TY x TZ interior points and its boxes: BX = 32 + 6 rounded up
 // to a multiple of 4 floats, BY = TY + 6, BZ = TZ + 6 (three ghost layers on
-// every side); slots of the staged fields 128-byte aligned.
-template <int TY_, int TZ_ = 1>
+// every side); slots of the staged fields 128-byte aligned.  NST: staged
+// fields, 8 (W, gt_ij, alpha) or 11 (and beta^i).
+template <int TY_, int TZ_ = 1, int NST_ = NSTAGED>
 struct TmaShape {
-  static constexpr int TX = 32, TY = TY_, TZ = TZ_;
+  static constexpr int TX = 32, TY = TY_, TZ = TZ_, NST = NST_;
   static constexpr int BX = 40, BY = TY + 2 * GH, BZ = TZ + 2 * GH;
   static constexpr int BOX = BX * BY * BZ;                              // floats of one field's box
   static constexpr int SLOT = (BOX + 31) / 32 * 32;                     // slot stride
-  static constexpr unsigned BYTES = NSTAGED * BOX * sizeof(float);     // bytes the copies deliver
-  static constexpr int SMEM = NSTAGED * SLOT * (int)sizeof(float) + 128;  // + alignment slack
+  static constexpr unsigned BYTES = NST * BOX * sizeof(float);         // bytes the copies deliver
+  static constexpr int SMEM = NST * SLOT * (int)sizeof(float) + 128;  // + alignment slack
 };
 
 // the 32 x 4 x 1 tile (two blocks per SM): the batched kernel and the names below
@@ -39,11 +41,19 @@ constexpr int BOXF = TmaDefault::BOX, SLOTF = TmaDefault::SLOT;
 constexpr unsigned STAGED_BYTES = TmaDefault::BYTES;
 constexpr int SMEM_BYTES = TmaDefault::SMEM;
 
+// slot s -> field: W, gt_ij (6), alpha, then beta^i (slots 8-10, staged when
+// the shape has NST = 11)
 __host__ __device__ __forceinline__ int staged_field(int s) {
-  return s == 0 ? F_CHI : (s <= 6 ? F_GT + (s - 1) : F_ALP);
+  return s == 0 ? F_CHI : (s <= 6 ? F_GT + (s - 1) : (s == 7 ? F_ALP : F_BETA + (s - 8)));
 }
+// field -> slot, -1 for a field read through L1
+template <int NST = NSTAGED>
 __device__ __forceinline__ int staged_slot(int f) {
-  return f == F_CHI ? 0 : ((f >= F_GT && f < F_GT + 6) ? 1 + (f - F_GT) : (f == F_ALP ? 7 : -1));
+  if (f == F_CHI) return 0;
+  if (f >= F_GT && f < F_GT + 6) return 1 + (f - F_GT);
+  if (f == F_ALP) return 7;
+  if (NST > 8 && f >= F_BETA && f < F_BETA + 3) return 8 + (f - F_BETA);
+  return -1;
 }
 
 // Accessor: staged fields from the shared box, the others from global.
@@ -53,15 +63,15 @@ struct TileAccT {
   long long id, fs, sd[3];
   const float* sm;  // shared address of this point in slot 0
   __device__ __forceinline__ const float* ptr(int f) const {
-    const int sl = staged_slot(f);
+    const int sl = staged_slot<Sh::NST>(f);
     return sl >= 0 ? sm + sl * Sh::SLOT : st + (long long)f * fs + id;
   }
   __device__ __forceinline__ long long s(int f, int d) const {
-    return staged_slot(f) >= 0 ? (d == 0 ? 1 : (d == 1 ? Sh::BX : Sh::BX * Sh::BY)) : sd[d];
+    return staged_slot<Sh::NST>(f) >= 0 ? (d == 0 ? 1 : (d == 1 ? Sh::BX : Sh::BX * Sh::BY)) : sd[d];
   }
   template <typename T>
   __device__ __forceinline__ T ld(int f, const float* p) const {
-    return staged_slot(f) >= 0 ? T(*p) : T(__ldg(p));
+    return staged_slot<Sh::NST>(f) >= 0 ? T(*p) : T(__ldg(p));
   }
 };
 using TileAcc = TileAccT<TmaDefault>;
@@ -100,7 +110,7 @@ __device__ __forceinline__ void issue_staged_loads(const void* tmap, unsigned ba
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(Sh::BYTES)
                : "memory");
 #pragma unroll
-  for (int s = 0; s < NSTAGED; s++) {
+  for (int s = 0; s < Sh::NST; s++) {
     const int f = staged_field(s);
     asm volatile(
         "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
