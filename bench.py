@@ -70,11 +70,13 @@ DPINST_PER_POINT_RHS_ROWS = 1921.1
 ORACLE_FLOP_PER_POINT_RHS = 5395 + 7874 + 299
 # DRAM bytes (read + write) per interior point of one stage launch, the mean
 # over the four stages of one RK4 step, from ncu captures of single launches
-# at the benchmark size (128^3; dram__bytes_read.sum + dram__bytes_write.sum);
-# None where no capture of the kernel at that size exists.
-FP64_TRAFFIC_PER_POINT = None       # stage_fp64_kernel (grids with n0 % 32 != 0)
-FP64_ROWS_TRAFFIC_PER_POINT = 954.5  # stage_fp64_blocks_kernel 32x4x1/1: 8006.6 MB per step
-MIXED_TRAFFIC_PER_POINT = 565.3     # stage_mixed_tma_kernel tma32x4x1/2: 4741.9 MB per step
+# at the benchmark size (128^3; dram__bytes_read.sum + dram__bytes_write.sum),
+# by stage-kernel configuration; a configuration without a capture of its
+# current kernel at that size reports null.
+STAGE_TRAFFIC_PER_POINT = {
+    ("fp64", "32x4x1/1"): 954.5,       # stage_fp64_blocks_kernel: 8006.6 MB per step
+    ("mixed", "tma32x4x1/2"): 565.3,   # stage_mixed_tma_kernel, 8 staged fields: 4741.9 MB per step
+}
 # Float64 work per interior point of the analysis kernels (DADD + DMUL + 2 DFMA
 # from ncu instruction counts at 96^3).  psi4 and constraints include the
 # ADM-field pass that precedes them (36 flop per stored point, 44 per
@@ -429,13 +431,12 @@ def run_ours(args):
     rows = run["tile"] in ROWS_TILES and N_SIDE % 32 == 0
     if mixed:
         kernel = "stage_mixed_tma_kernel" if run["tile"].startswith("tma") else "stage_mixed_kernel"
-        roofline = hbm_roofline(run, "mixed", kernel, MIXED_TRAFFIC_PER_POINT)
+        roofline = hbm_roofline(run, "mixed", kernel, STAGE_TRAFFIC_PER_POINT.get(("mixed", run["tile"])))
     elif args.precision == "ff":
         roofline = hbm_roofline(run, "ff", "stage_ff_kernel", None)
     else:
         kernel = "stage_fp64_blocks_kernel" if rows else "stage_fp64_kernel"
-        roofline = hbm_roofline(run, "fp64", kernel,
-                                FP64_ROWS_TRAFFIC_PER_POINT if rows else FP64_TRAFFIC_PER_POINT)
+        roofline = hbm_roofline(run, "fp64", kernel, STAGE_TRAFFIC_PER_POINT.get(("fp64", run["tile"])))
         peaks = measured_peaks(B, torch, torch.cuda.Stream())
         flop_pt = FLOP_PER_POINT_RHS_ROWS if rows else FLOP_PER_POINT_RHS
         dpinst_pt = DPINST_PER_POINT_RHS_ROWS if rows else DPINST_PER_POINT_RHS
@@ -499,7 +500,7 @@ def extras(args):
         "metric": "BSSN RK4 point-updates/s (mixed FP32 RHS / FP64 state, Brill-Lindquist puncture 128^3)",
         "value": mixed["value"], "unit": "Mpoint-updates/s", "ms_per_step": mixed["ms"] / mixed["steps"],
         "steps": mixed["steps"], "dtype": "f32+f64", "tile": mixed["tile"],
-        "roofline": hbm_roofline(mixed, "mixed", kernel, MIXED_TRAFFIC_PER_POINT),
+        "roofline": hbm_roofline(mixed, "mixed", kernel, STAGE_TRAFFIC_PER_POINT.get(("mixed", mixed["tile"]))),
         "e2e": mixed["e2e"], "gpu_launches": mixed["stage_launches"] + mixed["boundary_launches"],
         "clocks": mixed["clocks"]}}
     bsteps = max(2, args.steps // 4)
