@@ -652,6 +652,7 @@ def served_run(args, precision, requests):
     gaps = rng.exponential(1.0 / lam, size=len(reqs))
     budget = int(args.budget_gb * (1 << 30))
     srv = B.Server(precision, budget_bytes=budget)
+    srv.set_policy(args.serve_policy, args.serve_min_points)
     clocks = ClockSampler(0)
     clocks.start()
     t0 = time.perf_counter()
@@ -681,6 +682,8 @@ def served_run(args, precision, requests):
             "dtype": {"fp64": "f64", "mixed": "f32+f64", "ff": "f32x2+f64"}[precision],
             "workload": f"first {len(reqs)} requests of the served stream (seed 3344): Poisson arrivals of "
                         f"Brill-Lindquist binaries, grids 32^3..192^3, 50..400 steps",
+            "policy": args.serve_policy,
+            "min_points": args.serve_min_points if args.serve_policy == "shortest" else None,
             "lambda_per_s": lam, "capacity_mpts": capacity,
             "capacity_source": f"{cap_n} requests of the same stream resident in one batch, 3 steps timed "
                                "with CUDA events in this run; lambda = 0.8 x capacity / mean work per request",
@@ -937,6 +940,10 @@ def main():
     ap.add_argument("--no-extras", action="store_true",
                     help="puncture workload: print the float64 line only, without the mixed, batched and "
                          "served parts of the metric")
+    ap.add_argument("--serve-policy", choices=["all", "shortest"], default="all",
+                    help="server: step every resident request, or the shortest remaining work first")
+    ap.add_argument("--serve-min-points", type=float, default=float(1 << 21),
+                    help="shortest-first policy: interior points a step advances at least")
     ap.add_argument("--served-sample", type=int, default=32,
                     help="requests of the served stream in the default line's served sample")
     ap.add_argument("--variants", default="mixed,mixed_ks64,ff",

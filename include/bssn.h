@@ -359,15 +359,26 @@ bssn_status bssn_batch_get_state(bssn_batch* b, int32_t member, double* host, do
 /* Advance every active member nsteps RK4 steps (asynchronous). */
 bssn_status bssn_batch_step(bssn_batch* b, int32_t nsteps);
 bssn_status bssn_batch_constraints(bssn_batch* b, int32_t member, double out[16]); /* synchronises */
+/* hold != 0: the member stays resident (registers, state, time) but the next
+ * bssn_batch_step calls leave it out; hold = 0 puts it back.  Its results do
+ * not change: a held member resumes from the same state.  ENOTFOUND for an
+ * unknown member. */
+bssn_status bssn_batch_hold(bssn_batch* b, int32_t member, int32_t hold);
 /* Tile configurations of the batched stage, each one launch per RK4 stage over
  * every active member's tiles:
  *   "TXxTYxTZ/B"     persistent kernels (resident blocks loop over the tiles);
  *   "tilesTXxTYxTZ/B" one block per tile (no loop, fewer register spills; the
  *                    graph is captured again when the membership changes);
- *   "tma32x4x1/2"    (last) persistent, staging W, gt_ij and alpha of each
- *                    32x4x1 tile in shared memory by tensor loads (mixed
- *                    batches only; BSSN_EINVAL for float64).
- * A new batch starts on "tma32x4x1/2" (mixed) or "32x4x1/3" (float64).  A
+ *   "tma32x4x1/2"    persistent, staging W, gt_ij and alpha of each 32x4x1
+ *                    tile in shared memory by tensor loads (mixed batches
+ *                    only; BSSN_EINVAL for float64);
+ *   "tma11_32x8x1/1" the same on 32x8x1 tiles, staging beta^i as well
+ *                    (one block per SM);
+ *   "fftiles32x4x1/MF+MR" (last) the double-word batches' one-block-per-tile
+ *                    kernels (register caps of the full-tile and the
+ *                    every-stencil kernel).
+ * A new batch starts on "tma11_32x8x1/1" (mixed), "32x4x1/3" (float64) or the
+ * first double-word configuration (double-word).  A
  * tensor-load wait that gives up (bounded) makes the next
  * bssn_batch_get_state or bssn_batch_constraints return BSSN_ETIMEOUT. */
 int32_t bssn_batch_tile_count(void);
@@ -392,7 +403,8 @@ bssn_status bssn_batch_test_stall_tma(bssn_batch* b, int32_t polls);
  * Continuous batching of evolution requests (no counterpart in the paper): a
  * scheduler thread admits queued requests at RK4 step boundaries while their
  * register bytes fit in hbm_budget_bytes, keeps their state on the device,
- * advances all resident evolutions together (bssn_batch_step) and retires
+ * advances the resident evolutions together (bssn_batch_step; all of them,
+ * or the shortest first: bssn_server_set_policy) and retires
  * each when it reaches its step count, reporting its constraint norms and
  * time from submission to completion.  d_pool (256-byte aligned) holds the
  * batch tables and every request's registers. */
@@ -411,6 +423,24 @@ bssn_status bssn_poll(bssn_server* s, uint64_t ticket, double norms_out[16], dou
  * out[2] seconds resident on the device.  Returns as bssn_poll (EAGAIN while
  * queued or running, ENOTFOUND for an unknown ticket). */
 bssn_status bssn_poll_detail(bssn_server* s, uint64_t ticket, double out[3]);
+/* Which resident requests a step advances.
+ *  - BSSN_SERVE_ALL (the default): every resident request, every step
+ *    (processor sharing).
+ *  - BSSN_SERVE_SHORTEST: shortest remaining work first.  Requests are
+ *    ordered by remaining steps x interior points; the step advances the
+ *    first ones until they hold at least min_points interior points (at
+ *    least one request).  The others stay resident on the device and wait.
+ *    The set changes only when a request is admitted or retired.
+ * Each request's results are the same under either policy: the per-point
+ * arithmetic does not depend on which members share a step.  EINVAL for an
+ * unknown policy or min_points < 0. */
+enum { BSSN_SERVE_ALL = 0, BSSN_SERVE_SHORTEST = 1 };
+bssn_status bssn_server_set_policy(bssn_server* s, int32_t policy, double min_points);
+/* The selection of BSSN_SERVE_SHORTEST on host arrays (no device work): of n
+ * requests with remaining_work[i] and points[i], marks selected[i] = 1 for
+ * the ones a step advances, 0 for the others; returns how many. */
+int32_t bssn_serve_select(int32_t n, const double* remaining_work, const double* points, double min_points,
+                          int32_t* selected);
 /* out[0] completed, [1] failed, [2] queued, [3] resident, [4] interior
  * point-updates done, [5] seconds spent stepping, [6] seconds since create,
  * [7] bytes of the budget in use. */

@@ -25,6 +25,7 @@ SLICING = {"1+log": 0, "harmonic": 1, "geodesic": 2}
 SHIFT = {"gamma-driver": 0, "frozen": 1}
 PRECISION = {"fp64": 0, "mixed": 1, "ff": 2}
 ID_KIND = {"flat": 0, "gauge_wave": 1, "bl": 2, "kasner": 3}
+SERVE_POLICY = {"all": 0, "shortest": 1}
 STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "EAGAIN", 5: "ETIMEOUT",
           6: "ENOTFOUND", 7: "EFAILED"}
 
@@ -175,6 +176,7 @@ _SIGS += [
     ("bssn_batch_step", [ctypes.c_void_p, ctypes.c_int32], ctypes.c_int),
     ("bssn_batch_constraints", [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_double)],
      ctypes.c_int),
+    ("bssn_batch_hold", [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32], ctypes.c_int),
     ("bssn_batch_test_stall_tma", [ctypes.c_void_p, ctypes.c_int32], ctypes.c_int),
     ("bssn_batch_tile_count", [], ctypes.c_int32),
     ("bssn_batch_tile_name", [ctypes.c_int32], ctypes.c_char_p),
@@ -190,6 +192,9 @@ _SIGS += [
                    ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     ("bssn_poll_detail", [ctypes.c_void_p, ctypes.c_uint64, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     ("bssn_server_stats", [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+    ("bssn_server_set_policy", [ctypes.c_void_p, ctypes.c_int32, ctypes.c_double], ctypes.c_int),
+    ("bssn_serve_select", [ctypes.c_int32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                           ctypes.c_double, ctypes.POINTER(ctypes.c_int32)], ctypes.c_int32),
     ("bssn_server_destroy", [ctypes.c_void_p], ctypes.c_int),
 ]
 
@@ -389,6 +394,17 @@ def bssn_profile(ctx: int, enable: bool):
     out = (ctypes.c_double * 4)()
     _check(load().bssn_profile(ctypes.c_void_p(ctx), 1 if enable else 0, out))
     return None if enable else (out[0], int(out[1]), out[2], int(out[3]))
+
+
+def bssn_serve_select(remaining_work, points, min_points: float) -> np.ndarray:
+    """The shortest-work-first selection of the server on host arrays: a 0/1
+    array marking the requests one step advances."""
+    n = len(remaining_work)
+    w = _dbl_array([float(v) for v in remaining_work])
+    p = _dbl_array([float(v) for v in points])
+    out = (ctypes.c_int32 * max(n, 1))()
+    load().bssn_serve_select(int(n), w, p, float(min_points), out)
+    return np.array(out[:n], dtype=np.int32)
 
 
 def bssn_constraints_noalloc(params: Params, d_state: int, punctures=(), stream: int = 0) -> np.ndarray:
@@ -645,6 +661,10 @@ class Batch:
     def synchronize(self):
         self.stream.synchronize()
 
+    def hold(self, member: int, hold: bool = True):
+        """Keep the member resident but leave it out of the next steps (hold=False resumes it)."""
+        _check(load().bssn_batch_hold(ctypes.c_void_p(self.handle), int(member), 1 if hold else 0))
+
     def constraints(self, member: int):
         out = (ctypes.c_double * 16)()
         _check(load().bssn_batch_constraints(ctypes.c_void_p(self.handle), int(member), out))
@@ -716,6 +736,13 @@ class Server:
         if st not in (0, 7):
             raise BssnError(st, load().bssn_last_error().decode())
         return out[0], out[1], out[2]
+
+    def set_policy(self, policy: str = "all", min_points: float = 0.0):
+        """Which resident requests a step advances: "all" (every one) or
+        "shortest" (least remaining work first, until they hold min_points
+        interior points)."""
+        code = SERVE_POLICY[policy]
+        _check(load().bssn_server_set_policy(ctypes.c_void_p(self.handle), code, float(min_points)))
 
     def stats(self):
         out = (ctypes.c_double * 8)()

@@ -35,8 +35,8 @@ struct BatchWork {
 };
 
 // Tile configurations of the batched stage: persistent fused kernels (both
-// precisions), one-block-per-tile fused kernels (both precisions), and last
-// the TMA-staged kernel (mixed only).
+// precisions), one-block-per-tile fused kernels (both precisions), the two
+// TMA-staged kernels (mixed only), then the double-word configurations.
 int batch_tile_config_count();
 const char* batch_tile_config_name(int c);
 void batch_tile_shape(int c, int& tx, int& ty, int& tz);
@@ -54,10 +54,13 @@ bool batch_tile_full(int cfg, const Grid& g);
 // error word (a bounded wait of the TMA kernel gave up).
 cudaError_t launch_batch_stage(int cfg, bool mixed, bool full, const MemberDev* mem, const BatchWork* wk,
                                unsigned ntiles, int stage, int* err, cudaStream_t s);
-// TMA-staged form (k_batch_tma.cu)
-void batch_tma_tile_shape(int& tx, int& ty, int& tz);
-cudaError_t prepare_batch_stage_tma();
-cudaError_t launch_batch_stage_tma(const MemberDev* mem, const BatchWork* wk, int stage, int* err,
+// TMA-staged forms (k_batch_tma.cu), variant v: 0 = 32x4x1 tiles with 8
+// staged fields, 1 = 32x8x1 tiles with 11; batch_tma_variant(cfg): the
+// variant of configuration cfg, -1 for the others
+int batch_tma_variant(int cfg);
+void batch_tma_tile_shape(int v, int& tx, int& ty, int& tz);
+cudaError_t prepare_batch_stage_tma(int v);
+cudaError_t launch_batch_stage_tma(int v, const MemberDev* mem, const BatchWork* wk, int stage, int* err,
                                    cudaStream_t s);
 // Boundary of every active member after a stage (Sommerfeld or periodic).
 cudaError_t launch_batch_boundary(bool mixed, const MemberDev* mem, const BatchWork* wk, int stage,

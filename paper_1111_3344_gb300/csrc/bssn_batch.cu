@@ -124,6 +124,7 @@ MemberLayout member_layout(const bssn_params* p, const Grid& g) {
 
 struct Member {
   bool used = false, active = false;
+  bool held = false;  // resident but left out of the steps (bssn_batch_hold)
   bssn_params p{};
   Grid g{};
   MemberLayout L{};
@@ -231,7 +232,9 @@ void fill_member_dev(bssn_batch* b, int id) {
       a.w_thr = M.p.w_fp64_threshold;
       a.mode = mode[s];
       a.stall_polls = b->stall_polls;
-      if (make_stage_tensor_map(M.g, a.src, &D.tmap[s]) != cudaSuccess) b->tma_ok = false;
+      // the box of the batch's TMA variant (32x8x1 tiles: tensor-map variant 1)
+      if (make_stage_tensor_map(M.g, a.src, &D.tmap[s], batch_tma_variant(b->cfg) == 1 ? 1 : 0) != cudaSuccess)
+        b->tma_ok = false;
     }
   }
 }
@@ -252,7 +255,7 @@ cudaError_t rebuild_work(bssn_batch* b) {
   unsigned long long bb = 0;
   for (int id = 0; id < b->maxm; id++) {
     const Member& M = b->m[id];
-    if (!M.used || !M.active) continue;
+    if (!M.used || !M.active || M.held) continue;
     const MemberDev& D = b->h_mem[id];
     const unsigned tiles = (unsigned)D.tiles[0] * D.tiles[1] * D.tiles[2];
     const int v = batch_tile_full(b->cfg, M.g) ? WORK_FULL : WORK_REST;
@@ -368,7 +371,7 @@ bool tile_usable(const bssn_batch* b, int c) {
 // Switch the batch to tile configuration cfg (stream idle): member tables
 // refilled and uploaded, work list and graph rebuilt at the next step.
 cudaError_t apply_cfg(bssn_batch* b, int cfg) {
-  cudaError_t e = batch_tile_is_tma(cfg) ? prepare_batch_stage_tma() : cudaSuccess;
+  cudaError_t e = batch_tile_is_tma(cfg) ? prepare_batch_stage_tma(batch_tma_variant(cfg)) : cudaSuccess;
   if (e != cudaSuccess) return e;
   b->cfg = cfg;
   for (int id = 0; id < b->maxm && e == cudaSuccess; id++)
@@ -448,7 +451,7 @@ bssn_status bssn_batch_create(int32_t precision, int32_t max_members, void* d_po
   b->d_work = (BatchWork*)(b->pool + aup(sizeof(MemberDev) * (size_t)max_members));
   b->d_err = (int*)((char*)b->d_work + aup(NWORK * sizeof(BatchWork)));
   b->cfg = precision == BSSN_FF ? batch_default_tile_ff() : batch_default_tile(precision == BSSN_MIXED);
-  cudaError_t e = batch_tile_is_tma(b->cfg) ? prepare_batch_stage_tma() : cudaSuccess;
+  cudaError_t e = batch_tile_is_tma(b->cfg) ? prepare_batch_stage_tma(batch_tma_variant(b->cfg)) : cudaSuccess;
   if (e == cudaSuccess) e = cudaMemsetAsync(b->d_err, 0, sizeof(int), b->stream);
   if (e == cudaSuccess) e = rebuild_work(b);
   if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
@@ -599,12 +602,43 @@ bssn_status bssn_batch_step(bssn_batch* b, int32_t nsteps) {
   }
   for (int id = 0; id < b->maxm; id++) {
     Member& M = b->m[id];
-    if (M.used && M.active) {
+    if (M.used && M.active && !M.held) {
       M.t += nsteps * M.p.dt;
       M.steps += nsteps;
     }
   }
   return BSSN_OK;
+}
+
+bssn_status bssn_batch_hold(bssn_batch* b, int32_t id, int32_t hold) {
+  if (!b) return bfail(BSSN_EINVAL, "batch is NULL");
+  std::lock_guard<std::mutex> lk(b->mu);
+  if (!member_ok(b, id)) return bfail(BSSN_ENOTFOUND, "no such member");
+  Member& M = b->m[id];
+  const bool h = hold != 0;
+  if (M.held != h && M.active) b->work_dirty = true;
+  M.held = h;
+  return BSSN_OK;
+}
+
+int32_t bssn_serve_select(int32_t n, const double* remaining_work, const double* points, double min_points,
+                          int32_t* selected) {
+  if (n <= 0 || !remaining_work || !points || !selected) return 0;
+  std::vector<int> order(n);
+  for (int i = 0; i < n; i++) order[i] = i;
+  // shortest remaining work first; ties by index, so the choice is deterministic
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int a, int c) { return remaining_work[a] < remaining_work[c]; });
+  for (int i = 0; i < n; i++) selected[i] = 0;
+  double acc = 0.0;
+  int32_t count = 0;
+  for (int i = 0; i < n; i++) {
+    if (count > 0 && acc >= min_points) break;
+    selected[order[i]] = 1;
+    acc += points[order[i]];
+    count++;
+  }
+  return count;
 }
 
 bssn_status bssn_batch_constraints(bssn_batch* b, int32_t id, double out[16]) {
@@ -709,8 +743,10 @@ bssn_status bssn_batch_autotune(bssn_batch* b, int32_t reps, int32_t* best, doub
 // Continuous batching: a scheduler thread owns a batch.  At every step
 // boundary it admits queued requests (in arrival order, skipping any that do
 // not fit) while their register bytes fit in the HBM budget and the batch has
-// a slot, sets their initial data on the device, advances every resident
-// evolution one RK4 step in one batched graph replay, and retires the ones
+// a slot, sets their initial data on the device, advances the resident
+// evolutions one RK4 step in one batched graph replay (every one of them, or
+// under the shortest-work-first policy the ones with the least work left,
+// the others held), and retires the ones
 // that reached their step count: their constraint norms are read back, a
 // NaN/Inf marks only that request failed, and their registers return to the
 // pool.  State stays on the device from admission to retirement.
@@ -746,6 +782,7 @@ struct Act {
   double t_submit;
   long long points;  // interior points
   double t_admit;
+  bool held;  // left out of the steps by the shortest-work-first policy
 };
 
 }  // namespace
@@ -761,6 +798,9 @@ struct bssn_server {
   std::thread th;
   std::atomic<bool> stop{false};
   uint64_t next_ticket = 1;
+  // which resident requests a step advances (bssn_server_set_policy)
+  int policy = BSSN_SERVE_ALL;
+  double min_points = 0.0;
   // statistics
   double t_start = 0.0, busy = 0.0;
   double point_updates = 0.0;
@@ -837,7 +877,7 @@ void scheduler(bssn_server* S) {
         continue;
       }
       Act a{r.ticket, r.nsteps, r.bytes, r.t_submit,
-            (long long)r.p.n[0] * r.p.n[1] * r.p.n[2], now_s()};
+            (long long)r.p.n[0] * r.p.n[1] * r.p.n[2], now_s(), false};
       if (a.remaining <= 0) {
         retire(S, id, a);
         continue;
@@ -846,10 +886,33 @@ void scheduler(bssn_server* S) {
       S->active[id] = a;
     }
     std::vector<std::pair<int, Act>> done;
+    std::vector<std::pair<int, bool>> holds;  // members whose hold changes
     {
       std::lock_guard<std::mutex> lk(S->mu);
       if (S->active.empty()) continue;
+      // shortest remaining work first: advance the resident requests with the
+      // least work left (steps x interior points) until they hold min_points
+      // interior points; the others stay resident and wait
+      const int n = (int)S->active.size();
+      std::vector<double> work(n), pts(n);
+      std::vector<int32_t> sel(n, 1);
+      int i = 0;
+      for (auto& kv : S->active) {
+        work[i] = (double)kv.second.remaining * (double)kv.second.points;
+        pts[i] = (double)kv.second.points;
+        i++;
+      }
+      if (S->policy == BSSN_SERVE_SHORTEST) bssn_serve_select(n, work.data(), pts.data(), S->min_points, sel.data());
+      i = 0;
+      for (auto& kv : S->active) {
+        const bool h = sel[i++] == 0;
+        if (h != kv.second.held) {
+          kv.second.held = h;
+          holds.emplace_back(kv.first, h);
+        }
+      }
     }
+    for (auto& hc : holds) bssn_batch_hold(S->batch, hc.first, hc.second ? 1 : 0);
     // ---- one RK4 step for every resident evolution
     const double t0 = now_s();
     bssn_status st = bssn_batch_step(S->batch, 1);
@@ -864,6 +927,10 @@ void scheduler(bssn_server* S) {
         break;
       }
       for (auto it = S->active.begin(); it != S->active.end();) {
+        if (it->second.held) {
+          ++it;
+          continue;
+        }
         S->point_updates += (double)it->second.points;
         if (--it->second.remaining <= 0) {
           done.push_back(*it);
@@ -943,6 +1010,16 @@ bssn_status bssn_poll(bssn_server* S, uint64_t ticket, double norms_out[16], dou
   if (norms_out) memcpy(norms_out, it->second.norms, sizeof(it->second.norms));
   if (latency_s) *latency_s = it->second.latency;
   return it->second.status;
+}
+
+bssn_status bssn_server_set_policy(bssn_server* S, int32_t policy, double min_points) {
+  if (!S) return bfail(BSSN_EINVAL, "server is NULL");
+  if (policy != BSSN_SERVE_ALL && policy != BSSN_SERVE_SHORTEST) return bfail(BSSN_EINVAL, "unknown policy");
+  if (!(min_points >= 0.0)) return bfail(BSSN_EINVAL, "min_points must be >= 0");
+  std::lock_guard<std::mutex> lk(S->mu);
+  S->policy = policy;
+  S->min_points = min_points;
+  return BSSN_OK;
 }
 
 bssn_status bssn_poll_detail(bssn_server* S, uint64_t ticket, double out[3]) {

@@ -241,25 +241,33 @@ static const TileCfgB k_tcfg[] = {TCFG(32, 4, 1, 2), TCFG(32, 8, 1, 1)};
 
 constexpr int N_FUSED = (int)(sizeof(k_bcfg) / sizeof(k_bcfg[0]));
 constexpr int N_TILE = (int)(sizeof(k_tcfg) / sizeof(k_tcfg[0]));
-constexpr int C_TMA = N_FUSED + N_TILE;
+constexpr int C_TMA = N_FUSED + N_TILE;  // then C_TMA + 1: the 11-field TMA variant
+constexpr int N_TMA_B = 2;
 
-int batch_tile_config_count() { return C_TMA + 1 + batch_ff_config_count(); }
-int batch_ff_cfg_index(int v) { return C_TMA + 1 + v; }
+int batch_tile_config_count() { return C_TMA + N_TMA_B + batch_ff_config_count(); }
+int batch_ff_cfg_index(int v) { return C_TMA + N_TMA_B + v; }
 int batch_ff_variant(int cfg) {
-  const int v = cfg - (C_TMA + 1);
+  const int v = cfg - (C_TMA + N_TMA_B);
   return (v >= 0 && v < batch_ff_config_count()) ? v : -1;
+}
+int batch_tma_variant(int cfg) {
+  const int v = cfg - C_TMA;
+  return (v >= 0 && v < N_TMA_B) ? v : -1;
 }
 // Default tile of a new batch (the serving loop keeps it): the fastest
 // persistent configuration of the 64-binary batched workload on GB300 -- the
-// TMA-staged kernel for mixed batches, 32x4x1/3 for float64 ones.
-int batch_default_tile(bool mixed) { return mixed ? C_TMA : 2; }
+// eleven-field TMA-staged kernel for mixed batches (30.3 ms per stage over
+// the 64 members against 33.1 for the eight-field one), 32x4x1/3 for float64
+// ones.
+int batch_default_tile(bool mixed) { return mixed ? C_TMA + 1 : 2; }
 // double-word batches: the 64-register one-block-per-tile configuration
 int batch_default_tile_ff() { return batch_ff_cfg_index(0); }
-bool batch_tile_is_tma(int c) { return c == C_TMA; }
+bool batch_tile_is_tma(int c) { return batch_tma_variant(c) >= 0; }
 bool batch_tile_is_per_tile(int c) { return (c >= N_FUSED && c < C_TMA) || batch_ff_variant(c) >= 0; }
 const char* batch_tile_config_name(int c) {
   if (batch_ff_variant(c) >= 0) return batch_ff_config_name(batch_ff_variant(c));
   if (c == C_TMA) return "tma32x4x1/2";
+  if (c == C_TMA + 1) return "tma11_32x8x1/1";
   if (batch_tile_is_per_tile(c)) return k_tcfg[c - N_FUSED].name;
   return (c >= 0 && c < N_FUSED) ? k_bcfg[c].name : "";
 }
@@ -268,8 +276,8 @@ void batch_tile_shape(int c, int& tx, int& ty, int& tz) {
     batch_ff_tile_shape(batch_ff_variant(c), tx, ty, tz);
     return;
   }
-  if (c == C_TMA) {
-    batch_tma_tile_shape(tx, ty, tz);
+  if (batch_tma_variant(c) >= 0) {
+    batch_tma_tile_shape(batch_tma_variant(c), tx, ty, tz);
     return;
   }
   if (batch_tile_is_per_tile(c)) {
@@ -293,7 +301,7 @@ bool batch_tile_full(int cfg, const Grid& g) {
 
 cudaError_t launch_batch_stage(int cfg, bool mixed, bool full, const MemberDev* mem, const BatchWork* wk,
                                unsigned ntiles, int stage, int* err, cudaStream_t s) {
-  if (cfg == C_TMA && mixed) return launch_batch_stage_tma(mem, wk, stage, err, s);
+  if (batch_tma_variant(cfg) >= 0 && mixed) return launch_batch_stage_tma(batch_tma_variant(cfg), mem, wk, stage, err, s);
   if (batch_tile_is_per_tile(cfg) && batch_ff_variant(cfg) < 0) {
     const TileCfgB& c = k_tcfg[cfg - N_FUSED];
     if (ntiles == 0) return cudaSuccess;

@@ -4,7 +4,8 @@
 //
 // Each block takes tiles t = blockIdx.x, blockIdx.x + gridDim.x, ... of the
 // batch's work list.  Per tile, thread 0 reads the member's arguments into
-// shared memory, then issues the eight tensor loads of the tile's boxes with
+// shared memory, then issues the tensor loads of the tile's boxes (one per
+// staged field: 8 on 32x4x1 tiles, or 11 with beta^i on 32x8x1 tiles) with
 // the member's tensor map for this stage (held in the member table in device
 // memory, written by the host before the launch), all completing on one
 // mbarrier whose phase alternates from tile to tile.  Every thread then
@@ -33,7 +34,8 @@ __device__ __forceinline__ int find_member_tma(const unsigned* __restrict__ base
   return lo;
 }
 
-__global__ void __launch_bounds__(TTX * TTY * TTZ, 2)
+template <typename Sh, int MINB>
+__global__ void __launch_bounds__(Sh::TX * Sh::TY * Sh::TZ, MINB)
     batch_stage_tma_kernel(const MemberDev* __restrict__ mem, const BatchWork* __restrict__ wk, int stage,
                            int* __restrict__ err) {
   extern __shared__ __align__(128) float smem_raw[];
@@ -44,7 +46,7 @@ __global__ void __launch_bounds__(TTX * TTY * TTZ, 2)
   __shared__ unsigned slocal;
   __shared__ const CUtensorMap* smap;
   float* smem = smem_raw + ((128 - (smem_addr(smem_raw) & 127)) & 127) / sizeof(float);
-  const int tid = threadIdx.x + TTX * (threadIdx.y + TTY * threadIdx.z);
+  const int tid = threadIdx.x + Sh::TX * (threadIdx.y + Sh::TY * threadIdx.z);
   const unsigned bar = smem_addr(&mbar);
   if (tid == 0) mbar_init(bar);
   const unsigned total = wk->total_tiles;
@@ -77,14 +79,14 @@ __global__ void __launch_bounds__(TTX * TTY * TTZ, 2)
     lt /= (unsigned)stile[0];
     const int by = (int)(lt % (unsigned)stile[1]);
     const int bz = (int)(lt / (unsigned)stile[1]);
-    const int ii0 = bx * TTX, jj0 = by * TTY, kk0 = bz * TTZ;
+    const int ii0 = bx * Sh::TX, jj0 = by * Sh::TY, kk0 = bz * Sh::TZ;
     const bool stall = sa.stall_polls > 0;  // test hook: no copy, short wait
     if (tid == 0) {
       // the map was written through the generic proxy (a copy from the host)
       asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(smap) : "memory");
       // the boxes were last read through the generic proxy; the loads write them
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      if (!stall) issue_staged_loads(smap, bar, smem, ii0, jj0, kk0);
+      if (!stall) issue_staged_loads<Sh>(smap, bar, smem, ii0, jj0, kk0);
     }
     const bool ok = mbar_wait(bar, phase, stall ? (long long)sa.stall_polls : WAIT_LIMIT);
     if (__syncthreads_or(!ok)) {
@@ -99,14 +101,14 @@ __global__ void __launch_bounds__(TTX * TTY * TTZ, 2)
     const int ii = ii0 + ti, jj = jj0 + tj, kk = kk0 + tk;
     if (ii < sg.n0 && jj < sg.n1 && kk < sg.n2) {
       const int i = ii + GH, j = jj + GH, k = kk + GH;
-      TileAcc acc;
+      TileAccT<Sh> acc;
       acc.st = sa.src;
       acc.id = lin(sg, i, j, k);
       acc.fs = sg.fstride;
       acc.sd[0] = 1;
       acc.sd[1] = sg.pitch;
       acc.sd[2] = sg.plane;
-      acc.sm = smem + ((tk + GH) * BYP + (tj + GH)) * BXP + (ti + GH);
+      acc.sm = smem + ((tk + GH) * Sh::BY + (tj + GH)) * Sh::BX + (ti + GH);
       stage_point_mixed_acc(sg, sa, acc, ii, jj, kk);
     }
   }
@@ -114,30 +116,46 @@ __global__ void __launch_bounds__(TTX * TTY * TTZ, 2)
 
 }  // namespace
 
-void batch_tma_tile_shape(int& tx, int& ty, int& tz) {
-  tx = TTX;
-  ty = TTY;
-  tz = TTZ;
+// variant 0: 32x4x1 tiles, 8 staged fields, two blocks per SM; 1: 32x8x1
+// tiles, 11 staged fields (beta^i too), one block per SM
+using BatchTma0 = TmaShape<4>;
+using BatchTma1 = TmaShape<8, 1, 11>;
+
+void batch_tma_tile_shape(int v, int& tx, int& ty, int& tz) {
+  tx = 32;
+  ty = v == 1 ? BatchTma1::TY : BatchTma0::TY;
+  tz = 1;
 }
 
 // Dynamic shared memory above the default limit; called when the batch
 // selects this kernel, outside graph capture.
-cudaError_t prepare_batch_stage_tma() {
-  return cudaFuncSetAttribute(batch_stage_tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+cudaError_t prepare_batch_stage_tma(int v) {
+  if (v == 1)
+    return cudaFuncSetAttribute(batch_stage_tma_kernel<BatchTma1, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                BatchTma1::SMEM);
+  return cudaFuncSetAttribute(batch_stage_tma_kernel<BatchTma0, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              BatchTma0::SMEM);
 }
 
-cudaError_t launch_batch_stage_tma(const MemberDev* mem, const BatchWork* wk, int stage, int* err,
-                                   cudaStream_t s) {
-  const int bytes = SMEM_BYTES;
+template <typename Sh, int MINB>
+static cudaError_t launch_tma_b(const MemberDev* mem, const BatchWork* wk, int stage, int* err, cudaStream_t s) {
+  const int bytes = Sh::SMEM;
   int dev = 0, sms = 0, per = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e == cudaSuccess)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batch_stage_tma_kernel, TTX * TTY * TTZ, bytes);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batch_stage_tma_kernel<Sh, MINB>,
+                                                      Sh::TX * Sh::TY * Sh::TZ, bytes);
   if (e != cudaSuccess) return e;
   if (per < 1) per = 1;
-  batch_stage_tma_kernel<<<sms * per, dim3(TTX, TTY, TTZ), bytes, s>>>(mem, wk, stage, err);
+  batch_stage_tma_kernel<Sh, MINB><<<sms * per, dim3(Sh::TX, Sh::TY, Sh::TZ), bytes, s>>>(mem, wk, stage, err);
   return cudaGetLastError();
+}
+
+cudaError_t launch_batch_stage_tma(int v, const MemberDev* mem, const BatchWork* wk, int stage, int* err,
+                                   cudaStream_t s) {
+  return v == 1 ? launch_tma_b<BatchTma1, 1>(mem, wk, stage, err, s)
+                : launch_tma_b<BatchTma0, 2>(mem, wk, stage, err, s);
 }
 
 }  // namespace bssn

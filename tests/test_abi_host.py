@@ -88,3 +88,41 @@ def test_batch_table_bytes_grow_with_members():
     assert (t64 - t2) >= 62 * 4 * 128  # at least the four 128-byte tensor maps per member
     assert int(lib.bssn_batch_table_bytes(256)) > t64
     assert int(lib.bssn_batch_table_bytes(0)) == 0 and int(lib.bssn_batch_table_bytes(257)) == 0
+
+
+def _select_reference(work, pts, min_points):
+    """The shortest-work-first rule written out: order by remaining work (ties
+    by index), take requests until their points reach min_points, at least
+    one."""
+    order = sorted(range(len(work)), key=lambda i: (work[i], i))
+    sel, acc = [0] * len(work), 0.0
+    for k, i in enumerate(order):
+        if k > 0 and acc >= min_points:
+            break
+        sel[i] = 1
+        acc += pts[i]
+    return sel
+
+
+def test_serve_select_shortest_work_first():
+    """bssn_serve_select, the server's shortest-work-first choice, on host
+    arrays: the shortest request alone when min_points is 0; the shortest
+    ones until they hold min_points; everything when min_points exceeds the
+    total; ties by index; and the rule restated above on seeded random sets."""
+    import numpy as np
+    assert list(B.bssn_serve_select([], [], 1.0)) == []
+    work = [50.0, 10.0, 30.0, 20.0]
+    pts = [5.0, 1.0, 3.0, 2.0]
+    assert list(B.bssn_serve_select(work, pts, 0.0)) == [0, 1, 0, 0]
+    assert list(B.bssn_serve_select(work, pts, 2.5)) == [0, 1, 0, 1]  # 1 + 2 >= 2.5
+    assert list(B.bssn_serve_select(work, pts, 3.0)) == [0, 1, 0, 1]
+    assert list(B.bssn_serve_select(work, pts, 3.5)) == [0, 1, 1, 1]
+    assert list(B.bssn_serve_select(work, pts, 1e9)) == [1, 1, 1, 1]
+    assert list(B.bssn_serve_select([7.0, 7.0, 7.0], [1.0, 1.0, 1.0], 1.5)) == [1, 1, 0]
+    rng = np.random.default_rng(3344)
+    for _ in range(200):
+        n = int(rng.integers(1, 40))
+        w = list(rng.integers(1, 20, n).astype(float))  # repeated values exercise the ties
+        p = list(rng.integers(1, 9, n).astype(float))
+        m = float(rng.uniform(0, sum(p) * 1.2))
+        assert list(B.bssn_serve_select(w, p, m)) == _select_reference(w, p, m)

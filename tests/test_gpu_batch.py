@@ -173,7 +173,12 @@ def _req(n, L=6.0, precision="mixed"):
                   w_fp64_threshold=0.2, r_excise=1.0)
 
 
-def test_server_results_same_alone_and_in_the_mix(torch_cuda):
+@pytest.mark.parametrize("policy", ["all", "shortest"])
+def test_server_results_same_alone_and_in_the_mix(torch_cuda, policy):
+    """Each request's constraint norms are the same bits alone and arriving
+    while another request runs, whether every resident request steps every
+    time or the shortest remaining work goes first (min_points small enough
+    that requests are held while others step)."""
     from paper_1111_3344_gb300.bssn import Server
     reqs = [(24, [1, 0.5, 0.3, 0.0, 0.0], 12), (32, [2, 0.6, 1.0, 0.0, 0.0, 0.4, -1.5, 0.0, 0.0], 5),
             (20, [1, 1.0, 0.0, 0.0, 0.0], 20), (28, [1, 0.7, 0.0, 0.2, 0.0], 8)]
@@ -186,6 +191,7 @@ def test_server_results_same_alone_and_in_the_mix(torch_cuda):
         alone[i] = norms
         s.close()
     s = Server("mixed", budget_bytes=1 << 29)
+    s.set_policy(policy, min_points=20 ** 3)
     long_t = s.submit(_req(24), "bl", reqs[0][1], 400)   # keeps the batch busy
     t0 = time.time()
     while s.stats()["resident"] < 1 and time.time() - t0 < 30:
@@ -200,7 +206,35 @@ def test_server_results_same_alone_and_in_the_mix(torch_cuda):
     assert st == 0
     stats = s.stats()
     assert stats["completed"] == 5 and stats["failed"] == 0 and stats["point_updates"] > 0
+    # every request advanced exactly its own steps
+    assert stats["point_updates"] == 24 ** 3 * 400 + sum(n ** 3 * steps for n, _, steps in reqs)
     s.close()
+
+
+def test_batch_hold_leaves_member_unchanged(torch_cuda):
+    """A held member keeps its state and time while the others step; resumed,
+    it reaches the same bits as a member that was never held."""
+    from paper_1111_3344_gb300.bssn import Batch
+    cs = _members("mixed")[:2]
+    b = Batch("mixed", pool_bytes=1 << 29)
+    ids = [b.add(gpu_params(c)) for c in cs]
+    for m, c in zip(ids, cs):
+        _load(b, m, c)
+    before, t0 = b.get_state(ids[0])
+    b.hold(ids[0])
+    b.step(3)
+    held, t1 = b.get_state(ids[0])
+    assert np.array_equal(before, held) and t1 == t0
+    b.hold(ids[0], False)
+    b.step(2)
+    got = b.get_state(ids[0])[0]
+    b.close()
+    ref = Batch("mixed", pool_bytes=1 << 29)
+    rid = ref.add(gpu_params(cs[0]))
+    _load(ref, rid, cs[0])
+    ref.step(2)
+    assert np.array_equal(ref.get_state(rid)[0], got)
+    ref.close()
 
 
 def test_server_budget_and_failure_isolation(torch_cuda):
@@ -285,16 +319,18 @@ def test_batch_fp64_configurations_agree_bitwise(torch_cuda):
             assert np.array_equal(x, y), names[c]
 
 
-def test_batch_tma_tile_matches_single_grid_tma(torch_cuda):
-    """The TMA-staged batched kernel (mixed): each member's state is the same
-    bit for bit alone and in the mix, and matches the single-grid evolution on
-    the TMA-staged kernel to the mixed parity bar (the same per-point source,
+@pytest.mark.parametrize("tile", ["tma32x4x1/2", "tma11_32x8x1/1"])
+def test_batch_tma_tile_matches_single_grid_tma(torch_cuda, tile):
+    """The TMA-staged batched kernels (mixed; 8 staged fields on 32x4x1 tiles,
+    or 11 on 32x8x1 tiles): each member's state is the same bit for bit alone
+    and in the mix, and matches the single-grid evolution on the same
+    TMA-staged tile to the mixed parity bar (the same per-point source,
     compiled into two kernels whose floating-point contractions may differ);
     the float64 batch refuses the tile."""
     from paper_1111_3344_gb300 import bssn as B
     n_cfg = B.load().bssn_batch_tile_count()
     names = [B.load().bssn_batch_tile_name(c).decode() for c in range(n_cfg)]
-    tma = names.index("tma32x4x1/2")
+    tma = names.index(tile)
     cases = _members("mixed")
     steps = 3
     mix = B.Batch("mixed", pool_bytes=1 << 30)
@@ -303,7 +339,7 @@ def test_batch_tma_tile_matches_single_grid_tma(torch_cuda):
         _load(mix, mid, c)
     mix.set_tile(tma)
     mix.step(steps)
-    single_tma = [B.bssn_tile_name(c) for c in range(B.bssn_tile_count())].index("tma32x4x1/2")
+    single_tma = [B.bssn_tile_name(c) for c in range(B.bssn_tile_count())].index(tile)
     for mid, c in zip(ids, cases):
         got, _ = mix.get_state(mid)
         evo = B.Evolution(gpu_params(c))
