@@ -12,10 +12,12 @@ advanced one RK4 step).
 At N = 1 the same line also carries the rest of the benchmark's metric, each
 part timed with its own CUDA events and clock sample: ``mixed`` (the same
 puncture with float32 stencils and right-hand side, float64 RK4 state),
-``batched`` (64 Brill-Lindquist binaries on grids 48^3..128^3, float64 and
-mixed, a few of their 100 steps) and ``served_sample`` (the first requests of
-the served workload's Poisson stream at 0.8x a capacity measured in the same
-run, with p50/p99 completion latency).
+``batched`` (64 Brill-Lindquist binaries on grids 48^3..128^3, float64,
+mixed and double-word, a few of their 100 steps) and ``served_sample`` (the
+first requests of the served workload's Poisson stream at 0.8x a capacity
+measured in the same run, with p50/p99 completion latency; the server steps
+the shortest remaining work first, at least 2^21 interior points per step,
+unless ``--serve-policy all``).
 
 Launch: ``python bench.py [--gpus N] [--steps K] [--warmup W]`` for N = 1, or
 under torchrun for N > 1 (one independent replica per GPU: the path does not
@@ -940,7 +942,7 @@ def main():
     ap.add_argument("--no-extras", action="store_true",
                     help="puncture workload: print the float64 line only, without the mixed, batched and "
                          "served parts of the metric")
-    ap.add_argument("--serve-policy", choices=["all", "shortest"], default="all",
+    ap.add_argument("--serve-policy", choices=["all", "shortest"], default="shortest",
                     help="server: step every resident request, or the shortest remaining work first")
     ap.add_argument("--serve-min-points", type=float, default=float(1 << 21),
                     help="shortest-first policy: interior points a step advances at least")
