@@ -637,7 +637,7 @@ def served_capacity(reqs, precision, steps=3):
     return pts * steps / (ms * 1e-3) / 1e6, len(sample)
 
 
-def served_run(args, precision, requests):
+def served_run(args, precision, requests, keep_norms=False):
     """Poisson arrivals of puncture evolutions admitted by HBM budget into a
     continuous-batching server: the arrival rate is 0.8x the capacity
     measured on the same request mix just before; reports p50/p99 time from
@@ -662,12 +662,13 @@ def served_run(args, precision, requests):
     for (p, idp, st), gap in zip(reqs, gaps):
         time.sleep(gap)
         tickets.append(srv.submit(p, "bl", idp, st))
-    lats, queued, fails = [], [], 0
+    lats, queued, fails, all_norms = [], [], 0, []
     for t in tickets:
         st, norms, lat = srv.wait(t, timeout=3600)
         lats.append(lat)
         queued.append(srv.detail(t)[1])
         fails += st != 0
+        all_norms.append(norms)
     wall = time.perf_counter() - t0
     clk = clocks.stop()
     stats = srv.stats()
@@ -675,7 +676,8 @@ def served_run(args, precision, requests):
     lats, queued = np.array(lats), np.array(queued)
     p99 = float(np.percentile(lats, 99))
     i99 = int(np.argmin(np.abs(lats - p99)))
-    return {"metric": "served BSSN evolutions: p50/p99 completion latency, aggregate point-updates/s",
+    extra = {"norms": np.array(all_norms)} if keep_norms else {}
+    return {**extra, "metric": "served BSSN evolutions: p50/p99 completion latency, aggregate point-updates/s",
             "value": stats["point_updates"] / wall / 1e6, "unit": "Mpoint-updates/s",
             "busy_value": stats["point_updates"] / stats["busy_s"] / 1e6,
             "p50_s": float(np.percentile(lats, 50)), "p99_s": p99,
@@ -701,6 +703,40 @@ def run_batched(args):
 def run_served(args):
     line = served_run(args, args.precision, args.requests)
     line.update({"n_gpus": 1, "higher_is_better": True, "data": "synthetic"})
+    print(json.dumps(line))
+
+
+def run_precision_served(args):
+    """The served workload's first args.requests requests through the server
+    in float64 and in each of args.variants (mixed, ff), each at 0.8x its own
+    measured capacity (the same seeded arrival gaps scaled by its rate): every
+    request's 16 constraint norms against the same request's float64 norms,
+    and the serving throughput (point-updates over the seconds the server
+    spent stepping, and over wall time) against float64."""
+    variants = [v for v in args.variants.split(",") if v in ("mixed", "ff")]
+    runs = {prec: served_run(args, prec, args.requests, keep_norms=True) for prec in ["fp64"] + variants}
+    ref = runs["fp64"]["norms"]
+    res = {}
+    for prec in variants:
+        r = runs[prec]
+        rel = np.abs(r["norms"] - ref) / np.where(ref != 0, np.abs(ref), np.inf)
+        res[prec] = {"busy_Mpts": r["busy_value"], "wall_Mpts": r["value"],
+                     "busy_speedup_over_fp64": r["busy_value"] / runs["fp64"]["busy_value"],
+                     "p50_s": r["p50_s"], "p99_s": r["p99_s"], "failed": r["failed"],
+                     "max_constraint_norm_rel_diff": float(rel.max()),
+                     "max_rel_diff_full_domain": float(rel[:, :8].max()),
+                     "max_rel_diff_excised": float(rel[:, 8:].max()),
+                     "requests_within_1e-6": int((rel.max(axis=1) <= 1e-6).sum()),
+                     "clocks": r["clocks"]}
+    f = runs["fp64"]
+    line = {"metric": "served reduced-precision forms vs float64: per-request constraint-norm relative "
+                      "difference, serving throughput",
+            "workload": f"first {args.requests} requests of the served stream (seed 3344), each form at 0.8x "
+                        f"its own measured capacity, policy {args.serve_policy}",
+            "requests": args.requests, "bar": "constraint norms within 1e-6 relative of the float64 run",
+            "fp64": {"busy_Mpts": f["busy_value"], "wall_Mpts": f["value"], "p50_s": f["p50_s"],
+                     "p99_s": f["p99_s"], "failed": f["failed"], "clocks": f["clocks"]},
+            "variants": res, "n_gpus": 1, "data": "synthetic"}
     print(json.dumps(line))
 
 
@@ -931,6 +967,7 @@ def main():
                     help="default: mixed for the served workload (its configuration), float64 otherwise")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", choices=["puncture", "batched", "served", "precision", "precision_batched",
+                                           "precision_served",
                                            "analysis"],
                     default="puncture",
                     help="puncture: the benchmark line (single 128^3 puncture); batched / served: "
@@ -970,6 +1007,8 @@ def main():
         run_precision(args)
     elif args.workload == "precision_batched":
         run_precision_batched(args)
+    elif args.workload == "precision_served":
+        run_precision_served(args)
     elif args.workload == "analysis":
         run_analysis(args)
     else:
