@@ -78,6 +78,7 @@ ORACLE_FLOP_PER_POINT_RHS = 5395 + 7874 + 299
 STAGE_TRAFFIC_PER_POINT = {
     ("fp64", "32x4x1/1"): 954.5,       # stage_fp64_blocks_kernel: 8006.6 MB per step
     ("mixed", "tma32x4x1/2"): 565.3,   # stage_mixed_tma_kernel, 8 staged fields: 4741.9 MB per step
+    ("mixed", "tma11_32x8x1/1"): 565.4,  # stage_mixed_tma_kernel, 11 staged fields: 4742.4 MB per step
 }
 # Float64 work per interior point of the analysis kernels (DADD + DMUL + 2 DFMA
 # from ncu instruction counts at 96^3).  psi4 and constraints include the
