@@ -34,6 +34,31 @@ struct BatchWork {
   unsigned long long bc_base[BATCH_MAX + 1];
 };
 
+// The boundary work list of a batch copied to shared memory by every block of
+// a boundary kernel (prefix sums of the boundary items and the member of each
+// slot, at most 3 KB), so that the member search of each item reads shared
+// memory instead of a chain of dependent global loads.
+struct BcList {
+  unsigned long long base[BATCH_MAX + 1];
+  int member[BATCH_MAX];
+};
+// every thread of the (one-dimensional) block calls this before its item loop
+__device__ __forceinline__ void load_bc_list(BcList& L, const BatchWork* __restrict__ wk, int count) {
+  for (int i = threadIdx.x; i <= count; i += blockDim.x) L.base[i] = wk->bc_base[i];
+  for (int i = threadIdx.x; i < count; i += blockDim.x) L.member[i] = wk->member[i];
+  __syncthreads();
+}
+// slot of boundary item t: the largest slot with base[slot] <= t
+__device__ __forceinline__ int find_bc(const BcList& L, int count, unsigned long long t) {
+  int lo = 0, hi = count;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (L.base[mid] <= t) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
 // Tile configurations of the batched stage: persistent fused kernels (both
 // precisions), one-block-per-tile fused kernels (both precisions), the two
 // TMA-staged kernels (mixed only), then the double-word configurations.

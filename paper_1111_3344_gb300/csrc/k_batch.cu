@@ -24,17 +24,6 @@ __device__ __forceinline__ int find_member(const unsigned* base, int count, unsi
   return lo;
 }
 
-__device__ __forceinline__ int find_member64(const unsigned long long* base, int count,
-                                             unsigned long long t) {
-  int lo = 0, hi = count;
-  while (hi - lo > 1) {
-    const int mid = (lo + hi) >> 1;
-    if (base[mid] <= t) lo = mid;
-    else hi = mid;
-  }
-  return lo;
-}
-
 template <int TX, int TY, int TZ, int MINB>
 __global__ void __launch_bounds__(TX * TY * TZ, MINB)
     batch_stage_kernel(const MemberDev* __restrict__ mem, const BatchWork* __restrict__ wk, int stage) {
@@ -171,13 +160,15 @@ __global__ void __launch_bounds__(TX * TY * TZ, MINB)
 template <bool MIXED>
 __global__ void batch_boundary_kernel(const MemberDev* __restrict__ mem, const BatchWork* __restrict__ wk,
                                       int stage) {
+  __shared__ BcList L;
   const unsigned long long total = wk->total_bc;
   const int count = wk->count;
+  load_bc_list(L, wk, count);
   for (unsigned long long t = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
        t += (unsigned long long)gridDim.x * blockDim.x) {
-    const int slot = find_member64(wk->bc_base, count, t);
-    const MemberDev& M = mem[wk->member[slot]];
-    const unsigned long long local = t - wk->bc_base[slot];
+    const int slot = find_bc(L, count, t);
+    const MemberDev& M = mem[L.member[slot]];
+    const unsigned long long local = t - L.base[slot];
     if (M.g.periodic) {
       const unsigned q = (unsigned)local;
       if constexpr (MIXED) {

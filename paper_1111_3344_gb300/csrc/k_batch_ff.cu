@@ -64,18 +64,15 @@ __global__ void __launch_bounds__(32 * TY * TZ, MINB)
 
 __global__ void batch_boundary_ff_kernel(const MemberDev* __restrict__ mem, const BatchWork* __restrict__ wk,
                                          int stage) {
+  __shared__ BcList L;
   const unsigned long long total = wk->total_bc;
   const int count = wk->count;
+  load_bc_list(L, wk, count);
   for (unsigned long long t = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
        t += (unsigned long long)gridDim.x * blockDim.x) {
-    int lo = 0, hi = count;
-    while (hi - lo > 1) {
-      const int mid = (lo + hi) >> 1;
-      if (wk->bc_base[mid] <= t) lo = mid;
-      else hi = mid;
-    }
-    const MemberDev& M = mem[wk->member[lo]];
-    const unsigned q = (unsigned)(t - wk->bc_base[lo]);
+    const int lo = find_bc(L, count, t);
+    const MemberDev& M = mem[L.member[lo]];
+    const unsigned q = (unsigned)(t - L.base[lo]);
     const StageArgsFF& a = M.aff[stage];
     if (M.g.periodic) {
       // the copy moves 8-byte values whatever they hold
