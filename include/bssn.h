@@ -364,8 +364,8 @@ bssn_status bssn_batch_constraints(bssn_batch* b, int32_t member, double out[16]
  * not change: a held member resumes from the same state.  ENOTFOUND for an
  * unknown member. */
 bssn_status bssn_batch_hold(bssn_batch* b, int32_t member, int32_t hold);
-/* Tile configurations of the batched stage, each one launch per RK4 stage over
- * every active member's tiles:
+/* Tile configurations of the batched stage, each but "members" one launch per
+ * RK4 stage over every active member's tiles:
  *   "TXxTYxTZ/B"     persistent kernels (resident blocks loop over the tiles);
  *   "tilesTXxTYxTZ/B" one block per tile (no loop, fewer register spills; the
  *                    graph is captured again when the membership changes);
@@ -374,11 +374,19 @@ bssn_status bssn_batch_hold(bssn_batch* b, int32_t member, int32_t hold);
  *                    only; BSSN_EINVAL for float64);
  *   "tma11_32x8x1/1" the same on 32x8x1 tiles, staging beta^i as well
  *                    (one block per SM);
+ *   "members"        each member's stages and boundaries launched with the
+ *                    single-grid kernels (float64 "32x4x1/1", mixed
+ *                    "tma11_32x8x1/1", double-word "ffrows32x4x1/8"), the
+ *                    members' chains side by side on 16 auxiliary streams in
+ *                    one captured graph, so that one member's boundary
+ *                    overlaps another's stage (a launch per member per stage,
+ *                    not one per stage; each member gets the same bits as a
+ *                    single-grid evolution on that tile);
  *   "fftiles32x4x1/MF+MR" (last) the double-word batches' one-block-per-tile
  *                    kernels (register caps of the full-tile and the
  *                    every-stencil kernel).
- * A new batch starts on "tma11_32x8x1/1" (mixed), "32x4x1/3" (float64) or the
- * first double-word configuration (double-word).  A
+ * A new batch starts on "members" (float64 and mixed) or the first
+ * double-word configuration (double-word).  A
  * tensor-load wait that gives up (bounded) makes the next
  * bssn_batch_get_state or bssn_batch_constraints return BSSN_ETIMEOUT. */
 int32_t bssn_batch_tile_count(void);

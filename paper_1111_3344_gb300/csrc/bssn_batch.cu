@@ -156,6 +156,13 @@ struct bssn_batch {
   int cfg = 0;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
+  // per-member configuration: auxiliary streams the members' launch chains
+  // are spread over, and the events that fork them from and join them to
+  // the batch's stream (made when the configuration is first selected)
+  static constexpr int NAUX = 16;
+  cudaStream_t aux[NAUX] = {};
+  cudaEvent_t ev_fork = nullptr, ev_join[NAUX] = {};
+  bool aux_ok = false;
   std::mutex mu;  // guards everything above against concurrent API calls
 };
 
@@ -233,7 +240,8 @@ void fill_member_dev(bssn_batch* b, int id) {
       a.mode = mode[s];
       a.stall_polls = b->stall_polls;
       // the box of the batch's TMA variant (32x8x1 tiles: tensor-map variant 1)
-      if (make_stage_tensor_map(M.g, a.src, &D.tmap[s], batch_tma_variant(b->cfg) == 1 ? 1 : 0) != cudaSuccess)
+      const bool box8 = batch_tma_variant(b->cfg) == 1 || batch_tile_is_members(b->cfg);
+      if (make_stage_tensor_map(M.g, a.src, &D.tmap[s], box8 ? 1 : 0) != cudaSuccess)
         b->tma_ok = false;
     }
   }
@@ -280,7 +288,7 @@ cudaError_t rebuild_work(bssn_batch* b) {
   b->work_dirty = false;
   // the one-block-per-tile kernels are captured with the lists' tile counts as
   // their grids: the graph is made again for the new composition
-  if (batch_tile_is_per_tile(b->cfg)) {
+  if (batch_tile_is_per_tile(b->cfg) || batch_tile_is_members(b->cfg)) {
     if (b->exec) {
       cudaGraphExecDestroy(b->exec);
       b->exec = nullptr;
@@ -293,11 +301,101 @@ cudaError_t rebuild_work(bssn_batch* b) {
   return cudaMemcpyAsync(b->d_work, b->h_work, sizeof(b->h_work), cudaMemcpyHostToDevice, b->stream);
 }
 
+// ---- per-member configuration
+// the single-grid configurations it launches (looked up by name once)
+int single_fp64_cfg() {
+  static int c = -1;
+  if (c < 0)
+    for (int q = 0; q < tile_config_count(); q++)
+      if (!strcmp(tile_config_name(q), "32x4x1/1")) c = q;
+  return c < 0 ? 0 : c;
+}
+int single_ff_cfg() {
+  static int c = -1;
+  if (c < 0)
+    for (int q = 0; q < ff_config_count(); q++)
+      if (!strcmp(ff_config_name(q), "ffrows32x4x1/8")) c = q;
+  return c < 0 ? 0 : c;
+}
+
+cudaError_t ensure_aux(bssn_batch* b) {
+  if (b->aux_ok) return cudaSuccess;
+  cudaError_t e = cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming);
+  for (int k = 0; k < bssn_batch::NAUX && e == cudaSuccess; k++) {
+    e = cudaStreamCreateWithFlags(&b->aux[k], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_join[k], cudaEventDisableTiming);
+  }
+  if (e == cudaSuccess) b->aux_ok = true;
+  return e;
+}
+
+void destroy_aux(bssn_batch* b) {
+  for (int k = 0; k < bssn_batch::NAUX; k++) {
+    if (b->aux[k]) cudaStreamDestroy(b->aux[k]);
+    if (b->ev_join[k]) cudaEventDestroy(b->ev_join[k]);
+  }
+  if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+  b->aux_ok = false;
+}
+
+// member id's stage with the single-grid stage kernel of the batch's precision
+cudaError_t member_stage(bssn_batch* b, int id, int stage, cudaStream_t s) {
+  const MemberDev& D = b->h_mem[id];
+  if (b->precision == BSSN_MIXED) return launch_stage_mixed_tma(D.g, D.amx[stage], D.tmap[stage], b->d_err, s, 2);
+  if (b->precision == BSSN_FF) return launch_stage_ff(D.g, D.aff[stage], s, single_ff_cfg());
+  return launch_stage_fp64(D.g, D.a64[stage], s, single_fp64_cfg());
+}
+
+// member id's boundary after a stage, with the single-grid boundary kernels
+// (the same per-point operations as the batched boundary kernel)
+cudaError_t member_boundary(bssn_batch* b, int id, int stage, cudaStream_t s) {
+  const MemberDev& D = b->h_mem[id];
+  const Grid& g = D.g;
+  if (b->precision == BSSN_MIXED) {
+    const StageArgsMixed& a = D.amx[stage];
+    if (!g.periodic) return launch_sommerfeld_mixed(g, a, a.kshell, s);
+    cudaError_t e = launch_periodic_fill_mixed(g, a.out0, a.out0w, s);
+    return (e == cudaSuccess && a.mode == MODE_LAST) ? launch_periodic_fill(g, a.yn, s) : e;
+  }
+  if (b->precision == BSSN_FF) {
+    const StageArgsFF& a = D.aff[stage];
+    if (!g.periodic) return launch_sommerfeld_ff(g, a, a.kshell, s);
+    // the copy moves 8-byte values whatever they hold
+    cudaError_t e = launch_periodic_fill(g, reinterpret_cast<double*>(a.out0), s);
+    return (e == cudaSuccess && a.mode == MODE_LAST) ? launch_periodic_fill(g, a.yn, s) : e;
+  }
+  const StageArgs& a = D.a64[stage];
+  if (!g.periodic) return launch_sommerfeld(g, a, a.kshell, s, nullptr);
+  return launch_periodic_fill(g, a.mode == MODE_LAST ? a.yn : a.out0, s);
+}
+
+// Stages [s0, s1) of every active member: each member's chain (stage, then its
+// boundary when bc) on auxiliary stream (slot % NAUX), forked from and joined
+// back to the batch's stream, so that different members' kernels overlap.
+cudaError_t launch_members(bssn_batch* b, int s0, int s1, bool bc) {
+  cudaError_t e = cudaEventRecord(b->ev_fork, b->stream);
+  for (int k = 0; k < bssn_batch::NAUX && e == cudaSuccess; k++) e = cudaStreamWaitEvent(b->aux[k], b->ev_fork, 0);
+  const BatchWork& W = b->h_work[WORK_ALL];
+  for (int slot = 0; slot < W.count && e == cudaSuccess; slot++) {
+    cudaStream_t s = b->aux[slot % bssn_batch::NAUX];
+    for (int st = s0; st < s1 && e == cudaSuccess; st++) {
+      e = member_stage(b, W.member[slot], st, s);
+      if (e == cudaSuccess && bc) e = member_boundary(b, W.member[slot], st, s);
+    }
+  }
+  for (int k = 0; k < bssn_batch::NAUX && e == cudaSuccess; k++) {
+    e = cudaEventRecord(b->ev_join[k], b->aux[k]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->ev_join[k], 0);
+  }
+  return e;
+}
+
 // The stage launches of one RK4 stage under configuration cfg: persistent and
 // TMA-staged kernels, one launch over every member; one-block-per-tile
 // kernels, one launch per float64 list (members with full tiles, the others),
 // or one over every member (mixed).
 cudaError_t launch_stage_lists(bssn_batch* b, int cfg, int stage) {
+  if (batch_tile_is_members(cfg)) return launch_members(b, stage, stage + 1, false);
   const bool mixed = b->precision == BSSN_MIXED;
   if (b->precision == BSSN_FF) {
     const int v = batch_ff_variant(cfg);
@@ -331,7 +429,10 @@ cudaError_t capture(bssn_batch* b) {
   cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) return e;
   const bool mixed = b->precision == BSSN_MIXED;
-  for (int s = 0; s < 4 && e == cudaSuccess; s++) {
+  // per-member configuration: each member's whole step (4 stages and their
+  // boundaries) as one chain, the chains side by side
+  if (batch_tile_is_members(b->cfg)) e = launch_members(b, 0, 4, true);
+  for (int s = 0; s < 4 && e == cudaSuccess && !batch_tile_is_members(b->cfg); s++) {
     e = launch_stage_lists(b, b->cfg, s);
     if (e == cudaSuccess)
       e = b->precision == BSSN_FF ? launch_batch_boundary_ff(b->d_mem, b->d_work + WORK_ALL, s, b->stream)
@@ -364,14 +465,26 @@ cudaError_t after_state(bssn_batch* b, Member& M) {
 bool member_ok(bssn_batch* b, int id) { return b && id >= 0 && id < b->maxm && b->m[id].used; }
 
 bool tile_usable(const bssn_batch* b, int c) {
+  if (batch_tile_is_members(c)) return b->precision != BSSN_MIXED || b->tma_ok;
   if ((batch_ff_variant(c) >= 0) != (b->precision == BSSN_FF)) return false;
   return !batch_tile_is_tma(c) || (b->precision == BSSN_MIXED && b->tma_ok);
 }
 
 // Switch the batch to tile configuration cfg (stream idle): member tables
 // refilled and uploaded, work list and graph rebuilt at the next step.
-cudaError_t apply_cfg(bssn_batch* b, int cfg) {
+// What configuration cfg needs before its first launch (outside graph capture):
+// the TMA kernels' shared-memory limit, the per-member configuration's streams.
+cudaError_t prepare_cfg(bssn_batch* b, int cfg) {
   cudaError_t e = batch_tile_is_tma(cfg) ? prepare_batch_stage_tma(batch_tma_variant(cfg)) : cudaSuccess;
+  if (e == cudaSuccess && batch_tile_is_members(cfg)) {
+    e = ensure_aux(b);
+    if (e == cudaSuccess && b->precision == BSSN_MIXED) e = prepare_stage_mixed_tma(2);
+  }
+  return e;
+}
+
+cudaError_t apply_cfg(bssn_batch* b, int cfg) {
+  cudaError_t e = prepare_cfg(b, cfg);
   if (e != cudaSuccess) return e;
   b->cfg = cfg;
   for (int id = 0; id < b->maxm && e == cudaSuccess; id++)
@@ -451,11 +564,12 @@ bssn_status bssn_batch_create(int32_t precision, int32_t max_members, void* d_po
   b->d_work = (BatchWork*)(b->pool + aup(sizeof(MemberDev) * (size_t)max_members));
   b->d_err = (int*)((char*)b->d_work + aup(NWORK * sizeof(BatchWork)));
   b->cfg = precision == BSSN_FF ? batch_default_tile_ff() : batch_default_tile(precision == BSSN_MIXED);
-  cudaError_t e = batch_tile_is_tma(b->cfg) ? prepare_batch_stage_tma(batch_tma_variant(b->cfg)) : cudaSuccess;
+  cudaError_t e = prepare_cfg(b, b->cfg);
   if (e == cudaSuccess) e = cudaMemsetAsync(b->d_err, 0, sizeof(int), b->stream);
   if (e == cudaSuccess) e = rebuild_work(b);
   if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
   if (e != cudaSuccess) {
+    destroy_aux(b);
     delete b;
     return bcuda(e, "batch create");
   }
@@ -468,6 +582,7 @@ bssn_status bssn_batch_free(bssn_batch* b) {
   cudaError_t e = cudaStreamSynchronize(b->stream);
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
+  destroy_aux(b);
   delete b;
   if (e != cudaSuccess) return bcuda(e, "batch free");
   return BSSN_OK;
@@ -495,7 +610,11 @@ bssn_status bssn_batch_add(bssn_batch* b, const bssn_params* p, int32_t* member)
   fill_member_dev(b, id);
   cudaError_t e = upload_member(b, id);
   // a member whose tensor maps could not be encoded: fall back to a fused tile
-  if (e == cudaSuccess && !b->tma_ok && batch_tile_is_tma(b->cfg)) {
+  // (the TMA-staged configurations, and the per-member one on the mixed path,
+  // whose stage kernel is the TMA-staged one)
+  const bool needs_maps =
+      batch_tile_is_tma(b->cfg) || (batch_tile_is_members(b->cfg) && b->precision == BSSN_MIXED);
+  if (e == cudaSuccess && !b->tma_ok && needs_maps) {
     e = cudaStreamSynchronize(b->stream);
     if (e == cudaSuccess) e = apply_cfg(b, 0);
   }
@@ -662,7 +781,8 @@ bssn_status bssn_batch_test_stall_tma(bssn_batch* b, int32_t polls) {
   std::lock_guard<std::mutex> lk(b->mu);
   b->stall_polls = polls;
   // the captured graph reads the member tables from device memory: refill
-  // and upload them in stream order, no re-capture
+  // and upload them in stream order, no re-capture (the per-member
+  // configuration holds the arguments in its launches: captured again)
   cudaError_t e = cudaSuccess;
   for (int id = 0; id < b->maxm && e == cudaSuccess; id++)
     if (b->m[id].used) {
@@ -670,6 +790,7 @@ bssn_status bssn_batch_test_stall_tma(bssn_batch* b, int32_t polls) {
       e = upload_member(b, id);
     }
   if (e != cudaSuccess) return bcuda(e, "batch member tables");
+  if (batch_tile_is_members(b->cfg)) b->work_dirty = true;
   return BSSN_OK;
 }
 
@@ -789,6 +910,7 @@ struct Act {
 
 struct bssn_server {
   bssn_batch* batch = nullptr;
+  int device = 0;  // the creating thread's device, made current in the scheduler thread
   size_t budget = 0, used = 0;
   std::mutex mu;
   std::condition_variable cv;
@@ -831,6 +953,15 @@ void retire(bssn_server* S, int id, const Act& a) {
 }
 
 void scheduler(bssn_server* S) {
+  // bind the device (and its primary context) to this thread before any other
+  // CUDA call: encoding a member's tensor maps is a driver call that needs a
+  // current context, and it comes before the first runtime call of an admission
+  if (cudaSetDevice(S->device) != cudaSuccess) {
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->error = "scheduler thread: cudaSetDevice failed";
+    S->stop = true;
+    return;
+  }
   while (!S->stop.load()) {
     // ---- admit at the step boundary
     std::vector<Req> admit;
@@ -962,6 +1093,7 @@ bssn_status bssn_server_create(int32_t precision, size_t hbm_budget_bytes, void*
     return bfail(BSSN_ENOMEM, "host allocation failed");
   }
   S->batch = b;
+  if (cudaGetDevice(&S->device) != cudaSuccess) S->device = 0;
   const size_t cap = pool_bytes - bssn_batch_table_bytes(BSSN_BATCH_MAX_MEMBERS);
   S->budget = std::min(hbm_budget_bytes, cap);
   S->t_start = now_s();

@@ -295,6 +295,8 @@ const char* tile_config_name(int c);
 cudaError_t make_stage_tensor_map(const Grid& g, const float* base, CUtensorMap* out, int variant = 0);
 cudaError_t launch_stage_mixed_tma(const Grid& g, const StageArgsMixed& a, const CUtensorMap& map,
                                    int* err, cudaStream_t s, int variant = 0);
+// sets the TMA variant's dynamic shared-memory limit (call outside graph capture)
+cudaError_t prepare_stage_mixed_tma(int variant);
 // Split mixed stage (k_stage_split.cu): a stencil pass into the derivative
 // register dr (split_slot_count() float fields of the register layout) and an
 // algebra pass.

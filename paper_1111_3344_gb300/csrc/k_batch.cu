@@ -234,23 +234,26 @@ constexpr int N_FUSED = (int)(sizeof(k_bcfg) / sizeof(k_bcfg[0]));
 constexpr int N_TILE = (int)(sizeof(k_tcfg) / sizeof(k_tcfg[0]));
 constexpr int C_TMA = N_FUSED + N_TILE;  // then C_TMA + 1: the 11-field TMA variant
 constexpr int N_TMA_B = 2;
+constexpr int C_MEMB = C_TMA + N_TMA_B;  // per-member launches of the single-grid kernels
 
-int batch_tile_config_count() { return C_TMA + N_TMA_B + batch_ff_config_count(); }
-int batch_ff_cfg_index(int v) { return C_TMA + N_TMA_B + v; }
+int batch_tile_config_count() { return C_MEMB + 1 + batch_ff_config_count(); }
+int batch_ff_cfg_index(int v) { return C_MEMB + 1 + v; }
 int batch_ff_variant(int cfg) {
-  const int v = cfg - (C_TMA + N_TMA_B);
+  const int v = cfg - (C_MEMB + 1);
   return (v >= 0 && v < batch_ff_config_count()) ? v : -1;
 }
+bool batch_tile_is_members(int c) { return c == C_MEMB; }
 int batch_tma_variant(int cfg) {
   const int v = cfg - C_TMA;
   return (v >= 0 && v < N_TMA_B) ? v : -1;
 }
 // Default tile of a new batch (the serving loop keeps it): the fastest
-// persistent configuration of the 64-binary batched workload on GB300 -- the
-// eleven-field TMA-staged kernel for mixed batches (30.3 ms per stage over
-// the 64 members against 33.1 for the eight-field one), 32x4x1/3 for float64
-// ones.
-int batch_default_tile(bool mixed) { return mixed ? C_TMA + 1 : 2; }
+// configuration of the 64-binary batched workload on GB300, for mixed and
+// float64 batches alike the per-member launches of the single-grid kernels
+// (whole steps over the 64 members: mixed 114.4 ms against 146.5 for the
+// eleven-field persistent TMA kernel; float64 843.8 against 867.8 for
+// tiles32x4x1/2 and 884.4 for the persistent 32x4x1/3).
+int batch_default_tile(bool) { return C_MEMB; }
 // double-word batches: the 64-register one-block-per-tile configuration
 int batch_default_tile_ff() { return batch_ff_cfg_index(0); }
 bool batch_tile_is_tma(int c) { return batch_tma_variant(c) >= 0; }
@@ -259,6 +262,7 @@ const char* batch_tile_config_name(int c) {
   if (batch_ff_variant(c) >= 0) return batch_ff_config_name(batch_ff_variant(c));
   if (c == C_TMA) return "tma32x4x1/2";
   if (c == C_TMA + 1) return "tma11_32x8x1/1";
+  if (c == C_MEMB) return "members";
   if (batch_tile_is_per_tile(c)) return k_tcfg[c - N_FUSED].name;
   return (c >= 0 && c < N_FUSED) ? k_bcfg[c].name : "";
 }
@@ -267,8 +271,8 @@ void batch_tile_shape(int c, int& tx, int& ty, int& tz) {
     batch_ff_tile_shape(batch_ff_variant(c), tx, ty, tz);
     return;
   }
-  if (batch_tma_variant(c) >= 0) {
-    batch_tma_tile_shape(batch_tma_variant(c), tx, ty, tz);
+  if (batch_tma_variant(c) >= 0 || c == C_MEMB) {  // members: the tiles of the 11-field TMA kernel
+    batch_tma_tile_shape(c == C_MEMB ? 1 : batch_tma_variant(c), tx, ty, tz);
     return;
   }
   if (batch_tile_is_per_tile(c)) {

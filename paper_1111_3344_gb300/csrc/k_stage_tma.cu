@@ -65,6 +65,11 @@ PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 }
 
 cudaError_t make_stage_tensor_map(const Grid& g, const float* base, CUtensorMap* out, int variant) {
+  // the encoding is a driver call and needs a current context: a thread whose
+  // first CUDA call this is has none until a runtime call binds the primary
+  // context of its device (cudaFree(nullptr) does, and frees nothing)
+  cudaError_t ce = cudaFree(nullptr);
+  if (ce != cudaSuccess) return ce;
   if (!g_encode) {
     cudaDriverEntryPointQueryResult q;
     cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", (void**)&g_encode, 12000,
@@ -84,9 +89,9 @@ cudaError_t make_stage_tensor_map(const Grid& g, const float* base, CUtensorMap*
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
+// dynamic shared memory above the default limit, once per kernel
 template <typename Sh, int MINB>
-static cudaError_t launch_tma(const Grid& g, const StageArgsMixed& a, const CUtensorMap& map, int* err,
-                              cudaStream_t s) {
+static cudaError_t tma_attr() {
   static bool attr = false;
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(stage_mixed_tma_kernel<Sh, MINB>,
@@ -94,6 +99,14 @@ static cudaError_t launch_tma(const Grid& g, const StageArgsMixed& a, const CUte
     if (e != cudaSuccess) return e;
     attr = true;
   }
+  return cudaSuccess;
+}
+
+template <typename Sh, int MINB>
+static cudaError_t launch_tma(const Grid& g, const StageArgsMixed& a, const CUtensorMap& map, int* err,
+                              cudaStream_t s) {
+  cudaError_t e = tma_attr<Sh, MINB>();
+  if (e != cudaSuccess) return e;
   dim3 block(Sh::TX, Sh::TY, Sh::TZ);
   dim3 grid((g.n0 + Sh::TX - 1) / Sh::TX, (g.n1 + Sh::TY - 1) / Sh::TY, (g.n2 + Sh::TZ - 1) / Sh::TZ);
   stage_mixed_tma_kernel<Sh, MINB><<<grid, block, Sh::SMEM, s>>>(map, g, a, err);
@@ -105,6 +118,11 @@ static cudaError_t launch_tma(const Grid& g, const StageArgsMixed& a, const CUte
 // through it); 2: 32 x 8 x 1 tiles staging beta^i as well (eleven fields,
 // 173 KB, one block per SM; the tensor map of variant 1 serves, same box);
 // map: a tensor map made for the same variant
+cudaError_t prepare_stage_mixed_tma(int variant) {
+  if (variant == 2) return tma_attr<TmaShape<8, 1, 11>, 1>();
+  return variant == 1 ? tma_attr<TmaShape<8>, 1>() : tma_attr<TmaShape<4>, 2>();
+}
+
 cudaError_t launch_stage_mixed_tma(const Grid& g, const StageArgsMixed& a, const CUtensorMap& map,
                                    int* err, cudaStream_t s, int variant) {
   if (variant == 2) return launch_tma<TmaShape<8, 1, 11>, 1>(g, a, map, err, s);

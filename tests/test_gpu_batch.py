@@ -300,7 +300,8 @@ def test_batch_fp64_configurations_agree_bitwise(torch_cuda):
     cases = [rows] + _members("fp64")[:3]
     lib = B.load()
     names = [lib.bssn_batch_tile_name(c).decode() for c in range(lib.bssn_batch_tile_count())]
-    fp64_cfgs = [c for c, nm in enumerate(names) if not nm.startswith(("tma", "ff"))]
+    # (the per-member configuration runs the single-grid kernels: its own test)
+    fp64_cfgs = [c for c, nm in enumerate(names) if not nm.startswith(("tma", "ff")) and nm != "members"]
     assert "32x4x1/3" in names and "tiles32x4x1/2" in names
     ref = None
     for c in fp64_cfgs:
@@ -365,3 +366,50 @@ def test_batch_tma_tile_matches_single_grid_tma(torch_cuda, tile):
     with pytest.raises(Exception):
         f64.set_tile(tma)
     f64.close()
+
+
+SINGLE_TILE = {"fp64": "32x4x1/1", "mixed": "tma11_32x8x1/1", "ff": "ffrows32x4x1/8"}
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed", "ff"])
+def test_members_configuration_equals_single_grid(torch_cuda, precision):
+    """The per-member batch configuration launches each member's stages and
+    boundaries with the single-grid kernels, the members' chains side by side
+    on auxiliary streams: every member's state after two steps is the same
+    bits as a single-grid evolution on the same tile, and the same alone as
+    in the mix (members with full and with ragged tiles, a periodic one)."""
+    from paper_1111_3344_gb300 import bssn as B
+    from paper_1111_3344_gb300.bssn import Batch
+    rows = dict(n=(64, 16, 8), xmin=(-8.0, -2.0, -1.0), h=0.25, boundary="sommerfeld", conformal="W",
+                slicing="1+log", shift="gamma-driver", eta=2.0, punctures=[(1.0, 0.05, 0.0, 0.0)],
+                precision=precision, w_fp64_threshold=0.3)
+    cases = [rows] + _members(precision)[:3]
+    lib = B.load()
+    bnames = [lib.bssn_batch_tile_name(c).decode() for c in range(lib.bssn_batch_tile_count())]
+    snames = [B.bssn_tile_name(c) for c in range(B.bssn_tile_count())]
+    b = Batch(precision, pool_bytes=1 << 30)
+    ids = [b.add(gpu_params(cs)) for cs in cases]
+    for m, cs in zip(ids, cases):
+        _load(b, m, cs)
+    b.set_tile(bnames.index("members"))
+    b.step(2)
+    got = [b.get_state(m)[0] for m in ids]
+    b.close()
+    for cs, g in zip(cases, got):
+        evo = B.Evolution(gpu_params(cs))
+        kind, p = _initial(cs)
+        if kind == "state":
+            evo.set_state(p, 0.0)
+        else:
+            evo.set_initial_data(kind, p)
+        B.bssn_set_tile(evo.ctx, snames.index(SINGLE_TILE[precision]))
+        evo.rk4_step(2)
+        assert np.array_equal(evo.get_state()[0], g), cs["n"]
+        evo.close()
+    alone = Batch(precision, pool_bytes=1 << 29)
+    aid = alone.add(gpu_params(cases[1]))
+    _load(alone, aid, cases[1])
+    alone.set_tile(bnames.index("members"))
+    alone.step(2)
+    assert np.array_equal(alone.get_state(aid)[0], got[1])
+    alone.close()
