@@ -474,9 +474,10 @@ def run_ours(args):
         "roofline": roofline,
         "rhs_evaluations_per_s": 4.0 * run["value"] * 1e6,  # four right-hand sides per point-update
         "e2e": run["e2e"],
-        # the split mixed stage is two kernels per stage (stencils, algebra)
+        # the split mixed stage is two kernels per stage (stencils, algebra);
+        # a float64 boundary pass is two (anchor pass, ghost points)
         "gpu_launches": run["stage_launches"] * (2 if run["tile"].startswith("split") else 1)
-                        + run["boundary_launches"],
+                        + run["boundary_launches"] * (2 if args.precision == "fp64" else 1),
         "clocks": run["clocks"],
     }
     if world == 1 and not args.no_extras and args.precision == "fp64":
@@ -568,11 +569,16 @@ def batched_run(args, precision, steps=None, members=None):
     # one-block-per-tile float64 configurations launch the members with full
     # tiles and the others separately
     tname = list(tile_ms)[best]
-    stage_launches = 1
+    stage_launches, bc_launches = 1, 1
     if tname.startswith(("tiles", "fftiles")) and precision in ("fp64", "ff"):
         tx, ty, tz = (int(v) for v in tname.split("tiles")[1].split("/")[0].split("x"))
         full = [tx == 32 and p.n[0] % 32 == 0 and p.n[1] % ty == 0 and p.n[2] % tz == 0 for p in params]
         stage_launches = int(any(full)) + int(not all(full))
+    elif tname == "members":
+        # per member and stage: its stage kernel and its Sommerfeld boundary
+        # (float64: the anchor pass and the ghost-point pass)
+        stage_launches = len(params)
+        bc_launches = len(params) * (2 if precision == "fp64" else 1)
     batch.close()
     del batch
     torch.cuda.empty_cache()
@@ -584,7 +590,8 @@ def batched_run(args, precision, steps=None, members=None):
             "interior_points": pts, "tile": tname,
             "autotune_ms_per_stage": {k: round(v, 3) for k, v in tile_ms.items() if v >= 0},
             "confirm_ms_per_step": {k: round(v, 3) for k, v in step_ms.items()},
-            "launches_per_step": 4 * (stage_launches + 1), "gpu_launches": 4 * (stage_launches + 1) * steps,
+            "launches_per_step": 4 * (stage_launches + bc_launches),
+            "gpu_launches": 4 * (stage_launches + bc_launches) * steps,
             "graph": True, "clocks": clk}
 
 
