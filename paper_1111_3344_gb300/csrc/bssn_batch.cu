@@ -383,9 +383,12 @@ cudaError_t launch_members(bssn_batch* b, int s0, int s1, bool bc) {
       if (e == cudaSuccess && bc) e = member_boundary(b, W.member[slot], st, s);
     }
   }
-  for (int k = 0; k < bssn_batch::NAUX && e == cudaSuccess; k++) {
-    e = cudaEventRecord(b->ev_join[k], b->aux[k]);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->ev_join[k], 0);
+  // join every auxiliary stream back, even after a failed launch, so that the
+  // batch's stream orders whatever was issued on them
+  for (int k = 0; k < bssn_batch::NAUX; k++) {
+    cudaError_t j = cudaEventRecord(b->ev_join[k], b->aux[k]);
+    if (j == cudaSuccess) j = cudaStreamWaitEvent(b->stream, b->ev_join[k], 0);
+    if (e == cudaSuccess) e = j;
   }
   return e;
 }
