@@ -77,7 +77,8 @@ def test_single_grid_wait_timeout_is_reported_and_recovered(torch_cuda):
     evo.close()
 
 
-def test_batch_wait_timeout_is_reported_and_recovered(torch_cuda):
+@pytest.mark.parametrize("tile", ["tma32x4x1/2", "members"])
+def test_batch_wait_timeout_is_reported_and_recovered(torch_cuda, tile):
     from paper_1111_3344_gb300 import bssn as B
     cases = [CASE, dict(CASE, n=(33, 17, 21), xmin=(-3.3, -1.7, -2.1), punctures=[(0.6, 0.2, 0.1, 0.0)])]
     states = [_state(c) for c in cases]
@@ -88,7 +89,7 @@ def test_batch_wait_timeout_is_reported_and_recovered(torch_cuda):
     def make():
         b = B.Batch("mixed", pool_bytes=sum(B.Batch.member_bytes(p) for p in params) + (16 << 20),
                     max_members=4)
-        b.set_tile(names.index("tma32x4x1/2"))
+        b.set_tile(names.index(tile))
         ids = [b.add(p) for p in params]
         for i, s in zip(ids, states):
             b.set_state(i, s, 0.0)
