@@ -364,7 +364,7 @@ bssn_status bssn_batch_constraints(bssn_batch* b, int32_t member, double out[16]
  * not change: a held member resumes from the same state.  ENOTFOUND for an
  * unknown member. */
 bssn_status bssn_batch_hold(bssn_batch* b, int32_t member, int32_t hold);
-/* Tile configurations of the batched stage, each but "members" one launch per
+/* Tile configurations of the batched stage, each but the "members" ones one launch per
  * RK4 stage over every active member's tiles:
  *   "TXxTYxTZ/B"     persistent kernels (resident blocks loop over the tiles);
  *   "tilesTXxTYxTZ/B" one block per tile (no loop, fewer register spills; the
@@ -382,11 +382,15 @@ bssn_status bssn_batch_hold(bssn_batch* b, int32_t member, int32_t hold);
  *                    overlaps another's stage (a launch per member per stage,
  *                    not one per stage; each member gets the same bits as a
  *                    single-grid evolution on that tile);
- *   "fftiles32x4x1/MF+MR" (last) the double-word batches' one-block-per-tile
+ *   "members4", "members1" the same on 4 streams, or one member after
+ *                    another on one stream (different double-word kernels
+ *                    sharing an SM slow each other: double-word batches start
+ *                    on "members1");
+ *   "fftiles32x4x1/MF+MR" (last) the double-word one-block-per-tile
  *                    kernels (register caps of the full-tile and the
  *                    every-stencil kernel).
- * A new batch starts on "members" (float64 and mixed) or the first
- * double-word configuration (double-word).  A
+ * A new batch starts on "members" (float64 and mixed) or "members1"
+ * (double-word).  A
  * tensor-load wait that gives up (bounded) makes the next
  * bssn_batch_get_state or bssn_batch_constraints return BSSN_ETIMEOUT. */
 int32_t bssn_batch_tile_count(void);

@@ -68,11 +68,14 @@ void batch_tile_shape(int c, int& tx, int& ty, int& tz);
 bool batch_tile_is_tma(int c);
 bool batch_tile_is_per_tile(int c);
 int batch_default_tile(bool mixed);
-// The per-member configuration ("members"): each member's stages run as
+// The per-member configurations ("members", "members4", "members1"): each member's stages run as
 // launches of the single-grid stage and boundary kernels (the float64 32x4x1/1
 // tiles, the mixed 11-field TMA kernel, the double-word ffrows32x4x1/8), the
 // members' launch chains side by side on auxiliary streams (bssn_batch.cu).
 bool batch_tile_is_members(int c);
+// auxiliary streams the members' chains of configuration c are spread over
+// ("members" 16, "members4" 4, "members1" 1; 0 for other configurations)
+int batch_members_streams(int c);
 int batch_default_tile_ff();
 // Whether a float64 member has full tiles under configuration cfg (n0 a
 // multiple of 32 = the tile's x extent, n1 and n2 of its y and z extents).

@@ -376,8 +376,9 @@ cudaError_t launch_members(bssn_batch* b, int s0, int s1, bool bc) {
   cudaError_t e = cudaEventRecord(b->ev_fork, b->stream);
   for (int k = 0; k < bssn_batch::NAUX && e == cudaSuccess; k++) e = cudaStreamWaitEvent(b->aux[k], b->ev_fork, 0);
   const BatchWork& W = b->h_work[WORK_ALL];
+  const int nstreams = batch_members_streams(b->cfg);
   for (int slot = 0; slot < W.count && e == cudaSuccess; slot++) {
-    cudaStream_t s = b->aux[slot % bssn_batch::NAUX];
+    cudaStream_t s = b->aux[slot % nstreams];
     for (int st = s0; st < s1 && e == cudaSuccess; st++) {
       e = member_stage(b, W.member[slot], st, s);
       if (e == cudaSuccess && bc) e = member_boundary(b, W.member[slot], st, s);

@@ -234,15 +234,20 @@ constexpr int N_FUSED = (int)(sizeof(k_bcfg) / sizeof(k_bcfg[0]));
 constexpr int N_TILE = (int)(sizeof(k_tcfg) / sizeof(k_tcfg[0]));
 constexpr int C_TMA = N_FUSED + N_TILE;  // then C_TMA + 1: the 11-field TMA variant
 constexpr int N_TMA_B = 2;
-constexpr int C_MEMB = C_TMA + N_TMA_B;  // per-member launches of the single-grid kernels
+// per-member launches of the single-grid kernels, the members' chains on 16,
+// 4 or 1 auxiliary streams
+constexpr int C_MEMB = C_TMA + N_TMA_B;
+constexpr int N_MEMB = 3;
+constexpr int k_memb_streams[N_MEMB] = {16, 4, 1};
 
-int batch_tile_config_count() { return C_MEMB + 1 + batch_ff_config_count(); }
-int batch_ff_cfg_index(int v) { return C_MEMB + 1 + v; }
+int batch_tile_config_count() { return C_MEMB + N_MEMB + batch_ff_config_count(); }
+int batch_ff_cfg_index(int v) { return C_MEMB + N_MEMB + v; }
 int batch_ff_variant(int cfg) {
-  const int v = cfg - (C_MEMB + 1);
+  const int v = cfg - (C_MEMB + N_MEMB);
   return (v >= 0 && v < batch_ff_config_count()) ? v : -1;
 }
-bool batch_tile_is_members(int c) { return c == C_MEMB; }
+bool batch_tile_is_members(int c) { return c >= C_MEMB && c < C_MEMB + N_MEMB; }
+int batch_members_streams(int c) { return batch_tile_is_members(c) ? k_memb_streams[c - C_MEMB] : 0; }
 int batch_tma_variant(int cfg) {
   const int v = cfg - C_TMA;
   return (v >= 0 && v < N_TMA_B) ? v : -1;
@@ -254,8 +259,11 @@ int batch_tma_variant(int cfg) {
 // eleven-field persistent TMA kernel; float64 843.8 against 867.8 for
 // tiles32x4x1/2 and 884.4 for the persistent 32x4x1/3).
 int batch_default_tile(bool) { return C_MEMB; }
-// double-word batches: the 64-register one-block-per-tile configuration
-int batch_default_tile_ff() { return batch_ff_cfg_index(0); }
+// double-word batches: the per-member chains one after another on a single
+// stream (89.1 M point-updates/s over the 64 binaries against 73.9 for
+// fftiles32x4x1/8+8 and 71.7 for chains on 16 streams, where different
+// double-word kernels sharing an SM's instruction cache slow each other)
+int batch_default_tile_ff() { return C_MEMB + 2; }
 bool batch_tile_is_tma(int c) { return batch_tma_variant(c) >= 0; }
 bool batch_tile_is_per_tile(int c) { return (c >= N_FUSED && c < C_TMA) || batch_ff_variant(c) >= 0; }
 const char* batch_tile_config_name(int c) {
@@ -263,6 +271,8 @@ const char* batch_tile_config_name(int c) {
   if (c == C_TMA) return "tma32x4x1/2";
   if (c == C_TMA + 1) return "tma11_32x8x1/1";
   if (c == C_MEMB) return "members";
+  if (c == C_MEMB + 1) return "members4";
+  if (c == C_MEMB + 2) return "members1";
   if (batch_tile_is_per_tile(c)) return k_tcfg[c - N_FUSED].name;
   return (c >= 0 && c < N_FUSED) ? k_bcfg[c].name : "";
 }
@@ -271,8 +281,8 @@ void batch_tile_shape(int c, int& tx, int& ty, int& tz) {
     batch_ff_tile_shape(batch_ff_variant(c), tx, ty, tz);
     return;
   }
-  if (batch_tma_variant(c) >= 0 || c == C_MEMB) {  // members: the tiles of the 11-field TMA kernel
-    batch_tma_tile_shape(c == C_MEMB ? 1 : batch_tma_variant(c), tx, ty, tz);
+  if (batch_tma_variant(c) >= 0 || batch_tile_is_members(c)) {  // members: the 11-field TMA kernel's tiles
+    batch_tma_tile_shape(batch_tile_is_members(c) ? 1 : batch_tma_variant(c), tx, ty, tz);
     return;
   }
   if (batch_tile_is_per_tile(c)) {

@@ -301,7 +301,7 @@ def test_batch_fp64_configurations_agree_bitwise(torch_cuda):
     lib = B.load()
     names = [lib.bssn_batch_tile_name(c).decode() for c in range(lib.bssn_batch_tile_count())]
     # (the per-member configuration runs the single-grid kernels: its own test)
-    fp64_cfgs = [c for c, nm in enumerate(names) if not nm.startswith(("tma", "ff")) and nm != "members"]
+    fp64_cfgs = [c for c, nm in enumerate(names) if not nm.startswith(("tma", "ff", "members"))]
     assert "32x4x1/3" in names and "tiles32x4x1/2" in names
     ref = None
     for c in fp64_cfgs:
@@ -371,8 +371,9 @@ def test_batch_tma_tile_matches_single_grid_tma(torch_cuda, tile):
 SINGLE_TILE = {"fp64": "32x4x1/1", "mixed": "tma11_32x8x1/1", "ff": "ffrows32x4x1/8"}
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed", "ff"])
-def test_members_configuration_equals_single_grid(torch_cuda, precision):
+@pytest.mark.parametrize("precision,tile", [("fp64", "members"), ("mixed", "members"), ("ff", "members"),
+                                            ("ff", "members1"), ("mixed", "members4")])
+def test_members_configuration_equals_single_grid(torch_cuda, precision, tile):
     """The per-member batch configuration launches each member's stages and
     boundaries with the single-grid kernels, the members' chains side by side
     on auxiliary streams: every member's state after two steps is the same
@@ -391,7 +392,7 @@ def test_members_configuration_equals_single_grid(torch_cuda, precision):
     ids = [b.add(gpu_params(cs)) for cs in cases]
     for m, cs in zip(ids, cases):
         _load(b, m, cs)
-    b.set_tile(bnames.index("members"))
+    b.set_tile(bnames.index(tile))
     b.step(2)
     got = [b.get_state(m)[0] for m in ids]
     b.close()
@@ -409,7 +410,7 @@ def test_members_configuration_equals_single_grid(torch_cuda, precision):
     alone = Batch(precision, pool_bytes=1 << 29)
     aid = alone.add(gpu_params(cases[1]))
     _load(alone, aid, cases[1])
-    alone.set_tile(bnames.index("members"))
+    alone.set_tile(bnames.index(tile))
     alone.step(2)
     assert np.array_equal(alone.get_state(aid)[0], got[1])
     alone.close()
