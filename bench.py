@@ -574,7 +574,7 @@ def batched_run(args, precision, steps=None, members=None):
         tx, ty, tz = (int(v) for v in tname.split("tiles")[1].split("/")[0].split("x"))
         full = [tx == 32 and p.n[0] % 32 == 0 and p.n[1] % ty == 0 and p.n[2] % tz == 0 for p in params]
         stage_launches = int(any(full)) + int(not all(full))
-    elif tname == "members":
+    elif tname.startswith("members"):
         # per member and stage: its stage kernel and its Sommerfeld boundary
         # (float64: the anchor pass and the ghost-point pass)
         stage_launches = len(params)
