@@ -81,6 +81,8 @@ struct Pool {
 // Register layout of one member inside its pool block.
 struct MemberLayout {
   size_t yn, ks, s1, s2, ksh;      // float64 path (ks, ksh also double-word)
+  size_t gtab;                     // float64 Sommerfeld: ghost-geometry table (per-member chains)
+  bool has_gtab;
   size_t m32[3], mw[3], ks32, ksw; // mixed path
   size_t f2[3];                    // double-word path: stage buffers (f2[0] the shadow of y_n)
   size_t part, out16, total;
@@ -100,6 +102,8 @@ MemberLayout member_layout(const bssn_params* p, const Grid& g) {
     L.s1 = o; o += regb;
     L.s2 = o; o += regb;
     L.ksh = o; if (som) o += regb;
+    L.has_gtab = som;
+    L.gtab = o; if (som) o += aup(ghost_table_size(g));
   } else if (p->precision == BSSN_FF) {
     L.ks = o; o += regb;
     for (int q = 0; q < 3; q++) {
@@ -365,7 +369,8 @@ cudaError_t member_boundary(bssn_batch* b, int id, int stage, cudaStream_t s) {
     return (e == cudaSuccess && a.mode == MODE_LAST) ? launch_periodic_fill(g, a.yn, s) : e;
   }
   const StageArgs& a = D.a64[stage];
-  if (!g.periodic) return launch_sommerfeld(g, a, a.kshell, s, nullptr);
+  const Member& M = b->m[id];
+  if (!g.periodic) return launch_sommerfeld(g, a, a.kshell, s, M.L.has_gtab ? mptr(b, M, M.L.gtab) : nullptr);
   return launch_periodic_fill(g, a.mode == MODE_LAST ? a.yn : a.out0, s);
 }
 
@@ -613,6 +618,9 @@ bssn_status bssn_batch_add(bssn_batch* b, const bssn_params* p, int32_t* member)
   b->m[id] = M;
   fill_member_dev(b, id);
   cudaError_t e = upload_member(b, id);
+  // float64 Sommerfeld members: the ghost-geometry table of the single-grid
+  // boundary kernels (the per-member chains use them)
+  if (e == cudaSuccess && M.L.has_gtab) e = launch_ghost_table(M.g, mptr(b, M, M.L.gtab), b->stream);
   // a member whose tensor maps could not be encoded: fall back to a fused tile
   // (the TMA-staged configurations, and the per-member one on the mixed path,
   // whose stage kernel is the TMA-staged one)
