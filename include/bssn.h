@@ -407,8 +407,9 @@ bssn_status bssn_batch_autotune(bssn_batch* b, int32_t reps, int32_t* best, doub
  * every block issue no tile copy and give up after that many polls; the next
  * bssn_batch_get_state or bssn_batch_constraints returns BSSN_ETIMEOUT (and
  * clears the error word).  The member tables are re-uploaded in stream order;
- * the captured graph is kept.  polls in [0, 2^20]; 0 restores normal
- * operation. */
+ * the captured graph is kept, except under the per-member configurations,
+ * whose launches carry the arguments themselves: their graph is captured
+ * again at the next step.  polls in [0, 2^20]; 0 restores normal operation. */
 bssn_status bssn_batch_test_stall_tma(bssn_batch* b, int32_t polls);
 
 /* ------------------------------------------------------------- server
@@ -423,7 +424,10 @@ bssn_status bssn_batch_test_stall_tma(bssn_batch* b, int32_t polls);
 bssn_status bssn_server_create(int32_t precision, size_t hbm_budget_bytes, void* d_pool,
                                size_t pool_bytes, void* cuda_stream, bssn_server** out);
 /* Enqueue a request; never blocks.  EINVAL if it alone exceeds the budget or
- * its parameters are bad.  id_kind/id_p/np as for bssn_set_initial_data. */
+ * its parameters are bad.  id_kind/id_p/np as for bssn_set_initial_data.  A
+ * request that finds no free block of the pool at admission waits in the
+ * queue until a resident request retires; with none resident it fails
+ * (bssn_poll returns BSSN_ENOMEM). */
 bssn_status bssn_submit(bssn_server* s, const bssn_params* p, int32_t id_kind, const double* id_p,
                         int32_t np, int32_t nsteps, uint64_t* ticket);
 /* EAGAIN while queued or running; then BSSN_OK (norms_out as bssn_constraints,

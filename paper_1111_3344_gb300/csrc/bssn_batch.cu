@@ -322,6 +322,20 @@ int single_ff_cfg() {
   return c < 0 ? 0 : c;
 }
 
+void destroy_aux(bssn_batch* b) {
+  for (int k = 0; k < bssn_batch::NAUX; k++) {
+    if (b->aux[k]) cudaStreamDestroy(b->aux[k]);
+    if (b->ev_join[k]) cudaEventDestroy(b->ev_join[k]);
+    b->aux[k] = nullptr;
+    b->ev_join[k] = nullptr;
+  }
+  if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+  b->ev_fork = nullptr;
+  b->aux_ok = false;
+}
+
+// the auxiliary streams and events, made once; a partial failure releases
+// what was made, so that a later call starts again from nothing
 cudaError_t ensure_aux(bssn_batch* b) {
   if (b->aux_ok) return cudaSuccess;
   cudaError_t e = cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming);
@@ -329,17 +343,12 @@ cudaError_t ensure_aux(bssn_batch* b) {
     e = cudaStreamCreateWithFlags(&b->aux[k], cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_join[k], cudaEventDisableTiming);
   }
-  if (e == cudaSuccess) b->aux_ok = true;
-  return e;
-}
-
-void destroy_aux(bssn_batch* b) {
-  for (int k = 0; k < bssn_batch::NAUX; k++) {
-    if (b->aux[k]) cudaStreamDestroy(b->aux[k]);
-    if (b->ev_join[k]) cudaEventDestroy(b->ev_join[k]);
+  if (e != cudaSuccess) {
+    destroy_aux(b);
+    return e;
   }
-  if (b->ev_fork) cudaEventDestroy(b->ev_fork);
-  b->aux_ok = false;
+  b->aux_ok = true;
+  return cudaSuccess;
 }
 
 // member id's stage with the single-grid stage kernel of the batch's precision
@@ -1006,7 +1015,10 @@ void scheduler(bssn_server* S) {
         if (id >= 0) bssn_batch_remove(S->batch, id);
         std::lock_guard<std::mutex> lk(S->mu);
         S->used -= r.bytes;
-        if (st == BSSN_ENOMEM) {  // pool fragmented: retry at a later boundary
+        // pool fragmented: retry at a later boundary, once a resident request
+        // has retired; with none resident the pool is empty and a retry would
+        // fail the same way, so the request fails instead
+        if (st == BSSN_ENOMEM && !S->active.empty()) {
           S->queue.push_front(std::move(r));
         } else {
           Res res;
