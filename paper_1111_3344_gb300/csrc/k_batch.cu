@@ -312,7 +312,11 @@ cudaError_t launch_batch_stage(int cfg, bool mixed, bool full, const MemberDev* 
     if (ntiles == 0) return cudaSuccess;
     full = full && !mixed;
     const void* fn = mixed ? c.kmx : (full ? c.k64full : c.k64);
-    const size_t smem = full ? (size_t)11 * (c.ty + 4) * c.tz * 32 * sizeof(double) : 0;
+    const size_t smem = full ? fp64_block_smem(c.ty, c.tz) : 0;
+    if (smem > 48 * 1024) {
+      cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+    }
     dim3 block(c.tx, c.ty, c.tz);
     void* args[] = {(void*)&mem, (void*)&wk, (void*)&stage};
     return cudaLaunchKernel(fn, dim3(ntiles), block, args, smem, s);
@@ -321,11 +325,12 @@ cudaError_t launch_batch_stage(int cfg, bool mixed, bool full, const MemberDev* 
   const BatchCfg& c = k_bcfg[cfg];
   const void* fn = mixed ? c.kmx : c.k64;
   const int threads = c.tx * c.ty * c.tz;
-  // float64 full-block tiles exchange the first differences along z of 11
-  // fields over the block's rows and two halo rows on each side
-  const size_t smem = (!mixed && c.tx == 32) ? (size_t)11 * (c.ty + 4) * c.tz * 32 * sizeof(double) : 0;
+  // float64 full-block tiles exchange first differences through shared memory
+  const size_t smem = (!mixed && c.tx == 32) ? fp64_block_smem(c.ty, c.tz) : 0;
   int dev = 0, sms = 0, per = 0;
-  cudaError_t e = cudaGetDevice(&dev);
+  cudaError_t e = smem > 48 * 1024 ? cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+                                   : cudaSuccess;
+  if (e == cudaSuccess) e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, threads, smem);
   if (e != cudaSuccess) return e;

@@ -132,6 +132,41 @@ __device__ __forceinline__ T dmx_shfl(const A& acc, int f, const P* p, long long
   const T vp2 = lane <= W - 3 ? sp2 : ve;
   return fmaT<T>(T(8), vp1 - vm1, -(vp2 - vm2));
 }
+// The same mixed difference with the four first differences past the ends of
+// the row already formed (full blocks, float64): xe[0..3] hold them at
+// x_0 - 2, x_0 - 1, x_{W-1} + 1, x_{W-1} + 2, in shared memory.
+template <int W, typename T>
+__device__ __forceinline__ T dmx_pre(T v, const T* xe) {
+  const int lane = threadIdx.x & (W - 1);
+  const T sm2 = shflT(v, lane - 2, W);
+  const T sm1 = shflT(v, lane - 1, W);
+  const T sp1 = shflT(v, lane + 1, W);
+  const T sp2 = shflT(v, lane + 2, W);
+  // indices clamped to 0..3 on every lane, so that no lane reads past xe
+  const T vm2 = lane >= 2 ? sm2 : xe[lane < 2 ? lane : 0];
+  const T vm1 = lane >= 1 ? sm1 : xe[1];
+  const T vp1 = lane <= W - 2 ? sp1 : xe[2];
+  const T vp2 = lane <= W - 3 ? sp2 : xe[lane >= W - 2 ? lane - W + 4 : 3];
+  return fmaT<T>(T(8), vp1 - vm1, -(vp2 - vm2));
+}
+
+// x-mixed difference of the q-th of the 11 twice-differenced fields (gt_ij,
+// phi|W, alpha, beta^i) along axis b (1 or 2): from the staged end-of-row
+// values on float64 full blocks, else with the end lanes forming their own.
+template <int W, int YROWS, typename T, typename A, typename P>
+__device__ __forceinline__ T dmx_row(const A& acc, int f, const P* p, long long sb, T v, T i12h, const T* xep,
+                                     int b, int q) {
+  if constexpr (YROWS > 0 && is_f64<T>) return dmx_pre<W>(v, xep + ((b == 2 ? 11 : 0) + q) * 4);
+  else return dmx_shfl<W>(acc, f, p, sb, v, i12h);
+}
+
+// Dynamic shared memory of a float64 full-block stage (32 x ty x tz points):
+// the first differences along z of 11 fields over the block's rows and two
+// halo rows on each side, then per warp the 88 first differences along y and
+// z past the ends of its row (dmx_pre).
+__host__ __device__ constexpr size_t fp64_block_smem(int ty, int tz) {
+  return ((size_t)11 * (ty + 4) * tz * 32 + (size_t)ty * tz * 88) * sizeof(double);
+}
 
 // the same helpers over the plain read-only global path (one field)
 template <typename T, typename S>
@@ -275,6 +310,7 @@ __device__ __forceinline__ void rhs_point_acc(const Grid& g, const A& acc, int i
 
   // ---- D_y D_z through shared memory (full blocks of full rows)
   [[maybe_unused]] T dyz[11];  // gt_ij (6), phi|W, alpha, beta^i (3)
+  [[maybe_unused]] const T* xep = nullptr;  // this warp's 88 end-of-row first differences (float64)
   if constexpr (YROWS > 0 && XSEG == 32 && !is_f32<T>) {
     extern __shared__ double yz_smem[];  // 8-byte slots: float64 or double-word values
     T* yz = reinterpret_cast<T*>(yz_smem);
@@ -295,6 +331,28 @@ __device__ __forceinline__ void rhs_point_acc(const Grid& g, const A& acc, int i
     if (ty >= YROWS - 2) {  // rows y0+YROWS, y0+YROWS+1 above it
 #pragma unroll
       for (int q = 0; q < 11; q++) at(q, ty + 4) = d1u<T>(acc, field_of(q), PF(field_of(q)) + 2 * sy, sz) * i12h;
+    }
+    if constexpr (is_f64<T>) {
+      // The x-mixed differences need, for each of the 11 fields and for y
+      // and z, the first differences at the four points past the ends of
+      // this warp's row: 88 values.  All 32 lanes form them, three rounds of
+      // one value each, into shared memory (item 4 p + e: pair p = field
+      // q + 11 (0 for y, 1 for z), point e = x_0 - 2, x_0 - 1, x_0 + 32,
+      // x_0 + 33), rather than the two lanes at each end of the row with the
+      // other 30 lanes of every such instruction idle.  Same arithmetic.
+      T* xe = yz + 11 * ROWS * ZS * 32 + (tz * YROWS + ty) * 88;
+#pragma unroll
+      for (int r = 0; r < 3; r++) {
+        const int idx = r * 32 + lane;
+        if (idx < 88) {
+          const int pr = idx >> 2, e = idx & 3;
+          const int q = pr < 11 ? pr : pr - 11;
+          const int f = field_of(q);
+          const int dx = (e < 2 ? e - 2 : 30 + e) - lane;  // x offset from this lane's point (unit stride)
+          xe[idx] = d1u<T>(acc, f, PF(f) + dx, pr < 11 ? sy : sz) * i12h;
+        }
+      }
+      xep = xe;
     }
     __syncthreads();
 #pragma unroll
@@ -409,9 +467,9 @@ __device__ __forceinline__ void rhs_point_acc(const Grid& g, const A& acc, int i
             sc = i12h;
 #pragma unroll
             for (int m = 0; m < 6; m++)
-              dd[m] = dmx_shfl<XSEG>(acc, F_GT + m, PF(F_GT + m), SD(F_GT + m, pb), dgt[pb][m], i12h);
-            ddchi[pq] = dmx_shfl<XSEG>(acc, F_CHI, PF(F_CHI), SD(F_CHI, pb), dchi[pb], i12h) * i12h;
-            ddalp[pq] = dmx_shfl<XSEG>(acc, F_ALP, PF(F_ALP), SD(F_ALP, pb), dalp[pb], i12h);
+              dd[m] = dmx_row<XSEG, YROWS>(acc, F_GT + m, PF(F_GT + m), SD(F_GT + m, pb), dgt[pb][m], i12h, xep, pb, m);
+            ddchi[pq] = dmx_row<XSEG, YROWS>(acc, F_CHI, PF(F_CHI), SD(F_CHI, pb), dchi[pb], i12h, xep, pb, 6) * i12h;
+            ddalp[pq] = dmx_row<XSEG, YROWS>(acc, F_ALP, PF(F_ALP), SD(F_ALP, pb), dalp[pb], i12h, xep, pb, 7);
           } else if constexpr (YROWS > 0) {  // (1, 2)
             sc = i12h;
 #pragma unroll
@@ -446,7 +504,8 @@ __device__ __forceinline__ void rhs_point_acc(const Grid& g, const A& acc, int i
             v = d2u<T>(acc, F_BETA + a, PF(F_BETA + a), SD(F_BETA + a, pa), beta[a]);
           } else if constexpr (XSEG > 0 && !is_f32<T>) {
             if (pa == 0)
-              v = dmx_shfl<XSEG>(acc, F_BETA + a, PF(F_BETA + a), SD(F_BETA + a, pb), db[pb][a], i12h);
+              v = dmx_row<XSEG, YROWS>(acc, F_BETA + a, PF(F_BETA + a), SD(F_BETA + a, pb), db[pb][a], i12h, xep,
+                                       pb, 8 + a);
             else if constexpr (YROWS > 0)
               v = dyz[8 + a];
             else
