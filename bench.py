@@ -76,7 +76,7 @@ ORACLE_FLOP_PER_POINT_RHS = 5395 + 7874 + 299
 # by stage-kernel configuration; a configuration without a capture of its
 # current kernel at that size reports null.
 STAGE_TRAFFIC_PER_POINT = {
-    ("fp64", "32x4x1/1"): 954.5,       # stage_fp64_blocks_kernel: 8006.6 MB per step
+    ("fp64", "32x4x1/1"): 937.2,       # stage_fp64_blocks_kernel: 7861.6 MB per step
     ("mixed", "tma32x4x1/2"): 565.3,   # stage_mixed_tma_kernel, 8 staged fields: 4741.9 MB per step
     ("mixed", "tma11_32x8x1/1"): 565.4,  # stage_mixed_tma_kernel, 11 staged fields: 4742.4 MB per step
 }

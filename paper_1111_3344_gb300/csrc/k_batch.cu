@@ -312,7 +312,7 @@ cudaError_t launch_batch_stage(int cfg, bool mixed, bool full, const MemberDev* 
     if (ntiles == 0) return cudaSuccess;
     full = full && !mixed;
     const void* fn = mixed ? c.kmx : (full ? c.k64full : c.k64);
-    const size_t smem = full ? fp64_block_smem(c.ty, c.tz) : 0;
+    const size_t smem = full ? rows_block_smem(c.ty, c.tz, true) : 0;
     if (smem > 48 * 1024) {
       cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       if (e != cudaSuccess) return e;
@@ -326,7 +326,7 @@ cudaError_t launch_batch_stage(int cfg, bool mixed, bool full, const MemberDev* 
   const void* fn = mixed ? c.kmx : c.k64;
   const int threads = c.tx * c.ty * c.tz;
   // float64 full-block tiles exchange first differences through shared memory
-  const size_t smem = (!mixed && c.tx == 32) ? fp64_block_smem(c.ty, c.tz) : 0;
+  const size_t smem = (!mixed && c.tx == 32) ? rows_block_smem(c.ty, c.tz, true) : 0;
   int dev = 0, sms = 0, per = 0;
   cudaError_t e = smem > 48 * 1024 ? cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
                                    : cudaSuccess;

@@ -113,7 +113,11 @@ cudaError_t launch_batch_stage_ff(int v, bool full, const MemberDev* mem, const 
   if (ntiles == 0) return cudaSuccess;
   const FfBatchCfg& c = k_ffcfg[v];
   const void* fn = full ? c.kfull : c.krest;
-  const size_t smem = full ? (size_t)11 * (c.ty + 4) * c.tz * 32 * sizeof(ff) : 0;
+  const size_t smem = full ? rows_block_smem(c.ty, c.tz, false) : 0;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
   void* args[] = {(void*)&mem, (void*)&wk, (void*)&stage};
   return cudaLaunchKernel(fn, dim3(ntiles), dim3(32, c.ty, c.tz), args, smem, s);
 }

@@ -35,7 +35,7 @@ cudaError_t launch_fp64_rows(const Grid& g, const StageArgs& a, cudaStream_t s) 
   dim3 block(32, TY, TZ);
   dim3 grid(g.n0 / 32, (g.n1 + TY - 1) / TY, (g.n2 + TZ - 1) / TZ);
   if (g.n1 % TY == 0 && g.n2 % TZ == 0 && TY >= 2) {
-    constexpr int smem = (int)fp64_block_smem(TY, TZ);
+    constexpr int smem = (int)rows_block_smem(TY, TZ, true);
     if constexpr (smem > 48 * 1024) {  // above the default limit: opt in once
       static bool attr = false;
       if (!attr) {

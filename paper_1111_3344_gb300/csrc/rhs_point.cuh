@@ -133,7 +133,7 @@ __device__ __forceinline__ T dmx_shfl(const A& acc, int f, const P* p, long long
   return fmaT<T>(T(8), vp1 - vm1, -(vp2 - vm2));
 }
 // The same mixed difference with the four first differences past the ends of
-// the row already formed (full blocks, float64): xe[0..3] hold them at
+// the row already formed (float64 full blocks): xe[0..3] hold them at
 // x_0 - 2, x_0 - 1, x_{W-1} + 1, x_{W-1} + 2, in shared memory.
 template <int W, typename T>
 __device__ __forceinline__ T dmx_pre(T v, const T* xe) {
@@ -153,6 +153,9 @@ __device__ __forceinline__ T dmx_pre(T v, const T* xe) {
 // x-mixed difference of the q-th of the 11 twice-differenced fields (gt_ij,
 // phi|W, alpha, beta^i) along axis b (1 or 2): from the staged end-of-row
 // values on float64 full blocks, else with the end lanes forming their own.
+// (Double-word blocks keep the end lanes' own: the 88 values per warp cost
+// them shared memory that their register spills use as L1, and the stage
+// measured 3 % slower, 30 % in the batch.)
 template <int W, int YROWS, typename T, typename A, typename P>
 __device__ __forceinline__ T dmx_row(const A& acc, int f, const P* p, long long sb, T v, T i12h, const T* xep,
                                      int b, int q) {
@@ -160,12 +163,14 @@ __device__ __forceinline__ T dmx_row(const A& acc, int f, const P* p, long long 
   else return dmx_shfl<W>(acc, f, p, sb, v, i12h);
 }
 
-// Dynamic shared memory of a float64 full-block stage (32 x ty x tz points):
-// the first differences along z of 11 fields over the block's rows and two
-// halo rows on each side, then per warp the 88 first differences along y and
-// z past the ends of its row (dmx_pre).
-__host__ __device__ constexpr size_t fp64_block_smem(int ty, int tz) {
-  return ((size_t)11 * (ty + 4) * tz * 32 + (size_t)ty * tz * 88) * sizeof(double);
+// Dynamic shared memory of a float64 or double-word full-block stage (32 x ty
+// x tz points; 8-byte values): the first differences along z of 11 fields
+// over the block's rows and two halo rows on each side, then, for float64
+// (ends), per warp the 88 first differences along y and z past the ends of
+// its row (dmx_pre).
+static_assert(sizeof(ff) == sizeof(double), "double-word values take 8-byte slots");
+__host__ __device__ constexpr size_t rows_block_smem(int ty, int tz, bool ends) {
+  return ((size_t)11 * (ty + 4) * tz * 32 + (ends ? (size_t)ty * tz * 88 : 0)) * sizeof(double);
 }
 
 // the same helpers over the plain read-only global path (one field)
@@ -403,12 +408,13 @@ __device__ __forceinline__ void rhs_point_acc(const Grid& g, const A& acc, int i
           const bool y = pb == 1;
 #pragma unroll
           for (int m = 0; m < 6; m++)
-            dd[m] = dmx_shfl<XSEG>(acc, F_GT + m, PF(F_GT + m), sb, y ? dgt[1][m] : dgt[2][m], i12h);
-          vchi = dmx_shfl<XSEG>(acc, F_CHI, PF(F_CHI), sb, y ? dchi[1] : dchi[2], i12h) * i12h;
-          valp = dmx_shfl<XSEG>(acc, F_ALP, PF(F_ALP), sb, y ? dalp[1] : dalp[2], i12h);
+            dd[m] = dmx_row<XSEG, YROWS>(acc, F_GT + m, PF(F_GT + m), sb, y ? dgt[1][m] : dgt[2][m], i12h, xep, pb, m);
+          vchi = dmx_row<XSEG, YROWS>(acc, F_CHI, PF(F_CHI), sb, y ? dchi[1] : dchi[2], i12h, xep, pb, 6) * i12h;
+          valp = dmx_row<XSEG, YROWS>(acc, F_ALP, PF(F_ALP), sb, y ? dalp[1] : dalp[2], i12h, xep, pb, 7);
 #pragma unroll
           for (int a = 0; a < 3; a++)
-            vb[a] = dmx_shfl<XSEG>(acc, F_BETA + a, PF(F_BETA + a), sb, y ? db[1][a] : db[2][a], i12h);
+            vb[a] = dmx_row<XSEG, YROWS>(acc, F_BETA + a, PF(F_BETA + a), sb, y ? db[1][a] : db[2][a], i12h, xep,
+                                         pb, 8 + a);
         }
       } else if (YROWS > 0 && pa == 1) {  // (1, 2) from the rows' differences along z
         sc = i12h;

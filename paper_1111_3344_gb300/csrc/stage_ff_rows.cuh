@@ -39,7 +39,16 @@ cudaError_t launch_ff_rows(const Grid& g, const StageArgsFF& a, cudaStream_t s) 
   dim3 block(32, TY, TZ);
   dim3 grid(g.n0 / 32, (g.n1 + TY - 1) / TY, (g.n2 + TZ - 1) / TZ);
   if (g.n1 % TY == 0 && g.n2 % TZ == 0 && TY >= 2) {
-    const int smem = 11 * (TY + 4) * TZ * 32 * (int)sizeof(ff);
+    constexpr int smem = (int)rows_block_smem(TY, TZ, false);
+    if constexpr (smem > 48 * 1024) {  // above the default limit: opt in once
+      static bool attr = false;
+      if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(stage_ff_blocks_kernel<TY, TZ, MINB>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+      }
+    }
     stage_ff_blocks_kernel<TY, TZ, MINB><<<grid, block, smem, s>>>(g, a);
   } else {
     stage_ff_rows_kernel<TY, TZ, MINB><<<grid, block, 0, s>>>(g, a);
