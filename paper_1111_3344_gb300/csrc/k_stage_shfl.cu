@@ -20,7 +20,9 @@ __global__ void __launch_bounds__(32 * TY * TZ, MINB) stage_fp64_rows_kernel(Gri
 
 // Full blocks (n1 % TY == 0 and n2 % TZ == 0 as well): every thread is inside
 // the grid, so the block can also exchange first differences along z through
-// shared memory for D_y D_z.
+// shared memory for D_y D_z, and each warp's 32 lanes form the first
+// differences past the ends of its row that D_x D_y and D_x D_z need, into
+// shared memory, instead of the two lanes at each end (dmx_pre).
 template <int TY, int TZ, int MINB>
 __global__ void __launch_bounds__(32 * TY * TZ, MINB) stage_fp64_blocks_kernel(Grid g, StageArgs a) {
   const int ii = blockIdx.x * 32 + threadIdx.x;
