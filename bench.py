@@ -57,12 +57,13 @@ ALG_BYTES_PER_POINT_STEP = {"fp64": 3072.0, "mixed": 2496.0, "ff": 3456.0}
 # (right-hand side plus RK4 combine), from ncu instruction counts at 64^3
 # (DADD + DMUL + 2 DFMA): the every-stencil kernel 535 DADD + 239 DMUL + 1485
 # DFMA; the full-block kernel (32-wide rows, D_y D_z through shared memory)
-# 302.5 DADD + 251.8 DMUL + 1366.8 DFMA.
+# 299.5 DADD + 246.8 DMUL + 1359.8 DFMA (per warp of 32 points, 1934 warp
+# instructions issued to the float64 pipe).
 FLOP_PER_POINT_RHS = 3744.0
 DPINST_PER_POINT_RHS = 2259.0
 ROWS_TILES = ("32x8x1/1", "32x4x1/1", "32x4x2/1", "32x2x2/2")
-FLOP_PER_POINT_RHS_ROWS = 3287.9
-DPINST_PER_POINT_RHS_ROWS = 1921.1
+FLOP_PER_POINT_RHS_ROWS = 3265.8
+DPINST_PER_POINT_RHS_ROWS = 1906.0
 # Operations of one right-hand side at an interior point in the oracle's
 # printed arrangement (its instrumented build, W variant, Gamma-driver shift:
 # 5395 additions, 7874 multiplications, 299 divisions).  The arrangement
