@@ -1,6 +1,7 @@
 // Internal definitions shared by the CUDA translation units of libbssn.
 // Not part of the public ABI (include/bssn.h is).
 #pragma once
+#include <atomic>
 #include <cstdint>
 #include <string>
 #include <type_traits>
@@ -91,6 +92,23 @@ template <>
 __host__ __device__ __forceinline__ float gc<float>(double, float f, float) { return f; }
 template <>
 __host__ __device__ __forceinline__ ff gc<ff>(double, float f, float l) { return ff(f, l); }
+
+// Raise kernel's dynamic shared-memory limit to bytes on the current device,
+// once per device: the attribute belongs to the kernel as loaded in that
+// device's context.  done holds one bit per device (devices 32 and up set the
+// attribute at every call); concurrent callers may both set it, which is
+// harmless.
+template <typename K>
+inline cudaError_t smem_optin(K kernel, int bytes, std::atomic<unsigned>& done) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const unsigned bit = dev >= 0 && dev < 32 ? 1u << dev : 0u;
+  if (bit && (done.load(std::memory_order_acquire) & bit)) return cudaSuccess;
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess && bit) done.fetch_or(bit, std::memory_order_acq_rel);
+  return e;
+}
 
 template <typename T>
 constexpr bool is_f32 = std::is_same<T, float>::value;

@@ -89,17 +89,11 @@ cudaError_t make_stage_tensor_map(const Grid& g, const float* base, CUtensorMap*
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-// dynamic shared memory above the default limit, once per kernel
+// dynamic shared memory above the default limit, once per kernel and device
 template <typename Sh, int MINB>
 static cudaError_t tma_attr() {
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(stage_mixed_tma_kernel<Sh, MINB>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, Sh::SMEM);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
-  return cudaSuccess;
+  static std::atomic<unsigned> done{0};
+  return smem_optin(stage_mixed_tma_kernel<Sh, MINB>, Sh::SMEM, done);
 }
 
 template <typename Sh, int MINB>

@@ -40,14 +40,10 @@ cudaError_t launch_ff_rows(const Grid& g, const StageArgsFF& a, cudaStream_t s) 
   dim3 grid(g.n0 / 32, (g.n1 + TY - 1) / TY, (g.n2 + TZ - 1) / TZ);
   if (g.n1 % TY == 0 && g.n2 % TZ == 0 && TY >= 2) {
     constexpr int smem = (int)rows_block_smem(TY, TZ, false);
-    if constexpr (smem > 48 * 1024) {  // above the default limit: opt in once
-      static bool attr = false;
-      if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(stage_ff_blocks_kernel<TY, TZ, MINB>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e != cudaSuccess) return e;
-        attr = true;
-      }
+    if constexpr (smem > 48 * 1024) {  // above the default limit: opt in once per device
+      static std::atomic<unsigned> done{0};
+      cudaError_t e = smem_optin(stage_ff_blocks_kernel<TY, TZ, MINB>, smem, done);
+      if (e != cudaSuccess) return e;
     }
     stage_ff_blocks_kernel<TY, TZ, MINB><<<grid, block, smem, s>>>(g, a);
   } else {
