@@ -17,9 +17,11 @@ every side and no padding.  Point index ``i`` on an axis sits at
 ``xmin + (i - 3 + 0.5) h``.
 
 Parity status per function: every function is pinned by tests under
-``tests/test_oracle_*.py`` except the Sommerfeld power-law correction term
-and the per-variable X0/v0 choice, which are readings of an under-specified
-passage (parity unpinned beyond the pure outgoing-wave part).
+``tests/test_oracle_*.py``.  In the Sommerfeld condition, the pure
+outgoing-wave part, the power-law correction (an exact C/r^2 tail carried
+outwards), X0 (flat space stays exactly flat) and v0 = sqrt(2) for alpha and K
+(the 1+log gauge speed) are pinned; v0 = 1 for the other fields is a reading
+of an under-specified passage (parity unpinned for that choice).
 """
 from __future__ import annotations
 

@@ -28,10 +28,12 @@
  * flat space staying flat, Kasner closed form under geodesic and 1+log
  * slicing, gauge-wave and boosted Kerr-Schild exact solutions at 4th order,
  * closed-form Hamiltonian/momentum constraints, Brill-Lindquist constraint
- * convergence, the outgoing-wave Sommerfeld condition.  The Sommerfeld
- * power-law correction term, the choice of X0/v0 per variable and the
- * initial lapse are readings of an under-specified passage: parity there is
- * unpinned beyond the pure-wave part.
+ * convergence, the outgoing-wave Sommerfeld condition with its power-law
+ * correction (an exact C/r^2 tail carried outwards), X0 per variable (flat
+ * space stays exactly flat) and v0 = sqrt(2) for alpha and K (the speed at
+ * which 1+log slicing carries a lapse pulse).  v0 = 1 for the other fields and
+ * the initial lapse are readings of an under-specified passage: parity of
+ * those two choices is unpinned.
  */
 #include <complex.h>
 #undef I /* the imaginary unit is written _Complex_I below */

@@ -6,9 +6,11 @@ decaying like r^-2, d_t X = -v0 u'(r)/r + C/r^2; given that exact right-hand
 side in the interior, the boundary right-hand side (second-order radiative
 part plus the p = 2 power-law correction from the inner neighbour, layer by
 layer, with diagonal neighbours on edges and corners) reproduces it at
-second order in h on all three ghost layers.  The per-variable X0 and v0 are
-readings (X0 = 1 for alpha, W and the diagonal of gt; v0 = sqrt(2) for alpha
-and K): parity of that choice is unpinned.
+second order in h on all three ghost layers.  The per-variable X0 (1 for
+alpha, W and the diagonal of gt, 0 otherwise) is pinned by flat space staying
+exactly flat; v0 = sqrt(2) for alpha and K is pinned as the speed at which the
+1+log slicing carries a lapse pulse.  v0 = 1 for the other fields is a reading
+(parity of that choice unpinned).
 
 Flat space: the right-hand side is bit-exactly zero on every stored point for
 both conformal variables and both boundaries, and RK4 leaves the state
@@ -168,3 +170,51 @@ def test_rhs_points_periodic_ghosts_are_zero():
     got = O.rhs_points(cfg, st, ijk)
     want = np.stack([whole[:, k, j, i] for (i, j, k) in ijk])
     assert np.array_equal(got, want)
+
+
+def _gauge_pulse(cfg, eps, r0, s):
+    """Flat space (W = 1, gt = delta, beta = 0) with an outgoing 1+log lapse
+    pulse: alpha = 1 + eps P(r)/r, K = (sqrt2 / 2) eps P'(r)/r, so that
+    d_t alpha = -2 alpha K is the outgoing wave's -sqrt2 eps P'/r to first
+    order.  Returns the state, r, and K's analytic P''(r)/r term."""
+    Zc, Yc, Xc = np.meshgrid(cfg.coords(2), cfg.coords(1), cfg.coords(0), indexing="ij")
+    r = np.sqrt(Xc ** 2 + Yc ** 2 + Zc ** 2)
+    x = (r - r0) / s
+    P = np.exp(-x * x)
+    dP = -2.0 * x / s * P
+    d2P = (4.0 * x * x - 2.0) / (s * s) * P
+    st = np.zeros(cfg.shape)
+    st[O.F_CHI] = 1.0
+    for m in (0, 3, 5):
+        st[O.F_GT + m] = 1.0
+    st[O.F_ALP] = 1.0 + eps * P / r
+    c = math.sqrt(2.0) / 2.0 * eps
+    st[O.F_TRK] = c * dP / r
+    return st, r, c * d2P / r
+
+
+def test_sommerfeld_speed_of_lapse_and_K_is_the_1plog_gauge_speed():
+    """The radiative speed v0 = sqrt2 of alpha and K is the speed at which the
+    1+log slicing carries a small lapse pulse on flat space.  For the
+    outgoing pulse of _gauge_pulse the outgoing-wave condition gives d_t K =
+    -v0 (d_r K + K/r) = -v0 (sqrt2/2) eps P''/r; the oracle's interior right-hand
+    side (d_t K = -D^2 alpha + O(eps^2) = -eps P''/r) agrees with it for v0 =
+    sqrt2 to truncation error (3.0e-3 of the largest value at h = 0.125,
+    2.2e-4 at h/2: fourth order), and misses it by (sqrt2 - 1)/sqrt2 = 29 % for
+    v0 = 1.  With test_sommerfeld_reproduces_outgoing_wave_with_power_law_tail,
+    which builds its exact waves with these speeds, this pins the oracle
+    boundary's choice for alpha and K."""
+    eps = 1e-6
+    cfg = O.Config(n=(48, 48, 48), h=0.125, xmin=(-3.0,) * 3, periodic=False, shift="frozen",
+                   slicing="1+log", ko_eps=0.0)
+    st, r, cK = _gauge_pulse(cfg, eps, r0=1.8, s=0.45)
+    got = O.rhs(cfg, st)[O.F_TRK]
+    g = O.GHOST
+    inner = (slice(g, -g),) * 3
+    band = (r[inner] > 1.2) & (r[inner] < 2.4)
+    dK = got[inner][band]
+    scale = np.abs(dK).max()
+    e_sqrt2 = np.abs(dK - (-math.sqrt(2.0) * cK[inner][band])).max() / scale
+    e_one = np.abs(dK - (-1.0 * cK[inner][band])).max() / scale
+    assert e_sqrt2 < 6e-3, e_sqrt2
+    assert e_one > 0.25, e_one
