@@ -73,9 +73,11 @@ DPINST_PER_POINT_RHS_ROWS = 1906.0
 ORACLE_FLOP_PER_POINT_RHS = 5395 + 7874 + 299
 # DRAM bytes (read + write) per interior point of one stage launch, the mean
 # over the four stages of one RK4 step, from ncu captures of single launches
-# at the benchmark size (128^3; dram__bytes_read.sum + dram__bytes_write.sum),
-# by stage-kernel configuration; a configuration without a capture of its
-# current kernel at that size reports null.
+# at the benchmark size (TRAFFIC_N^3; dram__bytes_read.sum +
+# dram__bytes_write.sum), by stage-kernel configuration; a configuration
+# without a capture of its current kernel, or a run at another grid size
+# (where the share of ghosts, padding and L2 hits differs), reports null.
+TRAFFIC_N = 128
 STAGE_TRAFFIC_PER_POINT = {
     ("fp64", "32x4x1/1"): 937.2,       # stage_fp64_blocks_kernel: 7861.6 MB per step
     ("mixed", "tma32x4x1/2"): 565.3,   # stage_mixed_tma_kernel, 8 staged fields: 4741.9 MB per step
@@ -419,7 +421,7 @@ def hbm_roofline(run, precision, kernel, traffic_per_point):
             "frac": gbs / HBM_MEASURED_GBS,
             "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs, burst copy)",
             "algorithmic_bytes_per_launch": bytes_launch,
-            "traffic": traffic_per_point * pts if traffic_per_point else None,
+            "traffic": traffic_per_point * pts if traffic_per_point and N_SIDE == TRAFFIC_N else None,
             "launch_ms": run["stage_launch_ms"], "launches": run["stage_launches"],
             "boundary_launch_ms": run["boundary_launch_ms"]}
 

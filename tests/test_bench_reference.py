@@ -42,3 +42,30 @@ def test_bench_oracle_flop_count_is_the_oracles():
     st = O.initial_data(cfg, "bl", [1, 1.0, 0.0, 0.0, 0.0])
     c = O.rhs_opcount(cfg, st, (9, 8, 7))
     assert c["add"] + c["mul"] + c["div"] == bench.ORACLE_FLOP_PER_POINT_RHS
+
+
+def test_hbm_roofline_arithmetic():
+    """The roofline object of the bench line: achieved = algorithmic bytes of
+    one stage launch (a quarter of the per-step bytes per interior point, times
+    the interior points) over the mean launch time; frac = achieved over the
+    measured copy bandwidth; traffic = the captured DRAM bytes per point times
+    the points, only at the grid size the capture was made at."""
+    sys.path.insert(0, ROOT)
+    import bench
+    run = {"stage_launch_ms": 7.25, "stage_launches": 80, "boundary_launch_ms": 0.3}
+    n_saved = bench.N_SIDE
+    try:
+        bench.N_SIDE = 128
+        r = bench.hbm_roofline(run, "fp64", "stage_fp64_blocks_kernel", 937.2)
+        pts = 128 ** 3
+        assert r["algorithmic_bytes_per_launch"] == 3072.0 / 4.0 * pts
+        assert abs(r["achieved"] - 768.0 * pts / 7.25e-3 / 1e9) < 1e-9
+        assert abs(r["frac"] - r["achieved"] / bench.HBM_MEASURED_GBS) < 1e-15
+        assert r["traffic"] == 937.2 * pts and r["unit"] == "GB/s" and r["bound"] == "hbm"
+        r = bench.hbm_roofline(run, "mixed", "stage_mixed_tma_kernel", None)
+        assert r["algorithmic_bytes_per_launch"] == 2496.0 / 4.0 * pts and r["traffic"] is None
+        bench.N_SIDE = 64  # not the capture size: no traffic figure
+        r = bench.hbm_roofline(run, "fp64", "stage_fp64_blocks_kernel", 937.2)
+        assert r["traffic"] is None and r["algorithmic_bytes_per_launch"] == 768.0 * 64 ** 3
+    finally:
+        bench.N_SIDE = n_saved
