@@ -126,3 +126,19 @@ def test_serve_select_shortest_work_first():
         p = list(rng.integers(1, 9, n).astype(float))
         m = float(rng.uniform(0, sum(p) * 1.2))
         assert list(B.bssn_serve_select(w, p, m)) == _select_reference(w, p, m)
+
+
+@pytest.mark.parametrize("n", [(4096, 4096, 4096), (4096, 4, 4), (4, 4096, 4096)])
+def test_sizes_at_the_largest_grids(n):
+    """At the largest accepted sides (4096) the layout and the byte counts are
+    formed in 64-bit arithmetic: a float64 register of 24 fields exceeds 2^32
+    points and 2^40 bytes at 4096^3 and must not wrap."""
+    p = B.Params(n=n, xmin=(0.0,) * 3, h=0.1, boundary="sommerfeld")
+    lay = B.bssn_layout_of(p)
+    assert lay["stored"] == tuple(x + 6 for x in n)
+    assert lay["pitch"] >= n[0] + 6 and lay["plane"] == lay["pitch"] * (n[1] + 6)
+    assert lay["field_stride"] == lay["plane"] * (n[2] + 6)
+    nb = B.bssn_required_bytes(p)
+    assert nb >= 5 * 24 * lay["field_stride"] * 8
+    if n == (4096, 4096, 4096):
+        assert nb > 1 << 42
