@@ -330,11 +330,19 @@ bssn_status bssn_autotune(bssn_ctx* ctx, int32_t reps, int32_t* best, double* ms
 
 /* ------------------------------------------------------------ batches
  * Many independent evolutions (different grids and parameters, one precision)
- * advanced together: bssn_batch_step runs one persistent launch per RK4 stage
- * over the tiles of every active member plus one boundary launch, replayed
- * from a CUDA graph captured once per tile shape.  Members join and leave
- * between steps without re-capture (the graph reads a device work-list).  A
- * member computes the same bits as the same evolution run alone through a
+ * advanced together by bssn_batch_step, one RK4 step replayed from a captured
+ * CUDA graph.  Two forms, chosen by the batch's tile configuration
+ * (bssn_batch_set_tile, bssn_batch_autotune):
+ *  - work-list configurations: one launch per RK4 stage over the tiles of
+ *    every active member (persistent or one block per tile) plus one boundary
+ *    launch; the graph reads a device work-list, so members join and leave
+ *    between steps without re-capture;
+ *  - per-member configurations ("members", "members4", "members1"; the
+ *    defaults): each member's stages and boundaries with the single-grid
+ *    kernels, one launch chain per member, the chains side by side on 16, 4
+ *    or 1 auxiliary streams inside the graph, which is captured again when
+ *    the membership changes.
+ * A member computes the same bits as the same evolution run alone through a
  * bssn_ctx.  All device memory comes from the caller's pool: the batch tables
  * (bssn_batch_table_bytes) at its start, then member registers carved by a
  * first-fit sub-allocator (bssn_batch_member_bytes each). */
@@ -343,8 +351,8 @@ typedef struct bssn_batch bssn_batch;
 
 size_t bssn_batch_table_bytes(int32_t max_members);   /* 0 if out of range */
 size_t bssn_batch_member_bytes(const bssn_params* p); /* 0 on bad p */
-/* precision: BSSN_FP64 or BSSN_MIXED for every member; cuda_stream must not be
- * the legacy default stream (graphs are captured on it). */
+/* precision: BSSN_FP64, BSSN_MIXED or BSSN_FF for every member; cuda_stream
+ * must not be the legacy default stream (graphs are captured on it). */
 bssn_status bssn_batch_create(int32_t precision, int32_t max_members, void* d_pool,
                               size_t pool_bytes, void* cuda_stream, bssn_batch** out);
 bssn_status bssn_batch_free(bssn_batch* b); /* synchronises; does not free the pool */

@@ -583,8 +583,11 @@ class Evolution:
 
 # ---------------------------------------------------------------- batches
 class Batch:
-    """Many evolutions advanced together (persistent launch per RK stage under a
-    captured CUDA graph).  Owns a torch device pool and a dedicated stream."""
+    """Many evolutions advanced together, one RK4 step per replay of a
+    captured CUDA graph: by default each member's single-grid kernels in a
+    launch chain of its own, the chains side by side; or one launch per RK4
+    stage over every member's tiles (see include/bssn.h).  precision: "fp64",
+    "mixed" or "ff".  Owns a torch device pool and a dedicated stream."""
 
     def __init__(self, precision: str = "fp64", pool_bytes: int = 1 << 30, max_members: int = 64,
                  device: str = "cuda"):
