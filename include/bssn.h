@@ -364,7 +364,8 @@ bssn_status bssn_batch_set_initial_data(bssn_batch* b, int32_t member, int32_t k
                                         const double* p, int32_t np);
 bssn_status bssn_batch_set_state(bssn_batch* b, int32_t member, const double* host, double t);
 bssn_status bssn_batch_get_state(bssn_batch* b, int32_t member, double* host, double* t);
-/* Advance every active member nsteps RK4 steps (asynchronous). */
+/* Advance every active member that is not held (bssn_batch_hold) nsteps RK4
+ * steps (asynchronous). */
 bssn_status bssn_batch_step(bssn_batch* b, int32_t nsteps);
 bssn_status bssn_batch_constraints(bssn_batch* b, int32_t member, double out[16]); /* synchronises */
 /* hold != 0: the member stays resident (registers, state, time) but the next
